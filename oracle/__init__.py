@@ -1,0 +1,18 @@
+"""Plain FP64 CPU oracle of the nodal DG Euler hot path (test infrastructure).
+
+This package is the independent check of the CUDA library: slow, written for
+reading, in float64 numpy. It is used only by the tests, by the bench's CPU
+baseline leg and by the smoke check; the library never imports it, and it
+imports nothing from the library (its only shared input is the seeded
+workload module, which holds no DG arithmetic).
+
+Modules:
+  reference_element  nodes, interpolation, derivative / mass / lift matrices
+                     (Appendix A, Eqs. 10-11), built from a monomial basis with
+                     exact integrals
+  geometry           affine maps, normals, face matching by coordinates
+  euler_dg           Euler fluxes (Eqs. 1-2), boundary ghost states (section
+                     2.2, Eq. 4), local Lax-Friedrichs flux, semi-discrete
+                     right-hand side (Eqs. 10, 12), low-storage RK4, probes,
+                     boundary-flux ledger and conserved totals
+"""

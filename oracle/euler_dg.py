@@ -1,0 +1,305 @@
+"""Nodal DG right-hand side and time step for 3D Euler (test infrastructure, float64).
+
+What is computed, with the passage it follows:
+
+* Conserved variables q = (rho, rho u, rho v, rho w, E) and the fluxes of the
+  3D compressible Euler equations (section 2.1, Eq. 1), closed by the
+  ideal-gas law E = p/(gamma-1) + rho |u|^2 / 2 (Eq. 2). Eq. 1 as printed has
+  two typos (a "+p" in the z-momentum entry of the y-flux and in the
+  y-momentum entry of the z-flux); the oracle uses the standard Euler fluxes,
+  which is what Eq. 1 describes in words.
+* Element-wise DG discretisation (Appendix A, Eqs. 8-12): for each element
+      dq/dt = -(div F)_h + LIFT (Fscale * (n.F(q-) - F*)),
+  i.e. the strong form of Eq. 10 obtained by integrating its volume term by
+  parts back; on straight-sided elements with the nodal interpolant of the
+  flux the two forms are the same discrete operator.
+* Numerical flux on the shared face: local Lax-Friedrichs (section 1.1),
+      F* = (n.F(q-) + n.F(q+))/2 - lambda (q+ - q-)/2,
+      lambda = max(|u-.n| + c-, |u+.n| + c+) at each face node.
+* Outer-boundary ghost states q+:
+    FREESTREAM      the paper's pass-through condition: the ghost is the
+                    initial (free-stream) state (section 2.2, Eq. 3);
+    CHARACTERISTIC  Riemann-invariant far-field ghost (the characteristic
+                    approach named in section 1 as the main far-field
+                    technique): R+ = u.n + 2c/(g-1) from inside,
+                    R- = u_inf.n - 2c_inf/(g-1) from the free stream; normal
+                    velocity (R+ + R-)/2, sound speed (g-1)(R+ - R-)/4;
+                    entropy p/rho^g and tangential velocity from inside when
+                    that normal velocity is >= 0 (outflow), else from the
+                    free stream;
+    SLIP_WALL       reflective wall (section 2.3, Eq. 4): normal velocity
+                    mirrored, rho and p unchanged. Eq. 4 as printed mixes
+                    components (u - 2 u n_x, ...); the oracle mirrors the
+                    normal component, u+ = u- - 2 (u-.n) n, which is what the
+                    text around Eq. 4 states.
+* Time integration of the ODE system dc/dt = f(c) (Eq. 12) by the five-stage
+  2N-storage fourth-order Runge-Kutta scheme of Carpenter and Kennedy (1994)
+  instead of the paper's RK2 (section 1.1), stage by stage:
+      res <- a_k res + dt f(q, t + c_k dt);  q <- q + b_k res.
+* Sensors (section 3): point values of the five conserved variables through
+  the element's interpolant.
+* Boundary-flux ledger: the integral over outer faces of F*.n, integrated in
+  time by the same stages, so that total(t) - total(0) + ledger(t) = 0.
+
+Parity status: pinned (tests/test_oracle_euler.py: flux consistency and
+antisymmetry, free-stream preservation, discrete conservation, p+1
+convergence against exact solutions, axis-permutation and inversion
+symmetry, LSRK order conditions, the characteristic ghost on 1D states).
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+
+from .geometry import Geometry, inscribed_radius
+
+FREESTREAM = 0
+CHARACTERISTIC = 1
+SLIP_WALL = 2
+
+# Carpenter & Kennedy (1994), NASA TM-109112, five-stage 2N-storage RK4
+LSRK_A = [Fraction(0), Fraction(-567301805773, 1357537059087),
+          Fraction(-2404267990393, 2016746695238),
+          Fraction(-3550918686646, 2091501179385),
+          Fraction(-1275806237668, 842570457699)]
+LSRK_B = [Fraction(1432997174477, 9575080441755),
+          Fraction(5161836677717, 13612068292357),
+          Fraction(1720146321549, 2090206949498),
+          Fraction(3134564353537, 4481467310338),
+          Fraction(2277821191437, 14882151754819)]
+LSRK_C = [Fraction(0), Fraction(1432997174477, 9575080441755),
+          Fraction(2526269341429, 6820363962896),
+          Fraction(2006345519317, 3224310063776),
+          Fraction(2802321613138, 2924317926251)]
+
+
+class Gas:
+    """Ideal gas with a free stream (rho_inf, u_inf, p_inf)."""
+
+    def __init__(self, gamma, rho0, p0, u0=(0.0, 0.0, 0.0)):
+        self.gamma = float(gamma)
+        self.rho0 = float(rho0)
+        self.p0 = float(p0)
+        self.u0 = np.asarray(u0, dtype=np.float64)
+        self.c0 = np.sqrt(self.gamma * self.p0 / self.rho0)
+        self.E0 = self.p0 / (self.gamma - 1.0) + 0.5 * self.rho0 * float(self.u0 @ self.u0)
+
+    def freestream(self):
+        return np.array([self.rho0, *(self.rho0 * self.u0), self.E0])
+
+
+# ---------------------------------------------------------------- Eqs. 1-2
+
+def pressure(q, gamma):
+    """p from conserved variables (Eq. 2); q has the 5 variables on axis -1."""
+    rho = q[..., 0]
+    m = q[..., 1:4]
+    return (gamma - 1.0) * (q[..., 4] - 0.5 * np.sum(m * m, axis=-1) / rho)
+
+
+def euler_fluxes(q, gamma):
+    """x, y, z fluxes of Eq. 1 (standard form); q[..., 5] -> three arrays [..., 5]."""
+    rho = q[..., 0]
+    u = q[..., 1:4] / rho[..., None]
+    p = pressure(q, gamma)
+    E = q[..., 4]
+    out = []
+    for d in range(3):
+        f = np.empty_like(q)
+        f[..., 0] = q[..., 1 + d]
+        for e in range(3):
+            f[..., 1 + e] = q[..., 1 + e] * u[..., d] + (p if d == e else 0.0)
+        f[..., 4] = u[..., d] * (E + p)
+        out.append(f)
+    return out
+
+
+def normal_flux(q, n, gamma):
+    F, G, H = euler_fluxes(q, gamma)
+    return n[..., 0:1] * F + n[..., 1:2] * G + n[..., 2:3] * H
+
+
+def wave_speed(q, n, gamma):
+    """|u.n| + c."""
+    rho = q[..., 0]
+    un = np.sum(q[..., 1:4] * n, axis=-1) / rho
+    c = np.sqrt(gamma * pressure(q, gamma) / rho)
+    return np.abs(un) + c
+
+
+def llf_flux(qm, qp, n, gamma):
+    """Local Lax-Friedrichs normal flux F*(q-, q+, n)."""
+    lam = np.maximum(wave_speed(qm, n, gamma), wave_speed(qp, n, gamma))
+    return 0.5 * (normal_flux(qm, n, gamma) + normal_flux(qp, n, gamma)) \
+        - 0.5 * lam[..., None] * (qp - qm)
+
+
+# ---------------------------------------------------------- ghost states
+
+def ghost_freestream(qm, n, gas):
+    return np.broadcast_to(gas.freestream(), qm.shape).copy()
+
+
+def ghost_slip_wall(qm, n, gas):
+    qp = qm.copy()
+    mn = np.sum(qm[..., 1:4] * n, axis=-1)
+    qp[..., 1:4] = qm[..., 1:4] - 2.0 * mn[..., None] * n
+    return qp
+
+
+def ghost_characteristic(qm, n, gas):
+    g = gas.gamma
+    rho = qm[..., 0]
+    u = qm[..., 1:4] / rho[..., None]
+    p = pressure(qm, g)
+    c = np.sqrt(g * p / rho)
+    un = np.sum(u * n, axis=-1)
+    un_inf = np.sum(gas.u0 * n, axis=-1)
+    Rp = un + 2.0 * c / (g - 1.0)
+    Rm = un_inf - 2.0 * gas.c0 / (g - 1.0)
+    unb = 0.5 * (Rp + Rm)
+    cb = 0.25 * (g - 1.0) * (Rp - Rm)
+    out = unb >= 0.0
+    s_in = p / rho ** g
+    s_inf = gas.p0 / gas.rho0 ** g
+    s = np.where(out, s_in, s_inf)
+    ut = np.where(out[..., None], u - un[..., None] * n,
+                  gas.u0 - un_inf[..., None] * n)
+    rhob = (cb * cb / (g * s)) ** (1.0 / (g - 1.0))
+    pb = rhob * cb * cb / g
+    ub = ut + unb[..., None] * n
+    qp = np.empty_like(qm)
+    qp[..., 0] = rhob
+    qp[..., 1:4] = rhob[..., None] * ub
+    qp[..., 4] = pb / (g - 1.0) + 0.5 * rhob * np.sum(ub * ub, axis=-1)
+    return qp
+
+
+GHOSTS = {FREESTREAM: ghost_freestream, CHARACTERISTIC: ghost_characteristic,
+          SLIP_WALL: ghost_slip_wall}
+
+
+# ----------------------------------------------------------------- solver
+
+class Solver:
+    """Semi-discrete DG operator plus time stepping on one mesh.
+
+    ``bc_id[K, 4]`` gives a boundary id per face (ignored on interior faces;
+    default 0 everywhere); ``bc_mode[id]`` the ghost rule of that id.
+    """
+
+    def __init__(self, geom: Geometry, gas: Gas, bc_id=None, bc_mode=None):
+        self.g = geom
+        self.ref = geom.ref
+        self.gas = gas
+        K = geom.K
+        self.bc_id = np.zeros((K, 4), dtype=np.int64) if bc_id is None else np.asarray(bc_id)
+        self.bc_mode = {0: CHARACTERISTIC} if bc_mode is None else dict(bc_mode)
+        # physical face-integration weights of the face nodes: sJ * column sums of face mass
+        self.face_w = np.stack([fm.sum(axis=0) for fm in self.ref.face_mass])  # [4, Nfp]
+
+    # -- Eq. 10 / Eq. 12 right-hand side
+    def rhs(self, q, t=0.0, want_ledger=False):
+        g, ref, gas = self.g, self.ref, self.gas
+        gam = gas.gamma
+        K, Np, Nfp = g.K, ref.Np, ref.Nfp
+        qn = np.transpose(q, (0, 2, 1))                       # [K, Np, 5]
+        F, G, H = euler_fluxes(qn, gam)
+        flux = [np.transpose(f, (0, 2, 1)) for f in (F, G, H)]  # [K, 5, Np]
+        D = [ref.Dr, ref.Ds, ref.Dt]
+        div = np.zeros_like(q)
+        for a in range(3):
+            for b in range(3):
+                dab = np.einsum("ij,kvj->kvi", D[a], flux[b])
+                div += g.drdx[:, a, b][:, None, None] * dab
+        # face traces
+        flat = qn.reshape(K * Np, 5)
+        qm = flat[g.vmapM]                                    # [K, 4, Nfp, 5]
+        qp = flat[g.vmapP].copy()
+        n = np.broadcast_to(g.nrm[:, :, None, :], (K, 4, Nfp, 3))
+        if np.any(g.boundary):
+            bidx = np.nonzero(g.boundary)
+            for ident in np.unique(self.bc_id[bidx]):
+                sel = tuple(ix[self.bc_id[bidx] == ident] for ix in bidx)
+                rule = GHOSTS[self.bc_mode[int(ident)]]
+                qp[sel] = rule(qm[sel], n[sel], gas)
+        fstar = llf_flux(qm, qp, n, gam)
+        dF = g.Fscale[:, :, None, None] * (normal_flux(qm, n, gam) - fstar)
+        dF = np.transpose(dF, (0, 3, 1, 2)).reshape(K, 5, 4 * Nfp)
+        lift = np.einsum("ij,kvj->kvi", ref.LIFT, dF)
+        out = -div + lift
+        if not want_ledger:
+            return out
+        w = g.sJ[:, :, None] * self.face_w[None, :, :]        # [K, 4, Nfp]
+        w = w * g.boundary[:, :, None]
+        ledger = np.einsum("kfm,kfmv->v", w, fstar)
+        return out, ledger
+
+    # -- Eq. 12 integrated by the 2N-storage RK4
+    def step(self, q, t, dt, res=None, ledger=None):
+        """One full time step. Returns (q, t, res, ledger, ledger_res)."""
+        res = np.zeros_like(q) if res is None else res
+        L = np.zeros(5) if ledger is None else ledger[0]
+        Lres = np.zeros(5) if ledger is None else ledger[1]
+        for k in range(5):
+            a, b, c = float(LSRK_A[k]), float(LSRK_B[k]), float(LSRK_C[k])
+            rhs, lrhs = self.rhs(q, t + c * dt, want_ledger=True)
+            res = a * res + dt * rhs
+            q = q + b * res
+            Lres = a * Lres + dt * lrhs
+            L = L + b * Lres
+        return q, t + dt, res, (L, Lres)
+
+    def run(self, q, dt, nsteps, t=0.0, probes=None):
+        """nsteps steps from q; returns (q, t, ledger, probe samples [nsteps, n, 5])."""
+        res = np.zeros_like(q)
+        led = (np.zeros(5), np.zeros(5))
+        samples = []
+        for _ in range(nsteps):
+            q, t, res, led = self.step(q, t, dt, res, led)
+            if probes is not None:
+                samples.append(probes.sample(q))
+        return q, t, led[0], (np.array(samples) if probes is not None else None)
+
+    # -- diagnostics
+    def totals(self, q):
+        """sum_e J_e 1^T M q_e for each conserved variable."""
+        Mq = np.einsum("ij,kvj->kvi", self.ref.M, q)
+        return np.einsum("k,kvi->v", self.g.J, Mq)
+
+    def stable_dt(self, q, cfl=0.5):
+        """CFL * min r_in / ((p+1)^2 * max(|u| + c)) at the given state."""
+        qn = np.transpose(q, (0, 2, 1))
+        rho = qn[..., 0]
+        u = qn[..., 1:4] / rho[..., None]
+        c = np.sqrt(self.gas.gamma * pressure(qn, self.gas.gamma) / rho)
+        smax = np.max(np.linalg.norm(u, axis=-1) + c)
+        p = self.ref.p
+        return cfl * np.min(inscribed_radius(self.g)) / ((p + 1) ** 2 * smax)
+
+
+class Probes:
+    """Point sensors: element lookup and interpolation rows."""
+
+    def __init__(self, geom: Geometry, pts, tol=1e-12):
+        pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+        v = geom.verts
+        self.elem = np.zeros(len(pts), dtype=np.int64)
+        self.rows = np.zeros((len(pts), geom.ref.Np))
+        for i, x in enumerate(pts):
+            # barycentrics of x in every element: solve the affine map
+            T = np.stack([v[:, 1] - v[:, 0], v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]], axis=2)
+            lam = np.linalg.solve(T, (x - v[:, 0])[:, :, None])[:, :, 0]   # lam2..lam4
+            lam1 = 1.0 - lam.sum(axis=1)
+            inside = (lam.min(axis=1) >= -tol) & (lam1 >= -tol)
+            hit = np.nonzero(inside)[0]
+            if hit.size == 0:
+                raise ValueError(f"probe {i} lies outside the mesh")
+            e = hit[0]
+            r, s, t = -1 + 2 * lam[e]
+            self.elem[i] = e
+            self.rows[i] = geom.ref.interp_row(r, s, t)[0]
+
+    def sample(self, q):
+        return np.einsum("pn,pvn->pv", self.rows, q[self.elem])

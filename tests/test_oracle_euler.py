@@ -1,0 +1,377 @@
+"""Pins of the oracle's Euler DG operator and time stepping.
+
+Each test checks the oracle against something other than itself: the
+eigenstructure of the Euler flux, exact non-reflection of an outgoing simple
+wave, free-stream preservation, discrete conservation, convergence at rate
+p+1 against exact solutions, exact mesh symmetry, the Runge-Kutta order
+conditions, and a brute-force quadrature of the weak form (Eq. 10).
+"""
+from fractions import Fraction
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import euler_dg as ED
+from oracle.euler_dg import (CHARACTERISTIC, FREESTREAM, SLIP_WALL, Gas, Probes, Solver,
+                             euler_fluxes, ghost_characteristic, ghost_slip_wall, llf_flux,
+                             normal_flux, pressure)
+from oracle.geometry import Geometry
+from oracle.reference_element import ReferenceElement, vandermonde3
+from paper_1710_03887_gb300 import workloads as W
+
+GOLDEN = Path(__file__).parent / "golden"
+
+
+def state(rho, u, p, gamma=1.4):
+    u = np.asarray(u, dtype=float)
+    return np.array([rho, *(rho * u), p / (gamma - 1) + 0.5 * rho * u @ u])
+
+
+def test_eq3_scaled_free_stream():
+    vals = {}
+    for line in (GOLDEN / "initial_state_eq3.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    gas = Gas(vals["gamma"], vals["rho0"], vals["p0"])
+    assert gas.c0 == pytest.approx(vals["c0"], rel=1e-15)
+    assert gas.E0 == pytest.approx(vals["E0"], rel=1e-15)
+    assert pressure(gas.freestream(), gas.gamma) == pytest.approx(vals["p0"], rel=1e-15)
+
+
+def test_flux_jacobian_eigenvalues():
+    """dF_n/dq has eigenvalues u.n - c, u.n (x3), u.n + c (hyperbolicity of Eq. 1)."""
+    rng = np.random.default_rng(0)
+    g = 1.4
+    for _ in range(5):
+        rho, p = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+        u = rng.normal(size=3) * 0.3
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        q = state(rho, u, p, g)
+        J = np.zeros((5, 5))
+        for j in range(5):
+            h = 1e-6 * max(abs(q[j]), 1.0)
+            e = np.zeros(5)
+            e[j] = h
+            J[:, j] = (normal_flux(q + e, n, g) - normal_flux(q - e, n, g)) / (2 * h)
+        ev = np.sort(np.linalg.eigvals(J).real)
+        un, c = u @ n, np.sqrt(g * p / rho)
+        np.testing.assert_allclose(ev, [un - c, un, un, un, un + c], atol=1e-6)
+
+
+def test_fluxes_in_primitive_form():
+    g = 1.4
+    q = state(1.3, [0.2, -0.1, 0.4], 0.9, g)
+    F, G, H = euler_fluxes(q, g)
+    rho, u, v, w, p, E = 1.3, 0.2, -0.1, 0.4, 0.9, q[4]
+    np.testing.assert_allclose(F, [rho * u, rho * u * u + p, rho * u * v, rho * u * w, u * (E + p)])
+    np.testing.assert_allclose(G, [rho * v, rho * u * v, rho * v * v + p, rho * v * w, v * (E + p)])
+    np.testing.assert_allclose(H, [rho * w, rho * u * w, rho * v * w, rho * w * w + p, w * (E + p)])
+
+
+def test_llf_consistency_and_antisymmetry():
+    rng = np.random.default_rng(1)
+    g = 1.4
+    a = state(1.2, rng.normal(size=3) * 0.2, 1.1, g)
+    b = state(0.9, rng.normal(size=3) * 0.2, 0.8, g)
+    n = np.array([0.6, 0.0, 0.8])
+    np.testing.assert_allclose(llf_flux(a, a, n, g), normal_flux(a, n, g), rtol=1e-15)
+    np.testing.assert_array_equal(llf_flux(a, b, n, g), -llf_flux(b, a, -n, g))
+
+
+def test_characteristic_ghost_free_stream_and_outgoing_wave():
+    gas = Gas(1.4, 1.225, 101325.0)
+    g = gas.gamma
+    n = np.array([0.0, 0.6, 0.8])
+    # free stream maps onto itself
+    q = gas.freestream()
+    np.testing.assert_allclose(ghost_characteristic(q, n, gas), q, rtol=1e-14)
+    # an outgoing simple wave (incoming invariant and entropy of the free
+    # stream, no tangential velocity) is returned unchanged: no reflection
+    for delta in (1e-3 * gas.c0, 0.05 * gas.c0):
+        c = gas.c0 + 0.5 * (g - 1) * delta
+        s_inf = gas.p0 / gas.rho0 ** g
+        rho = (c * c / (g * s_inf)) ** (1 / (g - 1))
+        qi = state(rho, delta * n, rho * c * c / g, g)
+        np.testing.assert_allclose(ghost_characteristic(qi, n, gas), qi, rtol=1e-12)
+    # inflow: entropy and tangential velocity of the free stream
+    qi = state(1.3, -0.1 * gas.c0 * n + np.array([5.0, 0.0, 0.0]), 1.02e5, g)
+    qg = ghost_characteristic(qi, n, gas)
+    ug = qg[1:4] / qg[0]
+    assert ug @ n < 0
+    np.testing.assert_allclose(ug - (ug @ n) * n, 0.0, atol=1e-10)
+    assert pressure(qg, g) / qg[0] ** g == pytest.approx(gas.p0 / gas.rho0 ** g, rel=1e-12)
+
+
+def test_slip_wall_flux_has_no_mass_or_energy_flux():
+    gas = Gas(1.4, 1.0, 1.0)
+    n = np.array([1.0, 2.0, -2.0]) / 3.0
+    qi = state(1.1, [0.3, -0.2, 0.1], 0.95)
+    qp = ghost_slip_wall(qi, n, gas)
+    f = llf_flux(qi, qp, n, 1.4)
+    assert abs(f[0]) < 1e-15 and abs(f[4]) < 1e-15
+    # the momentum flux is normal to the wall
+    m = f[1:4]
+    np.testing.assert_allclose(m - (m @ n) * n, 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("mode", [CHARACTERISTIC, FREESTREAM])
+def test_free_stream_preservation(mode):
+    gas = Gas(1.4, 1.225, 101325.0, u0=(30.0, -12.0, 5.0))
+    for p in (1, 3):
+        ref = ReferenceElement(p)
+        xyz, EToV = W.kuhn_cube(3, jitter=0.15, seed=p)
+        geom = Geometry(ref, xyz, EToV)
+        S = Solver(geom, gas, bc_mode={0: mode})
+        q = W.uniform_state(geom.K, ref.Np, gas.rho0, gas.u0, gas.p0, gas.gamma)
+        rhs = S.rhs(q)
+        # scale: |F| / h with |F| ~ E c
+        scale = gas.E0 * gas.c0 / (2.0 / 3)
+        assert np.abs(rhs).max() <= 1e-12 * scale
+        dt = S.stable_dt(q)
+        q2, _, _, _ = S.run(q, dt, 20)
+        assert np.abs(q2 - q).max() <= 1e-13 * gas.E0
+
+
+def test_wall_box_at_rest_stays_at_rest():
+    gas = Gas(1.4, 1.0, 1.0)
+    ref = ReferenceElement(2)
+    xyz, EToV = W.kuhn_cube(2, jitter=0.1)
+    S = Solver(Geometry(ref, xyz, EToV), gas, bc_mode={0: SLIP_WALL})
+    q = W.uniform_state(len(EToV), ref.Np, 1.0, (0, 0, 0), 1.0, 1.4)
+    assert np.abs(S.rhs(q)).max() < 1e-13
+
+
+def test_discrete_conservation_periodic_and_ledger():
+    gas = Gas(1.4, 1.4, 1.0)
+    ref = ReferenceElement(2)
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=5)
+    # periodic box: totals constant
+    geom = Geometry(ref, xyz, EToV, period=(2.0, 2.0, 2.0))
+    S = Solver(geom, gas)
+    q = W.random_smooth_state(geom.x, 1.4, 1.4, 1.0, 0.1, seed=2)
+    t0 = S.totals(q)
+    q2, _, led, _ = S.run(q, S.stable_dt(q), 30)
+    np.testing.assert_allclose(S.totals(q2), t0, rtol=0, atol=1e-13 * np.abs(t0).max())
+    assert np.all(led == 0.0)
+    # outer boundaries: totals(t) - totals(0) + ledger = 0
+    geom = Geometry(ref, xyz, EToV)
+    S = Solver(geom, gas)
+    q = W.gaussian_pulse_state(geom.x, 1.4, 1.4, 1.0, 0.2, 0.6)
+    t0 = S.totals(q)
+    q2, _, led, _ = S.run(q, S.stable_dt(q), 60)
+    bal = S.totals(q2) - t0 + led
+    assert np.abs(led).max() > 1e-4                      # mass/energy really left the box
+    assert np.abs(bal).max() <= 1e-13 * np.abs(t0).max()
+
+
+def _stability_polynomial():
+    """Amplification factor of the 2N-storage scheme on y' = z y, as exact coefficients."""
+    # represent polynomials in z as coefficient lists of Fractions
+    def add(a, b):
+        n = max(len(a), len(b))
+        return [(a[i] if i < len(a) else 0) + (b[i] if i < len(b) else 0) for i in range(n)]
+
+    def scale(a, s):
+        return [x * s for x in a]
+
+    def times_z(a):
+        return [Fraction(0)] + a
+
+    y = [Fraction(1)]
+    res = [Fraction(0)]
+    for a, b in zip(ED.LSRK_A, ED.LSRK_B):
+        res = add(scale(res, a), times_z(y))      # dt = 1, f(y) = z y
+        y = add(y, scale(res, b))
+    return y
+
+
+def test_lsrk_coefficients_and_order_conditions():
+    rows = [list(map(int, l.split()[1:])) for l in (GOLDEN / "lsrk_carpenter_kennedy.txt").read_text().splitlines()
+            if l.strip() and not l.startswith("#")]
+    for k, r in enumerate(rows):
+        assert ED.LSRK_A[k] == Fraction(r[0], r[1])
+        assert ED.LSRK_B[k] == Fraction(r[2], r[3])
+        assert ED.LSRK_C[k] == Fraction(r[4], r[5])
+    R = _stability_polynomial()
+    taylor = [1, 1, Fraction(1, 2), Fraction(1, 6), Fraction(1, 24)]
+    for k in range(5):
+        assert abs(float(R[k]) - float(taylor[k])) < 1e-12
+    assert len(R) == 6 and abs(float(R[5])) > 1e-4                 # fifth stage: not RK5
+    # stage times: c_k is the time reached by the k-th stage input on y' = 1
+    t, res = Fraction(0), Fraction(0)
+    for k in range(5):
+        assert abs(float(t) - float(ED.LSRK_C[k])) < 1e-12
+        res = ED.LSRK_A[k] * res + 1
+        t = t + ED.LSRK_B[k] * res
+    assert abs(float(t) - 1.0) < 1e-14
+
+
+def _density_wave(geom, gas, t, u0):
+    x = geom.x
+    rho = 1.0 + 0.2 * np.sin(np.pi * (x[..., 0] - t * u0[0]))
+    q = np.empty((geom.K, 5, geom.ref.Np))
+    q[:, 0] = rho
+    for d in range(3):
+        q[:, 1 + d] = rho * u0[d]
+    q[:, 4] = 1.0 / (gas.gamma - 1) + 0.5 * rho * float(np.dot(u0, u0))
+    return q
+
+
+@pytest.mark.parametrize("p,ns", [(1, (2, 4, 8)), (3, (2, 3, 4))])
+def test_convergence_density_wave(p, ns):
+    """Exact nonlinear Euler solution (density advected at uniform velocity and
+    pressure) on the periodic cube: L2 error falls at rate p+1.
+
+    Odd orders are pinned; on this Kuhn lattice even orders (p=2, 4) were
+    measured to converge at rate ~p only, with the upwind flux as well as with
+    local Lax-Friedrichs (an observation about the discretisation recorded
+    with the design notes, not a defect of either implementation)."""
+    gas = Gas(1.4, 1.0, 1.0)
+    u0 = np.array([0.5, 0.3, 0.2])
+    ref = ReferenceElement(p)
+    errs, hs = [], []
+    T = 0.1
+    for n in ns:
+        xyz, EToV = W.kuhn_cube(n)
+        geom = Geometry(ref, xyz, EToV, period=(2.0, 2.0, 2.0))
+        S = Solver(geom, gas)
+        q = _density_wave(geom, gas, 0.0, u0)
+        nst = int(np.ceil(T / S.stable_dt(q, 0.4)))
+        q, _, _, _ = S.run(q, T / nst, nst)
+        d = q[:, 0] - _density_wave(geom, gas, T, u0)[:, 0]
+        errs.append(np.sqrt(np.einsum("k,ij,ki,kj->", geom.J, ref.M, d, d)))
+        hs.append(2.0 / n)
+    rates = np.diff(np.log(errs)) / np.diff(np.log(hs))
+    assert rates[-1] > p + 0.5, (errs, rates)
+
+
+def test_convergence_small_amplitude_spherical_pulse():
+    """Linear acoustics limit: r p'(r,t) obeys the 1D wave equation, so a
+    Gaussian pulse at rest evolves as p' = [(r-ct) f(r-ct) + (r+ct) f(r+ct)] / (2r).
+    With amplitude 1e-6 the Euler solution matches it to O(A^2)."""
+    gas = Gas(1.4, 1.4, 1.0)                        # c0 = 1
+    A, w, T, p = 1e-6, 0.35, 0.25, 1
+    ref = ReferenceElement(p)
+
+    def exact(x, t):
+        r = np.linalg.norm(x, axis=-1)
+        f = lambda s: A * np.exp(-(s / w) ** 2)
+        rr = np.where(r > 1e-12, r, 1e-12)
+        val = ((rr - t) * f(rr - t) + (rr + t) * f(rr + t)) / (2 * rr)
+        # at the centre the limit is d/dr [(r + t) f(r + t)] = f(t) + t f'(t)
+        return np.where(r > 1e-12, val, (1 - 2 * t * t / w ** 2) * f(t))
+
+    errs = []
+    for n in (4, 8):
+        xyz, EToV = W.kuhn_cube(n)
+        geom = Geometry(ref, xyz, EToV)
+        S = Solver(geom, gas)
+        q = W.gaussian_pulse_state(geom.x, 1.4, 1.4, 1.0, A, w)
+        nst = int(np.ceil(T / S.stable_dt(q, 0.5)))
+        q, _, _, _ = S.run(q, T / nst, nst)
+        pp = pressure(np.transpose(q, (0, 2, 1)), 1.4) - 1.0
+        ex = exact(geom.x, T)
+        inner = np.linalg.norm(geom.x, axis=-1).max(axis=1) < 0.75
+        d = (pp - ex)[inner]
+        errs.append(np.sqrt(np.einsum("k,ij,ki,kj->", geom.J[inner], ref.M, d, d)))
+    rate = np.log(errs[0] / errs[1]) / np.log(2.0)
+    assert rate > p + 0.5, (errs, rate)
+
+
+def test_centred_pulse_keeps_mesh_symmetry():
+    """The Kuhn lattice is invariant under axis permutations and x -> -x; a
+    centred pulse must stay invariant to rounding."""
+    gas = Gas(1.4, 1.4, 1.0)
+    ref = ReferenceElement(2)
+    xyz, EToV = W.kuhn_cube(3)
+    geom = Geometry(ref, xyz, EToV)
+    S = Solver(geom, gas)
+    q = W.gaussian_pulse_state(geom.x, 1.4, 1.4, 1.0, 0.1, 0.4)
+    q, _, _, _ = S.run(q, S.stable_dt(q), 15)
+    # a node is identified by its element (centroid) and its position: DG
+    # values are double-valued on shared faces
+    cen = np.repeat(geom.x.mean(axis=1), ref.Np, axis=0)
+    x = geom.x.reshape(-1, 3)
+    pp = pressure(np.transpose(q, (0, 2, 1)), 1.4).reshape(-1)
+    m = np.transpose(q[:, 1:4], (0, 2, 1)).reshape(-1, 3)
+    key = {tuple(np.round(np.concatenate([c, v]), 9)): i for i, (c, v) in enumerate(zip(cen, x))}
+    assert len(key) == len(x)
+    amp = np.abs(pp - 1.0).max()
+    for perm in ([1, 2, 0], [2, 0, 1], [1, 0, 2], [0, 2, 1]):
+        for sgn in (1.0, -1.0):
+            j = np.array([key[tuple(np.round(np.concatenate([sgn * c[perm], sgn * v[perm]]), 9))]
+                          for c, v in zip(cen, x)])
+            assert np.abs(pp[j] - pp).max() <= 1e-11 * amp
+            np.testing.assert_allclose(sgn * m[:, perm], m[j], atol=1e-11 * np.abs(m).max())
+
+
+def test_strong_form_equals_weak_form_quadrature():
+    """Brute force of Eq. 10 on small meshes: the weak form integrated by
+    quadrature (volume integral of grad(l_i) . I(F), surface integral of
+    l_i times the face interpolant of F*) equals the strong-form operator."""
+    from .test_oracle_reference import duffy_quadrature
+    gas = Gas(1.4, 1.0, 1.0)
+    p = 2
+    ref = ReferenceElement(p)
+    xyz, EToV = W.kuhn_cube(1, jitter=0.0)
+    xyz = xyz + 0.05 * np.sin(3 * xyz[:, ::-1])      # distort the vertices
+    geom = Geometry(ref, xyz, EToV)
+    S = Solver(geom, gas, bc_mode={0: FREESTREAM})
+    q = W.random_smooth_state(geom.x, 1.4, 1.0, 1.0, 0.1, seed=9)
+    strong = S.rhs(q)
+    qr, qs, qt, qw = duffy_quadrature(6)
+    L = vandermonde3(p, qr, qs, qt) @ ref.Vinv                     # [nq, Np]
+    Lr = vandermonde3(p, qr, qs, qt, "r") @ ref.Vinv
+    Ls = vandermonde3(p, qr, qs, qt, "s") @ ref.Vinv
+    Lt = vandermonde3(p, qr, qs, qt, "t") @ ref.Vinv
+    # triangle quadrature on the parameter triangle (collapsed Gauss)
+    x1, w1 = np.polynomial.legendre.leggauss(6)
+    A, B = np.meshgrid(x1, x1, indexing="ij")
+    u = ((1 + A) * (1 - B) / 2 - 1).ravel()
+    v = B.ravel()
+    tw = (w1[:, None] * w1[None, :] * (1 - B) / 2).ravel()
+    face_pts = [(u, v, -np.ones_like(u)), (u, -np.ones_like(u), v), (-1 - u - v, u, v),
+                (-np.ones_like(u), u, v)]
+    qn = np.transpose(q, (0, 2, 1))
+    flat = qn.reshape(-1, 5)
+    for k in range(geom.K):
+        Fk = euler_fluxes(qn[k], 1.4)                              # 3 x [Np, 5]
+        grad = [Lr, Ls, Lt]
+        vol = np.zeros((ref.Np, 5))
+        for b in range(3):
+            IF = L @ Fk[b]                                          # flux interpolant at quad pts
+            dldx = sum(geom.drdx[k, a, b] * grad[a] for a in range(3))   # [nq, Np]
+            vol += np.einsum("q,qi,qv->iv", qw, dldx, IF) * geom.J[k]
+        surf = np.zeros((ref.Np, 5))
+        for f in range(4):
+            n = geom.nrm[k, f]
+            qm = flat[geom.vmapM[k, f]]
+            qp = flat[geom.vmapP[k, f]]
+            if geom.boundary[k, f]:
+                qp = ED.ghost_freestream(qm, n, gas)
+            fstar = llf_flux(qm, qp, np.broadcast_to(n, qm.shape[:-1] + (3,)), 1.4)
+            nodal = np.zeros((ref.Np, 5))
+            nodal[ref.Fmask[f]] = fstar                             # face interpolant of F*
+            pr, ps, pt = face_pts[f]
+            Lf = vandermonde3(p, pr, ps, pt) @ ref.Vinv
+            surf += np.einsum("q,qi,qv->iv", tw, Lf, Lf @ nodal) * geom.sJ[k, f]
+        weak = np.linalg.solve(geom.J[k] * ref.M, vol - surf)      # [Np, 5]
+        np.testing.assert_allclose(weak.T, strong[k], atol=1e-11 * np.abs(strong).max())
+
+
+def test_probes_interpolate_linear_fields():
+    ref = ReferenceElement(1)
+    xyz, EToV = W.kuhn_cube(2, jitter=0.1)
+    geom = Geometry(ref, xyz, EToV)
+    q = np.zeros((geom.K, 5, ref.Np))
+    lin = lambda x: 1.0 + 0.3 * x[..., 0] - 0.2 * x[..., 1] + 0.1 * x[..., 2]
+    for v in range(5):
+        q[:, v] = (v + 1) * lin(geom.x)
+    pts = np.array([[0.1, 0.2, 0.3], [-0.7, 0.5, -0.1], [0.0, 0.0, 0.0]])
+    P = Probes(geom, pts)
+    np.testing.assert_allclose(P.sample(q), np.outer(lin(pts), np.arange(1, 6)), rtol=1e-13)
+    with pytest.raises(ValueError):
+        Probes(geom, [[2.0, 0.0, 0.0]])
