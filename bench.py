@@ -1,0 +1,350 @@
+"""Throughput of the GB300 DG Euler time step (DOF-updates/s), one JSON line.
+
+Workload (the ~200k-element p=3 ball): the Kuhn lattice n=32 on [-1,1]^3
+mapped onto the unit ball (196,608 tetrahedra, jittered interior vertices,
+seed 0), order p=3 (20 nodes per element, 1.97e7 DOF), SI air at rest with a
+10% p0 Gaussian pressure pulse of width 0.15 at the centre, characteristic
+pass-through boundary on the sphere, CFL 0.5 time step. One step = one full
+five-stage low-storage RK4 time step of the whole mesh.
+
+  value      device-resident state, K steps timed with CUDA events on the
+             solver's stream; max over ranks; DOF-updates/s = 5 Np K_elem steps / s
+  e2e        same metric through the C ABI with host buffers: dg_set_state
+             from pinned host memory, dg_step, sensor read-back and
+             dg_get_state to host, all inside the timed region (wall clock)
+  roofline   stage kernel: algorithmic float64 flops per launch / average
+             launch time (CUDA event pairs around every stage launch)
+  cpu_baseline  the float64 CPU oracle on a bounded sample of the workload
+
+``--impl reference`` times the CPU oracle itself on that sample instead.
+Multi-GPU (torchrun): independent replicas, one per GPU (the method has no
+data exchange on one mesh); value = all ranks' DOF-updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "DOF-updates/s (p=3 3D Euler DG, 1 GB300); mixed/learned-BC vs FP64 at error"
+UNIT = "DOF-updates/s"
+WORKLOAD = dict(n=32, radius=1.0, jitter=0.1, seed=0, order=3, amplitude=0.1, width=0.15, cfl=0.5)
+WORKLOAD_NAME = ("ball r=1: Kuhn lattice n=32 radially mapped, 196608 tets, jitter 0.1h seed 0; "
+                 "p=3 nodal DG (Np=20); SI air, 10% p0 Gaussian pulse w=0.15; characteristic BC")
+# CPU sample: the elements of the same mesh whose centroid lies within this radius
+CPU_SAMPLE_RADIUS = 0.25
+
+
+def stage_flops_per_element(p):
+    """Algorithmic float64 flops of one stage per element (1 FMA = 2 flops).
+
+    node:      Euler flux + metric fold (103) + RK update (25)   per node
+    volume:    3 derivative matrices x 5 variables x Np^2 FMAs
+    face node: two normal fluxes + wave speeds, LLF, jump (101)   per face node
+    lift:      5 variables x Np x 4 Nfp FMAs
+    """
+    Np = (p + 1) * (p + 2) * (p + 3) // 6
+    Nfp = (p + 1) * (p + 2) // 2
+    return Np * (103 + 25) + 30 * Np * Np + 4 * Nfp * 101 + 40 * Np * Nfp
+
+
+def fp64_peak_gflops(sm_mhz=2070.0):
+    """Nominal GB300 float64 rate: 1.25 TFLOP/s at the 2070 MHz boost clock over
+    152 SMs, i.e. 4 flops per SM per clock; scaled to the given clock."""
+    return 152 * 4 * sm_mhz * 1e-3
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload():
+    from paper_1710_03887_gb300 import workloads as W
+    w = WORKLOAD
+    xyz, EToV = W.ball(w["n"], w["radius"], jitter=w["jitter"], seed=w["seed"])
+    return xyz, EToV
+
+
+def cpu_sample_run(steps, warmup, xyz, EToV):
+    """Time the float64 CPU oracle on the sample of the workload; DOF-updates/s."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle.euler_dg import Gas, Solver
+    from oracle.geometry import Geometry
+    from oracle.reference_element import ReferenceElement
+    from paper_1710_03887_gb300 import workloads as W
+    w = WORKLOAD
+    cen = W.element_centroids(xyz, EToV)
+    keep = np.linalg.norm(cen, axis=1) < CPU_SAMPLE_RADIUS
+    sx, sE = W.submesh(xyz, EToV, keep)
+    ref = ReferenceElement(w["order"])
+    geom = Geometry(ref, sx, sE)
+    gas = Gas(W.GAMMA, W.RHO0_SI, W.P0_SI)
+    S = Solver(geom, gas)
+    q = W.gaussian_pulse_state(geom.x, W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"], w["width"])
+    dt = S.stable_dt(q, w["cfl"])
+    res = np.zeros_like(q)
+    led = (np.zeros(5), np.zeros(5))
+    t = 0.0
+    for _ in range(warmup):
+        q, t, res, led = S.step(q, t, dt, res, led)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        q, t, res, led = S.step(q, t, dt, res, led)
+        times.append(time.perf_counter() - t0)
+    dof = 5 * ref.Np * geom.K
+    total = sum(times)
+    sample = (f"{geom.K} elements of the workload mesh (centroid radius < {CPU_SAMPLE_RADIUS}), "
+              f"p=3, {steps} full RK4 steps, numpy float64 oracle")
+    return dof * steps / total, sample, geom.K
+
+
+def reduce_max(x, dist, device):
+    """Max of a scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world, dof_per_rank, steps, seconds):
+    """Whole-job DOF-updates/s: every replica advanced dof_per_rank DOF by steps."""
+    return world * dof_per_rank * steps / seconds
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    xyz, EToV = build_workload()
+    value, sample, _ = cpu_sample_run(args.steps, args.warmup, xyz, EToV)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOAD
+    xyz, EToV = build_workload()
+    S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI)
+    stream = torch.cuda.current_stream(dev)
+    S.set_stream(stream.cuda_stream)
+    S.upload_mesh(xyz, EToV)
+    nodes = S.node_coords()
+    q0 = W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"], w["width"])
+    dt = S.stable_dt(q0, w["cfl"])
+    K = S.K
+    Np = S.Np
+    dof = 5 * Np * K
+    probes = np.array([[0.5 * np.cos(a), 0.5 * np.sin(a), 0.1] for a in np.linspace(0, 6, 32)])
+    S.set_probes(probes, capacity=max(args.steps, 1))
+    q0_dev = torch.from_numpy(q0).to(dev)
+    # -- device-resident timing
+    S.set_state(q0_dev)
+    S.step(args.warmup, dt)
+    torch.cuda.synchronize(dev)
+    S.read_probes()
+    S.set_kernel_timing(True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        S.step(args.steps, dt)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    kms, klaunch = S.read_kernel_timing()
+    S.set_kernel_timing(False)
+    S.sync()
+    ms = reduce_max(ms, dist, dev)
+    value = aggregate_value(world, dof, args.steps, ms * 1e-3)
+    # -- end to end through the C ABI with host buffers
+    q0_host = torch.from_numpy(q0).pin_memory()
+    q_out = torch.empty_like(q0_host).pin_memory()
+    nprobe = probes.shape[0]
+    psamples = np.zeros((args.steps, nprobe, 5))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    S.set_state(q0_host)
+    S.step(args.steps, dt)
+    S.read_probes(args.steps, out=psamples)
+    S.get_state(q_out)
+    t1 = time.perf_counter()
+    e2e_s = t1 - t0
+    e2e_s = reduce_max(e2e_s, dist, dev)
+    e2e = aggregate_value(world, dof, args.steps, e2e_s)
+    state_bytes = dof * 8
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    flops = stage_flops_per_element(w["order"]) * K
+    avg_launch_s = (kms * 1e-3) / max(klaunch, 1)
+    achieved = flops / avg_launch_s * 1e-9
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    peak = fp64_peak_gflops(2070.0)
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "stage_fp64_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tr = json.load(f)
+            if tr.get("order") == w["order"]:
+                traffic = tr.get("bytes_per_launch_full")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "elements": K, "order": w["order"], "dof": dof,
+                   "dt": dt, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state 157 MB x 4 streams per stage); no flush"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": (state_bytes + nprobe * 5 * 8 * args.steps) / args.steps},
+        "gpu_launches": args.steps * 11,
+        "roofline": {"bound": "alu", "achieved": achieved * 1e-3, "peak": peak * 1e-3, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "stage_fp64_kernel<3>",
+                     "note": ("float64 pipe; peak = nominal 1.25 TFLOP/s = 152 SMs x 4 flop/clk "
+                              f"x 2070 MHz (recipe); median SM clock under load {sm_mhz} MHz"),
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches": klaunch},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],
+                    help="lattice size of the ball (32 = the benchmark; smaller for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    WORKLOAD["n"] = args.mesh_n
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if args.impl != "reference":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * dg_euler.h - C ABI of the GB300 nodal discontinuous Galerkin solver for the
+ * 3D compressible Euler equations on straight-sided tetrahedral meshes with
+ * pass-through (non-reflecting) outer boundaries.
+ *
+ * What is computed (citations are to Resch, "How the three-dimensional
+ * geometry of computational domain(s) affects the accuracy of non-reflective
+ * boundary conditions in acoustic simulation", arXiv:1710.03887):
+ *   - conserved variables (rho, rho u, rho v, rho w, E) of the Euler system,
+ *     section 2.1 Eq. 1, closed by the ideal-gas law Eq. 2;
+ *   - the element-wise DG semi-discretisation of Appendix A (Eqs. 8-12), in
+ *     nodal strong form: dq/dt = -div F + LIFT (Fscale (n.F(q-) - F*));
+ *   - local Lax-Friedrichs numerical flux on every face (section 1.1);
+ *   - outer-boundary ghost states: the paper's free-stream pass-through
+ *     condition (section 2.2), a characteristic (Riemann-invariant)
+ *     far-field ghost (section 1) and the reflective wall of section 2.3 Eq. 4;
+ *   - time integration of the ODE system of Eq. 12 with the five-stage
+ *     2N-storage fourth-order Runge-Kutta scheme of Carpenter & Kennedy (1994);
+ *   - sensors (section 3) and the time-integrated boundary flux.
+ *
+ * Conventions
+ *   - Every function returns an int status: DG_OK (0) or a negative DG_ERR_*.
+ *     dg_last_error() gives a message for the last failure on a context.
+ *     No C++ exception crosses this interface.
+ *   - Host arrays passed in are read during the call and never retained;
+ *     arrays passed out are written before the call returns.
+ *   - "device" pointers are CUDA global-memory pointers of the current
+ *     device (for instance from torch). The library does not retain them.
+ *   - The context owns its device buffers (allocated on first device use,
+ *     freed by dg_destroy). Device work is enqueued on the stream given by
+ *     dg_set_stream (default: the legacy default stream); calls that return
+ *     host data synchronise that stream.
+ *   - State layout everywhere: q[K][5][Np] (element-major, then variable,
+ *     then node), float64. Node order: lattice (i,j,k), i+j+k <= p, with k
+ *     outermost and i innermost; reference tetrahedron vertices v1=(-1,-1,-1),
+ *     v2=(1,-1,-1), v3=(-1,1,-1), v4=(-1,-1,1) map to element vertices
+ *     EToV[e][0..3].
+ *   - A device error (non-finite state, non-positive density or pressure) is
+ *     latched in a status word on the device and reported as
+ *     DG_ERR_NONFINITE by the next call that synchronises (dg_sync,
+ *     dg_get_state, dg_read_*), which also clears it.
+ */
+#ifndef DG_EULER_H
+#define DG_EULER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_ERR_ARG (-1)         /* bad argument (null pointer, size, range)      */
+#define DG_ERR_MESH (-2)        /* inverted element, non-manifold/unmatched face */
+#define DG_ERR_CUDA (-3)        /* a CUDA runtime call failed                    */
+#define DG_ERR_ORDER (-4)       /* call out of order (e.g. step before state)    */
+#define DG_ERR_NONFINITE (-5)   /* device saw a non-finite or non-physical state */
+#define DG_ERR_UNSUPPORTED (-6) /* order / mode not built into this library      */
+
+/* Boundary ghost rules (dg_set_bc) */
+#define DG_BC_FREESTREAM 0      /* ghost = free-stream state (section 2.2, Eq. 3)       */
+#define DG_BC_CHARACTERISTIC 1  /* Riemann-invariant far-field ghost (default)          */
+#define DG_BC_SLIP_WALL 2       /* normal velocity mirrored (section 2.3, Eq. 4)        */
+
+/* Arithmetic of the time step (dg_params.precision) */
+#define DG_PREC_FP64 0          /* float64 state, fluxes and contractions               */
+
+/* Free-stream gas and defaults of a context. */
+typedef struct dg_params {
+  double gamma;       /* ratio of specific heats (> 1)                           */
+  double rho0;        /* free-stream density (> 0)                                */
+  double p0;          /* free-stream pressure (> 0)                               */
+  double u0[3];       /* free-stream velocity                                     */
+  int32_t default_bc; /* ghost rule of every boundary id until dg_set_bc          */
+  int32_t precision;  /* DG_PREC_*                                                */
+} dg_params;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Create a solver of polynomial order 1..4 (Np = 4, 10, 20, 35 nodes per
+ * element). Builds the reference-element operators on the host (the
+ * orthonormal basis of Appendix A, Eq. 11). Touches no GPU. */
+int dg_create(int order, const dg_params* params, dg_ctx** out);
+/* Free the context and its device buffers (synchronises its stream). NULL ok. */
+int dg_destroy(dg_ctx* ctx);
+/* Message of the last failed call on ctx (static lifetime within ctx). */
+const char* dg_last_error(const dg_ctx* ctx);
+/* Stream for all subsequent device work (a cudaStream_t; NULL = default). */
+int dg_set_stream(dg_ctx* ctx, void* cuda_stream);
+
+/* Upload a straight-sided tetrahedral mesh (Appendix A, Eq. 9).
+ *   xyz[nvert][3]   vertex coordinates
+ *   EToV[K][4]      vertex ids per element, positively oriented
+ *   face_tag[K][4]  nullable; boundary id 0..7 of faces without a neighbour
+ *                   (a negative tag there is an error; tags of interior faces
+ *                   are ignored). NULL: every boundary face gets id 0.
+ *   vert_class[nvert] nullable; identity used to match faces (vertices with
+ *                   equal class are the same vertex for connectivity, e.g. a
+ *                   periodic box). NULL: the vertex id itself.
+ * Host only: computes J, d(r,s,t)/dx, normals, face areas and connectivity.
+ * Errors: DG_ERR_MESH for J <= 0, a face shared by more than two elements,
+ * or matched faces that are not back to back. Replaces any previous mesh and
+ * invalidates the state. */
+int dg_upload_mesh(dg_ctx* ctx, int64_t nvert, const double* xyz, int64_t K,
+                   const int32_t* EToV, const int8_t* face_tag,
+                   const int64_t* vert_class);
+/* Ghost rule of boundary id bc_id (0..7). */
+int dg_set_bc(dg_ctx* ctx, int bc_id, int mode);
+/* Sizes: number of elements, nodes per element, nodes per face. */
+int dg_sizes(const dg_ctx* ctx, int64_t* K, int32_t* Np, int32_t* Nfp);
+/* Physical node coordinates xyz[K][Np][3] (host). */
+int dg_node_coords(const dg_ctx* ctx, double* xyz);
+/* Geometric factors as computed by dg_upload_mesh (host; any pointer may be
+ * NULL): J[K], drdx[K][3][3] (d r_a / d x_b), nrm[K][4][3], sJ[K][4],
+ * EToE[K][4] (-1 on boundary faces), EToF[K][4], bc[K][4] (-1 interior). */
+int dg_get_geometry(const dg_ctx* ctx, double* J, double* drdx, double* nrm,
+                    double* sJ, int32_t* EToE, int8_t* EToF, int8_t* bc);
+/* Stable time step  cfl * min_e r_in / ((p+1)^2 * max(|u| + c))  of a host
+ * state q[K][5][Np] (host computation; r_in = 3 V / total face area). */
+int dg_stable_dt(const dg_ctx* ctx, const double* q, double cfl, double* dt);
+
+/* Reference operators of order p (host only, no context): node coordinates
+ * rst[3][Np], derivative matrices Dr/Ds/Dt[Np][Np] (row = node where the
+ * derivative is taken), LIFT[Np][4*Nfp], Fmask[4][Nfp]. Any output may be
+ * NULL. */
+int dg_reference_operators(int order, double* rst, double* Dr, double* Ds,
+                           double* Dt, double* LIFT, int32_t* Fmask);
+
+/* State q[K][5][Np] from host memory at time t; resets the Runge-Kutta
+ * residual, the boundary-flux ledger and the probe buffer. */
+int dg_set_state(dg_ctx* ctx, const double* q, double t);
+/* Same, from a device pointer. */
+int dg_set_state_device(dg_ctx* ctx, const double* dq, double t);
+/* Copy the state to host memory (synchronises); t may be NULL. */
+int dg_get_state(dg_ctx* ctx, double* q, double* t);
+/* Copy the state to a device buffer (enqueued on the stream; t on host). */
+int dg_get_state_device(dg_ctx* ctx, double* dq, double* t);
+
+/* Advance n full time steps of size dt (n >= 0, dt > 0): 5 Runge-Kutta stages
+ * each, every stage one evaluation of the semi-discrete operator (Eq. 12).
+ * Enqueued on the stream; returns without waiting. */
+int dg_step(dg_ctx* ctx, int n, double dt);
+/* One evaluation of the right-hand side f(q) of Eq. 12 at the current state
+ * and time, copied to host rhs[K][5][Np] (synchronises). Does not change the
+ * state or the time-stepping residual. */
+int dg_eval_rhs(dg_ctx* ctx, double* rhs);
+
+/* Sensors (section 3): n points xyz[n][3], each located in the element of
+ * lowest index that contains it (barycentrics >= -1e-12); DG_ERR_ARG if a
+ * point lies outside the mesh. After every completed step the five conserved
+ * variables are interpolated at each point into a device ring buffer of
+ * `capacity` steps. */
+int dg_set_probes(dg_ctx* ctx, int n, const double* xyz, int capacity);
+/* Read the samples recorded since the last read, oldest first, as
+ * out[steps][n][5] (host); at most min(max_steps, capacity) steps, the most
+ * recent ones if more were recorded. *got = steps written. Synchronises. */
+int dg_read_probes(dg_ctx* ctx, int max_steps, double* out, int* got);
+
+/* Time integral, since dg_set_state, of the outward numerical flux through
+ * all boundary faces: out[5] (host, synchronises). With it,
+ * totals(t) - totals(0) + ledger(t) = 0 up to rounding. */
+int dg_read_boundary_flux(dg_ctx* ctx, double out[5]);
+/* Conserved totals  sum_e J_e 1^T M q_e  (host, synchronises). */
+int dg_conserved_totals(dg_ctx* ctx, double out[5]);
+
+/* Wait for the stream; report (and clear) a latched device error. */
+int dg_sync(dg_ctx* ctx);
+
+/* Per-launch timing of the Runge-Kutta stage kernel: when enabled, dg_step
+ * records a CUDA event pair on the stream around every stage launch.
+ * dg_read_kernel_timing synchronises, returns the summed stage-kernel time in
+ * milliseconds and the number of timed launches since the last read, and
+ * resets both. Enabling/disabling discards pending records. */
+int dg_set_kernel_timing(dg_ctx* ctx, int enable);
+int dg_read_kernel_timing(dg_ctx* ctx, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_EULER_H */

@@ -1,0 +1,263 @@
+"""Python binding of the C ABI in include/dg_euler.h (argument marshalling only).
+
+Every function of the header is exposed under the same name on ``lib`` (a
+ctypes handle); ``Solver`` wraps a context for numpy / torch callers. Device
+pointers may come from torch tensors (``tensor.data_ptr()``); the library
+never holds on to them. There is no fallback: if the shared library cannot be
+loaded the import of ``lib`` fails with the reason.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+from . import build_lib
+
+DG_OK = 0
+DG_ERR_ARG = -1
+DG_ERR_MESH = -2
+DG_ERR_CUDA = -3
+DG_ERR_ORDER = -4
+DG_ERR_NONFINITE = -5
+DG_ERR_UNSUPPORTED = -6
+
+DG_BC_FREESTREAM = 0
+DG_BC_CHARACTERISTIC = 1
+DG_BC_SLIP_WALL = 2
+
+DG_PREC_FP64 = 0
+
+
+class dg_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("rho0", C.c_double), ("p0", C.c_double),
+                ("u0", C.c_double * 3), ("default_bc", C.c_int32), ("precision", C.c_int32)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "dg_create": (C.c_int, [C.c_int, C.POINTER(dg_params), C.POINTER(_P)]),
+    "dg_destroy": (C.c_int, [_P]),
+    "dg_last_error": (C.c_char_p, [_P]),
+    "dg_set_stream": (C.c_int, [_P, _P]),
+    "dg_upload_mesh": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, _P, _P]),
+    "dg_set_bc": (C.c_int, [_P, C.c_int, C.c_int]),
+    "dg_sizes": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "dg_node_coords": (C.c_int, [_P, _P]),
+    "dg_get_geometry": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "dg_stable_dt": (C.c_int, [_P, _P, C.c_double, _D]),
+    "dg_reference_operators": (C.c_int, [C.c_int, _P, _P, _P, _P, _P, _P]),
+    "dg_set_state": (C.c_int, [_P, _P, C.c_double]),
+    "dg_set_state_device": (C.c_int, [_P, _P, C.c_double]),
+    "dg_get_state": (C.c_int, [_P, _P, _D]),
+    "dg_get_state_device": (C.c_int, [_P, _P, _D]),
+    "dg_step": (C.c_int, [_P, C.c_int, C.c_double]),
+    "dg_eval_rhs": (C.c_int, [_P, _P]),
+    "dg_set_probes": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dg_read_probes": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
+    "dg_read_boundary_flux": (C.c_int, [_P, _P]),
+    "dg_conserved_totals": (C.c_int, [_P, _P]),
+    "dg_sync": (C.c_int, [_P]),
+    "dg_set_kernel_timing": (C.c_int, [_P, C.c_int]),
+    "dg_read_kernel_timing": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
+}
+
+_lib = None
+
+
+def header_symbols():
+    """Names of the functions declared in include/*.h."""
+    import re
+    names = []
+    for h in sorted((Path(__file__).resolve().parent.parent / "include").glob("*.h")):
+        text = h.read_text()
+        names += re.findall(r"^\s*(?:int|const char\*)\s+(dg_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def load(build=True):
+    """Load (building first if needed) the shared library and declare signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_lib.build() if build else build_lib.LIB
+    if not Path(path).exists():
+        raise OSError(f"{path} is missing: the CUDA library was not built")
+    lib = C.CDLL(str(path))
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dg error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    """Address of a numpy array (C-contiguous) or a torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def reference_operators(order):
+    """Library-built reference operators (host only): dict of numpy arrays."""
+    lib = load()
+    Np = (order + 1) * (order + 2) * (order + 3) // 6
+    Nfp = (order + 1) * (order + 2) // 2
+    rst = np.zeros((3, Np))
+    Dr, Ds, Dt = (np.zeros((Np, Np)) for _ in range(3))
+    LIFT = np.zeros((Np, 4 * Nfp))
+    Fmask = np.zeros((4, Nfp), dtype=np.int32)
+    rc = lib.dg_reference_operators(order, _ptr(rst), _ptr(Dr), _ptr(Ds), _ptr(Dt), _ptr(LIFT),
+                                    _ptr(Fmask))
+    if rc != DG_OK:
+        raise DGError(rc, "dg_reference_operators failed")
+    return dict(r=rst[0], s=rst[1], t=rst[2], Dr=Dr, Ds=Ds, Dt=Dt, LIFT=LIFT, Fmask=Fmask)
+
+
+class Solver:
+    """One solver context (order p, free stream, float64)."""
+
+    def __init__(self, order, gamma=1.4, rho0=1.225, p0=101325.0, u0=(0.0, 0.0, 0.0),
+                 default_bc=DG_BC_CHARACTERISTIC, precision=DG_PREC_FP64):
+        self.lib = load()
+        prm = dg_params(gamma, rho0, p0, (C.c_double * 3)(*u0), default_bc, precision)
+        h = _P()
+        rc = self.lib.dg_create(order, C.byref(prm), C.byref(h))
+        if rc != DG_OK:
+            raise DGError(rc, "dg_create failed (order or parameters)")
+        self.h = h
+        self.order = order
+        self.K = 0
+        self.Np = (order + 1) * (order + 2) * (order + 3) // 6
+        self.Nfp = (order + 1) * (order + 2) // 2
+
+    def _check(self, rc):
+        if rc != DG_OK:
+            raise DGError(rc, self.lib.dg_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle):
+        self._check(self.lib.dg_set_stream(self.h, stream_handle))
+
+    def upload_mesh(self, xyz, EToV, face_tag=None, vert_class=None):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        EToV = np.ascontiguousarray(EToV, dtype=np.int32)
+        ft = None if face_tag is None else np.ascontiguousarray(face_tag, dtype=np.int8)
+        vc = None if vert_class is None else np.ascontiguousarray(vert_class, dtype=np.int64)
+        self._check(self.lib.dg_upload_mesh(self.h, xyz.shape[0], _ptr(xyz), EToV.shape[0],
+                                            _ptr(EToV), _ptr(ft), _ptr(vc)))
+        self.K = EToV.shape[0]
+
+    def set_bc(self, bc_id, mode):
+        self._check(self.lib.dg_set_bc(self.h, bc_id, mode))
+
+    def node_coords(self):
+        out = np.zeros((self.K, self.Np, 3))
+        self._check(self.lib.dg_node_coords(self.h, _ptr(out)))
+        return out
+
+    def geometry(self):
+        K = self.K
+        g = dict(J=np.zeros(K), drdx=np.zeros((K, 3, 3)), nrm=np.zeros((K, 4, 3)),
+                 sJ=np.zeros((K, 4)), EToE=np.zeros((K, 4), np.int32),
+                 EToF=np.zeros((K, 4), np.int8), bc=np.zeros((K, 4), np.int8))
+        self._check(self.lib.dg_get_geometry(self.h, *(_ptr(g[k]) for k in
+                                                       ("J", "drdx", "nrm", "sJ", "EToE", "EToF", "bc"))))
+        return g
+
+    def stable_dt(self, q, cfl=0.5):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        dt = C.c_double()
+        self._check(self.lib.dg_stable_dt(self.h, _ptr(q), cfl, C.byref(dt)))
+        return dt.value
+
+    def set_state(self, q, t=0.0):
+        """q: numpy [K,5,Np] (host) or a CUDA torch tensor of that shape (device)."""
+        if hasattr(q, "is_cuda") and q.is_cuda:
+            assert q.is_contiguous() and q.dtype.itemsize == 8
+            self._check(self.lib.dg_set_state_device(self.h, q.data_ptr(), t))
+        else:
+            if hasattr(q, "numpy"):
+                assert q.is_contiguous()
+                self._check(self.lib.dg_set_state(self.h, q.data_ptr(), t))
+            else:
+                qa = np.ascontiguousarray(q, dtype=np.float64)
+                self._check(self.lib.dg_set_state(self.h, _ptr(qa), t))
+
+    def get_state(self, out=None):
+        """Copy the state into ``out`` (numpy / CPU or CUDA tensor) or a new array; returns (q, t)."""
+        t = C.c_double()
+        if out is None:
+            out = np.zeros((self.K, 5, self.Np))
+        if hasattr(out, "is_cuda") and out.is_cuda:
+            self._check(self.lib.dg_get_state_device(self.h, out.data_ptr(), C.byref(t)))
+        else:
+            self._check(self.lib.dg_get_state(self.h, _ptr(out), C.byref(t)))
+        return out, t.value
+
+    def step(self, n, dt):
+        self._check(self.lib.dg_step(self.h, int(n), float(dt)))
+
+    def eval_rhs(self):
+        out = np.zeros((self.K, 5, self.Np))
+        self._check(self.lib.dg_eval_rhs(self.h, _ptr(out)))
+        return out
+
+    def set_probes(self, xyz, capacity=1024):
+        xyz = np.ascontiguousarray(np.atleast_2d(xyz), dtype=np.float64)
+        self._check(self.lib.dg_set_probes(self.h, xyz.shape[0], _ptr(xyz), capacity))
+        self.nprobe = xyz.shape[0]
+
+    def read_probes(self, max_steps=1 << 30, out=None):
+        n = getattr(self, "nprobe", 0)
+        if out is None:
+            cap = min(max_steps, 1 << 16)
+            out = np.zeros((cap, max(n, 1), 5))
+            max_steps = cap
+        got = C.c_int()
+        self._check(self.lib.dg_read_probes(self.h, max_steps, _ptr(out), C.byref(got)))
+        return out[: got.value, :n]
+
+    def boundary_flux(self):
+        out = np.zeros(5)
+        self._check(self.lib.dg_read_boundary_flux(self.h, _ptr(out)))
+        return out
+
+    def totals(self):
+        out = np.zeros(5)
+        self._check(self.lib.dg_conserved_totals(self.h, _ptr(out)))
+        return out
+
+    def sync(self):
+        self._check(self.lib.dg_sync(self.h))
+
+    def set_kernel_timing(self, enable=True):
+        self._check(self.lib.dg_set_kernel_timing(self.h, int(enable)))
+
+    def read_kernel_timing(self):
+        """(summed stage-kernel milliseconds, launches) since the last read."""
+        ms = C.c_double()
+        n = C.c_int64()
+        self._check(self.lib.dg_read_kernel_timing(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value

@@ -1,0 +1,615 @@
+// C ABI of the DG Euler library (declared in include/dg_euler.h): context,
+// mesh upload, device buffers and the time-stepping loop.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dg_euler.h"
+#include "dg_device.cuh"
+#include "dg_host.hpp"
+
+namespace {
+
+// Carpenter & Kennedy (1994), five-stage 2N-storage fourth-order Runge-Kutta
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                        -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0,
+                        -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+                        2526269341429.0 / 6820363962896.0, 2006345519317.0 / 3224310063776.0,
+                        2802321613138.0 / 2924317926251.0};
+
+constexpr int kTotalsBlocks = 256;
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct dg_ctx {
+  dg::RefElement ref;
+  dg::Mesh mesh;
+  dg_params prm{};
+  int bc_mode[8];
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool have_mesh = false, dev_ready = false, have_state = false;
+  double t = 0.0;
+  int cur = 0;
+  int ntiles = 0, nslots = 0, grid = 0, sms = 0;
+  dgk::Gas gas{};
+  // device buffers
+  double* q[2] = {nullptr, nullptr};
+  double* res = nullptr;
+  double* scratch = nullptr;       // state-sized, for dg_eval_rhs
+  double* geo = nullptr;
+  int32_t* conn = nullptr;
+  double* ops = nullptr;
+  uint8_t* tbl = nullptr;
+  int32_t* fmask = nullptr;
+  int32_t* slot = nullptr;
+  double* ledger_part = nullptr;
+  double* ledger = nullptr;        // L[5], Lres[5]
+  double* mass_w = nullptr;
+  double* totals_part = nullptr;   // [kTotalsBlocks*5 + 5]
+  int* status = nullptr;
+  // sensors
+  int nprobe = 0, pcap = 0;
+  int64_t precorded = 0;
+  int32_t* pelem = nullptr;
+  double* prow = nullptr;
+  double* pring = nullptr;
+  std::vector<double> mass_w_host;
+  // stage-kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;   // created lazily, reused
+  size_t ev_used = 0;
+  void clear_events() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+    ev_used = 0;
+  }
+
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return DG_ERR_CUDA;
+  }
+  void free_device() {
+    if (dev_ready) cudaStreamSynchronize(stream);
+    clear_events();
+    dfree(q[0]); dfree(q[1]); dfree(res); dfree(scratch); dfree(geo); dfree(conn);
+    dfree(ops); dfree(tbl); dfree(fmask); dfree(slot); dfree(ledger_part); dfree(ledger);
+    dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
+    dev_ready = false;
+    have_state = false;
+    nprobe = 0;
+  }
+  size_t state_elems() const { return size_t(mesh.K) * 5 * ref.Np; }
+};
+
+namespace {
+
+#define DG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return c->cuda_fail(e_, #call); \
+  } while (0)
+
+// Allocate and fill the device copies of the mesh and operators.
+int ensure_device(dg_ctx* c) {
+  if (c->dev_ready) return DG_OK;
+  if (!c->have_mesh) return c->fail(DG_ERR_ORDER, "no mesh uploaded");
+  const int p = c->ref.p, Np = c->ref.Np, Nfp = c->ref.Nfp, NF = 4 * Nfp;
+  const int64_t K = c->mesh.K;
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  int bps = 0;
+  DG_CUDA(dgk::stage_prepare(p, &bps));
+  if (bps < 1) return c->fail(DG_ERR_CUDA, "stage kernel does not fit on an SM");
+  const int ET = dgk::stage_tile_elems(p);
+  c->ntiles = int((K + ET - 1) / ET);
+  c->grid = std::min(c->ntiles, c->sms * bps);
+  const size_t nq = c->state_elems();
+  DG_CUDA(cudaMalloc(&c->q[0], nq * 8));
+  DG_CUDA(cudaMalloc(&c->q[1], nq * 8));
+  DG_CUDA(cudaMalloc(&c->res, nq * 8));
+  DG_CUDA(cudaMalloc(&c->scratch, nq * 8));
+  // geometry records
+  std::vector<double> geo(size_t(K) * dgk::kGeoStride, 0.0);
+  for (int64_t e = 0; e < K; ++e) {
+    double* g = &geo[size_t(e) * dgk::kGeoStride];
+    for (int i = 0; i < 9; ++i) g[dgk::kGeoDrdx + i] = c->mesh.drdx[size_t(e) * 9 + i];
+    for (int i = 0; i < 12; ++i) g[dgk::kGeoNrm + i] = c->mesh.nrm[size_t(e) * 12 + i];
+    for (int f = 0; f < 4; ++f) {
+      g[dgk::kGeoFscale + f] = c->mesh.Fscale[size_t(e) * 4 + f];
+      g[dgk::kGeoSJ + f] = c->mesh.sJ[size_t(e) * 4 + f];
+    }
+    g[dgk::kGeoJ] = c->mesh.J[e];
+  }
+  DG_CUDA(cudaMalloc(&c->geo, geo.size() * 8));
+  DG_CUDA(cudaMemcpy(c->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice));
+  // face connection words and ledger slots of tiles that own boundary faces
+  std::vector<int32_t> conn(size_t(K) * 4);
+  std::vector<int32_t> slot(c->ntiles, -1);
+  int nslots = 0;
+  for (int64_t e = 0; e < K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const size_t i = size_t(e) * 4 + f;
+      if (c->mesh.EToE[i] >= 0) {
+        conn[i] = dgk::conn_interior(c->mesh.EToE[i], c->mesh.EToF[i], c->mesh.orient[i]);
+      } else {
+        conn[i] = -1 - c->mesh.bc[i];
+        const int tile = int(e / ET);
+        if (slot[tile] < 0) slot[tile] = nslots++;
+      }
+    }
+  c->nslots = std::max(nslots, 1);
+  DG_CUDA(cudaMalloc(&c->conn, conn.size() * 4));
+  DG_CUDA(cudaMemcpy(c->conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMalloc(&c->slot, slot.size() * 4));
+  DG_CUDA(cudaMemcpy(c->slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMalloc(&c->ledger_part, size_t(c->nslots) * 5 * 8));
+  DG_CUDA(cudaMemset(c->ledger_part, 0, size_t(c->nslots) * 5 * 8));
+  DG_CUDA(cudaMalloc(&c->ledger, 10 * 8));
+  DG_CUDA(cudaMemset(c->ledger, 0, 10 * 8));
+  // operators, transposed so that consecutive nodes are consecutive words
+  std::vector<double> ops(size_t(3) * Np * Np + size_t(NF) * Np + NF);
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) {
+      ops[size_t(j) * Np + i] = c->ref.Dr[size_t(i) * Np + j];
+      ops[size_t(Np) * Np + size_t(j) * Np + i] = c->ref.Ds[size_t(i) * Np + j];
+      ops[size_t(2) * Np * Np + size_t(j) * Np + i] = c->ref.Dt[size_t(i) * Np + j];
+    }
+  for (int i = 0; i < Np; ++i)
+    for (int m = 0; m < NF; ++m)
+      ops[size_t(3) * Np * Np + size_t(m) * Np + i] = c->ref.LIFT[size_t(i) * NF + m];
+  for (int m = 0; m < NF; ++m) ops[size_t(3) * Np * Np + size_t(NF) * Np + m] = c->ref.face_w[m];
+  DG_CUDA(cudaMalloc(&c->ops, ops.size() * 8));
+  DG_CUDA(cudaMemcpy(c->ops, ops.data(), ops.size() * 8, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMalloc(&c->tbl, c->ref.nbr_node.size()));
+  DG_CUDA(cudaMemcpy(c->tbl, c->ref.nbr_node.data(), c->ref.nbr_node.size(),
+                     cudaMemcpyHostToDevice));
+  std::vector<int32_t> fm(c->ref.Fmask.begin(), c->ref.Fmask.end());
+  DG_CUDA(cudaMalloc(&c->fmask, fm.size() * 4));
+  DG_CUDA(cudaMemcpy(c->fmask, fm.data(), fm.size() * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMalloc(&c->mass_w, size_t(Np) * 8));
+  DG_CUDA(cudaMemcpy(c->mass_w, c->mass_w_host.data(), size_t(Np) * 8, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMalloc(&c->totals_part, size_t(kTotalsBlocks + 1) * 5 * 8));
+  DG_CUDA(cudaMalloc(&c->status, sizeof(int)));
+  DG_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+  c->dev_ready = true;
+  return DG_OK;
+}
+
+dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* res, double a,
+                          double b, double dt) {
+  dgk::StageArgs A{};
+  A.q_in = qin;
+  A.q_out = qout;
+  A.res = res;
+  A.geo = c->geo;
+  A.conn = c->conn;
+  A.ops = c->ops;
+  A.nbr_tbl = c->tbl;
+  A.fmask = c->fmask;
+  A.ledger_slot = c->slot;
+  A.ledger_part = c->ledger_part;
+  A.status = c->status;
+  A.K = c->mesh.K;
+  A.ntiles = c->ntiles;
+  for (int i = 0; i < 8; ++i) A.bc_mode[i] = c->bc_mode[i];
+  A.a = a;
+  A.b = b;
+  A.dt = dt;
+  A.gas = c->gas;
+  return A;
+}
+
+int check_status(dg_ctx* c) {
+  int st = 0;
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  DG_CUDA(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    DG_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+    return c->fail(DG_ERR_NONFINITE, "device saw a non-finite or non-physical state "
+                                     "(density or pressure <= 0)");
+  }
+  return DG_OK;
+}
+
+// Event pair around a stage launch when timing is on.
+int record_event(dg_ctx* c) {
+  if (!c->timing) return DG_OK;
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    DG_CUDA(cudaEventCreate(&e));
+    c->ev_pool.push_back(e);
+  }
+  DG_CUDA(cudaEventRecord(c->ev_pool[c->ev_used++], c->stream));
+  return DG_OK;
+}
+
+int reset_run(dg_ctx* c, double t) {
+  c->t = t;
+  c->have_state = true;
+  c->precorded = 0;
+  DG_CUDA(cudaMemsetAsync(c->ledger, 0, 10 * 8, c->stream));
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_create(int order, const dg_params* params, dg_ctx** out) {
+  if (!out) return DG_ERR_ARG;
+  *out = nullptr;
+  if (!params) return DG_ERR_ARG;
+  if (!(params->gamma > 1.0) || !(params->rho0 > 0.0) || !(params->p0 > 0.0)) return DG_ERR_ARG;
+  if (params->default_bc < 0 || params->default_bc > 2) return DG_ERR_ARG;
+  if (params->precision != DG_PREC_FP64) return DG_ERR_UNSUPPORTED;
+  if (order < 1 || order > dg::kMaxOrder) return DG_ERR_UNSUPPORTED;
+  dg_ctx* c = new (std::nothrow) dg_ctx();
+  if (!c) return DG_ERR_ARG;
+  std::string err;
+  if (!dg::build_ref_element(order, c->ref, err)) {
+    delete c;
+    return DG_ERR_ARG;
+  }
+  c->prm = *params;
+  for (int i = 0; i < 8; ++i) c->bc_mode[i] = params->default_bc;
+  dgk::Gas& g = c->gas;
+  g.gamma = params->gamma;
+  g.gm1 = params->gamma - 1.0;
+  g.rho0 = params->rho0;
+  g.p0 = params->p0;
+  for (int d = 0; d < 3; ++d) g.u0[d] = params->u0[d];
+  g.c0 = std::sqrt(g.gamma * g.p0 / g.rho0);
+  g.E0 = g.p0 / g.gm1 + 0.5 * g.rho0 * (g.u0[0] * g.u0[0] + g.u0[1] * g.u0[1] + g.u0[2] * g.u0[2]);
+  g.s_inf = g.p0 / std::pow(g.rho0, g.gamma);
+  // mass-matrix column sums 1^T M with M = (V V^T)^-1 = invV^T invV
+  const int Np = c->ref.Np;
+  c->mass_w_host.assign(Np, 0.0);
+  for (int j = 0; j < Np; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < Np; ++i)
+      for (int m = 0; m < Np; ++m) s += c->ref.invV[size_t(m) * Np + i] * c->ref.invV[size_t(m) * Np + j];
+    c->mass_w_host[j] = s;
+  }
+  *out = c;
+  return DG_OK;
+}
+
+int dg_destroy(dg_ctx* c) {
+  if (!c) return DG_OK;
+  c->free_device();
+  delete c;
+  return DG_OK;
+}
+
+const char* dg_last_error(const dg_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+int dg_set_stream(dg_ctx* c, void* stream) {
+  if (!c) return DG_ERR_ARG;
+  if (c->dev_ready) cudaStreamSynchronize(c->stream);
+  c->stream = static_cast<cudaStream_t>(stream);
+  return DG_OK;
+}
+
+int dg_upload_mesh(dg_ctx* c, int64_t nvert, const double* xyz, int64_t K, const int32_t* EToV,
+                   const int8_t* face_tag, const int64_t* vert_class) {
+  if (!c) return DG_ERR_ARG;
+  if (K <= 0 || nvert <= 0 || !xyz || !EToV) return c->fail(DG_ERR_ARG, "empty mesh or null array");
+  if (K > (int64_t(1) << 26)) return c->fail(DG_ERR_ARG, "too many elements (max 2^26)");
+  c->free_device();
+  c->have_mesh = false;
+  std::string err;
+  if (!dg::build_mesh(c->ref, nvert, xyz, K, EToV, face_tag, vert_class, c->mesh, err))
+    return c->fail(DG_ERR_MESH, err);
+  c->have_mesh = true;
+  return DG_OK;
+}
+
+int dg_set_bc(dg_ctx* c, int bc_id, int mode) {
+  if (!c) return DG_ERR_ARG;
+  if (bc_id < 0 || bc_id > 7) return c->fail(DG_ERR_ARG, "boundary id must be 0..7");
+  if (mode < 0 || mode > 2) return c->fail(DG_ERR_ARG, "unknown boundary mode");
+  c->bc_mode[bc_id] = mode;
+  return DG_OK;
+}
+
+int dg_sizes(const dg_ctx* c, int64_t* K, int32_t* Np, int32_t* Nfp) {
+  if (!c) return DG_ERR_ARG;
+  if (K) *K = c->have_mesh ? c->mesh.K : 0;
+  if (Np) *Np = c->ref.Np;
+  if (Nfp) *Nfp = c->ref.Nfp;
+  return DG_OK;
+}
+
+int dg_node_coords(const dg_ctx* c, double* xyz) {
+  if (!c || !xyz) return DG_ERR_ARG;
+  if (!c->have_mesh) return DG_ERR_ORDER;
+  const int Np = c->ref.Np;
+  for (int64_t e = 0; e < c->mesh.K; ++e) {
+    const double* v = &c->mesh.verts[size_t(e) * 12];
+    for (int n = 0; n < Np; ++n) {
+      const double r = c->ref.r[n], s = c->ref.s[n], t = c->ref.t[n];
+      const double w[4] = {-0.5 * (1 + r + s + t), 0.5 * (1 + r), 0.5 * (1 + s), 0.5 * (1 + t)};
+      for (int d = 0; d < 3; ++d)
+        xyz[(size_t(e) * Np + n) * 3 + d] =
+            w[0] * v[d] + w[1] * v[3 + d] + w[2] * v[6 + d] + w[3] * v[9 + d];
+    }
+  }
+  return DG_OK;
+}
+
+int dg_get_geometry(const dg_ctx* c, double* J, double* drdx, double* nrm, double* sJ,
+                    int32_t* EToE, int8_t* EToF, int8_t* bc) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->have_mesh) return DG_ERR_ORDER;
+  const dg::Mesh& m = c->mesh;
+  if (J) std::memcpy(J, m.J.data(), m.J.size() * 8);
+  if (drdx) std::memcpy(drdx, m.drdx.data(), m.drdx.size() * 8);
+  if (nrm) std::memcpy(nrm, m.nrm.data(), m.nrm.size() * 8);
+  if (sJ) std::memcpy(sJ, m.sJ.data(), m.sJ.size() * 8);
+  if (EToE) std::memcpy(EToE, m.EToE.data(), m.EToE.size() * 4);
+  if (EToF) std::memcpy(EToF, m.EToF.data(), m.EToF.size());
+  if (bc) std::memcpy(bc, m.bc.data(), m.bc.size());
+  return DG_OK;
+}
+
+int dg_stable_dt(const dg_ctx* c, const double* q, double cfl, double* dt) {
+  if (!c || !q || !dt || !(cfl > 0.0)) return DG_ERR_ARG;
+  if (!c->have_mesh) return DG_ERR_ORDER;
+  const int Np = c->ref.Np;
+  const double g = c->prm.gamma;
+  double smax = 0.0, rmin = 1e300;
+  for (int64_t e = 0; e < c->mesh.K; ++e) {
+    rmin = std::min(rmin, c->mesh.rin[e]);
+    for (int n = 0; n < Np; ++n) {
+      const double* b = q + size_t(e) * 5 * Np + n;
+      const double rho = b[0], mx = b[Np], my = b[2 * Np], mz = b[3 * Np], E = b[4 * Np];
+      const double u2 = (mx * mx + my * my + mz * mz) / (rho * rho);
+      const double p = (g - 1.0) * (E - 0.5 * rho * u2);
+      if (!(rho > 0.0) || !(p > 0.0)) return DG_ERR_ARG;
+      smax = std::max(smax, std::sqrt(u2) + std::sqrt(g * p / rho));
+    }
+  }
+  const int p1 = c->ref.p + 1;
+  *dt = cfl * rmin / (double(p1) * p1 * smax);
+  return DG_OK;
+}
+
+int dg_reference_operators(int order, double* rst, double* Dr, double* Ds, double* Dt,
+                           double* LIFT, int32_t* Fmask) {
+  dg::RefElement re;
+  std::string err;
+  if (!dg::build_ref_element(order, re, err)) return DG_ERR_UNSUPPORTED;
+  const int Np = re.Np;
+  if (rst) {
+    std::memcpy(rst, re.r.data(), Np * 8);
+    std::memcpy(rst + Np, re.s.data(), Np * 8);
+    std::memcpy(rst + 2 * Np, re.t.data(), Np * 8);
+  }
+  if (Dr) std::memcpy(Dr, re.Dr.data(), re.Dr.size() * 8);
+  if (Ds) std::memcpy(Ds, re.Ds.data(), re.Ds.size() * 8);
+  if (Dt) std::memcpy(Dt, re.Dt.data(), re.Dt.size() * 8);
+  if (LIFT) std::memcpy(LIFT, re.LIFT.data(), re.LIFT.size() * 8);
+  if (Fmask)
+    for (size_t i = 0; i < re.Fmask.size(); ++i) Fmask[i] = re.Fmask[i];
+  return DG_OK;
+}
+
+int dg_set_state(dg_ctx* c, const double* q, double t) {
+  if (!c || !q) return DG_ERR_ARG;
+  int rc = ensure_device(c);
+  if (rc) return rc;
+  DG_CUDA(cudaMemcpyAsync(c->q[c->cur], q, c->state_elems() * 8, cudaMemcpyHostToDevice, c->stream));
+  return reset_run(c, t);
+}
+
+int dg_set_state_device(dg_ctx* c, const double* dq, double t) {
+  if (!c || !dq) return DG_ERR_ARG;
+  int rc = ensure_device(c);
+  if (rc) return rc;
+  DG_CUDA(cudaMemcpyAsync(c->q[c->cur], dq, c->state_elems() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  return reset_run(c, t);
+}
+
+int dg_get_state(dg_ctx* c, double* q, double* t) {
+  if (!c || !q) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  DG_CUDA(cudaMemcpyAsync(q, c->q[c->cur], c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (t) *t = c->t;
+  return check_status(c);
+}
+
+int dg_get_state_device(dg_ctx* c, double* dq, double* t) {
+  if (!c || !dq) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  DG_CUDA(cudaMemcpyAsync(dq, c->q[c->cur], c->state_elems() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (t) *t = c->t;
+  return DG_OK;
+}
+
+int dg_step(dg_ctx* c, int n, double dt) {
+  if (!c) return DG_ERR_ARG;
+  if (n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return c->fail(DG_ERR_ARG, "need n >= 0 and dt > 0");
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  for (int s = 0; s < n; ++s) {
+    for (int k = 0; k < 5; ++k) {
+      dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], c->res, kRkA[k], kRkB[k], dt);
+      int rc = record_event(c);
+      if (rc) return rc;
+      DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+      rc = record_event(c);
+      if (rc) return rc;
+      DG_CUDA(dgk::launch_ledger_update(c->ledger_part, c->nslots, c->ledger, kRkA[k], kRkB[k], dt,
+                                        c->stream));
+      c->cur = 1 - c->cur;
+    }
+    c->t += dt;
+    if (c->nprobe > 0) {
+      const int slotp = int(c->precorded % c->pcap);
+      DG_CUDA(dgk::launch_probe_sample(c->q[c->cur], c->ref.Np, c->nprobe, c->pelem, c->prow,
+                                       c->pring + size_t(slotp) * c->nprobe * 5, c->stream));
+      ++c->precorded;
+    }
+  }
+  return DG_OK;
+}
+
+int dg_eval_rhs(dg_ctx* c, double* rhs) {
+  if (!c || !rhs) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  // one stage with a = b = 0, dt = 1 writes f(q) into the scratch residual;
+  // the ledger slots it touches are rewritten by the next real stage
+  dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], c->scratch, 0.0, 0.0, 1.0);
+  DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+  DG_CUDA(cudaMemcpyAsync(rhs, c->scratch, c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
+  return check_status(c);
+}
+
+int dg_set_probes(dg_ctx* c, int n, const double* xyz, int capacity) {
+  if (!c) return DG_ERR_ARG;
+  if (n < 0 || n > 4096 || (n > 0 && (!xyz || capacity < 1))) return c->fail(DG_ERR_ARG, "bad probe arguments");
+  int rc = ensure_device(c);
+  if (rc) return rc;
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c->pelem); dfree(c->prow); dfree(c->pring);
+  c->nprobe = 0;
+  c->precorded = 0;
+  if (n == 0) return DG_OK;
+  const int Np = c->ref.Np;
+  std::vector<int32_t> elem(n);
+  std::vector<double> rows(size_t(n) * Np);
+  for (int i = 0; i < n; ++i) {
+    const double* x = xyz + 3 * i;
+    int64_t found = -1;
+    double rst[3] = {0, 0, 0};
+    for (int64_t e = 0; e < c->mesh.K && found < 0; ++e) {
+      const double* v = &c->mesh.verts[size_t(e) * 12];
+      const double* m = &c->mesh.drdx[size_t(e) * 9];
+      // (r,s,t) = -1 + drdx (x - v1) * ... : r_a + 1 = sum_b drdx[a][b] (x_b - v1_b)
+      double ref[3];
+      for (int a = 0; a < 3; ++a)
+        ref[a] = -1.0 + m[a * 3] * (x[0] - v[0]) + m[a * 3 + 1] * (x[1] - v[1]) + m[a * 3 + 2] * (x[2] - v[2]);
+      const double l2 = 0.5 * (1 + ref[0]), l3 = 0.5 * (1 + ref[1]), l4 = 0.5 * (1 + ref[2]);
+      const double l1 = 1.0 - l2 - l3 - l4;
+      const double tol = -1e-12;
+      if (l1 >= tol && l2 >= tol && l3 >= tol && l4 >= tol) {
+        found = e;
+        rst[0] = ref[0]; rst[1] = ref[1]; rst[2] = ref[2];
+      }
+    }
+    if (found < 0) return c->fail(DG_ERR_ARG, "probe " + std::to_string(i) + " lies outside the mesh");
+    elem[i] = int32_t(found);
+    // Lagrange basis at the point: l_j(x) = sum_m psi_m(x) invV[m][j]
+    std::vector<double> psi(Np);
+    dg::eval_basis(c->ref.p, 1, &rst[0], &rst[1], &rst[2], psi.data());
+    for (int j = 0; j < Np; ++j) {
+      double s = 0.0;
+      for (int m2 = 0; m2 < Np; ++m2) s += psi[m2] * c->ref.invV[size_t(m2) * Np + j];
+      rows[size_t(i) * Np + j] = s;
+    }
+  }
+  DG_CUDA(cudaMalloc(&c->pelem, size_t(n) * 4));
+  DG_CUDA(cudaMalloc(&c->prow, rows.size() * 8));
+  DG_CUDA(cudaMalloc(&c->pring, size_t(capacity) * n * 5 * 8));
+  DG_CUDA(cudaMemcpy(c->pelem, elem.data(), size_t(n) * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(c->prow, rows.data(), rows.size() * 8, cudaMemcpyHostToDevice));
+  c->nprobe = n;
+  c->pcap = capacity;
+  return DG_OK;
+}
+
+int dg_read_probes(dg_ctx* c, int max_steps, double* out, int* got) {
+  if (!c || !got || max_steps < 0 || (max_steps > 0 && !out)) return DG_ERR_ARG;
+  *got = 0;
+  if (c->nprobe == 0) return DG_OK;
+  int rc = check_status(c);
+  if (rc) return rc;
+  const int64_t avail = std::min<int64_t>(c->precorded, c->pcap);
+  const int take = int(std::min<int64_t>(avail, max_steps));
+  const size_t row = size_t(c->nprobe) * 5;
+  for (int i = 0; i < take; ++i) {
+    const int64_t step = c->precorded - take + i;
+    const int slotp = int(step % c->pcap);
+    DG_CUDA(cudaMemcpy(out + size_t(i) * row, c->pring + size_t(slotp) * row, row * 8,
+                       cudaMemcpyDeviceToHost));
+  }
+  c->precorded = 0;
+  *got = take;
+  return DG_OK;
+}
+
+int dg_read_boundary_flux(dg_ctx* c, double out[5]) {
+  if (!c || !out) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  int rc = check_status(c);
+  if (rc) return rc;
+  DG_CUDA(cudaMemcpy(out, c->ledger, 5 * 8, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int dg_conserved_totals(dg_ctx* c, double out[5]) {
+  if (!c || !out) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  DG_CUDA(dgk::launch_totals(c->q[c->cur], c->geo, c->mass_w, c->mesh.K, c->ref.Np, c->totals_part,
+                             kTotalsBlocks, c->totals_part + size_t(kTotalsBlocks) * 5, c->stream));
+  int rc = check_status(c);
+  if (rc) return rc;
+  DG_CUDA(cudaMemcpy(out, c->totals_part + size_t(kTotalsBlocks) * 5, 5 * 8, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int dg_sync(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->dev_ready) return DG_OK;
+  return check_status(c);
+}
+
+int dg_set_kernel_timing(dg_ctx* c, int enable) {
+  if (!c) return DG_ERR_ARG;
+  if (c->dev_ready) cudaStreamSynchronize(c->stream);
+  c->ev_used = 0;
+  c->timing = enable != 0;
+  return DG_OK;
+}
+
+int dg_read_kernel_timing(dg_ctx* c, double* total_ms, int64_t* launches) {
+  if (!c || !total_ms || !launches) return DG_ERR_ARG;
+  *total_ms = 0.0;
+  *launches = 0;
+  if (c->ev_used == 0) return DG_OK;
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  double sum = 0.0;
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    DG_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]));
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = int64_t(c->ev_used / 2);
+  c->ev_used = 0;
+  return DG_OK;
+}
+
+}  // extern "C"

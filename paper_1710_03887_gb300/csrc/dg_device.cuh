@@ -1,0 +1,61 @@
+// Device-side declarations shared by the library's CUDA translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgk {
+
+// per-element geometry record (float64), 32 words = 256 bytes
+constexpr int kGeoStride = 32;
+constexpr int kGeoDrdx = 0;     // 9: d r_a / d x_b at a*3+b
+constexpr int kGeoNrm = 9;      // 12: outward unit normal of face f at 9 + 3f
+constexpr int kGeoFscale = 21;  // 4: sJ / J
+constexpr int kGeoSJ = 25;      // 4: face area / 2
+constexpr int kGeoJ = 29;       // 1: volume / (4/3)
+
+// status bits latched by the kernels
+constexpr int kStatusBadState = 1;
+
+// face connection word: >= 0: (neighbour element << 5) | (neighbour face << 3) | orientation;
+// < 0: boundary, id = -1 - word
+__host__ __device__ inline int32_t conn_interior(int32_t e2, int f2, int o) {
+  return (e2 << 5) | (f2 << 3) | o;
+}
+
+struct Gas {
+  double gamma, gm1, rho0, p0, u0[3], c0, E0, s_inf;
+};
+
+struct StageArgs {
+  const double* q_in;
+  double* q_out;
+  double* res;
+  const double* geo;         // [K][kGeoStride]
+  const int32_t* conn;       // [K][4]
+  const double* ops;         // DrT | DsT | DtT ([j][i], Np*Np each) | LIFTT ([m][i], NF*Np) | face_w [NF]
+  const uint8_t* nbr_tbl;    // [4][4][6][Nfp]: neighbour volume node
+  const int32_t* fmask;      // [4][Nfp]
+  const int32_t* ledger_slot;  // [ntiles]: slot in ledger_part, or -1 (no boundary face)
+  double* ledger_part;       // [nslots][5]
+  int* status;
+  int64_t K;
+  int ntiles;
+  int bc_mode[8];
+  double a, b, dt;
+  Gas gas;
+};
+
+// launch helpers (stage_fp64.cu)
+int stage_tile_elems(int p);
+size_t stage_smem_bytes(int p);
+cudaError_t stage_prepare(int p, int* blocks_per_sm);
+cudaError_t launch_stage(int p, const StageArgs& a, int grid, cudaStream_t s);
+
+cudaError_t launch_ledger_update(const double* part, int nslots, double* ledger, double a,
+                                 double b, double dt, cudaStream_t s);
+cudaError_t launch_probe_sample(const double* q, int Np, int n, const int32_t* elem,
+                                const double* rows, double* out, cudaStream_t s);
+cudaError_t launch_totals(const double* q, const double* geo, const double* mass_w, int64_t K,
+                          int Np, double* partial, int nblocks, double* out, cudaStream_t s);
+
+}  // namespace dgk

@@ -1,0 +1,84 @@
+"""Shared set-up of matched oracle / library runs for the tests.
+
+Both sides get the same mesh arrays, boundary tags and initial state (the
+state is evaluated at the oracle's node coordinates, which the host-logic
+tests show agree with the library's to rounding).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle.euler_dg import CHARACTERISTIC, FREESTREAM, SLIP_WALL, Gas, Probes, Solver
+from oracle.geometry import Geometry
+from oracle.reference_element import ReferenceElement
+from paper_1710_03887_gb300 import workloads as W
+
+SI = dict(gamma=W.GAMMA, rho0=W.RHO0_SI, p0=W.P0_SI)
+SCALED = dict(gamma=1.4, rho0=1.4, p0=1.0)          # the paper's scaling, c0 = 1 (Eq. 3)
+
+
+def rel_err(a, b):
+    """Per conserved variable: max |a - b| / max |b| (q arrays [K, 5, Np])."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.abs(a - b).max(axis=(0, 2))
+    den = np.abs(b).max(axis=(0, 2))
+    return num / np.where(den > 0, den, 1.0)
+
+
+def state_err(a, b, gas):
+    """Per conserved variable: max |a - b| / scale, with scale = max |b| for
+    density and energy and rho0 * c0 for the momentum components."""
+    num = np.abs(np.asarray(a) - np.asarray(b)).max(axis=(0, 2))
+    den = np.abs(np.asarray(b)).max(axis=(0, 2))
+    den[1:4] = np.maximum(den[1:4], gas.rho0 * gas.c0)
+    return num / den
+
+
+def direction_tags(xyz, EToV, ref_geom):
+    """Boundary ids by outward normal direction: x faces 0, y faces 1, z faces 2."""
+    tags = np.full((EToV.shape[0], 4), -1, dtype=np.int8)
+    b = ref_geom.boundary
+    ax = np.argmax(np.abs(ref_geom.nrm), axis=2)
+    tags[b] = ax[b]
+    return tags
+
+
+class Case:
+    def __init__(self, p, xyz, EToV, gas=SI, tags=None, modes=None, period=None):
+        self.p = p
+        self.xyz, self.EToV = xyz, EToV
+        self.ref = ReferenceElement(p)
+        self.geom = Geometry(self.ref, xyz, EToV, period=period)
+        self.gas = Gas(gas["gamma"], gas["rho0"], gas["p0"])
+        self.gas_kw = gas
+        self.tags = tags
+        self.modes = {0: CHARACTERISTIC} if modes is None else modes
+        bc_id = None if tags is None else np.where(tags < 0, 0, tags)
+        self.oracle = Solver(self.geom, self.gas, bc_id=bc_id, bc_mode=self.modes)
+        self.period = period
+
+    def library(self):
+        from paper_1710_03887_gb300 import binding as B
+        S = B.Solver(self.p, **self.gas_kw)
+        vclass = None
+        if self.period is not None:
+            n = round(np.cbrt(self.EToV.shape[0] / 6))
+            vclass = W.periodic_vertex_classes(n)
+        S.upload_mesh(self.xyz, self.EToV, face_tag=self.tags, vert_class=vclass)
+        for ident, mode in self.modes.items():
+            S.set_bc(ident, mode)
+        return S
+
+    def pulse(self, amplitude, width=0.15, center=(0.0, 0.0, 0.0)):
+        g = self.gas_kw
+        return W.gaussian_pulse_state(self.geom.x, g["gamma"], g["rho0"], g["p0"],
+                                      amplitude, width, center)
+
+    def smooth(self, amplitude=0.05, seed=0):
+        g = self.gas_kw
+        return W.random_smooth_state(self.geom.x, g["gamma"], g["rho0"], g["p0"], amplitude, seed)
+
+
+__all__ = ["Case", "rel_err", "state_err", "direction_tags", "SI", "SCALED", "CHARACTERISTIC", "FREESTREAM",
+           "SLIP_WALL", "Probes"]

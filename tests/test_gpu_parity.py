@@ -1,0 +1,187 @@
+"""CUDA float64 path against the CPU oracle, element by element (GPU).
+
+Tolerance: per conserved variable, max |gpu - oracle| / scale_v <= 1e-11, where
+scale_v = max |oracle_v| for density and energy and rho0 * c0 for the momentum
+components. The momentum equation carries the pressure (rho u^2 + p), so its
+rounding floor is set by p0 ~ rho0 c0^2 rather than by the small acoustic
+momentum itself; measuring momentum against rho0 c0 makes the bound the same
+relative rounding level for every variable.
+"""
+import numpy as np
+import pytest
+
+from paper_1710_03887_gb300 import workloads as W
+
+from ._cases import CHARACTERISTIC, FREESTREAM, SCALED, SI, SLIP_WALL, Case, Probes, direction_tags, rel_err, state_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_rhs_matches_oracle_mixed_boundaries(cuda_device, p):
+    # jittered 3^3 Kuhn cube: 162 elements, several tiles plus a ragged tail
+    xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=p)
+    probe = Case(p, xyz, EToV)
+    tags = direction_tags(xyz, EToV, probe.geom)
+    case = Case(p, xyz, EToV, tags=tags,
+                modes={0: CHARACTERISTIC, 1: FREESTREAM, 2: SLIP_WALL})
+    q = case.smooth(0.05, seed=p)
+    ref = case.oracle.rhs(q)
+    S = case.library()
+    S.set_state(q)
+    got = S.eval_rhs()
+    err = rel_err(got, ref)
+    assert np.all(err < TOL), err
+
+
+def test_c1_pulse_100_steps(cuda_device):
+    """Config C1: p=1, 6x6x6x6 = 1296-element cube, 0.5% pulse, characteristic BC."""
+    xyz, EToV = W.kuhn_cube(6)
+    case = Case(1, xyz, EToV)
+    q0 = case.pulse(0.005, 0.15)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    pts = np.array([[0.3, 0.1, 0.05], [-0.5, 0.2, 0.4], [0.9, -0.9, 0.1]])
+    probes = Probes(case.geom, pts)
+    qo, to, ledger_o, samples_o = case.oracle.run(q0, dt, 100, probes=probes)
+    S = case.library()
+    S.set_state(q0)
+    S.set_probes(pts, capacity=128)
+    S.step(100, dt)
+    qg, tg = S.get_state()
+    assert tg == pytest.approx(to, rel=1e-15)
+    err = state_err(qg, qo, case.gas)
+    assert np.all(err < TOL), err
+    # the perturbation itself (q - q0) also agrees
+    dq = np.abs(qg - qo).max(axis=(0, 2)) / np.abs(qo - q0).max(axis=(0, 2))
+    assert np.all(dq[[0, 4]] < 1e-8), dq
+    samples = S.read_probes()
+    assert samples.shape == (100, 3, 5)
+    scale = np.abs(samples_o).max(axis=(0, 1))
+    assert np.all(np.abs(samples - samples_o).max(axis=(0, 1)) / scale < TOL)
+    led = S.boundary_flux()
+    tot = S.totals()
+    tot0 = case.oracle.totals(q0)
+    # library ledger vs oracle ledger, relative to the flux scale
+    assert np.allclose(led, ledger_o, rtol=1e-9, atol=1e-12 * np.abs(tot0).max())
+    # discrete conservation on the GPU: totals(t) - totals(0) + ledger = 0
+    bal = tot - tot0 + led
+    assert np.all(np.abs(bal) <= 1e-12 * np.maximum(np.abs(tot0), 1.0)), bal
+
+
+def test_p3_pulse_steps(cuda_device):
+    xyz, EToV = W.kuhn_cube(4, jitter=0.1)
+    case = Case(3, xyz, EToV)
+    q0 = case.pulse(0.1, 0.3)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    qo, _, _, _ = case.oracle.run(q0, dt, 20)
+    S = case.library()
+    S.set_state(q0)
+    S.step(20, dt)
+    qg, _ = S.get_state()
+    err = state_err(qg, qo, case.gas)
+    assert np.all(err < TOL), err
+
+
+def test_periodic_conservation_on_gpu(cuda_device):
+    xyz, EToV = W.kuhn_cube(4)
+    case = Case(2, xyz, EToV, gas=SCALED, period=(2.0, 2.0, 2.0))
+    q0 = case.smooth(0.05, seed=3)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    S = case.library()
+    S.set_state(q0)
+    t0 = S.totals()
+    S.step(50, dt)
+    t1 = S.totals()
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * np.maximum(np.abs(t0), 1.0))
+    qo, _, _, _ = case.oracle.run(q0, dt, 50)
+    qg, _ = S.get_state()
+    err = state_err(qg, qo, case.gas)
+    assert np.all(err < TOL), err
+
+
+def test_restart_is_bitwise(cuda_device):
+    """50 + save/restore + 50 steps equals 100 steps exactly (checkpoint/resume)."""
+    xyz, EToV = W.kuhn_cube(4)
+    case = Case(2, xyz, EToV)
+    q0 = case.pulse(0.05, 0.3)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    S = case.library()
+    S.set_state(q0)
+    S.step(100, dt)
+    a, _ = S.get_state()
+    S.set_state(q0)
+    S.step(50, dt)
+    mid, tm = S.get_state()
+    S2 = case.library()
+    S2.set_state(mid, tm)
+    S2.step(50, dt)
+    b, _ = S2.get_state()
+    assert np.array_equal(a, b)
+
+
+def test_device_state_roundtrip_and_errors(cuda_device):
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    xyz, EToV = W.kuhn_cube(2)
+    case = Case(1, xyz, EToV)
+    S = case.library()
+    with pytest.raises(B.DGError) as e:
+        S.step(1, 1e-5)
+    assert e.value.code == B.DG_ERR_ORDER
+    q0 = case.pulse(0.01, 0.3)
+    dq = torch.from_numpy(q0).to(cuda_device)
+    S.set_state(dq)
+    out = torch.empty_like(dq)
+    S.get_state(out)
+    torch.cuda.synchronize()
+    assert torch.equal(out.cpu(), dq.cpu())
+    with pytest.raises(B.DGError):
+        S.step(1, -1.0)
+    bad = q0.copy()
+    bad[3, 0, 1] = -1.0                      # negative density is latched and reported
+    S.set_state(bad)
+    with pytest.raises(B.DGError) as e:
+        S.eval_rhs()
+    assert e.value.code == B.DG_ERR_NONFINITE
+    S.set_state(q0)                           # the context stays usable
+    S.step(2, 1e-5)
+    S.sync()
+
+
+def test_full_size_ball_sampled_rhs(cuda_device):
+    """Bench workload (ball, n=32: 196,608 elements, p=3): sampled elements against
+    the oracle evaluated on the patch made of those elements and their neighbours."""
+    from oracle.euler_dg import Solver as OSolver
+    from oracle.geometry import Geometry
+    from oracle.reference_element import ReferenceElement
+    from paper_1710_03887_gb300 import binding as B
+    xyz, EToV = W.ball(32, 1.0, jitter=0.1, seed=0)
+    S = B.Solver(3, **SI)
+    S.upload_mesh(xyz, EToV)
+    nodes = S.node_coords()
+    q = W.gaussian_pulse_state(nodes, SI["gamma"], SI["rho0"], SI["p0"], 0.1, 0.15)
+    q += 0.0  # contiguous copy
+    S.set_state(q)
+    rhs = S.eval_rhs()
+    g = S.geometry()
+    rng = np.random.default_rng(0)
+    bdry = np.nonzero((g["EToE"] < 0).any(axis=1))[0]
+    sample = np.unique(np.concatenate([rng.choice(EToV.shape[0], 40, replace=False),
+                                       rng.choice(bdry, 10, replace=False),
+                                       [0, EToV.shape[0] - 1]]))
+    patch = np.unique(np.concatenate([sample, g["EToE"][sample].ravel()]))
+    patch = patch[patch >= 0]
+    sub_xyz, sub_EToV = W.submesh(xyz, EToV, np.isin(np.arange(EToV.shape[0]), patch))
+    ref = ReferenceElement(3)
+    geom = Geometry(ref, sub_xyz, sub_EToV)
+    # patch-local ids of the sampled elements; keep only faces that were
+    # boundary faces of the full mesh as boundary
+    local = np.searchsorted(patch, sample)
+    from oracle.euler_dg import Gas
+    osol = OSolver(geom, Gas(SI["gamma"], SI["rho0"], SI["p0"]))
+    ro = osol.rhs(q[patch])
+    assert np.array_equal(geom.boundary[local], g["EToE"][sample] < 0)
+    err = rel_err(rhs[sample], ro[local])
+    assert np.all(err < TOL), err

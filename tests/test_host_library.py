@@ -1,0 +1,114 @@
+"""Host side of the C ABI (no GPU needed): symbols, operators, geometry, errors."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle.geometry import Geometry, inscribed_radius
+from oracle.reference_element import ReferenceElement
+from paper_1710_03887_gb300 import binding as B
+from paper_1710_03887_gb300 import workloads as W
+
+
+def test_library_exports_every_header_symbol():
+    lib = B.load()
+    names = B.header_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+    # the binding declares every header function and nothing else
+    assert sorted(B._SIGS) == sorted(names)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_reference_operators_match_oracle(p):
+    L = B.reference_operators(p)
+    R = ReferenceElement(p)
+    for k in "rst":
+        np.testing.assert_allclose(L[k], getattr(R, k), atol=1e-15)
+    for k in ("Dr", "Ds", "Dt", "LIFT"):
+        ref = getattr(R, k)
+        np.testing.assert_allclose(L[k], ref, atol=1e-13 * np.abs(ref).max())
+    np.testing.assert_array_equal(L["Fmask"], R.Fmask)
+
+
+def test_unsupported_order_is_rejected():
+    with pytest.raises(B.DGError) as e:
+        B.Solver(7)
+    assert e.value.code == B.DG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.12])
+def test_geometry_and_connectivity_match_oracle(jitter):
+    p = 2
+    xyz, EToV = W.kuhn_cube(3, jitter=jitter, seed=3)
+    S = B.Solver(p)
+    S.upload_mesh(xyz, EToV)
+    g = S.geometry()
+    G = Geometry(ReferenceElement(p), xyz, EToV)
+    np.testing.assert_allclose(g["J"], G.J, rtol=1e-14)
+    np.testing.assert_allclose(g["drdx"], G.drdx, atol=1e-13)
+    np.testing.assert_allclose(g["nrm"], G.nrm, atol=1e-14)
+    np.testing.assert_allclose(g["sJ"], G.sJ, rtol=1e-13)
+    np.testing.assert_array_equal(g["EToE"] < 0, G.boundary)
+    inner = ~G.boundary
+    np.testing.assert_array_equal(g["EToE"][inner], G.EToE[inner])
+    np.testing.assert_array_equal(g["EToF"][inner], G.EToF[inner])
+    np.testing.assert_array_equal(g["bc"][G.boundary], 0)
+    np.testing.assert_allclose(S.node_coords(), G.x, atol=1e-15)
+
+
+def test_stable_dt_matches_oracle():
+    from oracle.euler_dg import Gas, Solver
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1)
+    S = B.Solver(3)
+    S.upload_mesh(xyz, EToV)
+    G = Geometry(ReferenceElement(3), xyz, EToV)
+    q = W.gaussian_pulse_state(G.x, W.GAMMA, W.RHO0_SI, W.P0_SI, 0.1, 0.3)
+    O = Solver(G, Gas(W.GAMMA, W.RHO0_SI, W.P0_SI))
+    assert S.stable_dt(q, 0.5) == pytest.approx(O.stable_dt(q, 0.5), rel=1e-12)
+    assert np.all(inscribed_radius(G) > 0)
+
+
+def test_periodic_vertex_classes_close_the_box():
+    xyz, EToV = W.kuhn_cube(3)
+    S = B.Solver(1)
+    S.upload_mesh(xyz, EToV, vert_class=W.periodic_vertex_classes(3))
+    assert np.all(S.geometry()["EToE"] >= 0)
+
+
+def test_mesh_errors():
+    xyz, EToV = W.kuhn_cube(2)
+    S = B.Solver(1)
+    bad = EToV.copy()
+    bad[3, [1, 2]] = bad[3, [2, 1]]                  # inverted element
+    with pytest.raises(B.DGError) as e:
+        S.upload_mesh(xyz, bad)
+    assert e.value.code == B.DG_ERR_MESH
+    dup = np.concatenate([EToV, EToV[:1]])           # a face shared by three elements
+    with pytest.raises(B.DGError) as e:
+        S.upload_mesh(xyz, dup)
+    assert e.value.code == B.DG_ERR_MESH
+    tags = np.full((EToV.shape[0], 4), -1, np.int8)  # boundary faces left untagged
+    with pytest.raises(B.DGError) as e:
+        S.upload_mesh(xyz, EToV, face_tag=tags)
+    assert e.value.code == B.DG_ERR_MESH
+    oob = EToV.copy()
+    oob[0, 0] = 10 ** 6
+    with pytest.raises(B.DGError):
+        S.upload_mesh(xyz, oob)
+    with pytest.raises(B.DGError):
+        S.set_bc(9, B.DG_BC_CHARACTERISTIC)
+    with pytest.raises(B.DGError):
+        S.set_bc(0, 17)
+
+
+def test_calls_out_of_order_fail_cleanly():
+    S = B.Solver(1)
+    with pytest.raises(B.DGError) as e:
+        S.step(1, 1e-3)
+    assert e.value.code == B.DG_ERR_ORDER
+    lib = B.load()
+    assert lib.dg_node_coords(S.h, None) == B.DG_ERR_ARG
+    assert lib.dg_destroy(None) == B.DG_OK
