@@ -65,6 +65,25 @@ def fp64_peak_gflops(sm_mhz=2070.0):
     return 152 * 4 * sm_mhz * 1e-3
 
 
+def profiled_traffic(summary, source):
+    """DRAM bytes per full-size launch from an ncu summary under profiles/, or
+    None when the kernel source changed after the counters were taken."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_1710_03887_gb300", "csrc", source), "rb").read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines()
+                  if line.startswith(("source_sha256_16:", "bytes_per_launch_full:")))
+    if fields.get("source_sha256_16", "").strip() != hashlib.sha256(src).hexdigest()[:16]:
+        return None
+    try:
+        return float(fields["bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -278,16 +297,7 @@ def run_gpu(args, rank, world):
     achieved = flops / avg_launch_s * 1e-9
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak = fp64_peak_gflops(2070.0)
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "stage_fp64_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                tr = json.load(f)
-            if tr.get("order") == w["order"]:
-                traffic = tr.get("bytes_per_launch_full")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = profiled_traffic("stage_fp64_p3_ball.md", "stage_fp64.cu")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
