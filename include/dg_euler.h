@@ -174,6 +174,33 @@ int dg_sync(dg_ctx* ctx);
 int dg_set_kernel_timing(dg_ctx* ctx, int enable);
 int dg_read_kernel_timing(dg_ctx* ctx, double* total_ms, int64_t* launches);
 
+/* Conserved totals that allocate nothing (no counterpart in the paper: this
+ * is a service for callers that cannot call cudaMalloc where they need the
+ * totals, e.g. code whose device memory is entirely owned by another
+ * allocator, or monitoring code inside a running time loop that must not
+ * allocate or free device memory).
+ *   out[v] = sum_e J[e] sum_i w[i] q[e][v][i],  v = 0..4
+ * q[K][5][Np], J[K], w[Np] (the mass-matrix column sums 1^T M of the
+ * reference element) and out[5] are device pointers supplied and owned by
+ * the caller; work is enqueued on `stream` (a cudaStream_t, NULL = default)
+ * and the call returns without waiting. The per-block partial sums live in
+ * one file-scope device array of DG_STATIC_TOTALS_MAX_BLOCKS x 5 doubles
+ * (160 KiB), which every GPU that loads the library keeps until the process
+ * exits. The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture. All calls share the array and it keeps the last
+ * call's contents (nothing in it needs to start at zero); calls on the same
+ * device that can overlap on the GPU (for instance on different streams)
+ * race on the array and must be serialised by the caller. Returns DG_ERR_ARG for a null pointer, K <= 0,
+ * K > DG_STATIC_TOTALS_MAX_ELEMENTS or Np outside 1..DG_STATIC_TOTALS_MAX_NP,
+ * before touching any memory. */
+#define DG_STATIC_TOTALS_MAX_BLOCKS 4096
+#define DG_STATIC_TOTALS_ELEMS_PER_BLOCK 4096
+#define DG_STATIC_TOTALS_MAX_ELEMENTS (4096LL * 4096LL)
+#define DG_STATIC_TOTALS_MAX_NP 35
+int dg_weighted_totals_static(const double* q, const double* J, const double* w,
+                              int64_t K, int Np, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

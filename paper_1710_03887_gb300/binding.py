@@ -62,6 +62,7 @@ _SIGS = {
     "dg_sync": (C.c_int, [_P]),
     "dg_set_kernel_timing": (C.c_int, [_P, C.c_int]),
     "dg_read_kernel_timing": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
+    "dg_weighted_totals_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, _P, _P]),
 }
 
 _lib = None
