@@ -100,11 +100,13 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index = index
+        self.index = index          # < 0: do not sample
         self.proc = None
         self.lines = []
 
     def __enter__(self):
+        if self.index < 0:
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
@@ -221,57 +223,51 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, rank, world):
+def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_clocks):
+    """Time one arithmetic form on the bench workload; returns a dict."""
     import torch
     from paper_1710_03887_gb300 import binding as B
     from paper_1710_03887_gb300 import workloads as W
-
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     w = WORKLOAD
-    xyz, EToV = build_workload()
-    S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI)
-    stream = torch.cuda.current_stream(dev)
+    prec = B.DG_PREC_F32 if precision == "f32" else B.DG_PREC_FP64
+    S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.set_stream(stream.cuda_stream)
     S.upload_mesh(xyz, EToV)
     nodes = S.node_coords()
     q0 = W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"], w["width"])
     dt = S.stable_dt(q0, w["cfl"])
-    K = S.K
-    Np = S.Np
-    dof = 5 * Np * K
+    dof = 5 * S.Np * S.K
     probes = np.array([[0.5 * np.cos(a), 0.5 * np.sin(a), 0.1] for a in np.linspace(0, 6, 32)])
     S.set_probes(probes, capacity=max(args.steps, 1))
     q0_dev = torch.from_numpy(q0).to(dev)
-    # -- device-resident timing
+    # device-resident timing
     S.set_state(q0_dev)
     S.step(args.warmup, dt)
     torch.cuda.synchronize(dev)
     S.read_probes()
+    S.set_state(q0_dev)
+    torch.cuda.synchronize(dev)
     S.set_kernel_timing(True)
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")) if sample_clocks else -1)
+    with clk:
         start.record(stream)
         S.step(args.steps, dt)
         stop.record(stream)
         torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    ms = start.elapsed_time(stop)
+    ms = reduce_max(start.elapsed_time(stop), dist, dev)
     kms, klaunch = S.read_kernel_timing()
     S.set_kernel_timing(False)
     S.sync()
-    ms = reduce_max(ms, dist, dev)
-    value = aggregate_value(world, dof, args.steps, ms * 1e-3)
-    # -- end to end through the C ABI with host buffers
+    q_end = torch.empty_like(q0_dev)
+    S.get_state(q_end)
+    # end to end through the C ABI with host buffers
     q0_host = torch.from_numpy(q0).pin_memory()
     q_out = torch.empty_like(q0_host).pin_memory()
     nprobe = probes.shape[0]
@@ -284,38 +280,102 @@ def run_gpu(args, rank, world):
     S.step(args.steps, dt)
     S.read_probes(args.steps, out=psamples)
     S.get_state(q_out)
-    t1 = time.perf_counter()
-    e2e_s = t1 - t0
-    e2e_s = reduce_max(e2e_s, dist, dev)
-    e2e = aggregate_value(world, dof, args.steps, e2e_s)
-    state_bytes = dof * 8
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    S.close()
+    return dict(precision=precision, ms=ms, kms=kms, klaunch=klaunch, dof=dof, K=len(EToV),
+                dt=dt, q0=q0, q_end=q_end.cpu().numpy(), e2e_s=e2e_s, nprobe=nprobe,
+                clocks=clk.summary() if sample_clocks else None,
+                value=aggregate_value(world, dof, args.steps, ms * 1e-3),
+                e2e=aggregate_value(world, dof, args.steps, e2e_s))
+
+
+def roofline_for(m, order):
+    """Roofline object of the stage kernel of one measured form."""
+    K = m["K"]
+    avg_launch_s = (m["kms"] * 1e-3) / max(m["klaunch"], 1)
+    if m["precision"] == "fp64":
+        achieved = stage_flops_per_element(order) * K / avg_launch_s * 1e-12
+        peak = fp64_peak_gflops(2070.0) * 1e-3
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": profiled_traffic("stage_fp64_p3_ball.md", "stage_fp64.cu"),
+                "kernel": "stage_fp64_kernel<3>",
+                "note": ("float64 pipe; peak = nominal 1.25 TFLOP/s = 152 SMs x 4 flop/clk x "
+                         "2070 MHz (recipe; ncu peak_sustained DFMA = 2/SM/clk)"),
+                "avg_launch_ms": avg_launch_s * 1e3, "launches": m["klaunch"]}
+    peaks = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_per_elem = stage_bytes_per_element(order, 4)
+    achieved = bytes_per_elem * K / avg_launch_s * 1e-9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm,
+            "traffic": profiled_traffic("stage_f32_p3_ball.md", "stage_f32.cu"),
+            "kernel": "stage_f32_kernel<3>",
+            "note": ("algorithmic bytes per stage: q, res read + q, res written (float32), "
+                     "geometry record 128 B, connections 16 B; peak = measured copy bandwidth "
+                     + ("(MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "(fallback)")),
+            "flops_frac_fp32": stage_flops_per_element(order) * K / avg_launch_s
+            / (152 * 256 * 2.07e9),
+            "avg_launch_ms": avg_launch_s * 1e3, "launches": m["klaunch"]}
+
+
+def stage_bytes_per_element(p, word):
+    """Algorithmic HBM bytes of one stage per element (word = 4 or 8 bytes)."""
+    Np = (p + 1) * (p + 2) * (p + 3) // 6
+    return 4 * 5 * Np * word + 32 * word + 16
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOAD
+    xyz, EToV = build_workload()
+    forms = [args.precision] + [f for f in ("f32", "fp64") if f != args.precision and not args.one_form]
+    res = {f: measure_form(args, f, xyz, EToV, dev, stream, dist, world, sample_clocks=(f == args.precision))
+           for f in forms}
     if rank != 0:
         return
-    clocks = clk.summary()
-    flops = stage_flops_per_element(w["order"]) * K
-    avg_launch_s = (kms * 1e-3) / max(klaunch, 1)
-    achieved = flops / avg_launch_s * 1e-9
-    sm_mhz = clocks["sm_mhz"] or 2070.0
-    peak = fp64_peak_gflops(2070.0)
-    traffic = profiled_traffic("stage_fp64_p3_ball.md", "stage_fp64.cu")
+    head = res[args.precision]
+    state_bytes = head["dof"] * 8
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "elements": K, "order": w["order"], "dof": dof,
-                   "dt": dt, "precision": "fp64", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (state 157 MB x 4 streams per stage); no flush"},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes / args.steps,
-                "d2h_bytes_per_step": (state_bytes + nprobe * 5 * 8 * args.steps) / args.steps},
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head["precision"], "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "elements": head["K"], "order": w["order"],
+                   "dof": head["dof"], "dt": head["dt"], "precision": head["precision"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": ("inputs larger than L2 (four state-sized streams per stage, "
+                          f"{state_bytes / (2 if head['precision'] == 'f32' else 1) / 1e6:.0f} MB each); no flush")},
+        "e2e": {"value": head["e2e"], "unit": UNIT, "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": (state_bytes + head["nprobe"] * 5 * 8 * args.steps) / args.steps},
         "gpu_launches": args.steps * 11,
-        "roofline": {"bound": "alu", "achieved": achieved * 1e-3, "peak": peak * 1e-3, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "stage_fp64_kernel<3>",
-                     "note": ("float64 pipe; peak = nominal 1.25 TFLOP/s = 152 SMs x 4 flop/clk "
-                              f"x 2070 MHz (recipe); median SM clock under load {sm_mhz} MHz"),
-                     "avg_launch_ms": avg_launch_s * 1e3, "launches": klaunch},
-        "clocks": clocks,
+        "roofline": roofline_for(head, w["order"]),
+        "clocks": head["clocks"],
     }
+    forms_out = {}
+    for f, m in res.items():
+        forms_out[f] = {"value": m["value"], "ms_per_step": m["ms"] / args.steps, "e2e": m["e2e"],
+                        "roofline": roofline_for(m, w["order"])}
+    if "f32" in res and "fp64" in res:
+        a, b = res["f32"], res["fp64"]
+        base = a["q0"].copy()
+        base[:, 0] = 1.225
+        base[:, 1:4] = 0.0
+        base[:, 4] = 101325.0 / 0.4
+        num = np.abs(a["q_end"] - b["q_end"]).max(axis=(0, 2))
+        den = np.abs(b["q_end"] - base).max(axis=(0, 2))
+        forms_out["f32_vs_fp64"] = {
+            "max_err_per_var_rel_to_perturbation": (num / den).tolist(),
+            "after_steps": args.steps,
+            "speedup": a["value"] / b["value"]}
+    line["forms"] = forms_out
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -330,6 +390,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="f32", choices=["f32", "fp64"],
+                    help="arithmetic form of the headline number (the other is measured beside it)")
+    ap.add_argument("--one-form", action="store_true", help="measure only --precision")
     ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],
                     help="lattice size of the ball (32 = the benchmark; smaller for profiling)")
     args = ap.parse_args()

@@ -64,6 +64,11 @@ extern "C" {
 
 /* Arithmetic of the time step (dg_params.precision) */
 #define DG_PREC_FP64 0          /* float64 state, fluxes and contractions               */
+#define DG_PREC_F32 1           /* float32 perturbation state q - q0 about the resting   */
+                                /* free stream (u0 must be 0); fluxes, contractions and  */
+                                /* update in float32; ghost states, geometry record and  */
+                                /* the ledger / totals accumulate in float64. The state  */
+                                /* still crosses the ABI as total float64 q[K][5][Np].   */
 
 /* Free-stream gas and defaults of a context. */
 typedef struct dg_params {

@@ -28,6 +28,7 @@ DG_BC_CHARACTERISTIC = 1
 DG_BC_SLIP_WALL = 2
 
 DG_PREC_FP64 = 0
+DG_PREC_F32 = 1
 
 
 class dg_params(C.Structure):

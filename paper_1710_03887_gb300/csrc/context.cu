@@ -48,9 +48,16 @@ struct dg_ctx {
   int ntiles = 0, nslots = 0, grid = 0, sms = 0;
   dgk::Gas gas{};
   // device buffers
+  int prec = DG_PREC_FP64;
   double* q[2] = {nullptr, nullptr};
   double* res = nullptr;
-  double* scratch = nullptr;       // state-sized, for dg_eval_rhs
+  double* scratch = nullptr;       // state-sized float64: dg_eval_rhs output / staging
+  // float32 perturbation form
+  float* q32[2] = {nullptr, nullptr};
+  float* res32 = nullptr;
+  float* scratch32 = nullptr;
+  float* geo32 = nullptr;
+  float* ops32 = nullptr;
   double* geo = nullptr;
   int32_t* conn = nullptr;
   double* ops = nullptr;
@@ -93,6 +100,7 @@ struct dg_ctx {
     dfree(q[0]); dfree(q[1]); dfree(res); dfree(scratch); dfree(geo); dfree(conn);
     dfree(ops); dfree(tbl); dfree(fmask); dfree(slot); dfree(ledger_part); dfree(ledger);
     dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
+    dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
     dev_ready = false;
     have_state = false;
     nprobe = 0;
@@ -117,16 +125,27 @@ int ensure_device(dg_ctx* c) {
   int dev = 0;
   DG_CUDA(cudaGetDevice(&dev));
   DG_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool f32 = c->prec == DG_PREC_F32;
   int bps = 0;
-  DG_CUDA(dgk::stage_prepare(p, &bps));
+  if (f32)
+    DG_CUDA(dgk::stage_f32_prepare(p, &bps));
+  else
+    DG_CUDA(dgk::stage_prepare(p, &bps));
   if (bps < 1) return c->fail(DG_ERR_CUDA, "stage kernel does not fit on an SM");
-  const int ET = dgk::stage_tile_elems(p);
+  const int ET = f32 ? dgk::stage_f32_tile_elems(p) : dgk::stage_tile_elems(p);
   c->ntiles = int((K + ET - 1) / ET);
   c->grid = std::min(c->ntiles, c->sms * bps);
   const size_t nq = c->state_elems();
-  DG_CUDA(cudaMalloc(&c->q[0], nq * 8));
-  DG_CUDA(cudaMalloc(&c->q[1], nq * 8));
-  DG_CUDA(cudaMalloc(&c->res, nq * 8));
+  if (f32) {
+    DG_CUDA(cudaMalloc(&c->q32[0], nq * 4));
+    DG_CUDA(cudaMalloc(&c->q32[1], nq * 4));
+    DG_CUDA(cudaMalloc(&c->res32, nq * 4));
+    DG_CUDA(cudaMalloc(&c->scratch32, nq * 4));
+  } else {
+    DG_CUDA(cudaMalloc(&c->q[0], nq * 8));
+    DG_CUDA(cudaMalloc(&c->q[1], nq * 8));
+    DG_CUDA(cudaMalloc(&c->res, nq * 8));
+  }
   DG_CUDA(cudaMalloc(&c->scratch, nq * 8));
   // geometry records
   std::vector<double> geo(size_t(K) * dgk::kGeoStride, 0.0);
@@ -142,6 +161,11 @@ int ensure_device(dg_ctx* c) {
   }
   DG_CUDA(cudaMalloc(&c->geo, geo.size() * 8));
   DG_CUDA(cudaMemcpy(c->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice));
+  if (f32) {
+    std::vector<float> g32(geo.begin(), geo.end());
+    DG_CUDA(cudaMalloc(&c->geo32, g32.size() * 4));
+    DG_CUDA(cudaMemcpy(c->geo32, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice));
+  }
   // face connection words and ledger slots of tiles that own boundary faces
   std::vector<int32_t> conn(size_t(K) * 4);
   std::vector<int32_t> slot(c->ntiles, -1);
@@ -180,6 +204,11 @@ int ensure_device(dg_ctx* c) {
   for (int m = 0; m < NF; ++m) ops[size_t(3) * Np * Np + size_t(NF) * Np + m] = c->ref.face_w[m];
   DG_CUDA(cudaMalloc(&c->ops, ops.size() * 8));
   DG_CUDA(cudaMemcpy(c->ops, ops.data(), ops.size() * 8, cudaMemcpyHostToDevice));
+  if (f32) {
+    std::vector<float> o32(ops.begin(), ops.end());
+    DG_CUDA(cudaMalloc(&c->ops32, o32.size() * 4));
+    DG_CUDA(cudaMemcpy(c->ops32, o32.data(), o32.size() * 4, cudaMemcpyHostToDevice));
+  }
   DG_CUDA(cudaMalloc(&c->tbl, c->ref.nbr_node.size()));
   DG_CUDA(cudaMemcpy(c->tbl, c->ref.nbr_node.data(), c->ref.nbr_node.size(),
                      cudaMemcpyHostToDevice));
@@ -217,6 +246,49 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
   A.dt = dt;
   A.gas = c->gas;
   return A;
+}
+
+// One Runge-Kutta stage from q[cur] to q[1-cur]; with to_scratch the residual
+// goes to the scratch buffer (used by dg_eval_rhs with a = b = 0, dt = 1).
+int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
+  if (c->prec == DG_PREC_F32) {
+    dgk::StageArgsF32 A{};
+    A.q_in = c->q32[c->cur];
+    A.q_out = c->q32[1 - c->cur];
+    A.res = to_scratch ? c->scratch32 : c->res32;
+    A.geo = c->geo32;
+    A.conn = c->conn;
+    A.ops = c->ops32;
+    A.nbr_tbl = c->tbl;
+    A.fmask = c->fmask;
+    A.ledger_slot = c->slot;
+    A.ledger_part = c->ledger_part;
+    A.status = c->status;
+    A.K = c->mesh.K;
+    A.ntiles = c->ntiles;
+    for (int i = 0; i < 8; ++i) A.bc_mode[i] = c->bc_mode[i];
+    A.a = float(a);
+    A.b = float(b);
+    A.dt = float(dt);
+    A.gas = c->gas;
+    DG_CUDA(dgk::launch_stage_f32(c->ref.p, A, c->grid, c->stream));
+  } else {
+    dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], to_scratch ? c->scratch : c->res,
+                                  a, b, dt);
+    DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+  }
+  return DG_OK;
+}
+
+// Total state (float64) of the current solution into the scratch buffer.
+int current_state_f64(dg_ctx* c, double* dst) {
+  if (c->prec == DG_PREC_F32)
+    DG_CUDA(dgk::launch_from_perturbation(c->q32[c->cur], dst, c->mesh.K, c->ref.Np, c->gas.rho0,
+                                          c->gas.E0, c->stream));
+  else if (dst != c->q[c->cur])
+    DG_CUDA(cudaMemcpyAsync(dst, c->q[c->cur], c->state_elems() * 8, cudaMemcpyDeviceToDevice,
+                            c->stream));
+  return DG_OK;
 }
 
 int check_status(dg_ctx* c) {
@@ -261,7 +333,10 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
   if (!params) return DG_ERR_ARG;
   if (!(params->gamma > 1.0) || !(params->rho0 > 0.0) || !(params->p0 > 0.0)) return DG_ERR_ARG;
   if (params->default_bc < 0 || params->default_bc > 2) return DG_ERR_ARG;
-  if (params->precision != DG_PREC_FP64) return DG_ERR_UNSUPPORTED;
+  if (params->precision != DG_PREC_FP64 && params->precision != DG_PREC_F32) return DG_ERR_UNSUPPORTED;
+  if (params->precision == DG_PREC_F32 &&
+      (params->u0[0] != 0.0 || params->u0[1] != 0.0 || params->u0[2] != 0.0))
+    return DG_ERR_UNSUPPORTED;   // the perturbation form is built around a resting base state
   if (order < 1 || order > dg::kMaxOrder) return DG_ERR_UNSUPPORTED;
   dg_ctx* c = new (std::nothrow) dg_ctx();
   if (!c) return DG_ERR_ARG;
@@ -271,6 +346,7 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
     return DG_ERR_ARG;
   }
   c->prm = *params;
+  c->prec = params->precision;
   for (int i = 0; i < 8; ++i) c->bc_mode[i] = params->default_bc;
   dgk::Gas& g = c->gas;
   g.gamma = params->gamma;
@@ -421,7 +497,13 @@ int dg_set_state(dg_ctx* c, const double* q, double t) {
   if (!c || !q) return DG_ERR_ARG;
   int rc = ensure_device(c);
   if (rc) return rc;
-  DG_CUDA(cudaMemcpyAsync(c->q[c->cur], q, c->state_elems() * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->prec == DG_PREC_F32) {
+    DG_CUDA(cudaMemcpyAsync(c->scratch, q, c->state_elems() * 8, cudaMemcpyHostToDevice, c->stream));
+    DG_CUDA(dgk::launch_to_perturbation(c->scratch, c->q32[c->cur], c->mesh.K, c->ref.Np,
+                                        c->gas.rho0, c->gas.E0, c->stream));
+  } else {
+    DG_CUDA(cudaMemcpyAsync(c->q[c->cur], q, c->state_elems() * 8, cudaMemcpyHostToDevice, c->stream));
+  }
   return reset_run(c, t);
 }
 
@@ -429,14 +511,24 @@ int dg_set_state_device(dg_ctx* c, const double* dq, double t) {
   if (!c || !dq) return DG_ERR_ARG;
   int rc = ensure_device(c);
   if (rc) return rc;
-  DG_CUDA(cudaMemcpyAsync(c->q[c->cur], dq, c->state_elems() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->prec == DG_PREC_F32)
+    DG_CUDA(dgk::launch_to_perturbation(dq, c->q32[c->cur], c->mesh.K, c->ref.Np, c->gas.rho0,
+                                        c->gas.E0, c->stream));
+  else
+    DG_CUDA(cudaMemcpyAsync(c->q[c->cur], dq, c->state_elems() * 8, cudaMemcpyDeviceToDevice, c->stream));
   return reset_run(c, t);
 }
 
 int dg_get_state(dg_ctx* c, double* q, double* t) {
   if (!c || !q) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
-  DG_CUDA(cudaMemcpyAsync(q, c->q[c->cur], c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
+  const double* src = c->q[c->cur];
+  if (c->prec == DG_PREC_F32) {
+    int rc = current_state_f64(c, c->scratch);
+    if (rc) return rc;
+    src = c->scratch;
+  }
+  DG_CUDA(cudaMemcpyAsync(q, src, c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
   if (t) *t = c->t;
   return check_status(c);
 }
@@ -444,7 +536,8 @@ int dg_get_state(dg_ctx* c, double* q, double* t) {
 int dg_get_state_device(dg_ctx* c, double* dq, double* t) {
   if (!c || !dq) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
-  DG_CUDA(cudaMemcpyAsync(dq, c->q[c->cur], c->state_elems() * 8, cudaMemcpyDeviceToDevice, c->stream));
+  int rc = current_state_f64(c, dq);
+  if (rc) return rc;
   if (t) *t = c->t;
   return DG_OK;
 }
@@ -455,10 +548,10 @@ int dg_step(dg_ctx* c, int n, double dt) {
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   for (int s = 0; s < n; ++s) {
     for (int k = 0; k < 5; ++k) {
-      dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], c->res, kRkA[k], kRkB[k], dt);
       int rc = record_event(c);
       if (rc) return rc;
-      DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+      rc = run_stage(c, false, kRkA[k], kRkB[k], dt);
+      if (rc) return rc;
       rc = record_event(c);
       if (rc) return rc;
       DG_CUDA(dgk::launch_ledger_update(c->ledger_part, c->nslots, c->ledger, kRkA[k], kRkB[k], dt,
@@ -468,8 +561,13 @@ int dg_step(dg_ctx* c, int n, double dt) {
     c->t += dt;
     if (c->nprobe > 0) {
       const int slotp = int(c->precorded % c->pcap);
-      DG_CUDA(dgk::launch_probe_sample(c->q[c->cur], c->ref.Np, c->nprobe, c->pelem, c->prow,
-                                       c->pring + size_t(slotp) * c->nprobe * 5, c->stream));
+      double* dst = c->pring + size_t(slotp) * c->nprobe * 5;
+      if (c->prec == DG_PREC_F32)
+        DG_CUDA(dgk::launch_probe_sample_f32(c->q32[c->cur], c->ref.Np, c->nprobe, c->pelem, c->prow,
+                                             c->gas.rho0, c->gas.E0, dst, c->stream));
+      else
+        DG_CUDA(dgk::launch_probe_sample(c->q[c->cur], c->ref.Np, c->nprobe, c->pelem, c->prow, dst,
+                                         c->stream));
       ++c->precorded;
     }
   }
@@ -481,8 +579,10 @@ int dg_eval_rhs(dg_ctx* c, double* rhs) {
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   // one stage with a = b = 0, dt = 1 writes f(q) into the scratch residual;
   // the ledger slots it touches are rewritten by the next real stage
-  dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], c->scratch, 0.0, 0.0, 1.0);
-  DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+  int rc = run_stage(c, true, 0.0, 0.0, 1.0);
+  if (rc) return rc;
+  if (c->prec == DG_PREC_F32)
+    DG_CUDA(dgk::launch_widen(c->scratch32, c->scratch, int64_t(c->state_elems()), c->stream));
   DG_CUDA(cudaMemcpyAsync(rhs, c->scratch, c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
   return check_status(c);
 }
@@ -572,7 +672,13 @@ int dg_read_boundary_flux(dg_ctx* c, double out[5]) {
 int dg_conserved_totals(dg_ctx* c, double out[5]) {
   if (!c || !out) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
-  DG_CUDA(dgk::launch_totals(c->q[c->cur], c->geo, c->mass_w, c->mesh.K, c->ref.Np, c->totals_part,
+  const double* src = c->q[c->cur];
+  if (c->prec == DG_PREC_F32) {
+    int rc = current_state_f64(c, c->scratch);
+    if (rc) return rc;
+    src = c->scratch;
+  }
+  DG_CUDA(dgk::launch_totals(src, c->geo, c->mass_w, c->mesh.K, c->ref.Np, c->totals_part,
                              kTotalsBlocks, c->totals_part + size_t(kTotalsBlocks) * 5, c->stream));
   int rc = check_status(c);
   if (rc) return rc;

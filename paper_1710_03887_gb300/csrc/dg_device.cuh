@@ -45,6 +45,38 @@ struct StageArgs {
   Gas gas;
 };
 
+// Float32 perturbation-form stage (stage_f32.cu)
+struct StageArgsF32 {
+  const float* q_in;         // q' = q - q0, [K][5][Np]
+  float* q_out;
+  float* res;
+  const float* geo;          // [K][kGeoStride] float32 copy of the geometry record
+  const int32_t* conn;
+  const float* ops;          // same packing as StageArgs::ops, float32
+  const uint8_t* nbr_tbl;
+  const int32_t* fmask;
+  const int32_t* ledger_slot;
+  double* ledger_part;
+  int* status;
+  int64_t K;
+  int ntiles;
+  int bc_mode[8];
+  float a, b, dt;
+  Gas gas;
+};
+
+int stage_f32_tile_elems(int p);
+cudaError_t stage_f32_prepare(int p, int* blocks_per_sm);
+cudaError_t launch_stage_f32(int p, const StageArgsF32& a, int grid, cudaStream_t s);
+cudaError_t launch_to_perturbation(const double* q, float* qp, int64_t K, int Np, double rho0,
+                                   double E0, cudaStream_t s);
+cudaError_t launch_from_perturbation(const float* qp, double* q, int64_t K, int Np, double rho0,
+                                     double E0, cudaStream_t s);
+cudaError_t launch_widen(const float* x, double* y, int64_t n, cudaStream_t s);
+cudaError_t launch_probe_sample_f32(const float* q, int Np, int n, const int32_t* elem,
+                                    const double* rows, double rho0, double E0, double* out,
+                                    cudaStream_t s);
+
 // launch helpers (stage_fp64.cu)
 int stage_tile_elems(int p);
 size_t stage_smem_bytes(int p);

@@ -1,0 +1,122 @@
+"""Float32 perturbation form (DG_PREC_F32) against the float64 oracle (GPU).
+
+Tolerances come from float32 arithmetic (unit roundoff u = 6e-8):
+* one right-hand side: every term is formed with a relative error of a few u
+  of the flux magnitude, and the Np-term contractions with entries up to
+  ~(p+1)^2 lose at most ~2 decimal digits to cancellation for the smooth
+  fields used here, so per variable max|f32 - oracle| <= 2e-5 max|oracle|;
+* a run: the error is measured on the perturbation q - q0 (the quantity the
+  form stores) relative to its own maximum; each stage adds ~dt |rhs| 1e-5,
+  so 100 steps stay below 2e-4.
+"""
+import numpy as np
+import pytest
+
+from paper_1710_03887_gb300 import workloads as W
+
+from ._cases import CHARACTERISTIC, FREESTREAM, SI, SLIP_WALL, Case, direction_tags, rel_err
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 2e-5
+RUN_TOL = 2e-4
+
+
+def f32_library(case):
+    from paper_1710_03887_gb300 import binding as B
+    S = B.Solver(case.p, precision=B.DG_PREC_F32, **case.gas_kw)
+    S.upload_mesh(case.xyz, case.EToV, face_tag=case.tags)
+    for ident, mode in case.modes.items():
+        S.set_bc(ident, mode)
+    return S
+
+
+def perturbation_err(qg, qo, q0):
+    num = np.abs(qg - qo).max(axis=(0, 2))
+    den = np.abs(qo - q0).max(axis=(0, 2))
+    return num / np.where(den > 0, den, 1.0)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_f32_rhs_matches_oracle(cuda_device, p):
+    xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=p)
+    probe = Case(p, xyz, EToV)
+    tags = direction_tags(xyz, EToV, probe.geom)
+    case = Case(p, xyz, EToV, tags=tags, modes={0: CHARACTERISTIC, 1: FREESTREAM, 2: SLIP_WALL})
+    q = case.smooth(0.05, seed=p)
+    ref = case.oracle.rhs(q)
+    S = f32_library(case)
+    S.set_state(q)
+    err = rel_err(S.eval_rhs(), ref)
+    assert np.all(err < RHS_TOL), err
+
+
+def test_f32_c1_pulse_run(cuda_device):
+    xyz, EToV = W.kuhn_cube(6)
+    case = Case(1, xyz, EToV)
+    q0 = case.pulse(0.005, 0.15)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    qo, _, ledger_o, _ = case.oracle.run(q0, dt, 100)
+    S = f32_library(case)
+    S.set_state(q0)
+    S.step(100, dt)
+    qg, _ = S.get_state()
+    base = q0.copy()
+    base[:] = W.uniform_state(1, q0.shape[2], SI["rho0"], (0, 0, 0), SI["p0"], SI["gamma"])[0]
+    err = perturbation_err(qg, qo, base)
+    assert np.all(err[[0, 4]] < RUN_TOL), err
+    # momentum: relative to the largest momentum of the oracle run
+    assert np.all(err[1:4] < RUN_TOL), err
+    # the boundary-flux ledger integrates the same fluxes
+    led = S.boundary_flux()
+    scale = np.abs(ledger_o).max()
+    assert np.abs(led - ledger_o).max() <= 1e-3 * scale
+
+
+def test_f32_p3_pulse_and_balance(cuda_device):
+    xyz, EToV = W.kuhn_cube(4, jitter=0.1)
+    case = Case(3, xyz, EToV)
+    q0 = case.pulse(0.1, 0.3)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    qo, _, _, _ = case.oracle.run(q0, dt, 20)
+    S = f32_library(case)
+    S.set_state(q0)
+    tot0 = S.totals()
+    S.step(20, dt)
+    qg, _ = S.get_state()
+    base = W.uniform_state(q0.shape[0], q0.shape[2], SI["rho0"], (0, 0, 0), SI["p0"], SI["gamma"])
+    err = perturbation_err(qg, qo, base)
+    assert np.all(err < RUN_TOL), err
+    # totals(t) - totals(0) + ledger = 0 at float32 resolution of the perturbation
+    bal = S.totals() - tot0 + S.boundary_flux()
+    pert_tot = np.abs(case.oracle.totals(q0 - base)).max()
+    assert np.abs(bal).max() <= 1e-5 * pert_tot, bal
+
+
+def test_f32_full_size_ball_rhs_sample(cuda_device):
+    from oracle.euler_dg import Gas
+    from oracle.euler_dg import Solver as OSolver
+    from oracle.geometry import Geometry
+    from oracle.reference_element import ReferenceElement
+    from paper_1710_03887_gb300 import binding as B
+    xyz, EToV = W.ball(32, 1.0, jitter=0.1, seed=0)
+    S = B.Solver(3, precision=B.DG_PREC_F32, **SI)
+    S.upload_mesh(xyz, EToV)
+    q = W.gaussian_pulse_state(S.node_coords(), SI["gamma"], SI["rho0"], SI["p0"], 0.1, 0.15)
+    S.set_state(q)
+    rhs = S.eval_rhs()
+    g = S.geometry()
+    rng = np.random.default_rng(1)
+    sample = np.unique(np.concatenate([rng.choice(EToV.shape[0], 40, replace=False), [0]]))
+    patch = np.unique(np.concatenate([sample, g["EToE"][sample].ravel()]))
+    patch = patch[patch >= 0]
+    sx, sE = W.submesh(xyz, EToV, np.isin(np.arange(EToV.shape[0]), patch))
+    osol = OSolver(Geometry(ReferenceElement(3), sx, sE), Gas(SI["gamma"], SI["rho0"], SI["p0"]))
+    ro = osol.rhs(q[patch])
+    local = np.searchsorted(patch, sample)
+    # the pulse (w = 0.15) lives near the centre: compare against the global rhs scale
+    # (at rest the density rhs is exactly zero on both sides)
+    num = np.abs(rhs[sample] - ro[local]).max(axis=(0, 2))
+    den = np.abs(rhs).max(axis=(0, 2))
+    den = np.where(den > 0, den, 1.0)
+    assert np.all(num / den < RHS_TOL), num / den
