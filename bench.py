@@ -229,7 +229,7 @@ def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_cl
     from paper_1710_03887_gb300 import binding as B
     from paper_1710_03887_gb300 import workloads as W
     w = WORKLOAD
-    prec = B.DG_PREC_F32 if precision == "f32" else B.DG_PREC_FP64
+    prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC, "fp64": B.DG_PREC_FP64}[precision]
     S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.set_stream(stream.cuda_stream)
     S.upload_mesh(xyz, EToV)
@@ -309,8 +309,10 @@ def roofline_for(m, order):
     achieved = bytes_per_elem * K / avg_launch_s * 1e-9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm,
-            "traffic": profiled_traffic("stage_f32_p3_ball.md", "stage_f32.cu"),
-            "kernel": "stage_f32_kernel<3>",
+            "traffic": (profiled_traffic("stage_tc_p3_ball.md", "stage_tc.cu")
+                        if m["precision"] == "f32_tc"
+                        else profiled_traffic("stage_f32_p3_ball.md", "stage_f32.cu")),
+            "kernel": "stage_tc_kernel<3>" if m["precision"] == "f32_tc" else "stage_f32_kernel<3>",
             "note": ("algorithmic bytes per stage: q, res read + q, res written (float32), "
                      "geometry record 128 B, connections 16 B; peak = measured copy bandwidth "
                      + ("(MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "(fallback)")),
@@ -337,7 +339,8 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     w = WORKLOAD
     xyz, EToV = build_workload()
-    forms = [args.precision] + [f for f in ("f32", "fp64") if f != args.precision and not args.one_form]
+    forms = [args.precision] + [f for f in ("f32_tc", "f32", "fp64")
+                                if f != args.precision and not args.one_form]
     res = {f: measure_form(args, f, xyz, EToV, dev, stream, dist, world, sample_clocks=(f == args.precision))
            for f in forms}
     if rank != 0:
@@ -363,18 +366,18 @@ def run_gpu(args, rank, world):
     for f, m in res.items():
         forms_out[f] = {"value": m["value"], "ms_per_step": m["ms"] / args.steps, "e2e": m["e2e"],
                         "roofline": roofline_for(m, w["order"])}
-    if "f32" in res and "fp64" in res:
-        a, b = res["f32"], res["fp64"]
-        base = a["q0"].copy()
-        base[:, 0] = 1.225
-        base[:, 1:4] = 0.0
-        base[:, 4] = 101325.0 / 0.4
-        num = np.abs(a["q_end"] - b["q_end"]).max(axis=(0, 2))
-        den = np.abs(b["q_end"] - base).max(axis=(0, 2))
-        forms_out["f32_vs_fp64"] = {
-            "max_err_per_var_rel_to_perturbation": (num / den).tolist(),
-            "after_steps": args.steps,
-            "speedup": a["value"] / b["value"]}
+    from paper_1710_03887_gb300 import workloads as W
+    for f in ("f32", "f32_tc"):
+        if f in res and "fp64" in res:
+            a, b = res[f], res["fp64"]
+            base = W.uniform_state(a["q0"].shape[0], a["q0"].shape[2], W.RHO0_SI, (0, 0, 0),
+                                   W.P0_SI, W.GAMMA)
+            num = np.abs(a["q_end"] - b["q_end"]).max(axis=(0, 2))
+            den = np.abs(b["q_end"] - base).max(axis=(0, 2))
+            forms_out[f + "_vs_fp64"] = {
+                "max_err_per_var_rel_to_perturbation": (num / den).tolist(),
+                "after_steps": args.steps,
+                "speedup": a["value"] / b["value"]}
     line["forms"] = forms_out
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
@@ -390,7 +393,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="f32", choices=["f32", "fp64"],
+    ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64"],
                     help="arithmetic form of the headline number (the other is measured beside it)")
     ap.add_argument("--one-form", action="store_true", help="measure only --precision")
     ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],

@@ -56,6 +56,7 @@ extern "C" {
 #define DG_ERR_ORDER (-4)       /* call out of order (e.g. step before state)    */
 #define DG_ERR_NONFINITE (-5)   /* device saw a non-finite or non-physical state */
 #define DG_ERR_UNSUPPORTED (-6) /* order / mode not built into this library      */
+#define DG_ERR_TIMEOUT (-7)     /* a bounded device wait gave up (kernel returned) */
 
 /* Boundary ghost rules (dg_set_bc) */
 #define DG_BC_FREESTREAM 0      /* ghost = free-stream state (section 2.2, Eq. 3)       */
@@ -69,6 +70,10 @@ extern "C" {
                                 /* update in float32; ghost states, geometry record and  */
                                 /* the ledger / totals accumulate in float64. The state  */
                                 /* still crosses the ABI as total float64 q[K][5][Np].   */
+#define DG_PREC_F32_TC 2        /* DG_PREC_F32 with both contractions (volume and LIFT,  */
+                                /* Eq. 10) as one tcgen05 tensor-core GEMM per tile of   */
+                                /* 25 elements, tf32 operands split in head + tail,      */
+                                /* float32 accumulation; orders 1..3                     */
 
 /* Free-stream gas and defaults of a context. */
 typedef struct dg_params {

@@ -22,6 +22,7 @@ DG_ERR_CUDA = -3
 DG_ERR_ORDER = -4
 DG_ERR_NONFINITE = -5
 DG_ERR_UNSUPPORTED = -6
+DG_ERR_TIMEOUT = -7
 
 DG_BC_FREESTREAM = 0
 DG_BC_CHARACTERISTIC = 1
@@ -29,6 +30,7 @@ DG_BC_SLIP_WALL = 2
 
 DG_PREC_FP64 = 0
 DG_PREC_F32 = 1
+DG_PREC_F32_TC = 2
 
 
 class dg_params(C.Structure):

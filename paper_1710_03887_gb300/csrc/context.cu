@@ -125,14 +125,18 @@ int ensure_device(dg_ctx* c) {
   int dev = 0;
   DG_CUDA(cudaGetDevice(&dev));
   DG_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
-  const bool f32 = c->prec == DG_PREC_F32;
+  const bool f32 = c->prec != DG_PREC_FP64;
+  const bool tcf = c->prec == DG_PREC_F32_TC;
   int bps = 0;
-  if (f32)
+  if (tcf)
+    DG_CUDA(dgk::stage_tc_prepare(p, &bps));
+  else if (f32)
     DG_CUDA(dgk::stage_f32_prepare(p, &bps));
   else
     DG_CUDA(dgk::stage_prepare(p, &bps));
   if (bps < 1) return c->fail(DG_ERR_CUDA, "stage kernel does not fit on an SM");
-  const int ET = f32 ? dgk::stage_f32_tile_elems(p) : dgk::stage_tile_elems(p);
+  const int ET = tcf ? dgk::stage_tc_tile_elems(p)
+                     : (f32 ? dgk::stage_f32_tile_elems(p) : dgk::stage_tile_elems(p));
   c->ntiles = int((K + ET - 1) / ET);
   c->grid = std::min(c->ntiles, c->sms * bps);
   const size_t nq = c->state_elems();
@@ -204,7 +208,14 @@ int ensure_device(dg_ctx* c) {
   for (int m = 0; m < NF; ++m) ops[size_t(3) * Np * Np + size_t(NF) * Np + m] = c->ref.face_w[m];
   DG_CUDA(cudaMalloc(&c->ops, ops.size() * 8));
   DG_CUDA(cudaMemcpy(c->ops, ops.data(), ops.size() * 8, cudaMemcpyHostToDevice));
-  if (f32) {
+  if (tcf) {
+    // operator matrix [-Dr | -Ds | -Dt | LIFT] as the tensor-core operand image
+    std::vector<unsigned char> img(dgk::stage_tc_ops_bytes(p));
+    dgk::build_tc_ops(p, c->ref.Dr.data(), c->ref.Ds.data(), c->ref.Dt.data(), c->ref.LIFT.data(),
+                      c->ref.face_w.data(), img.data());
+    DG_CUDA(cudaMalloc(&c->ops32, img.size()));
+    DG_CUDA(cudaMemcpy(c->ops32, img.data(), img.size(), cudaMemcpyHostToDevice));
+  } else if (f32) {
     std::vector<float> o32(ops.begin(), ops.end());
     DG_CUDA(cudaMalloc(&c->ops32, o32.size() * 4));
     DG_CUDA(cudaMemcpy(c->ops32, o32.data(), o32.size() * 4, cudaMemcpyHostToDevice));
@@ -251,7 +262,7 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
 // One Runge-Kutta stage from q[cur] to q[1-cur]; with to_scratch the residual
 // goes to the scratch buffer (used by dg_eval_rhs with a = b = 0, dt = 1).
 int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
-  if (c->prec == DG_PREC_F32) {
+  if (c->prec != DG_PREC_FP64) {
     dgk::StageArgsF32 A{};
     A.q_in = c->q32[c->cur];
     A.q_out = c->q32[1 - c->cur];
@@ -271,7 +282,10 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     A.b = float(b);
     A.dt = float(dt);
     A.gas = c->gas;
-    DG_CUDA(dgk::launch_stage_f32(c->ref.p, A, c->grid, c->stream));
+    if (c->prec == DG_PREC_F32_TC)
+      DG_CUDA(dgk::launch_stage_tc(c->ref.p, A, c->grid, c->stream));
+    else
+      DG_CUDA(dgk::launch_stage_f32(c->ref.p, A, c->grid, c->stream));
   } else {
     dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], to_scratch ? c->scratch : c->res,
                                   a, b, dt);
@@ -282,7 +296,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
 
 // Total state (float64) of the current solution into the scratch buffer.
 int current_state_f64(dg_ctx* c, double* dst) {
-  if (c->prec == DG_PREC_F32)
+  if (c->prec != DG_PREC_FP64)
     DG_CUDA(dgk::launch_from_perturbation(c->q32[c->cur], dst, c->mesh.K, c->ref.Np, c->gas.rho0,
                                           c->gas.E0, c->stream));
   else if (dst != c->q[c->cur])
@@ -297,6 +311,8 @@ int check_status(dg_ctx* c) {
   DG_CUDA(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st) {
     DG_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+    if (st & dgk::kStatusTimeout)
+      return c->fail(DG_ERR_TIMEOUT, "a bounded wait for tensor-core completion gave up");
     return c->fail(DG_ERR_NONFINITE, "device saw a non-finite or non-physical state "
                                      "(density or pressure <= 0)");
   }
@@ -333,8 +349,11 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
   if (!params) return DG_ERR_ARG;
   if (!(params->gamma > 1.0) || !(params->rho0 > 0.0) || !(params->p0 > 0.0)) return DG_ERR_ARG;
   if (params->default_bc < 0 || params->default_bc > 2) return DG_ERR_ARG;
-  if (params->precision != DG_PREC_FP64 && params->precision != DG_PREC_F32) return DG_ERR_UNSUPPORTED;
-  if (params->precision == DG_PREC_F32 &&
+  if (params->precision != DG_PREC_FP64 && params->precision != DG_PREC_F32 &&
+      params->precision != DG_PREC_F32_TC)
+    return DG_ERR_UNSUPPORTED;
+  if (params->precision == DG_PREC_F32_TC && order > 3) return DG_ERR_UNSUPPORTED;
+  if (params->precision != DG_PREC_FP64 &&
       (params->u0[0] != 0.0 || params->u0[1] != 0.0 || params->u0[2] != 0.0))
     return DG_ERR_UNSUPPORTED;   // the perturbation form is built around a resting base state
   if (order < 1 || order > dg::kMaxOrder) return DG_ERR_UNSUPPORTED;
@@ -497,7 +516,7 @@ int dg_set_state(dg_ctx* c, const double* q, double t) {
   if (!c || !q) return DG_ERR_ARG;
   int rc = ensure_device(c);
   if (rc) return rc;
-  if (c->prec == DG_PREC_F32) {
+  if (c->prec != DG_PREC_FP64) {
     DG_CUDA(cudaMemcpyAsync(c->scratch, q, c->state_elems() * 8, cudaMemcpyHostToDevice, c->stream));
     DG_CUDA(dgk::launch_to_perturbation(c->scratch, c->q32[c->cur], c->mesh.K, c->ref.Np,
                                         c->gas.rho0, c->gas.E0, c->stream));
@@ -511,7 +530,7 @@ int dg_set_state_device(dg_ctx* c, const double* dq, double t) {
   if (!c || !dq) return DG_ERR_ARG;
   int rc = ensure_device(c);
   if (rc) return rc;
-  if (c->prec == DG_PREC_F32)
+  if (c->prec != DG_PREC_FP64)
     DG_CUDA(dgk::launch_to_perturbation(dq, c->q32[c->cur], c->mesh.K, c->ref.Np, c->gas.rho0,
                                         c->gas.E0, c->stream));
   else
@@ -523,7 +542,7 @@ int dg_get_state(dg_ctx* c, double* q, double* t) {
   if (!c || !q) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   const double* src = c->q[c->cur];
-  if (c->prec == DG_PREC_F32) {
+  if (c->prec != DG_PREC_FP64) {
     int rc = current_state_f64(c, c->scratch);
     if (rc) return rc;
     src = c->scratch;
@@ -562,7 +581,7 @@ int dg_step(dg_ctx* c, int n, double dt) {
     if (c->nprobe > 0) {
       const int slotp = int(c->precorded % c->pcap);
       double* dst = c->pring + size_t(slotp) * c->nprobe * 5;
-      if (c->prec == DG_PREC_F32)
+      if (c->prec != DG_PREC_FP64)
         DG_CUDA(dgk::launch_probe_sample_f32(c->q32[c->cur], c->ref.Np, c->nprobe, c->pelem, c->prow,
                                              c->gas.rho0, c->gas.E0, dst, c->stream));
       else
@@ -581,7 +600,7 @@ int dg_eval_rhs(dg_ctx* c, double* rhs) {
   // the ledger slots it touches are rewritten by the next real stage
   int rc = run_stage(c, true, 0.0, 0.0, 1.0);
   if (rc) return rc;
-  if (c->prec == DG_PREC_F32)
+  if (c->prec != DG_PREC_FP64)
     DG_CUDA(dgk::launch_widen(c->scratch32, c->scratch, int64_t(c->state_elems()), c->stream));
   DG_CUDA(cudaMemcpyAsync(rhs, c->scratch, c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
   return check_status(c);
@@ -673,7 +692,7 @@ int dg_conserved_totals(dg_ctx* c, double out[5]) {
   if (!c || !out) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   const double* src = c->q[c->cur];
-  if (c->prec == DG_PREC_F32) {
+  if (c->prec != DG_PREC_FP64) {
     int rc = current_state_f64(c, c->scratch);
     if (rc) return rc;
     src = c->scratch;

@@ -15,6 +15,7 @@ constexpr int kGeoJ = 29;       // 1: volume / (4/3)
 
 // status bits latched by the kernels
 constexpr int kStatusBadState = 1;
+constexpr int kStatusTimeout = 2;   // a bounded wait for tensor-core completion gave up
 
 // face connection word: >= 0: (neighbour element << 5) | (neighbour face << 3) | orientation;
 // < 0: boundary, id = -1 - word
@@ -76,6 +77,15 @@ cudaError_t launch_widen(const float* x, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_probe_sample_f32(const float* q, int Np, int n, const int32_t* elem,
                                     const double* rows, double rho0, double E0, double* out,
                                     cudaStream_t s);
+
+// Tensor-core form of the float32 stage (stage_tc.cu), orders 1..3; uses
+// StageArgsF32 with ops pointing at the image built by build_tc_ops.
+size_t stage_tc_ops_bytes(int p);
+int stage_tc_tile_elems(int p);
+void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
+                  const double* face_w, unsigned char* out);
+cudaError_t stage_tc_prepare(int p, int* blocks_per_sm);
+cudaError_t launch_stage_tc(int p, const StageArgsF32& a, int grid, cudaStream_t s);
 
 // launch helpers (stage_fp64.cu)
 int stage_tile_elems(int p);

@@ -1,0 +1,437 @@
+// Tensor-core form of the float32 perturbation stage (DG_PREC_F32_TC).
+//
+// Same arithmetic as stage_f32.cu up to the two contractions, which become
+// one dense GEMM per tile of 25 elements on the tcgen05 tensor cores:
+//
+//   rhs[(e,v), i] = sum_k A[(e,v), k] B[i, k]
+//   A[(e,v), :] = [ Fr'_v(e, 0..Np) | Fs'_v | Ft'_v | dF_v(e, 0..4Nfp) ]     (M = 128 rows)
+//   B[i, :]     = [ -Dr[i, :] | -Ds[i, :] | -Dt[i, :] | LIFT[i, :] ]       (N = Np padded)
+//
+// i.e. the volume term and the surface lift of Eq. 10 in one contraction of
+// length K = 3 Np + 4 Nfp. Both operands are split into a tf32 head and a
+// tf32 tail (x = hi + lo) and the product is formed as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi in float32 accumulators in tensor memory,
+// which keeps float32-level accuracy (the dropped lo*lo term is ~2^-22).
+// The Runge-Kutta update runs in the epilogue straight out of tensor memory:
+// thread (warp w, lane l) owns row 32w + l = (element, variable) and updates
+// its Np contiguous values.
+#include <cmath>
+#include <cstring>
+
+#include "dg_device.cuh"
+#include "tc_ptx.cuh"
+
+namespace dgk {
+
+template <int P>
+struct OrderTC {
+  static constexpr int Np = (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int Nfp = (P + 1) * (P + 2) / 2;
+  static constexpr int NF = 4 * Nfp;
+  static constexpr int ET = 25;                        // 125 of the 128 MMA rows
+  static constexpr int M = 128;
+  static constexpr int N = Np <= 16 ? 16 : (Np + 15) / 16 * 16;
+  static constexpr int KU = 3 * Np + NF;               // used columns
+  static constexpr int K = (KU + 7) / 8 * 8;
+  static constexpr int NT = 512;
+  static constexpr uint32_t SBO = uint32_t(K / 4) * 128u;
+  static constexpr uint32_t kABytes = uint32_t(M / 8) * SBO;
+  static constexpr uint32_t kBBytes = uint32_t(N / 8) * SBO;
+  // shared memory (bytes): A_hi, A_lo, B_hi, B_lo, then the tile data
+  static constexpr size_t oAhi = 0;
+  static constexpr size_t oAlo = oAhi + kABytes;
+  static constexpr size_t oBhi = oAlo + kABytes;
+  static constexpr size_t oBlo = oBhi + kBBytes;
+  static constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+  static constexpr size_t oQ = oBlo + kBBytes;                             // ET*5*Np floats
+  static constexpr size_t oGeo = al16(oQ + size_t(ET) * 5 * Np * 4);      // ET*32 floats
+  static constexpr size_t oW = al16(oGeo + size_t(ET) * kGeoStride * 4);  // NF floats
+  static constexpr size_t oRed = (oW + size_t(NF) * 4 + 15) / 16 * 16;   // 16 warps x 5 doubles
+  static constexpr size_t oConn = oRed + 16 * 5 * 8;                 // ET*4 ints
+  static constexpr size_t oFmask = oConn + size_t(ET) * 16;          // 4*Nfp ints
+  static constexpr size_t oTbl = oFmask + size_t(NF) * 4;            // 96*Nfp bytes
+  static constexpr size_t oBar = (oTbl + 96 * Nfp + 15) / 16 * 16;   // mbarrier, tmem slot, flag
+  static constexpr size_t bytes = oBar + 32;
+  static constexpr size_t kOpsBytes = 2 * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
+};
+
+struct BaseF2 {
+  float rho0, p0, gamma, gm1, H0, c0;
+};
+
+__device__ __forceinline__ void prim_tc(const float q[5], const BaseF2& b, float& rinv, float u[3],
+                                        float& pp) {
+  rinv = 1.0f / (b.rho0 + q[0]);
+  u[0] = q[1] * rinv;
+  u[1] = q[2] * rinv;
+  u[2] = q[3] * rinv;
+  pp = b.gm1 * (q[4] - 0.5f * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+}
+
+__device__ __forceinline__ void normal_flux_tc(const float q[5], const float n[3], const BaseF2& b,
+                                               float fn[5], float& lam) {
+  float rinv, u[3], pp;
+  prim_tc(q, b, rinv, u, pp);
+  const float un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  fn[0] = q[1] * n[0] + q[2] * n[1] + q[3] * n[2];
+  fn[1] = q[1] * un + pp * n[0];
+  fn[2] = q[2] * un + pp * n[1];
+  fn[3] = q[3] * un + pp * n[2];
+  fn[4] = un * (b.H0 + q[4] + pp);
+  lam = fabsf(un) + sqrtf(b.gamma * (b.p0 + pp) * rinv);
+}
+
+// Ghost state as a float32 perturbation (see ghost_state_f in stage_f32.cu
+// for the derivation of this cancellation-free form).
+__device__ __forceinline__ void ghost_tc(int mode, const float qm[5], const float n[3],
+                                         const BaseF2& g, float qp[5]) {
+  if (mode == 0) {
+    for (int v = 0; v < 5; ++v) qp[v] = 0.0f;
+    return;
+  }
+  if (mode == 2) {
+    const float mn = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
+    qp[0] = qm[0];
+    qp[1] = qm[1] - 2.0f * mn * n[0];
+    qp[2] = qm[2] - 2.0f * mn * n[1];
+    qp[3] = qm[3] - 2.0f * mn * n[2];
+    qp[4] = qm[4];
+    return;
+  }
+  const float rinv = 1.0f / (g.rho0 + qm[0]);
+  const float u[3] = {qm[1] * rinv, qm[2] * rinv, qm[3] * rinv};
+  const float pp = g.gm1 * (qm[4] - 0.5f * (qm[1] * u[0] + qm[2] * u[1] + qm[3] * u[2]));
+  const float un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  const float c = sqrtf(g.gamma * (g.p0 + pp) * rinv);
+  const float dc = g.gamma * (g.rho0 * pp - g.p0 * qm[0]) * rinv / (g.rho0 * (c + g.c0));
+  const float unb = 0.5f * un + dc / g.gm1;
+  const float dcb = 0.25f * g.gm1 * un + 0.5f * dc;
+  const float lcb = log1pf(dcb / g.c0);
+  float ls = 0.0f, ut[3] = {0.0f, 0.0f, 0.0f};
+  if (unb >= 0.0f) {
+    ls = log1pf(pp / g.p0) - g.gamma * log1pf(qm[0] / g.rho0);
+    for (int d = 0; d < 3; ++d) ut[d] = u[d] - un * n[d];
+  }
+  const float lrho = (2.0f * lcb - ls) / g.gm1;
+  const float drho = g.rho0 * expm1f(lrho);
+  const float dp = g.p0 * expm1f(lrho + 2.0f * lcb);
+  const float rhob = g.rho0 + drho;
+  float ub[3];
+  for (int d = 0; d < 3; ++d) ub[d] = ut[d] + unb * n[d];
+  qp[0] = drho;
+  qp[1] = rhob * ub[0];
+  qp[2] = rhob * ub[1];
+  qp[3] = rhob * ub[2];
+  qp[4] = dp / g.gm1 + 0.5f * rhob * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+}
+
+// Store x into the A operand (hi and lo tf32 parts) at (row, k).
+template <uint32_t SBO>
+__device__ __forceinline__ void put_split(unsigned char* ahi, unsigned char* alo, int row, int k,
+                                          float x) {
+  const uint32_t off = tc::kmajor_offset(row, k, SBO);
+  const float hi = tc::to_tf32(x);
+  *reinterpret_cast<float*>(ahi + off) = hi;
+  *reinterpret_cast<float*>(alo + off) = tc::to_tf32(x - hi);
+}
+
+constexpr uint32_t kWaitTries = 1u << 24;   // bounded MMA completion wait
+
+template <int P>
+__global__ void __launch_bounds__(OrderTC<P>::NT, 1)
+stage_tc_kernel(const StageArgsF32 A) {
+  using O = OrderTC<P>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* sAhi = smem + O::oAhi;
+  unsigned char* sAlo = smem + O::oAlo;
+  float* sQ = reinterpret_cast<float*>(smem + O::oQ);
+  float* sGeo = reinterpret_cast<float*>(smem + O::oGeo);
+  float* sW = reinterpret_cast<float*>(smem + O::oW);
+  double* sRed = reinterpret_cast<double*>(smem + O::oRed);
+  int32_t* sConn = reinterpret_cast<int32_t*>(smem + O::oConn);
+  int32_t* sFmask = reinterpret_cast<int32_t*>(smem + O::oFmask);
+  uint8_t* sTbl = smem + O::oTbl;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + O::oBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + O::oBar + 8);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(smem + O::oBar + 12);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // constant operand B (host-built images in the operand layout), face
+  // weights, tables; zero A once so its padding rows/columns stay finite
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.ops);
+    uint4* dst = reinterpret_cast<uint4*>(smem + O::oBhi);
+    for (int i = tid; i < int(2 * O::kBBytes / 16); i += NT) dst[i] = src[i];
+    const float* w = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(A.ops) +
+                                                    2 * O::kBBytes);
+    for (int i = tid; i < NF; i += NT) sW[i] = w[i];
+    uint4* a = reinterpret_cast<uint4*>(smem + O::oAhi);
+    for (int i = tid; i < int(2 * O::kABytes / 16); i += NT) a[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 96 * Nfp; i += NT) sTbl[i] = A.nbr_tbl[i];
+    for (int i = tid; i < NF; i += NT) sFmask[i] = A.fmask[i];
+  }
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *sAbort = 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, 32);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const BaseF2 b{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
+                 float(A.gas.E0 + A.gas.p0), float(A.gas.c0)};
+  constexpr uint32_t idesc = tc::idesc_tf32(O::M, O::N);
+  uint32_t phase = 0;
+
+  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    const int64_t e0 = int64_t(tile) * ET;
+    const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
+    tc::fence_before_sync();
+    __syncthreads();   // previous epilogue done with sQ and with tensor memory
+    if (*sAbort) break;
+    tc::fence_after_sync();
+    {
+      const int nq = nE * 5 * Np;
+      if constexpr ((5 * Np) % 4 == 0) {        // rows of 16-byte multiples: vector loads
+        const float4* gq = reinterpret_cast<const float4*>(A.q_in + e0 * 5 * Np);
+        float4* q4 = reinterpret_cast<float4*>(sQ);
+        for (int i = tid; i < nq / 4; i += NT) q4[i] = gq[i];
+      } else {
+        const float* gq = A.q_in + e0 * 5 * Np;
+        for (int i = tid; i < nq; i += NT) sQ[i] = gq[i];
+      }
+      const float4* gg = reinterpret_cast<const float4*>(A.geo + e0 * kGeoStride);
+      float4* g4 = reinterpret_cast<float4*>(sGeo);
+      for (int i = tid; i < nE * kGeoStride / 4; i += NT) g4[i] = gg[i];
+      const int32_t* gc = A.conn + e0 * 4;
+      for (int i = tid; i < nE * 4; i += NT) sConn[i] = gc[i];
+    }
+    __syncthreads();
+
+    // ---- volume: reference-direction fluxes into A columns [0, 3 Np)
+    for (int it = tid; it < nE * Np; it += NT) {
+      const int le = it / Np, n = it - (it / Np) * Np;
+      float q[5];
+      for (int v = 0; v < 5; ++v) q[v] = sQ[(le * 5 + v) * Np + n];
+      float rinv, u[3], pp;
+      prim_tc(q, b, rinv, u, pp);
+      if (!(b.rho0 + q[0] > 0.0f) || !(b.p0 + pp > 0.0f) || !isfinite(q[4]) || !isfinite(pp))
+        atomicOr(A.status, kStatusBadState);
+      const float H = b.H0 + q[4] + pp;
+      float F[3][5];
+      for (int d = 0; d < 3; ++d) {
+        F[d][0] = q[1 + d];
+        F[d][1] = q[1] * u[d];
+        F[d][2] = q[2] * u[d];
+        F[d][3] = q[3] * u[d];
+        F[d][1 + d] += pp;
+        F[d][4] = u[d] * H;
+      }
+      const float* dr = sGeo + le * kGeoStride + kGeoDrdx;
+      for (int a = 0; a < 3; ++a) {
+        const float m0 = dr[a * 3], m1 = dr[a * 3 + 1], m2 = dr[a * 3 + 2];
+        for (int v = 0; v < 5; ++v)
+          put_split<O::SBO>(sAhi, sAlo, le * 5 + v, a * Np + n,
+                            m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v]);
+      }
+    }
+
+    // ---- faces: jumps Fscale (n.F(q-) - F*) into A columns [3 Np, 3 Np + 4 Nfp)
+    float led[5] = {0, 0, 0, 0, 0};
+    bool any_bdry = false;
+    for (int it = tid; it < nE * NF; it += NT) {
+      const int le = it / NF, fm = it - (it / NF) * NF;
+      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+      const int n = sFmask[f * Nfp + m];
+      float qm[5], qp[5];
+      for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
+      const float* geo = sGeo + le * kGeoStride;
+      const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
+      const int32_t c = sConn[le * 4 + f];
+      if (c >= 0) {
+        const int64_t e2 = c >> 5;
+        const int f2 = (c >> 3) & 3, o = c & 7;
+        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+        const float* src = A.q_in + e2 * 5 * Np + n2;
+        for (int v = 0; v < 5; ++v) qp[v] = __ldg(src + v * Np);
+      } else {
+        ghost_tc(A.bc_mode[(-1 - c) & 7], qm, nv, b, qp);
+      }
+      float fnm[5], fnp[5], lm, lp;
+      normal_flux_tc(qm, nv, b, fnm, lm);
+      normal_flux_tc(qp, nv, b, fnp, lp);
+      const float lam = fmaxf(lm, lp);
+      const float fs = geo[kGeoFscale + f];
+      for (int v = 0; v < 5; ++v) {
+        const float jump = 0.5f * (fnm[v] - fnp[v]) + 0.5f * lam * (qp[v] - qm[v]);
+        put_split<O::SBO>(sAhi, sAlo, le * 5 + v, 3 * Np + fm, fs * jump);
+        if (c < 0) {
+          const float fstar = 0.5f * (fnm[v] + fnp[v]) - 0.5f * lam * (qp[v] - qm[v]);
+          led[v] += sW[fm] * geo[kGeoSJ + f] * fstar;
+        }
+      }
+      any_bdry |= (c < 0);
+    }
+    // operand writes become visible to the tensor cores
+    tc::fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ahi = tc::smem_addr(sAhi), alo = tc::smem_addr(sAlo);
+      const uint32_t bhi = tc::smem_addr(smem + O::oBhi), blo = tc::smem_addr(smem + O::oBlo);
+#pragma unroll 1
+      for (int s = 0; s < O::K / 8; ++s) {
+        const uint32_t off = 256u * s;
+        const uint64_t dAhi = tc::smem_desc(ahi + off, 128u, O::SBO);
+        const uint64_t dAlo = tc::smem_desc(alo + off, 128u, O::SBO);
+        const uint64_t dBhi = tc::smem_desc(bhi + off, 128u, O::SBO);
+        const uint64_t dBlo = tc::smem_desc(blo + off, 128u, O::SBO);
+        tc::mma_tf32(tmem, dAhi, dBhi, idesc, s > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, dAhi, dBlo, idesc, 1u);
+        tc::mma_tf32(tmem, dAlo, dBhi, idesc, 1u);
+      }
+      tc::mma_commit(mbar);
+    }
+    // boundary-flux ledger of this tile (overlaps the MMAs)
+    if (__syncthreads_or(any_bdry)) {
+      for (int v = 0; v < 5; ++v) {
+        float x = led[v];
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) sRed[warp * 5 + v] = double(x);
+      }
+      __syncthreads();
+      if (tid < 5) {
+        double acc = 0.0;
+        for (int w = 0; w < NT / 32; ++w) acc += sRed[w * 5 + tid];
+        const int slot = A.ledger_slot[tile];
+        if (slot >= 0) A.ledger_part[size_t(slot) * 5 + tid] = acc;
+      }
+    }
+
+    // ---- epilogue: rows of tensor memory -> Runge-Kutta update
+    if (warp < 4) {
+      const bool done = tc::mbar_wait(mbar, phase, kWaitTries);
+      if (!done) {
+        if (lane == 0) {
+          atomicOr(A.status, kStatusTimeout);
+          *sAbort = 1;
+        }
+      } else {
+        tc::fence_after_sync();
+        float d[32];
+        tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16), d);
+        const int row = 32 * warp + lane;
+        if (row < nE * 5) {
+          const int le = row / 5, v = row - (row / 5) * 5;
+          const int64_t base = ((e0 + le) * 5 + v) * Np;
+          const float* qs = sQ + (le * 5 + v) * Np;
+#pragma unroll
+          for (int j = 0; j < Np; ++j) {
+            const float r = (A.a != 0.0f) ? A.a * A.res[base + j] + A.dt * d[j] : A.dt * d[j];
+            A.res[base + j] = r;
+            A.q_out[base + j] = qs[j] + A.b * r;
+          }
+        }
+      }
+    }
+    phase ^= 1u;
+  }
+  // a wait that gave up may leave MMAs in flight: give them a bounded chance
+  // to finish before the tensor memory is released
+  if (*sAbort && tid == 0) tc::mbar_wait(mbar, phase, kWaitTries);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 32);
+  }
+}
+
+size_t stage_tc_ops_bytes(int p) {
+  switch (p) {
+    case 1: return OrderTC<1>::kOpsBytes;
+    case 2: return OrderTC<2>::kOpsBytes;
+    default: return OrderTC<3>::kOpsBytes;
+  }
+}
+
+int stage_tc_tile_elems(int) { return 25; }
+
+// Host-side image of B = [-Dr | -Ds | -Dt | LIFT] in the operand layout,
+// split into tf32 head and tail, followed by the face weights.
+template <int P>
+static void build_ops_impl(const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
+                           const double* face_w, unsigned char* out) {
+  using O = OrderTC<P>;
+  auto tf32 = [](float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;   // round to nearest, ties away from zero
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+  };
+  std::memset(out, 0, O::kOpsBytes);
+  float* hi = reinterpret_cast<float*>(out);
+  float* lo = reinterpret_cast<float*>(out + O::kBBytes);
+  for (int i = 0; i < O::Np; ++i)
+    for (int k = 0; k < O::KU; ++k) {
+      double v;
+      if (k < 3 * O::Np) {
+        const double* D = k < O::Np ? Dr : (k < 2 * O::Np ? Ds : Dt);
+        v = -D[i * O::Np + (k % O::Np)];
+      } else {
+        v = LIFT[i * O::NF + (k - 3 * O::Np)];
+      }
+      const float x = float(v);
+      const float h = tf32(x);
+      const uint32_t off = tc::kmajor_offset(i, k, O::SBO) / 4;
+      hi[off] = h;
+      lo[off] = tf32(x - h);
+    }
+  float* w = reinterpret_cast<float*>(out + 2 * O::kBBytes);
+  for (int m = 0; m < O::NF; ++m) w[m] = float(face_w[m]);
+}
+
+void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
+                  const double* face_w, unsigned char* out) {
+  switch (p) {
+    case 1: build_ops_impl<1>(Dr, Ds, Dt, LIFT, face_w, out); break;
+    case 2: build_ops_impl<2>(Dr, Ds, Dt, LIFT, face_w, out); break;
+    default: build_ops_impl<3>(Dr, Ds, Dt, LIFT, face_w, out); break;
+  }
+}
+
+template <int P>
+static cudaError_t prepare_tc_impl(int* bps) {
+  cudaError_t e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(OrderTC<P>::bytes));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, stage_tc_kernel<P>, OrderTC<P>::NT,
+                                                       OrderTC<P>::bytes);
+}
+
+cudaError_t stage_tc_prepare(int p, int* bps) {
+  switch (p) {
+    case 1: return prepare_tc_impl<1>(bps);
+    case 2: return prepare_tc_impl<2>(bps);
+    default: return prepare_tc_impl<3>(bps);
+  }
+}
+
+cudaError_t launch_stage_tc(int p, const StageArgsF32& a, int grid, cudaStream_t s) {
+  switch (p) {
+    case 1: stage_tc_kernel<1><<<grid, OrderTC<1>::NT, OrderTC<1>::bytes, s>>>(a); break;
+    case 2: stage_tc_kernel<2><<<grid, OrderTC<2>::NT, OrderTC<2>::bytes, s>>>(a); break;
+    default: stage_tc_kernel<3><<<grid, OrderTC<3>::NT, OrderTC<3>::bytes, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dgk

@@ -22,9 +22,17 @@ RHS_TOL = 2e-5
 RUN_TOL = 2e-4
 
 
-def f32_library(case):
+PRECS = ["f32", "f32_tc"]   # SIMT contractions / tcgen05 tensor-core contractions
+
+
+def prec_code(name):
     from paper_1710_03887_gb300 import binding as B
-    S = B.Solver(case.p, precision=B.DG_PREC_F32, **case.gas_kw)
+    return {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC}[name]
+
+
+def f32_library(case, prec="f32"):
+    from paper_1710_03887_gb300 import binding as B
+    S = B.Solver(case.p, precision=prec_code(prec), **case.gas_kw)
     S.upload_mesh(case.xyz, case.EToV, face_tag=case.tags)
     for ident, mode in case.modes.items():
         S.set_bc(ident, mode)
@@ -37,27 +45,31 @@ def perturbation_err(qg, qo, q0):
     return num / np.where(den > 0, den, 1.0)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_f32_rhs_matches_oracle(cuda_device, p):
+def test_f32_rhs_matches_oracle(cuda_device, p, prec):
+    if prec == "f32_tc" and p > 3:
+        pytest.skip("the tensor-core form covers orders 1..3")
     xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=p)
     probe = Case(p, xyz, EToV)
     tags = direction_tags(xyz, EToV, probe.geom)
     case = Case(p, xyz, EToV, tags=tags, modes={0: CHARACTERISTIC, 1: FREESTREAM, 2: SLIP_WALL})
     q = case.smooth(0.05, seed=p)
     ref = case.oracle.rhs(q)
-    S = f32_library(case)
+    S = f32_library(case, prec)
     S.set_state(q)
     err = rel_err(S.eval_rhs(), ref)
     assert np.all(err < RHS_TOL), err
 
 
-def test_f32_c1_pulse_run(cuda_device):
+@pytest.mark.parametrize("prec", PRECS)
+def test_f32_c1_pulse_run(cuda_device, prec):
     xyz, EToV = W.kuhn_cube(6)
     case = Case(1, xyz, EToV)
     q0 = case.pulse(0.005, 0.15)
     dt = case.oracle.stable_dt(q0, 0.5)
     qo, _, ledger_o, _ = case.oracle.run(q0, dt, 100)
-    S = f32_library(case)
+    S = f32_library(case, prec)
     S.set_state(q0)
     S.step(100, dt)
     qg, _ = S.get_state()
@@ -73,13 +85,14 @@ def test_f32_c1_pulse_run(cuda_device):
     assert np.abs(led - ledger_o).max() <= 1e-3 * scale
 
 
-def test_f32_p3_pulse_and_balance(cuda_device):
+@pytest.mark.parametrize("prec", PRECS)
+def test_f32_p3_pulse_and_balance(cuda_device, prec):
     xyz, EToV = W.kuhn_cube(4, jitter=0.1)
     case = Case(3, xyz, EToV)
     q0 = case.pulse(0.1, 0.3)
     dt = case.oracle.stable_dt(q0, 0.5)
     qo, _, _, _ = case.oracle.run(q0, dt, 20)
-    S = f32_library(case)
+    S = f32_library(case, prec)
     S.set_state(q0)
     tot0 = S.totals()
     S.step(20, dt)
@@ -93,14 +106,15 @@ def test_f32_p3_pulse_and_balance(cuda_device):
     assert np.abs(bal).max() <= 1e-5 * pert_tot, bal
 
 
-def test_f32_full_size_ball_rhs_sample(cuda_device):
+@pytest.mark.parametrize("prec", PRECS)
+def test_f32_full_size_ball_rhs_sample(cuda_device, prec):
     from oracle.euler_dg import Gas
     from oracle.euler_dg import Solver as OSolver
     from oracle.geometry import Geometry
     from oracle.reference_element import ReferenceElement
     from paper_1710_03887_gb300 import binding as B
     xyz, EToV = W.ball(32, 1.0, jitter=0.1, seed=0)
-    S = B.Solver(3, precision=B.DG_PREC_F32, **SI)
+    S = B.Solver(3, precision=prec_code(prec), **SI)
     S.upload_mesh(xyz, EToV)
     q = W.gaussian_pulse_state(S.node_coords(), SI["gamma"], SI["rho0"], SI["p0"], 0.1, 0.15)
     S.set_state(q)

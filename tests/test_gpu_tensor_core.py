@@ -1,0 +1,57 @@
+"""Unit probe of the tcgen05 building blocks (tc_ptx.cuh) on the GPU.
+
+One CTA multiplies a 128 x K by a K x N operand (tf32 in, float32 out)
+through the same descriptor layout the stage kernel uses; the product is
+checked against float64 host arithmetic on the same tf32-rounded inputs.
+"""
+import ctypes
+import subprocess
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = Path(__file__).resolve().parent.parent
+SRC = ROOT / "tests" / "cuda" / "tc_gemm_probe.cu"
+OUT = ROOT / "paper_1710_03887_gb300" / "_build" / "tc_gemm_probe.so"
+
+
+def tf32_round(x):
+    """Round float32 to tf32 (10 explicit mantissa bits), nearest, ties away from zero."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x1000) & 0xFFFFE000
+    return b.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def probe():
+    from paper_1710_03887_gb300 import build_lib
+    OUT.parent.mkdir(exist_ok=True)
+    if not OUT.exists() or OUT.stat().st_mtime < SRC.stat().st_mtime:
+        subprocess.run([build_lib._nvcc(), *build_lib.ARCH, "-O2", "-std=c++17", "-Xcompiler",
+                        "-fPIC", "-shared", "-o", str(OUT), str(SRC)], check=True)
+    lib = ctypes.CDLL(str(OUT))
+    lib.tc_gemm_probe.restype = ctypes.c_int
+    lib.tc_gemm_probe.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    return lib
+
+
+@pytest.mark.parametrize("N,K", [(16, 8), (32, 104), (16, 56), (32, 24)])
+def test_tf32_mma_matches_host(cuda_device, probe, N, K):
+    import torch
+    rng = np.random.default_rng(N * 1000 + K)
+    A = rng.normal(size=(128, K)).astype(np.float32)
+    B = rng.normal(size=(N, K)).astype(np.float32)
+    dA = torch.from_numpy(A).to(cuda_device)
+    dB = torch.from_numpy(B).to(cuda_device)
+    dD = torch.full((128, N), float("nan"), dtype=torch.float32, device=cuda_device)
+    st = torch.zeros(1, dtype=torch.int32, device=cuda_device)
+    rc = probe.tc_gemm_probe(dA.data_ptr(), dB.data_ptr(), dD.data_ptr(), N, K, st.data_ptr())
+    assert rc == 0
+    assert int(st.item()) == 0, "MMA completion wait timed out"
+    ref = tf32_round(A).astype(np.float64) @ tf32_round(B).astype(np.float64).T
+    got = dD.cpu().numpy()
+    scale = np.abs(tf32_round(A)).astype(np.float64) @ np.abs(tf32_round(B)).astype(np.float64).T
+    assert np.all(np.abs(got - ref) <= 1e-6 * scale + 1e-30), np.abs(got - ref).max()
