@@ -62,6 +62,10 @@ extern "C" {
 #define DG_BC_FREESTREAM 0      /* ghost = free-stream state (section 2.2, Eq. 3)       */
 #define DG_BC_CHARACTERISTIC 1  /* Riemann-invariant far-field ghost (default)          */
 #define DG_BC_SLIP_WALL 2       /* normal velocity mirrored (section 2.3, Eq. 4)        */
+#define DG_BC_LEARNED 3         /* characteristic ghost + learned correction (float32   */
+                                /* forms; see dg_set_bc_mlp); falls back to the          */
+                                /* characteristic ghost where the result is not finite   */
+                                /* or has rho <= 0 or p <= 0                             */
 
 /* Arithmetic of the time step (dg_params.precision) */
 #define DG_PREC_FP64 0          /* float64 state, fluxes and contractions               */
@@ -183,6 +187,50 @@ int dg_sync(dg_ctx* ctx);
  * resets both. Enabling/disabling discards pending records. */
 int dg_set_kernel_timing(dg_ctx* ctx, int enable);
 int dg_read_kernel_timing(dg_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* ------------------------------------------------------------------------
+ * Learned boundary closure. The paper's pass-through condition (section 2.2)
+ * and the characteristic ghost both assume what lies outside the truncation
+ * surface; this closure learns it from the method's own solution in a larger
+ * domain. A network 12 -> 64 -> 64 -> 5 (tanh, float32) maps the interior
+ * trace at an outer-face node to a correction of the characteristic ghost:
+ *   z(q) = (rho'/rho0, m'/(rho0 c0), E'/(rho0 c0^2))   (perturbation, 5 values)
+ *   s = max|z(q-)| + 1e-12,  features = (z(q-)/s, n, x/R, 10 p'/p0)
+ *   z(q+) = z(q+_characteristic) + s * network(features)
+ * Parameters (DG_MLP_NPARAMS floats, row-major, input index first):
+ *   W1[12][64], b1[64], W2[64][64], b2[64], W3[64][5], b3[5].
+ * Training minimises (1/N) sum |network(features) - target|^2 over samples
+ * recorded with dg_sample_traces, full batch, Adam (beta 0.9 / 0.999,
+ * eps 1e-8), on the GPU. All float32. */
+#define DG_MLP_NPARAMS 5317
+
+/* Mass matrix M[Np][Np] of the reference element (host only, no context). */
+int dg_reference_mass(int order, double* M);
+/* Set the network parameters (host array of DG_MLP_NPARAMS floats) and the
+ * position scale R; resets the optimiser state. Allocates on first use. */
+int dg_set_bc_mlp(dg_ctx* ctx, const float* w, double radius);
+/* Copy the current network parameters to host memory. */
+int dg_get_bc_mlp(dg_ctx* ctx, float* w);
+/* Interior faces at which dg_sample_traces records (float32 forms only):
+ * face face[i] (0..3) of element elem[i], whose element is the inside.
+ * DG_ERR_ARG for boundary faces or ids out of range. */
+int dg_set_trace_faces(dg_ctx* ctx, int64_t n, const int32_t* elem, const int8_t* face);
+/* Training pairs from the current state at every node of the trace faces:
+ * X[n*Nfp][12] features of the inner trace, Y[n*Nfp][5] target
+ * (z(outer trace) - z(characteristic ghost of the inner trace)) / s.
+ * X, Y: device float32 buffers (caller-owned); enqueued on the stream. */
+int dg_sample_traces(dg_ctx* ctx, float* X, float* Y);
+/* Loss and gradient of the current network on device samples X[N][12],
+ * Y[N][5] (deterministic fixed-order reductions); either output may be NULL
+ * (host, double loss, float gradient[DG_MLP_NPARAMS]). Synchronises. */
+int dg_mlp_loss_grad(dg_ctx* ctx, const float* X, const float* Y, int64_t N, double* loss,
+                     float* grad);
+/* `iters` full-batch Adam steps with learning rate lr on device samples;
+ * loss_history (host, nullable) receives the loss before each step. */
+int dg_mlp_train(dg_ctx* ctx, const float* X, const float* Y, int64_t N, int iters, double lr,
+                 double* loss_history);
+/* Network outputs out[N][5] (device) for features X[N][12] (device). */
+int dg_mlp_forward(dg_ctx* ctx, const float* X, int64_t N, float* out);
 
 /* Conserved totals that allocate nothing (no counterpart in the paper: this
  * is a service for callers that cannot call cudaMalloc where they need the

@@ -57,6 +57,7 @@ from .geometry import Geometry, inscribed_radius
 FREESTREAM = 0
 CHARACTERISTIC = 1
 SLIP_WALL = 2
+LEARNED = 3        # characteristic ghost + network correction (oracle/mlp.py)
 
 # Carpenter & Kennedy (1994), NASA TM-109112, five-stage 2N-storage RK4
 LSRK_A = [Fraction(0), Fraction(-567301805773, 1357537059087),
@@ -180,6 +181,63 @@ GHOSTS = {FREESTREAM: ghost_freestream, CHARACTERISTIC: ghost_characteristic,
           SLIP_WALL: ghost_slip_wall}
 
 
+LEARNED_KAPPA = 0.5
+
+
+def acoustic_invariants(qp, n, gas):
+    """(w_out, w_in) = p' +- rho0 c0 u.n of perturbation states qp[..., 5]."""
+    rho = gas.rho0 + qp[..., 0]
+    pp = (gas.gamma - 1.0) * (qp[..., 4] - 0.5 * np.sum(qp[..., 1:4] ** 2, axis=-1) / rho)
+    zun = gas.rho0 * gas.c0 * np.sum(qp[..., 1:4] * n, axis=-1) / rho
+    return pp + zun, pp - zun
+
+
+def learned_target(qm, qo, n, gas):
+    """Training target of the closure at a face node with inner trace qm and
+    outer trace qo (total states): the correction of the incoming acoustic
+    invariant over the characteristic ghost's, in units of rho0 c0^2 s."""
+    from . import mlp
+    q0 = gas.freestream()
+    qc = ghost_characteristic(qm, n, gas)
+    _, s = mlp.features(qm - q0, n, np.zeros_like(n), gas, 1.0)
+    _, wi_o = acoustic_invariants(qo - q0, n, gas)
+    _, wi_c = acoustic_invariants(qc - q0, n, gas)
+    y = np.zeros(qm.shape)
+    y[..., 0] = (wi_o - wi_c) / (gas.rho0 * gas.c0 ** 2 * s)
+    return y
+
+
+def ghost_learned(qm, n, x, gas, w, radius):
+    """Learned closure. At rest the local Lax-Friedrichs flux takes the
+    outgoing acoustic invariant w_out from inside and only the incoming one,
+    g, from the ghost (boundary energy flux c (w_out^2 - g^2)). The network's
+    output 0 corrects the characteristic ghost's incoming invariant (in units
+    of rho0 c0^2 s); the result is bounded by |g| <= 0.5 |w_out(inside)|; the
+    characteristic ghost is moved to that invariant at fixed outgoing
+    invariant (isentropic increments D/2c0^2, -D n/2c0, D/2(gamma-1),
+    D = g - w_in(characteristic)). The characteristic ghost is kept where the
+    result is not finite or has non-positive density or pressure."""
+    from . import mlp
+    q0 = gas.freestream()
+    qc = ghost_characteristic(qm, n, gas)
+    feats, s = mlp.features(qm - q0, n, x, gas, radius)
+    y, _ = mlp.forward(w, feats.reshape(-1, mlp.N_IN))
+    y = y.reshape(qm.shape)
+    wo_m, _ = acoustic_invariants(qm - q0, n, gas)
+    _, wi_c = acoustic_invariants(qc - q0, n, gas)
+    # bound: the larger of the characteristic ghost's own |w_in| and kappa |w_out|
+    lim = np.maximum(np.abs(wi_c), LEARNED_KAPPA * np.abs(wo_m))
+    D = np.clip(wi_c + gas.rho0 * gas.c0 ** 2 * s * y[..., 0], -lim, lim) - wi_c
+    c0 = gas.c0
+    q = qc.copy()
+    q[..., 0] += D / (2 * c0 * c0)
+    q[..., 1:4] -= (D / (2 * c0))[..., None] * n
+    q[..., 4] += D / (2 * (gas.gamma - 1.0))
+    ok = np.all(np.isfinite(q), axis=-1) & (q[..., 0] > 0)
+    ok &= pressure(np.where(ok[..., None], q, qc), gas.gamma) > 0
+    return np.where(ok[..., None], q, qc)
+
+
 # ----------------------------------------------------------------- solver
 
 class Solver:
@@ -189,10 +247,11 @@ class Solver:
     default 0 everywhere); ``bc_mode[id]`` the ghost rule of that id.
     """
 
-    def __init__(self, geom: Geometry, gas: Gas, bc_id=None, bc_mode=None):
+    def __init__(self, geom: Geometry, gas: Gas, bc_id=None, bc_mode=None, mlp=None):
         self.g = geom
         self.ref = geom.ref
         self.gas = gas
+        self.mlp = mlp                      # (parameters, radius) of the learned closure
         K = geom.K
         self.bc_id = np.zeros((K, 4), dtype=np.int64) if bc_id is None else np.asarray(bc_id)
         self.bc_mode = {0: CHARACTERISTIC} if bc_mode is None else dict(bc_mode)
@@ -222,8 +281,12 @@ class Solver:
             bidx = np.nonzero(g.boundary)
             for ident in np.unique(self.bc_id[bidx]):
                 sel = tuple(ix[self.bc_id[bidx] == ident] for ix in bidx)
-                rule = GHOSTS[self.bc_mode[int(ident)]]
-                qp[sel] = rule(qm[sel], n[sel], gas)
+                mode = self.bc_mode[int(ident)]
+                if mode == LEARNED:
+                    xf = g.x[sel[0][:, None], ref.Fmask[sel[1]]]          # face node positions
+                    qp[sel] = ghost_learned(qm[sel], n[sel], xf, gas, *self.mlp)
+                else:
+                    qp[sel] = GHOSTS[mode](qm[sel], n[sel], gas)
         fstar = llf_flux(qm, qp, n, gam)
         dF = g.Fscale[:, :, None, None] * (normal_flux(qm, n, gam) - fstar)
         dF = np.transpose(dF, (0, 3, 1, 2)).reshape(K, 5, 4 * Nfp)

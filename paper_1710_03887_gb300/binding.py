@@ -27,6 +27,8 @@ DG_ERR_TIMEOUT = -7
 DG_BC_FREESTREAM = 0
 DG_BC_CHARACTERISTIC = 1
 DG_BC_SLIP_WALL = 2
+DG_BC_LEARNED = 3
+DG_MLP_NPARAMS = 5317
 
 DG_PREC_FP64 = 0
 DG_PREC_F32 = 1
@@ -66,6 +68,14 @@ _SIGS = {
     "dg_set_kernel_timing": (C.c_int, [_P, C.c_int]),
     "dg_read_kernel_timing": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
     "dg_weighted_totals_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, _P, _P]),
+    "dg_reference_mass": (C.c_int, [C.c_int, _P]),
+    "dg_set_bc_mlp": (C.c_int, [_P, _P, C.c_double]),
+    "dg_get_bc_mlp": (C.c_int, [_P, _P]),
+    "dg_set_trace_faces": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "dg_sample_traces": (C.c_int, [_P, _P, _P]),
+    "dg_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _D, _P]),
+    "dg_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_double, _P]),
+    "dg_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P]),
 }
 
 _lib = None
@@ -111,6 +121,17 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return a.data_ptr()
     return a.ctypes.data
+
+
+def reference_mass(order):
+    """Mass matrix of the library's reference element (host only)."""
+    lib = load()
+    Np = (order + 1) * (order + 2) * (order + 3) // 6
+    M = np.zeros((Np, Np))
+    rc = lib.dg_reference_mass(order, _ptr(M))
+    if rc != DG_OK:
+        raise DGError(rc, "dg_reference_mass failed")
+    return M
 
 
 def reference_operators(order):
@@ -255,6 +276,43 @@ class Solver:
 
     def sync(self):
         self._check(self.lib.dg_sync(self.h))
+
+    # -- learned closure
+    def set_bc_mlp(self, w, radius):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == DG_MLP_NPARAMS
+        self._check(self.lib.dg_set_bc_mlp(self.h, _ptr(w), float(radius)))
+
+    def get_bc_mlp(self):
+        w = np.zeros(DG_MLP_NPARAMS, dtype=np.float32)
+        self._check(self.lib.dg_get_bc_mlp(self.h, _ptr(w)))
+        return w
+
+    def set_trace_faces(self, elem, face):
+        elem = np.ascontiguousarray(elem, dtype=np.int32)
+        face = np.ascontiguousarray(face, dtype=np.int8)
+        self._check(self.lib.dg_set_trace_faces(self.h, elem.size, _ptr(elem), _ptr(face)))
+        self.ntrace = elem.size
+
+    def sample_traces(self, X, Y):
+        """Fill device tensors X [ntrace*Nfp, 12] and Y [ntrace*Nfp, 5] (float32)."""
+        self._check(self.lib.dg_sample_traces(self.h, X.data_ptr(), Y.data_ptr()))
+
+    def mlp_loss_grad(self, X, Y):
+        loss = C.c_double()
+        grad = np.zeros(DG_MLP_NPARAMS, dtype=np.float32)
+        self._check(self.lib.dg_mlp_loss_grad(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0],
+                                              C.byref(loss), _ptr(grad)))
+        return loss.value, grad
+
+    def mlp_train(self, X, Y, iters, lr):
+        hist = np.zeros(max(iters, 1))
+        self._check(self.lib.dg_mlp_train(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], int(iters),
+                                          float(lr), _ptr(hist)))
+        return hist[:iters]
+
+    def mlp_forward(self, X, out):
+        self._check(self.lib.dg_mlp_forward(self.h, X.data_ptr(), X.shape[0], out.data_ptr()))
 
     def set_kernel_timing(self, enable=True):
         self._check(self.lib.dg_set_kernel_timing(self.h, int(enable)))

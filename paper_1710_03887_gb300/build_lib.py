@@ -20,7 +20,7 @@ LIB = PKG / "libdgeuler.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SOURCES = ["operators.cpp", "mesh.cpp"]
-CU_SOURCES = ["context.cu", "stage_fp64.cu", "stage_f32.cu", "stage_tc.cu", "totals_static.cu"]
+CU_SOURCES = ["context.cu", "stage_fp64.cu", "stage_f32.cu", "stage_tc.cu", "learned.cu", "totals_static.cu"]
 
 
 def _nvcc():

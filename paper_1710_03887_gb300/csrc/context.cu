@@ -10,6 +10,7 @@
 #include "../../include/dg_euler.h"
 #include "dg_device.cuh"
 #include "dg_host.hpp"
+#include "ghost_f32.cuh"
 
 namespace {
 
@@ -76,6 +77,21 @@ struct dg_ctx {
   double* prow = nullptr;
   double* pring = nullptr;
   std::vector<double> mass_w_host;
+  // learned closure
+  float* bxyz = nullptr;           // boundary face node positions [slot][Nfp][3]
+  float* mlp_w = nullptr;          // network parameters (device), null until set
+  float* mlp_m = nullptr;          // Adam moments
+  float* mlp_v = nullptr;
+  float* mlp_grad = nullptr;
+  double* mlp_loss = nullptr;
+  float* mlp_part = nullptr;       // per-block partial gradients
+  size_t mlp_part_len = 0;
+  int mlp_t = 0;
+  double mlp_radius = 1.0;
+  int64_t ntrace = 0;
+  int32_t* tr_elem = nullptr;
+  int8_t* tr_face = nullptr;
+  float* txyz = nullptr;
   // stage-kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;   // created lazily, reused
@@ -101,6 +117,8 @@ struct dg_ctx {
     dfree(ops); dfree(tbl); dfree(fmask); dfree(slot); dfree(ledger_part); dfree(ledger);
     dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
     dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
+    dfree(bxyz); dfree(tr_elem); dfree(tr_face); dfree(txyz);
+    ntrace = 0;
     dev_ready = false;
     have_state = false;
     nprobe = 0;
@@ -115,6 +133,19 @@ namespace {
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return c->cuda_fail(e_, #call); \
   } while (0)
+
+// Physical position of volume node n of element e (affine map of the vertices).
+void node_position(const dg_ctx* c, int64_t e, int n, double x[3]) {
+  const double* v = &c->mesh.verts[size_t(e) * 12];
+  const double r = c->ref.r[n], s = c->ref.s[n], t = c->ref.t[n];
+  const double w[4] = {-0.5 * (1 + r + s + t), 0.5 * (1 + r), 0.5 * (1 + s), 0.5 * (1 + t)};
+  for (int d = 0; d < 3; ++d) x[d] = w[0] * v[d] + w[1] * v[3 + d] + w[2] * v[6 + d] + w[3] * v[9 + d];
+}
+
+dgk::mlp::Scales mlp_scales(const dg_ctx* c) {
+  return dgk::mlp::Scales{float(c->gas.rho0), float(c->gas.c0), float(c->gas.p0), float(c->gas.gm1),
+                          float(1.0 / c->mlp_radius)};
+}
 
 // Allocate and fill the device copies of the mesh and operators.
 int ensure_device(dg_ctx* c) {
@@ -173,6 +204,7 @@ int ensure_device(dg_ctx* c) {
   // face connection words and ledger slots of tiles that own boundary faces
   std::vector<int32_t> conn(size_t(K) * 4);
   std::vector<int32_t> slot(c->ntiles, -1);
+  std::vector<int64_t> bfaces;
   int nslots = 0;
   for (int64_t e = 0; e < K; ++e)
     for (int f = 0; f < 4; ++f) {
@@ -180,12 +212,29 @@ int ensure_device(dg_ctx* c) {
       if (c->mesh.EToE[i] >= 0) {
         conn[i] = dgk::conn_interior(c->mesh.EToE[i], c->mesh.EToF[i], c->mesh.orient[i]);
       } else {
-        conn[i] = -1 - c->mesh.bc[i];
+        // boundary id in the low 3 bits, boundary-face slot above them
+        conn[i] = -1 - (c->mesh.bc[i] + 8 * int32_t(bfaces.size()));
+        bfaces.push_back(int64_t(i));
         const int tile = int(e / ET);
         if (slot[tile] < 0) slot[tile] = nslots++;
       }
     }
   c->nslots = std::max(nslots, 1);
+  // node positions of every boundary face (features of the learned closure)
+  if (f32 && !bfaces.empty()) {
+    std::vector<float> bx(bfaces.size() * size_t(Nfp) * 3);
+    for (size_t b = 0; b < bfaces.size(); ++b) {
+      const int64_t e = bfaces[b] / 4;
+      const int f = int(bfaces[b] % 4);
+      for (int m = 0; m < Nfp; ++m) {
+        double x[3];
+        node_position(c, e, c->ref.Fmask[f * Nfp + m], x);
+        for (int d = 0; d < 3; ++d) bx[(b * Nfp + m) * 3 + d] = float(x[d]);
+      }
+    }
+    DG_CUDA(cudaMalloc(&c->bxyz, bx.size() * 4));
+    DG_CUDA(cudaMemcpy(c->bxyz, bx.data(), bx.size() * 4, cudaMemcpyHostToDevice));
+  }
   DG_CUDA(cudaMalloc(&c->conn, conn.size() * 4));
   DG_CUDA(cudaMemcpy(c->conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice));
   DG_CUDA(cudaMalloc(&c->slot, slot.size() * 4));
@@ -282,6 +331,9 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     A.b = float(b);
     A.dt = float(dt);
     A.gas = c->gas;
+    A.mlp_w = c->mlp_w;
+    A.bxyz = c->bxyz;
+    A.mlp_scales = mlp_scales(c);
     if (c->prec == DG_PREC_F32_TC)
       DG_CUDA(dgk::launch_stage_tc(c->ref.p, A, c->grid, c->stream));
     else
@@ -392,6 +444,8 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
 int dg_destroy(dg_ctx* c) {
   if (!c) return DG_OK;
   c->free_device();
+  dfree(c->mlp_w); dfree(c->mlp_m); dfree(c->mlp_v); dfree(c->mlp_grad); dfree(c->mlp_loss);
+  dfree(c->mlp_part);
   delete c;
   return DG_OK;
 }
@@ -425,7 +479,9 @@ int dg_upload_mesh(dg_ctx* c, int64_t nvert, const double* xyz, int64_t K, const
 int dg_set_bc(dg_ctx* c, int bc_id, int mode) {
   if (!c) return DG_ERR_ARG;
   if (bc_id < 0 || bc_id > 7) return c->fail(DG_ERR_ARG, "boundary id must be 0..7");
-  if (mode < 0 || mode > 2) return c->fail(DG_ERR_ARG, "unknown boundary mode");
+  if (mode < 0 || mode > 3) return c->fail(DG_ERR_ARG, "unknown boundary mode");
+  if (mode == DG_BC_LEARNED && c->prec == DG_PREC_FP64)
+    return c->fail(DG_ERR_UNSUPPORTED, "the learned closure runs in the float32 forms");
   c->bc_mode[bc_id] = mode;
   return DG_OK;
 }
@@ -734,6 +790,153 @@ int dg_read_kernel_timing(dg_ctx* c, double* total_ms, int64_t* launches) {
   *total_ms = sum;
   *launches = int64_t(c->ev_used / 2);
   c->ev_used = 0;
+  return DG_OK;
+}
+
+// ------------------------------------------------------- learned closure
+
+int dg_reference_mass(int order, double* M) {
+  dg::RefElement re;
+  std::string err;
+  if (!M) return DG_ERR_ARG;
+  if (!dg::build_ref_element(order, re, err)) return DG_ERR_UNSUPPORTED;
+  const int Np = re.Np;
+  // M = (V V^T)^-1 = invV^T invV for the orthonormal basis
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < Np; ++m) s += re.invV[size_t(m) * Np + i] * re.invV[size_t(m) * Np + j];
+      M[size_t(i) * Np + j] = s;
+    }
+  return DG_OK;
+}
+
+static int ensure_mlp(dg_ctx* c) {
+  if (c->mlp_w) return DG_OK;
+  const size_t n = dgk::mlp::kParams;
+  DG_CUDA(cudaMalloc(&c->mlp_w, n * 4));
+  DG_CUDA(cudaMalloc(&c->mlp_m, n * 4));
+  DG_CUDA(cudaMalloc(&c->mlp_v, n * 4));
+  DG_CUDA(cudaMalloc(&c->mlp_grad, n * 4));
+  DG_CUDA(cudaMalloc(&c->mlp_loss, 8));
+  DG_CUDA(cudaMemset(c->mlp_w, 0, n * 4));
+  return DG_OK;
+}
+
+int dg_set_bc_mlp(dg_ctx* c, const float* w, double radius) {
+  if (!c || !w || !(radius > 0.0)) return DG_ERR_ARG;
+  int rc = ensure_mlp(c);
+  if (rc) return rc;
+  if (c->dev_ready) DG_CUDA(cudaStreamSynchronize(c->stream));
+  DG_CUDA(cudaMemcpy(c->mlp_w, w, size_t(dgk::mlp::kParams) * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemset(c->mlp_m, 0, size_t(dgk::mlp::kParams) * 4));
+  DG_CUDA(cudaMemset(c->mlp_v, 0, size_t(dgk::mlp::kParams) * 4));
+  c->mlp_t = 0;
+  c->mlp_radius = radius;
+  return DG_OK;
+}
+
+int dg_get_bc_mlp(dg_ctx* c, float* w) {
+  if (!c || !w) return DG_ERR_ARG;
+  if (!c->mlp_w) return c->fail(DG_ERR_ORDER, "no network set");
+  if (c->dev_ready) DG_CUDA(cudaStreamSynchronize(c->stream));
+  DG_CUDA(cudaMemcpy(w, c->mlp_w, size_t(dgk::mlp::kParams) * 4, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int dg_set_trace_faces(dg_ctx* c, int64_t n, const int32_t* elem, const int8_t* face) {
+  if (!c || n < 0 || (n > 0 && (!elem || !face))) return DG_ERR_ARG;
+  if (c->prec == DG_PREC_FP64) return c->fail(DG_ERR_UNSUPPORTED, "traces are sampled in the float32 forms");
+  int rc = ensure_device(c);
+  if (rc) return rc;
+  const int Nfp = c->ref.Nfp;
+  std::vector<float> xyz(size_t(n) * Nfp * 3);
+  for (int64_t t = 0; t < n; ++t) {
+    if (elem[t] < 0 || elem[t] >= c->mesh.K || face[t] < 0 || face[t] > 3)
+      return c->fail(DG_ERR_ARG, "trace face out of range");
+    if (c->mesh.EToE[size_t(elem[t]) * 4 + face[t]] < 0)
+      return c->fail(DG_ERR_ARG, "trace faces must be interior faces");
+    for (int m = 0; m < Nfp; ++m) {
+      double x[3];
+      node_position(c, elem[t], c->ref.Fmask[face[t] * Nfp + m], x);
+      for (int d = 0; d < 3; ++d) xyz[(size_t(t) * Nfp + m) * 3 + d] = float(x[d]);
+    }
+  }
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c->tr_elem); dfree(c->tr_face); dfree(c->txyz);
+  c->ntrace = 0;
+  if (n == 0) return DG_OK;
+  DG_CUDA(cudaMalloc(&c->tr_elem, size_t(n) * 4));
+  DG_CUDA(cudaMalloc(&c->tr_face, size_t(n)));
+  DG_CUDA(cudaMalloc(&c->txyz, xyz.size() * 4));
+  DG_CUDA(cudaMemcpy(c->tr_elem, elem, size_t(n) * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(c->tr_face, face, size_t(n), cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(c->txyz, xyz.data(), xyz.size() * 4, cudaMemcpyHostToDevice));
+  c->ntrace = n;
+  return DG_OK;
+}
+
+int dg_sample_traces(dg_ctx* c, float* X, float* Y) {
+  if (!c || !X || !Y) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  if (c->ntrace == 0) return c->fail(DG_ERR_ORDER, "no trace faces set");
+  const dgk::BaseGhost bg{float(c->gas.rho0), float(c->gas.p0), float(c->gas.gamma),
+                          float(c->gas.gm1), float(c->gas.c0)};
+  DG_CUDA(dgk::launch_sample_traces(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->tr_elem, c->tr_face,
+                                    c->conn, c->tbl, c->fmask, c->geo32, c->txyz, c->ntrace, bg,
+                                    mlp_scales(c), X, Y, c->status, c->stream));
+  return DG_OK;
+}
+
+static int mlp_grad_dev(dg_ctx* c, const float* X, const float* Y, int64_t N) {
+  int dev = 0, sms = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nb = dgk::mlp_grad_blocks(N, sms);
+  const size_t need = size_t(nb) * (dgk::mlp::kParams + 1);
+  if (need > c->mlp_part_len) {
+    dfree(c->mlp_part);
+    DG_CUDA(cudaMalloc(&c->mlp_part, need * 4));
+    c->mlp_part_len = need;
+  }
+  DG_CUDA(dgk::launch_mlp_loss_grad(c->mlp_w, X, Y, N, nb, c->mlp_part,
+                                    c->mlp_part + size_t(nb) * dgk::mlp::kParams, c->mlp_grad,
+                                    c->mlp_loss, c->stream));
+  return DG_OK;
+}
+
+int dg_mlp_loss_grad(dg_ctx* c, const float* X, const float* Y, int64_t N, double* loss,
+                     float* grad) {
+  if (!c || !X || !Y || N <= 0) return DG_ERR_ARG;
+  if (!c->mlp_w) return c->fail(DG_ERR_ORDER, "no network set");
+  int rc = mlp_grad_dev(c, X, Y, N);
+  if (rc) return rc;
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  if (loss) DG_CUDA(cudaMemcpy(loss, c->mlp_loss, 8, cudaMemcpyDeviceToHost));
+  if (grad) DG_CUDA(cudaMemcpy(grad, c->mlp_grad, size_t(dgk::mlp::kParams) * 4, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int dg_mlp_train(dg_ctx* c, const float* X, const float* Y, int64_t N, int iters, double lr,
+                 double* loss_history) {
+  if (!c || !X || !Y || N <= 0 || iters < 0 || !(lr > 0.0)) return DG_ERR_ARG;
+  if (!c->mlp_w) return c->fail(DG_ERR_ORDER, "no network set");
+  for (int it = 0; it < iters; ++it) {
+    int rc = mlp_grad_dev(c, X, Y, N);
+    if (rc) return rc;
+    if (loss_history)
+      DG_CUDA(cudaMemcpyAsync(loss_history + it, c->mlp_loss, 8, cudaMemcpyDeviceToHost, c->stream));
+    ++c->mlp_t;
+    DG_CUDA(dgk::launch_adam(c->mlp_w, c->mlp_grad, c->mlp_m, c->mlp_v, float(lr), c->mlp_t, c->stream));
+  }
+  DG_CUDA(cudaStreamSynchronize(c->stream));
+  return DG_OK;
+}
+
+int dg_mlp_forward(dg_ctx* c, const float* X, int64_t N, float* out) {
+  if (!c || !X || !out || N < 0) return DG_ERR_ARG;
+  if (!c->mlp_w) return c->fail(DG_ERR_ORDER, "no network set");
+  DG_CUDA(dgk::launch_mlp_forward(c->mlp_w, X, N, out, c->stream));
   return DG_OK;
 }
 

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mlp.cuh"
+
 namespace dgk {
 
 // per-element geometry record (float64), 32 words = 256 bytes
@@ -64,6 +66,10 @@ struct StageArgsF32 {
   int bc_mode[8];
   float a, b, dt;
   Gas gas;
+  // learned closure (boundary mode 3)
+  const float* mlp_w;        // network parameters (mlp.cuh packing), or null
+  const float* bxyz;         // [boundary face slot][Nfp][3] node positions
+  mlp::Scales mlp_scales;
 };
 
 int stage_f32_tile_elems(int p);
@@ -86,6 +92,22 @@ void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, c
                   const double* face_w, unsigned char* out);
 cudaError_t stage_tc_prepare(int p, int* blocks_per_sm);
 cudaError_t launch_stage_tc(int p, const StageArgsF32& a, int grid, cudaStream_t s);
+
+// Learned closure (learned.cu)
+struct BaseGhost;
+cudaError_t launch_sample_traces(const float* q, int Np, int Nfp, const int32_t* tr_elem,
+                                 const int8_t* tr_face, const int32_t* conn, const uint8_t* tbl,
+                                 const int32_t* fmask, const float* geo, const float* txyz,
+                                 int64_t n, const BaseGhost& bg, const mlp::Scales& S, float* X,
+                                 float* Y, int* status, cudaStream_t s);
+int mlp_grad_blocks(int64_t N, int sms);
+cudaError_t launch_mlp_loss_grad(const float* w, const float* X, const float* Y, int64_t N,
+                                 int nblocks, float* part_grad, float* part_loss, float* grad,
+                                 double* loss, cudaStream_t s);
+cudaError_t launch_adam(float* w, const float* grad, float* m, float* v, float lr, int t,
+                        cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* w, const float* X, int64_t N, float* out,
+                               cudaStream_t s);
 
 // launch helpers (stage_fp64.cu)
 int stage_tile_elems(int p);

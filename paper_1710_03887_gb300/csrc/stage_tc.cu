@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "dg_device.cuh"
+#include "ghost_f32.cuh"
 #include "tc_ptx.cuh"
 
 namespace dgk {
@@ -79,50 +80,6 @@ __device__ __forceinline__ void normal_flux_tc(const float q[5], const float n[3
   fn[3] = q[3] * un + pp * n[2];
   fn[4] = un * (b.H0 + q[4] + pp);
   lam = fabsf(un) + sqrtf(b.gamma * (b.p0 + pp) * rinv);
-}
-
-// Ghost state as a float32 perturbation (see ghost_state_f in stage_f32.cu
-// for the derivation of this cancellation-free form).
-__device__ __forceinline__ void ghost_tc(int mode, const float qm[5], const float n[3],
-                                         const BaseF2& g, float qp[5]) {
-  if (mode == 0) {
-    for (int v = 0; v < 5; ++v) qp[v] = 0.0f;
-    return;
-  }
-  if (mode == 2) {
-    const float mn = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
-    qp[0] = qm[0];
-    qp[1] = qm[1] - 2.0f * mn * n[0];
-    qp[2] = qm[2] - 2.0f * mn * n[1];
-    qp[3] = qm[3] - 2.0f * mn * n[2];
-    qp[4] = qm[4];
-    return;
-  }
-  const float rinv = 1.0f / (g.rho0 + qm[0]);
-  const float u[3] = {qm[1] * rinv, qm[2] * rinv, qm[3] * rinv};
-  const float pp = g.gm1 * (qm[4] - 0.5f * (qm[1] * u[0] + qm[2] * u[1] + qm[3] * u[2]));
-  const float un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
-  const float c = sqrtf(g.gamma * (g.p0 + pp) * rinv);
-  const float dc = g.gamma * (g.rho0 * pp - g.p0 * qm[0]) * rinv / (g.rho0 * (c + g.c0));
-  const float unb = 0.5f * un + dc / g.gm1;
-  const float dcb = 0.25f * g.gm1 * un + 0.5f * dc;
-  const float lcb = log1pf(dcb / g.c0);
-  float ls = 0.0f, ut[3] = {0.0f, 0.0f, 0.0f};
-  if (unb >= 0.0f) {
-    ls = log1pf(pp / g.p0) - g.gamma * log1pf(qm[0] / g.rho0);
-    for (int d = 0; d < 3; ++d) ut[d] = u[d] - un * n[d];
-  }
-  const float lrho = (2.0f * lcb - ls) / g.gm1;
-  const float drho = g.rho0 * expm1f(lrho);
-  const float dp = g.p0 * expm1f(lrho + 2.0f * lcb);
-  const float rhob = g.rho0 + drho;
-  float ub[3];
-  for (int d = 0; d < 3; ++d) ub[d] = ut[d] + unb * n[d];
-  qp[0] = drho;
-  qp[1] = rhob * ub[0];
-  qp[2] = rhob * ub[1];
-  qp[3] = rhob * ub[2];
-  qp[4] = dp / g.gm1 + 0.5f * rhob * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
 }
 
 // Store x into the A operand (hi and lo tf32 parts) at (row, k).
@@ -186,6 +143,7 @@ stage_tc_kernel(const StageArgsF32 A) {
   const uint32_t tmem = *tslot;
   const BaseF2 b{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
                  float(A.gas.E0 + A.gas.p0), float(A.gas.c0)};
+  const BaseGhost bg{b.rho0, b.p0, b.gamma, b.gm1, b.c0};
   constexpr uint32_t idesc = tc::idesc_tf32(O::M, O::N);
   uint32_t phase = 0;
 
@@ -261,7 +219,14 @@ stage_tc_kernel(const StageArgsF32 A) {
         const float* src = A.q_in + e2 * 5 * Np + n2;
         for (int v = 0; v < 5; ++v) qp[v] = __ldg(src + v * Np);
       } else {
-        ghost_tc(A.bc_mode[(-1 - c) & 7], qm, nv, b, qp);
+        const int mode = A.bc_mode[(-1 - c) & 7];
+        if (mode == 3) {
+          const float* xb = A.bxyz + (size_t((-1 - c) >> 3) * Nfp + m) * 3;
+          const float xv[3] = {xb[0], xb[1], xb[2]};
+          ghost_learned_f(qm, nv, xv, bg, A.mlp_scales, A.mlp_w, qp);
+        } else {
+          ghost_state_f(mode, qm, nv, bg, qp);
+        }
       }
       float fnm[5], fnp[5], lm, lp;
       normal_flux_tc(qm, nv, b, fnm, lm);

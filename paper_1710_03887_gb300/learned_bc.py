@@ -1,0 +1,191 @@
+"""Learned boundary closure: data from the method itself, training, judging.
+
+Workflow (all device work in the library's kernels; this module only
+orchestrates calls and keeps tensors):
+
+1. ``nested_ball``: a ball of radius 2 whose lattice cube |x|_inf = 1/2 maps
+   onto the sphere of radius 1, so the truncated domain (r < 1) is exactly the
+   inner part of the large one, element for element.
+2. ``record``: seeded reference runs on the large ball; at the interior faces
+   on r = 1 the library samples (features of the inner trace, target
+   correction of the characteristic ghost towards the outer trace)
+   (dg_sample_traces).
+3. ``train``: full-batch Adam on the GPU with the library's own forward and
+   backward kernels (dg_mlp_train).
+4. ``reflected_energy``: the judge. The truncated ball with a given outer
+   condition and the large ball start from the same pulse; after the pulse
+   has left r < 1 in the large ball, the acoustic energy of their difference
+   inside r < 1, relative to the initial acoustic energy, is the reflection
+   error of the condition.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import binding as B
+from . import workloads as W
+
+
+@dataclass
+class Nested:
+    big: tuple            # (xyz, EToV) of the radius-2 ball
+    small: tuple          # (xyz, EToV) of the radius-1 ball (inner elements, same order)
+    inner: np.ndarray     # element ids of the big mesh that form the small one
+    radius: float         # truncation radius (1)
+
+
+def nested_ball(n, jitter=0.0, seed=0):
+    """Radius-2 ball on the n-lattice with the r = 1 sphere made of faces."""
+    if n % 4:
+        raise ValueError("n must be a multiple of 4")
+    xyz, EToV = W.ball(n, radius=2.0, jitter=jitter, seed=seed, sphere_from=0.5)
+    cen = W.element_centroids(xyz, EToV)
+    inner = np.nonzero(np.linalg.norm(cen, axis=1) < 1.0)[0]
+    keep = np.zeros(len(EToV), dtype=bool)
+    keep[inner] = True
+    sxyz, sE = W.submesh(xyz, EToV, keep)
+    return Nested((xyz, EToV), (sxyz, sE), inner, 1.0)
+
+
+def trace_faces(S_big, nested):
+    """Faces of inner elements whose neighbour is outside r = 1."""
+    g = S_big.geometry()
+    inside = np.zeros(S_big.K, dtype=bool)
+    inside[nested.inner] = True
+    elem, face = [], []
+    for e in nested.inner:
+        for f in range(4):
+            nb = g["EToE"][e, f]
+            if nb >= 0 and not inside[nb]:
+                elem.append(e)
+                face.append(f)
+    return np.array(elem, dtype=np.int32), np.array(face, dtype=np.int8)
+
+
+def pulse(nodes, amplitude, width, center):
+    return W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, amplitude, width, center)
+
+
+def run_seeds(seed, count):
+    """Seeded pulse parameters: centre uniform in |x| < 0.5, width in [0.1, 0.2]
+    scaled by ``width_scale`` at the call site, amplitude log-uniform in
+    [0.1 %, 10 %] of p0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        while True:
+            c = rng.uniform(-0.5, 0.5, size=3)
+            if np.linalg.norm(c) < 0.5:
+                break
+        w = rng.uniform(0.1, 0.2)
+        a = 10.0 ** rng.uniform(-3.0, -1.0)
+        out.append((c, w, a))
+    return out
+
+
+def crossing_time(center, width):
+    """Time for a pulse from ``center`` to have fully crossed the sphere r = 1."""
+    c0 = np.sqrt(W.GAMMA * W.P0_SI / W.RHO0_SI)
+    return (1.0 + np.linalg.norm(center) + 3.0 * width) / c0
+
+
+def record(order, nested, runs, every, device, width_scale=1.0, precision=None, min_rel=1e-3):
+    """Reference runs on the large ball; returns device tensors (X, Y).
+
+    Samples whose pressure perturbation is below ``min_rel`` times the run's
+    pulse amplitude (the far tail before the pulse arrives) are dropped."""
+    import torch
+    prec = B.DG_PREC_F32 if precision is None else precision
+    S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+    S.upload_mesh(*nested.big)
+    nodes = S.node_coords()
+    elem, face = trace_faces(S, nested)
+    S.set_trace_faces(elem, face)
+    n = len(elem) * S.Nfp
+    Xs, Ys = [], []
+    for c, w, a in runs:
+        q0 = pulse(nodes, a, w * width_scale, c)
+        dt = S.stable_dt(q0, 0.5)
+        steps = int(np.ceil(crossing_time(c, w * width_scale) / dt))
+        S.set_state(q0)
+        for _ in range(steps // every):
+            S.step(every, dt)
+            X = torch.empty((n, 12), dtype=torch.float32, device=device)
+            Y = torch.empty((n, 5), dtype=torch.float32, device=device)
+            S.sample_traces(X, Y)
+            # feature 11 is 10 w_out / (2 p0): keep the nodes the pulse actually reaches
+            keep = X[:, 11].abs() > 10.0 * min_rel * a
+            Xs.append(X[keep])
+            Ys.append(Y[keep])
+    S.sync()
+    S.close()
+    return torch.cat(Xs), torch.cat(Ys)
+
+
+def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
+    """Adam on the GPU from seeded Glorot weights; returns (weights, losses)."""
+    rng = np.random.default_rng(seed)
+    w0 = []
+    dims = [(12, 64), (64, 64), (64, 5)]
+    for a, b in dims:
+        lim = np.sqrt(6.0 / (a + b))
+        w0.append(rng.uniform(-lim, lim, size=(a, b)).ravel())
+        w0.append(np.zeros(b))
+    w0 = np.concatenate(w0).astype(np.float32)
+    w0[-5 - 64 * 5:-5] *= 0.01              # start close to the characteristic ghost
+    S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
+    S.set_bc_mlp(w0, radius)
+    hist = S.mlp_train(X, Y, iters, lr)
+    w = S.get_bc_mlp()
+    S.close()
+    return w, hist
+
+
+def acoustic_energy_weights(order):
+    """Quadrature weights 1^T M of the reference element."""
+    return B.reference_mass(order).sum(axis=0)
+
+
+def acoustic_energy(dq, J, wq):
+    """int (((gamma-1) dE)^2 / (2 rho0 c0^2) + |dm|^2 / (2 rho0)) dV of a state difference."""
+    c0sq = W.GAMMA * W.P0_SI / W.RHO0_SI
+    dp = (W.GAMMA - 1.0) * dq[:, 4]
+    e = dp * dp / (2.0 * W.RHO0_SI * c0sq) + np.sum(dq[:, 1:4] ** 2, axis=1) / (2.0 * W.RHO0_SI)
+    return float(np.einsum("k,i,ki->", J, wq, e))
+
+
+def reflected_energy(order, nested, amplitude, width, center, mode, weights=None,
+                     precision=None):
+    """Reflection error of outer condition ``mode`` on the truncated ball.
+
+    Returns (E_reflected / E_initial, details)."""
+    prec = B.DG_PREC_F32 if precision is None else precision
+    big = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+    big.upload_mesh(*nested.big)
+    small = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+    small.upload_mesh(*nested.small)
+    small.set_bc(0, mode)
+    if mode == B.DG_BC_LEARNED:
+        small.set_bc_mlp(weights, nested.radius)
+    qb = pulse(big.node_coords(), amplitude, width, center)
+    qs = qb[nested.inner].copy()
+    dt = big.stable_dt(qb, 0.5)                  # same step on both (the large one is the smaller)
+    steps = int(np.ceil(crossing_time(center, width) / dt))
+    big.set_state(qb)
+    small.set_state(qs)
+    big.step(steps, dt)
+    small.step(steps, dt)
+    qb1, _ = big.get_state()
+    qs1, _ = small.get_state()
+    J = small.geometry()["J"]
+    wq = acoustic_energy_weights(order)
+    base = W.uniform_state(len(qs), qs.shape[2], W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
+    e0 = acoustic_energy(qs - base, J, wq)
+    er = acoustic_energy(qs1 - qb1[nested.inner], J, wq)
+    left = acoustic_energy(qb1[nested.inner] - base, J, wq)
+    big.close()
+    small.close()
+    return er / e0, {"E0": e0, "E_reflected": er, "E_left_in_reference": left, "dt": dt,
+                     "steps": steps}

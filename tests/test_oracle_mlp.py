@@ -1,0 +1,149 @@
+"""Pins of the oracle's network and learned closure (CPU)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from oracle.euler_dg import Gas, ghost_characteristic, ghost_learned
+
+
+def test_parameter_count_and_packing():
+    assert mlp.N_PARAMS == 12 * 64 + 64 + 64 * 64 + 64 + 64 * 5 + 5 == 5317
+    w = np.arange(mlp.N_PARAMS, dtype=np.float64)
+    p = mlp.unpack(w)
+    assert p["W1"][0, 1] == 1 and p["b1"][0] == 768 and p["b3"][-1] == mlp.N_PARAMS - 1
+    np.testing.assert_array_equal(mlp.pack(p), w)
+
+
+def test_gradient_against_central_differences():
+    rng = np.random.default_rng(0)
+    w = mlp.init_params(seed=1)
+    w += 0.1 * rng.normal(size=w.shape)           # nonzero biases too
+    X = rng.normal(size=(40, 12))
+    T = rng.normal(size=(40, 5))
+    loss, g = mlp.loss_and_grad(w, X, T)
+    idx = rng.choice(mlp.N_PARAMS, 300, replace=False)
+    idx = np.concatenate([idx, np.arange(mlp.N_PARAMS - 5, mlp.N_PARAMS)])
+    for i in idx:
+        h = 1e-6
+        e = np.zeros_like(w)
+        e[i] = h
+        fd = (mlp.loss_and_grad(w + e, X, T)[0] - mlp.loss_and_grad(w - e, X, T)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9)
+
+
+def test_zero_weights_closed_form():
+    rng = np.random.default_rng(2)
+    w = np.zeros(mlp.N_PARAMS)
+    b3 = rng.normal(size=5)
+    w[-5:] = b3
+    X = rng.normal(size=(10, 12))
+    T = rng.normal(size=(10, 5))
+    y, _ = mlp.forward(w, X)
+    np.testing.assert_array_equal(y, np.tile(b3, (10, 1)))
+    loss, g = mlp.loss_and_grad(w, X, T)
+    assert loss == pytest.approx(np.sum((b3 - T) ** 2) / 10)
+    np.testing.assert_allclose(g[-5:], 2 * np.mean(b3 - T, axis=0))
+    # with W3 = 0 nothing reaches the first layers
+    assert np.all(g[:-5 - 64 * 5] == 0)
+
+
+def test_first_adam_step_moves_by_lr():
+    rng = np.random.default_rng(3)
+    w0 = mlp.init_params(seed=4)
+    X = rng.normal(size=(20, 12))
+    T = rng.normal(size=(20, 5))
+    _, g = mlp.loss_and_grad(w0, X, T)
+    w1, hist = mlp.adam(w0, X, T, iters=1, lr=1e-3)
+    # bias-corrected first moment / root second moment = g / (|g| + eps)
+    nz = np.abs(g) > 1e-6
+    np.testing.assert_allclose((w0 - w1)[nz], 1e-3 * g[nz] / (np.abs(g[nz]) + 1e-8), rtol=1e-9)
+    w50, hist = mlp.adam(w0, X, T, iters=50, lr=1e-2)
+    assert hist[-1] < 0.5 * hist[0]
+
+
+def _trace_states(gas, rng, k=7, amp=1e-3):
+    n = rng.normal(size=(k, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    qm = np.tile(gas.freestream(), (k, 1))
+    qm[:, 0] *= 1 + amp * rng.normal(size=k)
+    qm[:, 1:4] = amp * gas.rho0 * gas.c0 * rng.normal(size=(k, 3))
+    qm[:, 4] *= 1 + amp * rng.normal(size=k)
+    return qm, n, rng.normal(size=(k, 3))
+
+
+def test_learned_ghost_reduces_to_characteristic_without_correction():
+    gas = Gas(1.4, 1.225, 101325.0)
+    qm, n, x = _trace_states(gas, np.random.default_rng(5))
+    q0 = gas.freestream()
+    gc = ghost_characteristic(qm, n, gas)
+    w = np.zeros(mlp.N_PARAMS)
+    np.testing.assert_allclose(ghost_learned(qm, n, x, gas, w, 1.0), gc, rtol=1e-15)
+
+
+def test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound():
+    from oracle.euler_dg import LEARNED_KAPPA, acoustic_invariants
+    gas = Gas(1.4, 1.225, 101325.0)
+    rng = np.random.default_rng(6)
+    qm, n, x = _trace_states(gas, rng, k=50)
+    q0 = gas.freestream()
+    gc = ghost_characteristic(qm, n, gas)
+    wo_m, _ = acoustic_invariants(qm - q0, n, gas)
+    wo_c, wi_c = acoustic_invariants(gc - q0, n, gas)
+    _, s = mlp.features(qm - q0, n, x, gas, 1.0)
+    amp = np.abs(wo_m)
+    for b0 in (0.05, -0.05, 1e3):              # small corrections, and a huge one (clipped)
+        w = np.zeros(mlp.N_PARAMS)
+        w[-5] = b0                             # constant output 0 = b0
+        gl = ghost_learned(qm, n, x, gas, w, 1.0)
+        wo_l, wi_l = acoustic_invariants(gl - q0, n, gas)
+        lim = np.maximum(np.abs(wi_c), LEARNED_KAPPA * amp)
+        want = np.clip(wi_c + gas.rho0 * gas.c0 ** 2 * s * b0, -lim, lim)
+        # outgoing invariant unchanged, incoming one moved to the bounded target
+        # (linearised invariants: second-order terms ~ amplitude x change)
+        tol = 1e-2 * (amp + np.abs(want - wi_c))
+        assert np.all(np.abs(wo_l - wo_c) <= tol)
+        assert np.all(np.abs(wi_l - want) <= tol)
+    # the huge correction saturates at the bound
+    assert np.all(np.abs(np.abs(wi_l) - lim) <= 1e-2 * (amp + lim))
+
+
+def test_learned_target_is_the_incoming_invariant_gap():
+    from oracle.euler_dg import acoustic_invariants, learned_target
+    gas = Gas(1.4, 1.225, 101325.0)
+    rng = np.random.default_rng(8)
+    qm, n, _ = _trace_states(gas, rng, k=20)
+    qo, _, _ = _trace_states(gas, rng, k=20)
+    q0 = gas.freestream()
+    y = learned_target(qm, qo, n, gas)
+    _, wi_o = acoustic_invariants(qo - q0, n, gas)
+    _, wi_c = acoustic_invariants(ghost_characteristic(qm, n, gas) - q0, n, gas)
+    _, s = mlp.features(qm - q0, n, np.zeros_like(n), gas, 1.0)
+    np.testing.assert_allclose(y[:, 0] * gas.rho0 * gas.c0 ** 2 * s, wi_o - wi_c, rtol=1e-12)
+    assert np.all(y[:, 1:] == 0)
+    # with the outer trace equal to the characteristic ghost there is nothing to learn
+    assert np.allclose(learned_target(qm, ghost_characteristic(qm, n, gas), n, gas), 0, atol=1e-12)
+
+
+def test_features_definition():
+    gas = Gas(1.4, 1.0, 1.0 / 1.4)            # c0 = 1, p0 = 1/1.4, rho0 c0^2 = 1
+    q = np.array([[0.01, 0.02, -0.03, 0.04, 0.05]])
+    n = np.array([[0.0, 0.0, 1.0]])
+    x = np.array([[0.5, 0.0, 0.0]])
+    f, s = mlp.features(q, n, x, gas, 2.0)
+    rho = 1.01
+    pp = 0.4 * (0.05 - 0.5 * (0.02 ** 2 + 0.03 ** 2 + 0.04 ** 2) / rho)
+    wout = pp + 0.04 / rho
+    assert s[0] == pytest.approx(abs(wout) + 1e-12)
+    assert f[0, 0] == pytest.approx(np.sign(wout))
+    assert f[0, 1] == pytest.approx((0.01 - pp) / s[0])
+    np.testing.assert_allclose(f[0, 2:5], [0.02 / rho / s[0], -0.03 / rho / s[0], 0.0], atol=1e-15)
+    np.testing.assert_allclose(f[0, 5:8], [0, 0, 1])
+    np.testing.assert_allclose(f[0, 8:11], [0.25, 0, 0])
+    assert f[0, 11] == pytest.approx(10 * wout / (2 * gas.p0))
+    # the incoming invariant of the trace does not enter the features
+    q2 = q.copy()
+    dwin = 1e-3                                # change p' by dwin/2 and rho0 c0 u_n by -dwin/2
+    q2[0, 4] += dwin / 2 / 0.4
+    q2[0, 3] -= dwin / 2
+    f2, s2 = mlp.features(q2, n, x, gas, 2.0)
+    assert abs(s2[0] - s[0]) < 2e-2 * dwin          # second order: amplitude x change
