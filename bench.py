@@ -12,8 +12,16 @@ five-stage low-storage RK4 time step of the whole mesh.
   e2e        same metric through the C ABI with host buffers: dg_set_state
              from pinned host memory, dg_step, sensor read-back and
              dg_get_state to host, all inside the timed region (wall clock)
-  roofline   stage kernel: algorithmic float64 flops per launch / average
-             launch time (CUDA event pairs around every stage launch)
+  roofline   stage kernel of the headline form: algorithmic bytes (float32
+             forms, HBM bound) or float64 flops (float64 form, ALU bound) per
+             launch / average launch time (CUDA event pairs around every stage
+             launch on the solver's stream)
+  forms      every arithmetic form (float32 perturbation, its tensor-core
+             variant, float64) timed the same way, with the float32 forms'
+             error against float64 after the timed steps
+  learned_bc the learned boundary closure: traces recorded, network trained
+             and reflected energies judged on the GPU, and the closure timed on
+             the bench workload
   cpu_baseline  the float64 CPU oracle on a bounded sample of the workload
 
 ``--impl reference`` times the CPU oracle itself on that sample instead.
@@ -223,8 +231,9 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_clocks):
-    """Time one arithmetic form on the bench workload; returns a dict."""
+def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_clocks, mlp=None):
+    """Time one arithmetic form on the bench workload; returns a dict. With
+    ``mlp`` = (weights, radius) the sphere takes the learned closure."""
     import torch
     from paper_1710_03887_gb300 import binding as B
     from paper_1710_03887_gb300 import workloads as W
@@ -233,6 +242,9 @@ def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_cl
     S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.set_stream(stream.cuda_stream)
     S.upload_mesh(xyz, EToV)
+    if mlp is not None:
+        S.set_bc(0, B.DG_BC_LEARNED)
+        S.set_bc_mlp(*mlp)
     nodes = S.node_coords()
     q0 = W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"], w["width"])
     dt = S.stable_dt(q0, w["cfl"])
@@ -327,6 +339,53 @@ def stage_bytes_per_element(p, word):
     return 4 * 5 * Np * word + 32 * word + 16
 
 
+LEARNED_AMPLITUDES = (0.001, 0.005, 0.02, 0.1)
+
+
+def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
+    """The learned closure end to end on the GPU: seeded reference runs on the
+    radius-2 ball record traces at r = 1, the library trains the network,
+    the large ball judges the reflected energy of the free-stream,
+    characteristic and learned conditions on the truncated ball, and the
+    trained closure is timed on the bench workload."""
+    from paper_1710_03887_gb300 import learned_bc as L
+    n, runs, every, iters = args.learned_n, 8, 10, 600
+    t0 = time.perf_counter()
+    nested = L.nested_ball(n)
+    X, Y = L.record(WORKLOAD["order"], nested, L.run_seeds(0, runs), every=every, device=dev,
+                    width_scale=2.0)
+    t_rec = time.perf_counter() - t0
+    w, hist = L.train(X, Y, iters=iters, lr=3e-3, seed=0, radius=nested.radius,
+                      order=WORKLOAD["order"])
+    t_train = time.perf_counter() - t0 - t_rec
+    table = {}
+    for amp in LEARNED_AMPLITUDES:
+        table[f"{100 * amp:g}% p0"] = L.reflection_table(WORKLOAD["order"], nested, amp, 0.3,
+                                                         (0.0, 0.0, 0.0), w)
+    # a source off the centre, where the spherical memory is no longer exact
+    table["2% p0 off-centre (0.3,0.1,-0.2)"] = L.reflection_table(
+        WORKLOAD["order"], nested, 0.02, 0.25, (0.3, 0.1, -0.2), w)
+    t_judge = time.perf_counter() - t0 - t_rec - t_train
+    m = measure_form(args, "f32", xyz, EToV, dev, stream, dist, world, sample_clocks=False,
+                     mlp=(w, WORKLOAD["radius"]))
+    return {
+        "config": (f"radius-2 ball on the n={n} lattice ({len(nested.big[1])} tets), truncated at "
+                   f"r=1 ({len(nested.small[1])} tets); p=3 float32; {runs} seeded pulse runs "
+                   f"(centre |x|<0.5, width 0.2-0.4, amplitude 0.1-10% p0) sampled every "
+                   f"{every} steps at r=1; judged with centred pulses of width 0.3 and one "
+                   "off-centre pulse of width 0.25; 'spherical' is the memory closure w_in = psi "
+                   "without training"),
+        "samples": int(X.shape[0]), "iters": iters, "loss_first": float(hist[0]),
+        "loss_last": float(hist[-1]),
+        "reflected_energy_rel": table,
+        "gain_vs_characteristic": {k: v["characteristic"] / v["learned"] for k, v in table.items()},
+        "seconds": {"record": t_rec, "train": t_train, "judge": t_judge},
+        "bench_workload_learned_bc": {"value": m["value"], "unit": UNIT,
+                                      "ms_per_step": m["ms"] / args.steps,
+                                      "avg_stage_launch_ms": m["kms"] / max(m["klaunch"], 1)},
+    }
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -379,6 +438,12 @@ def run_gpu(args, rank, world):
                 "after_steps": args.steps,
                 "speedup": a["value"] / b["value"]}
     line["forms"] = forms_out
+    if args.learned_n > 0:
+        # rank 0 only, after the replicas' timed regions: no barrier inside
+        lb = learned_bc_section(args, xyz, EToV, dev, stream, None, 1)
+        lb["bench_workload_learned_bc"]["vs_characteristic"] = (
+            lb["bench_workload_learned_bc"]["value"] / res["f32"]["value"] if "f32" in res else None)
+        line["learned_bc"] = lb
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -396,6 +461,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64"],
                     help="arithmetic form of the headline number (the other is measured beside it)")
     ap.add_argument("--one-form", action="store_true", help="measure only --precision")
+    ap.add_argument("--learned-n", type=int, default=16,
+                    help="lattice of the learned-closure experiment's radius-2 ball (0 = skip)")
     ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],
                     help="lattice size of the ball (32 = the benchmark; smaller for profiling)")
     args = ap.parse_args()

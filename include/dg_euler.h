@@ -62,10 +62,10 @@ extern "C" {
 #define DG_BC_FREESTREAM 0      /* ghost = free-stream state (section 2.2, Eq. 3)       */
 #define DG_BC_CHARACTERISTIC 1  /* Riemann-invariant far-field ghost (default)          */
 #define DG_BC_SLIP_WALL 2       /* normal velocity mirrored (section 2.3, Eq. 4)        */
-#define DG_BC_LEARNED 3         /* characteristic ghost + learned correction (float32   */
-                                /* forms; see dg_set_bc_mlp); falls back to the          */
-                                /* characteristic ghost where the result is not finite   */
-                                /* or has rho <= 0 or p <= 0                             */
+#define DG_BC_LEARNED 3         /* characteristic ghost with a learned, bounded incoming */
+                                /* invariant (float32 forms; see dg_set_bc_mlp); falls   */
+                                /* back to the characteristic ghost where the result is  */
+                                /* not finite or has rho <= 0 or p <= 0                  */
 
 /* Arithmetic of the time step (dg_params.precision) */
 #define DG_PREC_FP64 0          /* float64 state, fluxes and contractions               */
@@ -192,11 +192,20 @@ int dg_read_kernel_timing(dg_ctx* ctx, double* total_ms, int64_t* launches);
  * Learned boundary closure. The paper's pass-through condition (section 2.2)
  * and the characteristic ghost both assume what lies outside the truncation
  * surface; this closure learns it from the method's own solution in a larger
- * domain. A network 12 -> 64 -> 64 -> 5 (tanh, float32) maps the interior
- * trace at an outer-face node to a correction of the characteristic ghost:
- *   z(q) = (rho'/rho0, m'/(rho0 c0), E'/(rho0 c0^2))   (perturbation, 5 values)
- *   s = max|z(q-)| + 1e-12,  features = (z(q-)/s, n, x/R, 10 p'/p0)
- *   z(q+) = z(q+_characteristic) + s * network(features)
+ * domain. A network 12 -> 64 -> 64 -> 5 (tanh, float32) acts as a learned
+ * impedance: from what leaves the domain at an outer-face node it predicts
+ * the acoustic wave that enters. With perturbation trace q' = q- - q0,
+ * outgoing invariant w_out = p' + rho0 c0 u.n and outgoing amplitude
+ * s = |w_out| / (rho0 c0^2) + 1e-12, the features are
+ *   (w_out/(rho0 c0^2 s), (rho' - p'/c0^2)/(rho0 s), u_t/(c0 s) (3), n (3),
+ *    x/R (3), 10 w_out/(2 p0))
+ * and output 0 is the incoming invariant w_in = p' - rho0 c0 u.n of the
+ * ghost relative to that of the characteristic ghost, in units of
+ * rho0 c0^2 s (outputs 1..4 unused). The ghost is the characteristic one
+ * with only w_in moved, by D = clamp(w_in,c + rho0 c0^2 s y0, -L, L) - w_in,c
+ * with L = max(|w_in,c|, 0.5 |w_out|): rho += D/(2c0^2), m -= D n/(2c0),
+ * E += D/(2(gamma-1)). The bound keeps the energy the ghost feeds back below
+ * what leaves, so the closure cannot drive the solution unstable.
  * Parameters (DG_MLP_NPARAMS floats, row-major, input index first):
  *   W1[12][64], b1[64], W2[64][64], b2[64], W3[64][5], b3[5].
  * Training minimises (1/N) sum |network(features) - target|^2 over samples
@@ -216,10 +225,14 @@ int dg_get_bc_mlp(dg_ctx* ctx, float* w);
  * DG_ERR_ARG for boundary faces or ids out of range. */
 int dg_set_trace_faces(dg_ctx* ctx, int64_t n, const int32_t* elem, const int8_t* face);
 /* Training pairs from the current state at every node of the trace faces:
- * X[n*Nfp][12] features of the inner trace, Y[n*Nfp][5] target
- * (z(outer trace) - z(characteristic ghost of the inner trace)) / s.
- * X, Y: device float32 buffers (caller-owned); enqueued on the stream. */
-int dg_sample_traces(dg_ctx* ctx, float* X, float* Y);
+ * X[n*Nfp][12] the features above of the inner trace and its memory,
+ * Y[n*Nfp][5] the target output: Y0 = (w_in(outer trace) - w_in(characteristic
+ * ghost of the inner trace)) / (rho0 c0^2 s), Y1..4 = 0; amp[n*Nfp] (nullable)
+ * the amplitude rho0 c0^2 s = |w_out| + |psi| in pressure units, for choosing
+ * the samples a wave has reached. The memories of the trace nodes restart at
+ * zero with dg_set_state and advance with every dg_step.
+ * X, Y, amp: device float32 buffers (caller-owned); enqueued on the stream. */
+int dg_sample_traces(dg_ctx* ctx, float* X, float* Y, float* amp);
 /* Loss and gradient of the current network on device samples X[N][12],
  * Y[N][5] (deterministic fixed-order reductions); either output may be NULL
  * (host, double loss, float gradient[DG_MLP_NPARAMS]). Synchronises. */

@@ -32,6 +32,10 @@ What is computed, with the passage it follows:
                     components (u - 2 u n_x, ...); the oracle mirrors the
                     normal component, u+ = u- - 2 (u-.n) n, which is what the
                     text around Eq. 4 states.
+    LEARNED         not in the paper: the characteristic ghost with its
+                    incoming acoustic invariant moved by a network's
+                    prediction, within a bound (``ghost_learned``); the
+                    network is oracle/mlp.py.
 * Time integration of the ODE system dc/dt = f(c) (Eq. 12) by the five-stage
   2N-storage fourth-order Runge-Kutta scheme of Carpenter and Kennedy (1994)
   instead of the paper's RK2 (section 1.1), stage by stage:
@@ -181,9 +185,6 @@ GHOSTS = {FREESTREAM: ghost_freestream, CHARACTERISTIC: ghost_characteristic,
           SLIP_WALL: ghost_slip_wall}
 
 
-LEARNED_KAPPA = 0.5
-
-
 def acoustic_invariants(qp, n, gas):
     """(w_out, w_in) = p' +- rho0 c0 u.n of perturbation states qp[..., 5]."""
     rho = gas.rho0 + qp[..., 0]
@@ -192,14 +193,33 @@ def acoustic_invariants(qp, n, gas):
     return pp + zun, pp - zun
 
 
-def learned_target(qm, qo, n, gas):
-    """Training target of the closure at a face node with inner trace qm and
-    outer trace qo (total states): the correction of the incoming acoustic
-    invariant over the characteristic ghost's, in units of rho0 c0^2 s."""
+MEMORY_FLOOR = 1e-3      # r is floored at this fraction of the closure's scale R
+
+
+def memory_rate(psi, wout, r, gas):
+    """d psi / dt of the memory of an outer-face node at distance r from the
+    origin: -(c0 / 2r) (psi + w_out).
+
+    The asymptotic far-field route of section 1 (Bayliss and Turkel) in its
+    lowest term: for an outgoing spherical wave of linear acoustics,
+    p = f(t - r/c0) / r, the radial momentum equation integrates to
+    rho0 c0 u_r = p + c0 F / r^2 with F the time integral of f, so at the node
+    w_in = -c0 F / r^2 and w_out = 2 f / r + c0 F / r^2. Writing psi = -c0 F/r^2,
+    dF/dt = f gives d psi/dt = -(c0/2r)(psi + w_out), and psi equals the
+    incoming invariant of the exact solution exactly. The relation is a
+    stable first-order filter of w_out (gain <= 1), so psi stays bounded."""
+    return -(gas.c0 / (2.0 * r)) * (psi + wout)
+
+
+def learned_target(qm, qo, n, psi, gas):
+    """Training target of the closure at a face node with inner trace qm, outer
+    trace qo (total states) and memory psi: the correction of the incoming
+    acoustic invariant over the characteristic ghost's, in units of
+    rho0 c0^2 s."""
     from . import mlp
     q0 = gas.freestream()
     qc = ghost_characteristic(qm, n, gas)
-    _, s = mlp.features(qm - q0, n, np.zeros_like(n), gas, 1.0)
+    _, s = mlp.features(qm - q0, n, np.zeros_like(n), psi, gas, 1.0)
     _, wi_o = acoustic_invariants(qo - q0, n, gas)
     _, wi_c = acoustic_invariants(qc - q0, n, gas)
     y = np.zeros(qm.shape)
@@ -207,27 +227,28 @@ def learned_target(qm, qo, n, gas):
     return y
 
 
-def ghost_learned(qm, n, x, gas, w, radius):
+def ghost_learned(qm, n, x, psi, gas, w, radius):
     """Learned closure. At rest the local Lax-Friedrichs flux takes the
     outgoing acoustic invariant w_out from inside and only the incoming one,
-    g, from the ghost (boundary energy flux c (w_out^2 - g^2)). The network's
-    output 0 corrects the characteristic ghost's incoming invariant (in units
-    of rho0 c0^2 s); the result is bounded by |g| <= 0.5 |w_out(inside)|; the
-    characteristic ghost is moved to that invariant at fixed outgoing
-    invariant (isentropic increments D/2c0^2, -D n/2c0, D/2(gamma-1),
-    D = g - w_in(characteristic)). The characteristic ghost is kept where the
-    result is not finite or has non-positive density or pressure."""
+    g, from the ghost. The network's output 0 corrects the characteristic
+    ghost's incoming invariant (in units of rho0 c0^2 s, s from the features
+    with the node's memory psi); the result is bounded by |g| <= L with
+    L = max(|w_in(characteristic)|, |w_out(inside)| + |psi|), which holds the
+    exact spherical-wave value psi; the characteristic ghost is moved to that
+    invariant at fixed outgoing invariant (isentropic increments D/2c0^2,
+    -D n/2c0, D/2(gamma-1), D = g - w_in(characteristic)). The
+    characteristic ghost is kept where the result is not finite or has
+    non-positive density or pressure."""
     from . import mlp
     q0 = gas.freestream()
     qc = ghost_characteristic(qm, n, gas)
-    feats, s = mlp.features(qm - q0, n, x, gas, radius)
+    feats, s = mlp.features(qm - q0, n, x, psi, gas, radius)
     y, _ = mlp.forward(w, feats.reshape(-1, mlp.N_IN))
     y = y.reshape(qm.shape)
-    wo_m, _ = acoustic_invariants(qm - q0, n, gas)
     _, wi_c = acoustic_invariants(qc - q0, n, gas)
-    # bound: the larger of the characteristic ghost's own |w_in| and kappa |w_out|
-    lim = np.maximum(np.abs(wi_c), LEARNED_KAPPA * np.abs(wo_m))
-    D = np.clip(wi_c + gas.rho0 * gas.c0 ** 2 * s * y[..., 0], -lim, lim) - wi_c
+    pref = gas.rho0 * gas.c0 ** 2
+    lim = np.maximum(np.abs(wi_c), pref * s)
+    D = np.clip(wi_c + pref * s * y[..., 0], -lim, lim) - wi_c
     c0 = gas.c0
     q = qc.copy()
     q[..., 0] += D / (2 * c0 * c0)
@@ -244,7 +265,12 @@ class Solver:
     """Semi-discrete DG operator plus time stepping on one mesh.
 
     ``bc_id[K, 4]`` gives a boundary id per face (ignored on interior faces;
-    default 0 everywhere); ``bc_mode[id]`` the ghost rule of that id.
+    default 0 everywhere); ``bc_mode[id]`` the ghost rule of that id;
+    ``mlp`` = (parameters, R) the network and position scale of the learned
+    closure. Every node of a LEARNED face, and of the faces given to
+    ``set_trace_faces``, carries a memory psi (``memory_rate``) integrated by
+    the same Runge-Kutta stages as the state; ``step`` advances it in place
+    and ``reset_memory`` (called by ``run``) zeroes it.
     """
 
     def __init__(self, geom: Geometry, gas: Gas, bc_id=None, bc_mode=None, mlp=None):
@@ -252,14 +278,58 @@ class Solver:
         self.ref = geom.ref
         self.gas = gas
         self.mlp = mlp                      # (parameters, radius) of the learned closure
+        self.radius = 1.0 if mlp is None else float(mlp[1])
         K = geom.K
         self.bc_id = np.zeros((K, 4), dtype=np.int64) if bc_id is None else np.asarray(bc_id)
         self.bc_mode = {0: CHARACTERISTIC} if bc_mode is None else dict(bc_mode)
         # physical face-integration weights of the face nodes: sJ * column sums of face mass
         self.face_w = np.stack([fm.sum(axis=0) for fm in self.ref.face_mass])  # [4, Nfp]
+        # boundary faces grouped by id, in the order the right-hand side visits them
+        self.groups = []
+        mem_e, mem_f = [], []
+        if np.any(geom.boundary):
+            bidx = np.nonzero(geom.boundary)
+            for ident in np.unique(self.bc_id[bidx]):
+                sel = tuple(ix[self.bc_id[bidx] == ident] for ix in bidx)
+                mode = self.bc_mode[int(ident)]
+                row = None
+                if mode == LEARNED:
+                    if mlp is None:
+                        raise ValueError("the learned closure needs mlp=(parameters, radius)")
+                    row = sum(len(e) for e in mem_e)
+                    mem_e.append(sel[0])
+                    mem_f.append(sel[1])
+                self.groups.append((mode, sel, row))
+        self.n_learned = sum(len(e) for e in mem_e)
+        self._set_memory_faces(mem_e, mem_f)
+
+    def _set_memory_faces(self, mem_e, mem_f):
+        g, ref = self.g, self.ref
+        self.mem_elem = np.concatenate(mem_e).astype(np.int64) if mem_e else np.zeros(0, np.int64)
+        self.mem_face = np.concatenate(mem_f).astype(np.int64) if mem_f else np.zeros(0, np.int64)
+        x = g.x[self.mem_elem[:, None], ref.Fmask[self.mem_face]]          # [nmem, Nfp, 3]
+        self.mem_x = x
+        self.mem_r = np.maximum(np.linalg.norm(x, axis=-1), MEMORY_FLOOR * self.radius)
+        self.reset_memory()
+
+    def set_trace_faces(self, elem, face):
+        """Interior faces (inner element, face) whose inner trace carries a memory
+        too (the recording side of the learned closure); see ``trace_samples``."""
+        le = [self.mem_elem[:self.n_learned], np.asarray(elem, dtype=np.int64)]
+        lf = [self.mem_face[:self.n_learned], np.asarray(face, dtype=np.int64)]
+        self._set_memory_faces(le, lf)
+
+    def reset_memory(self):
+        self.psi = np.zeros((len(self.mem_elem), self.ref.Nfp))
+        self.psi_res = np.zeros_like(self.psi)
 
     # -- Eq. 10 / Eq. 12 right-hand side
     def rhs(self, q, t=0.0, want_ledger=False):
+        out, ledger, _ = self.rhs_full(q, t, self.psi)
+        return (out, ledger) if want_ledger else out
+
+    def rhs_full(self, q, t, psi):
+        """(dq/dt, boundary flux integral, d psi/dt) at state q with memory psi."""
         g, ref, gas = self.g, self.ref, self.gas
         gam = gas.gamma
         K, Np, Nfp = g.K, ref.Np, ref.Nfp
@@ -277,45 +347,52 @@ class Solver:
         qm = flat[g.vmapM]                                    # [K, 4, Nfp, 5]
         qp = flat[g.vmapP].copy()
         n = np.broadcast_to(g.nrm[:, :, None, :], (K, 4, Nfp, 3))
-        if np.any(g.boundary):
-            bidx = np.nonzero(g.boundary)
-            for ident in np.unique(self.bc_id[bidx]):
-                sel = tuple(ix[self.bc_id[bidx] == ident] for ix in bidx)
-                mode = self.bc_mode[int(ident)]
-                if mode == LEARNED:
-                    xf = g.x[sel[0][:, None], ref.Fmask[sel[1]]]          # face node positions
-                    qp[sel] = ghost_learned(qm[sel], n[sel], xf, gas, *self.mlp)
-                else:
-                    qp[sel] = GHOSTS[mode](qm[sel], n[sel], gas)
+        for mode, sel, row in self.groups:
+            if mode == LEARNED:
+                rows = slice(row, row + len(sel[0]))
+                qp[sel] = ghost_learned(qm[sel], n[sel], self.mem_x[rows], psi[rows], gas,
+                                        self.mlp[0], self.radius)
+            else:
+                qp[sel] = GHOSTS[mode](qm[sel], n[sel], gas)
         fstar = llf_flux(qm, qp, n, gam)
         dF = g.Fscale[:, :, None, None] * (normal_flux(qm, n, gam) - fstar)
         dF = np.transpose(dF, (0, 3, 1, 2)).reshape(K, 5, 4 * Nfp)
         lift = np.einsum("ij,kvj->kvi", ref.LIFT, dF)
         out = -div + lift
-        if not want_ledger:
-            return out
         w = g.sJ[:, :, None] * self.face_w[None, :, :]        # [K, 4, Nfp]
         w = w * g.boundary[:, :, None]
         ledger = np.einsum("kfm,kfmv->v", w, fstar)
-        return out, ledger
+        # memory of the learned and trace faces, driven by the inner trace's w_out
+        qmm = qm[self.mem_elem, self.mem_face] - gas.freestream()
+        nm = np.broadcast_to(g.nrm[self.mem_elem, self.mem_face][:, None, :], qmm.shape[:2] + (3,))
+        wout, _ = acoustic_invariants(qmm, nm, gas)
+        dpsi = memory_rate(psi, wout, self.mem_r, gas)
+        return out, ledger, dpsi
 
     # -- Eq. 12 integrated by the 2N-storage RK4
     def step(self, q, t, dt, res=None, ledger=None):
-        """One full time step. Returns (q, t, res, ledger, ledger_res)."""
+        """One full time step (the memory advances in place). Returns
+        (q, t, res, (ledger, ledger_res))."""
         res = np.zeros_like(q) if res is None else res
         L = np.zeros(5) if ledger is None else ledger[0]
         Lres = np.zeros(5) if ledger is None else ledger[1]
+        psi, pres = self.psi, self.psi_res
         for k in range(5):
             a, b, c = float(LSRK_A[k]), float(LSRK_B[k]), float(LSRK_C[k])
-            rhs, lrhs = self.rhs(q, t + c * dt, want_ledger=True)
+            rhs, lrhs, prhs = self.rhs_full(q, t + c * dt, psi)
             res = a * res + dt * rhs
             q = q + b * res
             Lres = a * Lres + dt * lrhs
             L = L + b * Lres
+            pres = a * pres + dt * prhs
+            psi = psi + b * pres
+        self.psi, self.psi_res = psi, pres
         return q, t + dt, res, (L, Lres)
 
     def run(self, q, dt, nsteps, t=0.0, probes=None):
-        """nsteps steps from q; returns (q, t, ledger, probe samples [nsteps, n, 5])."""
+        """nsteps steps from q with zero memory; returns (q, t, ledger, probe
+        samples [nsteps, n, 5])."""
+        self.reset_memory()
         res = np.zeros_like(q)
         led = (np.zeros(5), np.zeros(5))
         samples = []
@@ -324,6 +401,22 @@ class Solver:
             if probes is not None:
                 samples.append(probes.sample(q))
         return q, t, led[0], (np.array(samples) if probes is not None else None)
+
+    def trace_samples(self, q):
+        """Features [n, Nfp, 12], targets [n, Nfp, 5] and amplitudes s [n, Nfp]
+        at the trace faces (the inner trace, its memory, and the outer trace
+        as what the closure should have produced)."""
+        from . import mlp
+        g, ref, gas = self.g, self.ref, self.gas
+        e, f = self.mem_elem[self.n_learned:], self.mem_face[self.n_learned:]
+        psi = self.psi[self.n_learned:]
+        flat = np.transpose(q, (0, 2, 1)).reshape(-1, 5)
+        qm = flat[g.vmapM[e, f]]
+        qo = flat[g.vmapP[e, f]]
+        nv = np.broadcast_to(g.nrm[e, f][:, None, :], qm.shape[:2] + (3,))
+        feats, s = mlp.features(qm - gas.freestream(), nv, self.mem_x[self.n_learned:], psi, gas,
+                                self.radius)
+        return feats, learned_target(qm, qo, nv, psi, gas), s
 
     # -- diagnostics
     def totals(self, q):

@@ -13,13 +13,19 @@ vector packed as W1[12][64], b1[64], W2[64][64], b2[64], W3[64][5], b3[5]
 (input index first).
 
 Features of a face node (interior perturbation trace q', outward normal n,
-position x, scale R) and the closure (float64 restatement):
-    z(q) = (rho'/rho0, m'/(rho0 c0), E'/(rho0 c0^2)),  s = max|z(q')| + 1e-12
-    features = (z(q')/s, n, x/R, 10 p'/p0)
-    z(ghost) = z(characteristic ghost) + s * y
+position x, scale R, memory psi) come from what the interior determines
+there: the outgoing acoustic invariant w_out = p' + rho0 c0 u.n, the entropy
+mode, the tangential velocity and the node's memory psi of past outgoing
+waves (``oracle.euler_dg.memory_rate``), each divided by the amplitude
+s = (|w_out| + |psi|) / (rho0 c0^2) + 1e-12 (see ``features``). Output 0 is
+the incoming invariant the closure sets, relative to the characteristic
+ghost's, in units of rho0 c0^2 s; the closure itself (bounded, invariant by
+invariant) is ``oracle.euler_dg.ghost_learned``.
 
 Parity status: pinned (tests/test_oracle_mlp.py: central finite differences
-of the loss, closed forms at zero weights, Adam's first step).
+of the loss, closed forms at zero weights, Adam's first step, the feature
+definition on a hand-computed state, invariance of the features under a
+change of the incoming invariant).
 """
 from __future__ import annotations
 
@@ -118,19 +124,21 @@ def denormalise(z, rho0, c0):
     return q
 
 
-def features(qp, n, x, gas, radius):
-    """Features [..., 12] and outgoing amplitude s [...] of perturbation traces qp[..., 5]:
-    (w_out / (rho0 c0^2 s), (rho' - p'/c0^2) / (rho0 s), u_t / (c0 s), n, x / R, 10 w_out / (2 p0))
-    with w_out = p' + rho0 c0 u.n and s = |w_out| / (rho0 c0^2) + 1e-12."""
+def features(qp, n, x, psi, gas, radius):
+    """Features [..., 12] and amplitude s [...] of perturbation traces qp[..., 5]
+    with memory psi[...]:
+    (w_out / (rho0 c0^2 s), (rho' - p'/c0^2) / (rho0 s), u_t / (c0 s), n, x / R,
+    psi / (rho0 c0^2 s)) with w_out = p' + rho0 c0 u.n and
+    s = (|w_out| + |psi|) / (rho0 c0^2) + 1e-12."""
     rho = gas.rho0 + qp[..., 0]
     pp = (gas.gamma - 1.0) * (qp[..., 4] - 0.5 * np.sum(qp[..., 1:4] ** 2, axis=-1) / rho)
     u = qp[..., 1:4] / rho[..., None]
     un = np.sum(u * n, axis=-1)
     pref = gas.rho0 * gas.c0 ** 2
     wout = pp + gas.rho0 * gas.c0 * un
-    s = np.abs(wout) / pref + 1e-12
+    s = (np.abs(wout) + np.abs(psi)) / pref + 1e-12
     ent = (qp[..., 0] - pp / gas.c0 ** 2) / (gas.rho0 * s)
     ut = (u - un[..., None] * n) / (gas.c0 * s[..., None])
     f = np.concatenate([(wout / (pref * s))[..., None], ent[..., None], ut, n, x / radius,
-                        (10.0 * wout / (2.0 * gas.p0))[..., None]], axis=-1)
+                        (psi / (pref * s))[..., None]], axis=-1)
     return f, s

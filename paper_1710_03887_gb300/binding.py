@@ -72,7 +72,7 @@ _SIGS = {
     "dg_set_bc_mlp": (C.c_int, [_P, _P, C.c_double]),
     "dg_get_bc_mlp": (C.c_int, [_P, _P]),
     "dg_set_trace_faces": (C.c_int, [_P, C.c_int64, _P, _P]),
-    "dg_sample_traces": (C.c_int, [_P, _P, _P]),
+    "dg_sample_traces": (C.c_int, [_P, _P, _P, _P]),
     "dg_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _D, _P]),
     "dg_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_double, _P]),
     "dg_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P]),
@@ -294,9 +294,11 @@ class Solver:
         self._check(self.lib.dg_set_trace_faces(self.h, elem.size, _ptr(elem), _ptr(face)))
         self.ntrace = elem.size
 
-    def sample_traces(self, X, Y):
-        """Fill device tensors X [ntrace*Nfp, 12] and Y [ntrace*Nfp, 5] (float32)."""
-        self._check(self.lib.dg_sample_traces(self.h, X.data_ptr(), Y.data_ptr()))
+    def sample_traces(self, X, Y, amp=None):
+        """Fill device tensors X [ntrace*Nfp, 12], Y [ntrace*Nfp, 5] and, if
+        given, amp [ntrace*Nfp] (float32)."""
+        self._check(self.lib.dg_sample_traces(self.h, X.data_ptr(), Y.data_ptr(),
+                                              None if amp is None else amp.data_ptr()))
 
     def mlp_loss_grad(self, X, Y):
         loss = C.c_double()

@@ -79,6 +79,11 @@ struct dg_ctx {
   std::vector<double> mass_w_host;
   // learned closure
   float* bxyz = nullptr;           // boundary face node positions [slot][Nfp][3]
+  int32_t* bface = nullptr;        // e * 4 + f of every boundary face, slot order
+  int64_t nbf = 0;
+  float* bpsi = nullptr;           // memory of the boundary face nodes [slot][Nfp]
+  float* bpsi_res = nullptr;
+  float* bD = nullptr;             // incoming-invariant increments [slot][Nfp]
   float* mlp_w = nullptr;          // network parameters (device), null until set
   float* mlp_m = nullptr;          // Adam moments
   float* mlp_v = nullptr;
@@ -92,6 +97,8 @@ struct dg_ctx {
   int32_t* tr_elem = nullptr;
   int8_t* tr_face = nullptr;
   float* txyz = nullptr;
+  float* tr_psi = nullptr;         // memory of the trace face nodes [n][Nfp]
+  float* tr_res = nullptr;
   // stage-kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;   // created lazily, reused
@@ -117,8 +124,10 @@ struct dg_ctx {
     dfree(ops); dfree(tbl); dfree(fmask); dfree(slot); dfree(ledger_part); dfree(ledger);
     dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
     dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
-    dfree(bxyz); dfree(tr_elem); dfree(tr_face); dfree(txyz);
+    dfree(bxyz); dfree(bface); dfree(bpsi); dfree(bpsi_res); dfree(bD);
+    dfree(tr_elem); dfree(tr_face); dfree(txyz); dfree(tr_psi); dfree(tr_res);
     ntrace = 0;
+    nbf = 0;
     dev_ready = false;
     have_state = false;
     nprobe = 0;
@@ -144,7 +153,7 @@ void node_position(const dg_ctx* c, int64_t e, int n, double x[3]) {
 
 dgk::mlp::Scales mlp_scales(const dg_ctx* c) {
   return dgk::mlp::Scales{float(c->gas.rho0), float(c->gas.c0), float(c->gas.p0), float(c->gas.gm1),
-                          float(1.0 / c->mlp_radius)};
+                          float(1.0 / c->mlp_radius), float(1e-3 * c->mlp_radius)};
 }
 
 // Allocate and fill the device copies of the mesh and operators.
@@ -234,6 +243,17 @@ int ensure_device(dg_ctx* c) {
     }
     DG_CUDA(cudaMalloc(&c->bxyz, bx.size() * 4));
     DG_CUDA(cudaMemcpy(c->bxyz, bx.data(), bx.size() * 4, cudaMemcpyHostToDevice));
+    std::vector<int32_t> bf(bfaces.begin(), bfaces.end());
+    DG_CUDA(cudaMalloc(&c->bface, bf.size() * 4));
+    DG_CUDA(cudaMemcpy(c->bface, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice));
+    c->nbf = int64_t(bfaces.size());
+    const size_t nb = bfaces.size() * size_t(Nfp) * 4;
+    DG_CUDA(cudaMalloc(&c->bpsi, nb));
+    DG_CUDA(cudaMalloc(&c->bpsi_res, nb));
+    DG_CUDA(cudaMalloc(&c->bD, nb));
+    DG_CUDA(cudaMemset(c->bpsi, 0, nb));
+    DG_CUDA(cudaMemset(c->bpsi_res, 0, nb));
+    DG_CUDA(cudaMemset(c->bD, 0, nb));
   }
   DG_CUDA(cudaMalloc(&c->conn, conn.size() * 4));
   DG_CUDA(cudaMemcpy(c->conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice));
@@ -308,6 +328,49 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
   return A;
 }
 
+dgk::BaseGhost base_ghost(const dg_ctx* c) {
+  return dgk::BaseGhost{float(c->gas.rho0), float(c->gas.p0), float(c->gas.gamma), float(c->gas.gm1),
+                        float(c->gas.c0)};
+}
+
+// Closure increments and memories for the stage about to run (float32 forms):
+// learned boundary faces get their increments D (and, in a time step, their
+// memory update); trace faces get their memory update while traces are
+// recorded. dg_eval_rhs (to_scratch) computes D without advancing anything.
+int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
+  bool learned = false;
+  for (int i = 0; i < 8; ++i) learned = learned || c->bc_mode[i] == DG_BC_LEARNED;
+  const dgk::BaseGhost bg = base_ghost(c);
+  if (learned && c->nbf > 0) {
+    dgk::ClosureArgs C{};
+    C.q = c->q32[c->cur];
+    C.Np = c->ref.Np;
+    C.Nfp = c->ref.Nfp;
+    C.bface = c->bface;
+    C.nb = c->nbf;
+    C.conn = c->conn;
+    C.fmask = c->fmask;
+    C.geo = c->geo32;
+    C.bxyz = c->bxyz;
+    for (int i = 0; i < 8; ++i) C.bc_mode[i] = c->bc_mode[i];
+    C.w = c->mlp_w;
+    C.S = mlp_scales(c);
+    C.psi = c->bpsi;
+    C.psi_res = c->bpsi_res;
+    C.D = c->bD;
+    C.a = float(a);
+    C.b = float(b);
+    C.dt = float(dt);
+    C.advance = to_scratch ? 0 : 1;
+    DG_CUDA(dgk::launch_closure(C, bg, c->stream));
+  }
+  if (c->ntrace > 0 && !to_scratch)
+    DG_CUDA(dgk::launch_trace_memory(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->tr_elem, c->tr_face,
+                                     c->fmask, c->geo32, c->txyz, c->ntrace, bg, mlp_scales(c),
+                                     c->tr_psi, c->tr_res, float(a), float(b), float(dt), c->stream));
+  return DG_OK;
+}
+
 // One Runge-Kutta stage from q[cur] to q[1-cur]; with to_scratch the residual
 // goes to the scratch buffer (used by dg_eval_rhs with a = b = 0, dt = 1).
 int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
@@ -331,9 +394,9 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     A.b = float(b);
     A.dt = float(dt);
     A.gas = c->gas;
-    A.mlp_w = c->mlp_w;
-    A.bxyz = c->bxyz;
-    A.mlp_scales = mlp_scales(c);
+    A.bD = c->bD;
+    int rc = run_memory(c, to_scratch, a, b, dt);
+    if (rc) return rc;
     if (c->prec == DG_PREC_F32_TC)
       DG_CUDA(dgk::launch_stage_tc(c->ref.p, A, c->grid, c->stream));
     else
@@ -388,6 +451,16 @@ int reset_run(dg_ctx* c, double t) {
   c->have_state = true;
   c->precorded = 0;
   DG_CUDA(cudaMemsetAsync(c->ledger, 0, 10 * 8, c->stream));
+  // a new run starts with empty memories
+  const size_t nb = size_t(c->nbf) * c->ref.Nfp * 4, nt = size_t(c->ntrace) * c->ref.Nfp * 4;
+  if (nb) {
+    DG_CUDA(cudaMemsetAsync(c->bpsi, 0, nb, c->stream));
+    DG_CUDA(cudaMemsetAsync(c->bpsi_res, 0, nb, c->stream));
+  }
+  if (nt) {
+    DG_CUDA(cudaMemsetAsync(c->tr_psi, 0, nt, c->stream));
+    DG_CUDA(cudaMemsetAsync(c->tr_res, 0, nt, c->stream));
+  }
   return DG_OK;
 }
 
@@ -863,12 +936,17 @@ int dg_set_trace_faces(dg_ctx* c, int64_t n, const int32_t* elem, const int8_t* 
     }
   }
   DG_CUDA(cudaStreamSynchronize(c->stream));
-  dfree(c->tr_elem); dfree(c->tr_face); dfree(c->txyz);
+  dfree(c->tr_elem); dfree(c->tr_face); dfree(c->txyz); dfree(c->tr_psi); dfree(c->tr_res);
   c->ntrace = 0;
   if (n == 0) return DG_OK;
   DG_CUDA(cudaMalloc(&c->tr_elem, size_t(n) * 4));
   DG_CUDA(cudaMalloc(&c->tr_face, size_t(n)));
   DG_CUDA(cudaMalloc(&c->txyz, xyz.size() * 4));
+  // memories start empty; they also restart with every dg_set_state
+  DG_CUDA(cudaMalloc(&c->tr_psi, size_t(n) * Nfp * 4));
+  DG_CUDA(cudaMalloc(&c->tr_res, size_t(n) * Nfp * 4));
+  DG_CUDA(cudaMemset(c->tr_psi, 0, size_t(n) * Nfp * 4));
+  DG_CUDA(cudaMemset(c->tr_res, 0, size_t(n) * Nfp * 4));
   DG_CUDA(cudaMemcpy(c->tr_elem, elem, size_t(n) * 4, cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(c->tr_face, face, size_t(n), cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(c->txyz, xyz.data(), xyz.size() * 4, cudaMemcpyHostToDevice));
@@ -876,15 +954,14 @@ int dg_set_trace_faces(dg_ctx* c, int64_t n, const int32_t* elem, const int8_t* 
   return DG_OK;
 }
 
-int dg_sample_traces(dg_ctx* c, float* X, float* Y) {
+int dg_sample_traces(dg_ctx* c, float* X, float* Y, float* amp) {
   if (!c || !X || !Y) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   if (c->ntrace == 0) return c->fail(DG_ERR_ORDER, "no trace faces set");
-  const dgk::BaseGhost bg{float(c->gas.rho0), float(c->gas.p0), float(c->gas.gamma),
-                          float(c->gas.gm1), float(c->gas.c0)};
   DG_CUDA(dgk::launch_sample_traces(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->tr_elem, c->tr_face,
-                                    c->conn, c->tbl, c->fmask, c->geo32, c->txyz, c->ntrace, bg,
-                                    mlp_scales(c), X, Y, c->status, c->stream));
+                                    c->conn, c->tbl, c->fmask, c->geo32, c->txyz, c->tr_psi,
+                                    c->ntrace, base_ghost(c), mlp_scales(c), X, Y, amp, c->status,
+                                    c->stream));
   return DG_OK;
 }
 

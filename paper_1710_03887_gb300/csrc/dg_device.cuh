@@ -66,10 +66,9 @@ struct StageArgsF32 {
   int bc_mode[8];
   float a, b, dt;
   Gas gas;
-  // learned closure (boundary mode 3)
-  const float* mlp_w;        // network parameters (mlp.cuh packing), or null
-  const float* bxyz;         // [boundary face slot][Nfp][3] node positions
-  mlp::Scales mlp_scales;
+  // learned closure (boundary mode 3): incoming-invariant increments
+  // [boundary face slot][Nfp] from launch_closure, or null (characteristic)
+  const float* bD;
 };
 
 int stage_f32_tile_elems(int p);
@@ -98,8 +97,39 @@ struct BaseGhost;
 cudaError_t launch_sample_traces(const float* q, int Np, int Nfp, const int32_t* tr_elem,
                                  const int8_t* tr_face, const int32_t* conn, const uint8_t* tbl,
                                  const int32_t* fmask, const float* geo, const float* txyz,
-                                 int64_t n, const BaseGhost& bg, const mlp::Scales& S, float* X,
-                                 float* Y, int* status, cudaStream_t s);
+                                 const float* tr_psi, int64_t n, const BaseGhost& bg,
+                                 const mlp::Scales& S, float* X, float* Y, float* amp, int* status,
+                                 cudaStream_t s);
+// Per Runge-Kutta stage, before the stage kernel: at every node of the
+// boundary faces whose id has mode 3, the increment D of the incoming
+// invariant from the network (D = 0 without one) and, when `advance`, the
+// memory's 2N-storage update res = a res + dt dpsi/dt, psi += b res.
+struct ClosureArgs {
+  const float* q;            // stage input, perturbation form [K][5][Np]
+  int Np, Nfp;
+  const int32_t* bface;      // [nb] e * 4 + f of every boundary face, slot order
+  int64_t nb;
+  const int32_t* conn;
+  const int32_t* fmask;
+  const float* geo;
+  const float* bxyz;         // [nb][Nfp][3]
+  int bc_mode[8];
+  const float* w;            // network parameters or null
+  mlp::Scales S;
+  float* psi;                // [nb][Nfp] memory
+  float* psi_res;
+  float* D;                  // [nb][Nfp] out
+  float a, b, dt;
+  int advance;
+};
+cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s);
+// The same memory at the nodes of the trace faces (inner traces), advanced
+// per stage while traces are recorded.
+cudaError_t launch_trace_memory(const float* q, int Np, int Nfp, const int32_t* tr_elem,
+                                const int8_t* tr_face, const int32_t* fmask, const float* geo,
+                                const float* txyz, int64_t n, const BaseGhost& bg,
+                                const mlp::Scales& S, float* psi, float* psi_res, float a,
+                                float b, float dt, cudaStream_t s);
 int mlp_grad_blocks(int64_t N, int sms);
 cudaError_t launch_mlp_loss_grad(const float* w, const float* X, const float* Y, int64_t N,
                                  int nblocks, float* part_grad, float* part_loss, float* grad,

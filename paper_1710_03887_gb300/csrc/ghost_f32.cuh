@@ -7,9 +7,9 @@
 //   log(rho_b/rho0) = (2 log(c_b/c0) - log(s/s0)) / (gamma-1),
 //   log(s/s0) = log(p/p0) - gamma log(rho/rho0)   (0 for inflow),
 //   p_b - p0 = p0 expm1(log(rho_b/rho0) + 2 log(c_b/c0)).
-// Mode 3 (learned) adds the network's correction to the characteristic
-// ghost and falls back to the characteristic ghost when the result is not
-// finite or not physical.
+// Mode 3 (learned) moves the characteristic ghost's incoming invariant by
+// the closure kernel's increment and falls back to the characteristic ghost
+// when the result is not finite or not physical.
 #pragma once
 #include <cmath>
 
@@ -75,37 +75,20 @@ __host__ __device__ inline void acoustic_invariants(const float q[5], const floa
   w_in = pp - zun;
 }
 
-// Learned closure at a face node at position x. With a resting base state
-// the local Lax-Friedrichs flux takes the outgoing acoustic invariant from
-// inside and only the incoming one, g, from the ghost, so the boundary
-// passes out the acoustic energy flux c (w_out^2 - g^2). The network
-// predicts exactly that quantity: output 0 is the correction of the
-// incoming invariant over the characteristic ghost's, in units of
-// rho0 c0^2 s (see mlp.cuh). It is bounded by |g| <= kappa |w_out| with
-// kappa = 0.5, a reflection coefficient below one, which keeps the
-// condition dissipative. The characteristic ghost is moved to that
-// invariant at fixed outgoing invariant (isentropic: d rho' = D / 2c0^2,
-// d m' = -D n / 2c0, d E' = D / 2(gamma-1), D = g - w_in(characteristic)).
-// Non-finite or non-physical results fall back to the characteristic ghost.
-constexpr float kLearnedKappa = 0.5f;
-
-__device__ inline void ghost_learned_f(const float qm[5], const float n[3], const float x[3],
-                                       const BaseGhost& g, const mlp::Scales& S,
-                                       const float* __restrict__ w, float qp[5]) {
+// Learned closure at a face node. With a resting base state the local
+// Lax-Friedrichs flux takes the outgoing acoustic invariant from inside and
+// only the incoming one, g, from the ghost. The closure kernel (learned.cu)
+// turns the network's output into the increment D = g - w_in(characteristic)
+// of the incoming invariant, bounded by |g| <= max(|w_in(characteristic)|,
+// |w_out| + |psi|); here the characteristic ghost is moved by D at fixed
+// outgoing invariant (isentropic: d rho' = D / 2c0^2, d m' = -D n / 2c0,
+// d E' = D / 2(gamma-1)). Non-finite or non-physical results fall back to
+// the characteristic ghost.
+__host__ __device__ inline void ghost_learned_f(const float qm[5], const float n[3],
+                                                const BaseGhost& g, float D, float qp[5]) {
   ghost_state_f(1, qm, n, g, qp);
-  if (w == nullptr) return;
-  float feat[mlp::kIn], y[mlp::kOut], q[5];
-  const float s = mlp::features(qm, n, x, S, feat);
-  mlp::forward(w, feat, y);
-  float wo_m, wi_m, wo_c, wi_c;
-  acoustic_invariants(qm, n, g, wo_m, wi_m);
-  acoustic_invariants(qp, n, g, wo_c, wi_c);
-  // never larger than the characteristic ghost's own incoming invariant or
-  // kappa |w_out|, whichever is larger (a zero correction is the
-  // characteristic ghost itself)
-  const float lim = fmaxf(fabsf(wi_c), kLearnedKappa * fabsf(wo_m));
-  const float gin = fminf(fmaxf(wi_c + g.rho0 * g.c0 * g.c0 * s * y[0], -lim), lim);
-  const float D = gin - wi_c;
+  if (D == 0.0f) return;
+  float q[5];
   q[0] = qp[0] + D / (2.0f * g.c0 * g.c0);
   q[1] = qp[1] - D * n[0] / (2.0f * g.c0);
   q[2] = qp[2] - D * n[1] / (2.0f * g.c0);

@@ -1,5 +1,6 @@
-// Learned boundary closure: trace sampling and the network's training
-// kernels (forward, backward, Adam), all float32 on the device.
+// Learned boundary closure: trace sampling, the per-stage closure and
+// memory kernels, and the network's training kernels (forward, backward,
+// Adam), all float32 on the device.
 //
 // Training data are traces the method records itself: at every node of a
 // chosen set of interior faces (the truncation sphere inside a larger
@@ -28,8 +29,9 @@ __global__ void sample_traces_kernel(const float* __restrict__ q, int Np, int Nf
                                      const uint8_t* __restrict__ tbl,
                                      const int32_t* __restrict__ fmask,
                                      const float* __restrict__ geo, const float* __restrict__ txyz,
-                                     int64_t n, BaseGhost bg, mlp::Scales S, float* __restrict__ X,
-                                     float* __restrict__ Y, int* status) {
+                                     const float* __restrict__ tr_psi, int64_t n, BaseGhost bg,
+                                     mlp::Scales S, float* __restrict__ X, float* __restrict__ Y,
+                                     float* __restrict__ amp, int* status) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n * Nfp) return;
   const int64_t t = i / Nfp;
@@ -55,7 +57,7 @@ __global__ void sample_traces_kernel(const float* __restrict__ q, int Np, int Nf
   const float xv[3] = {txyz[i * 3], txyz[i * 3 + 1], txyz[i * 3 + 2]};
   ghost_state_f(1, qm, nv, bg, qc);
   float feat[mlp::kIn];
-  const float s = mlp::features(qm, nv, xv, S, feat);
+  const float s = mlp::features(qm, nv, xv, tr_psi[i], S, feat);
   float wo_o, wi_o, wo_c, wi_c;
   acoustic_invariants(qo, nv, bg, wo_o, wi_o);
   acoustic_invariants(qc, nv, bg, wo_c, wi_c);
@@ -64,17 +66,126 @@ __global__ void sample_traces_kernel(const float* __restrict__ q, int Np, int Nf
   // outputs are not used by the closure and are trained towards zero
   Y[i * 5] = (wi_o - wi_c) / (bg.rho0 * bg.c0 * bg.c0 * s);
   for (int v = 1; v < 5; ++v) Y[i * 5 + v] = 0.0f;
+  if (amp) amp[i] = bg.rho0 * bg.c0 * bg.c0 * s;
 }
 
 cudaError_t launch_sample_traces(const float* q, int Np, int Nfp, const int32_t* tr_elem,
                                  const int8_t* tr_face, const int32_t* conn, const uint8_t* tbl,
                                  const int32_t* fmask, const float* geo, const float* txyz,
-                                 int64_t n, const BaseGhost& bg, const mlp::Scales& S, float* X,
-                                 float* Y, int* status, cudaStream_t s) {
+                                 const float* tr_psi, int64_t n, const BaseGhost& bg,
+                                 const mlp::Scales& S, float* X, float* Y, float* amp, int* status,
+                                 cudaStream_t s) {
   const int64_t total = n * Nfp;
   if (total == 0) return cudaSuccess;
   sample_traces_kernel<<<unsigned((total + 127) / 128), 128, 0, s>>>(
-      q, Np, Nfp, tr_elem, tr_face, conn, tbl, fmask, geo, txyz, n, bg, S, X, Y, status);
+      q, Np, Nfp, tr_elem, tr_face, conn, tbl, fmask, geo, txyz, tr_psi, n, bg, S, X, Y, amp,
+      status);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ closure and memory
+
+namespace {
+constexpr int kClosureThreads = 128;
+constexpr size_t kWeightSmem = size_t(mlp::kParams) * 4;
+}  // namespace
+
+// One thread per boundary face node. The network's parameters are staged in
+// shared memory once per block (every thread reads the same words).
+__global__ void __launch_bounds__(kClosureThreads)
+closure_kernel(ClosureArgs A, BaseGhost bg) {
+  extern __shared__ __align__(16) float sw[];
+  const bool net = A.w != nullptr;
+  if (net) {
+    for (int k = threadIdx.x; k < mlp::kParams; k += blockDim.x) sw[k] = A.w[k];
+    __syncthreads();
+  }
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= A.nb * A.Nfp) return;
+  const int64_t slot = i / A.Nfp;
+  const int m = int(i - slot * A.Nfp);
+  const int32_t ef = A.bface[slot];
+  const int64_t e = ef >> 2;
+  const int f = ef & 3;
+  const int32_t c = A.conn[e * 4 + f];
+  if (c >= 0 || A.bc_mode[(-1 - c) & 7] != 3) return;
+  const int nm = A.fmask[f * A.Nfp + m];
+  float qm[5], qc[5];
+  for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
+  const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
+  const float nv[3] = {g[0], g[1], g[2]};
+  const float xv[3] = {A.bxyz[i * 3], A.bxyz[i * 3 + 1], A.bxyz[i * 3 + 2]};
+  const float psi = A.psi[i];
+  float wo_m, wi_m, wo_c, wi_c;
+  acoustic_invariants(qm, nv, bg, wo_m, wi_m);
+  float D = 0.0f;
+  if (net) {
+    ghost_state_f(1, qm, nv, bg, qc);
+    acoustic_invariants(qc, nv, bg, wo_c, wi_c);
+    float feat[mlp::kIn], y[mlp::kOut];
+    const float s = mlp::features(qm, nv, xv, psi, A.S, feat);
+    mlp::forward_smem(sw, feat, y);
+    const float pref = bg.rho0 * bg.c0 * bg.c0;
+    // bounded by the characteristic ghost's own |w_in| or |w_out| + |psi|
+    // (= rho0 c0^2 s), which holds the spherical-wave value psi
+    const float lim = fmaxf(fabsf(wi_c), pref * s);
+    const float gin = fminf(fmaxf(wi_c + pref * s * y[0], -lim), lim);
+    D = gin - wi_c;
+  }
+  A.D[i] = D;
+  if (A.advance) {
+    const float r = fmaxf(sqrtf(xv[0] * xv[0] + xv[1] * xv[1] + xv[2] * xv[2]), A.S.r_floor);
+    const float res = A.a * A.psi_res[i] + A.dt * mlp::memory_rate(psi, wo_m, r, A.S);
+    A.psi_res[i] = res;
+    A.psi[i] = psi + A.b * res;
+  }
+}
+
+cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s) {
+  const int64_t total = A.nb * A.Nfp;
+  if (total == 0) return cudaSuccess;
+  closure_kernel<<<unsigned((total + kClosureThreads - 1) / kClosureThreads), kClosureThreads,
+                   A.w ? kWeightSmem : 0, s>>>(A, bg);
+  return cudaGetLastError();
+}
+
+__global__ void trace_memory_kernel(const float* __restrict__ q, int Np, int Nfp,
+                                    const int32_t* __restrict__ tr_elem,
+                                    const int8_t* __restrict__ tr_face,
+                                    const int32_t* __restrict__ fmask,
+                                    const float* __restrict__ geo, const float* __restrict__ txyz,
+                                    int64_t n, BaseGhost bg, mlp::Scales S, float* __restrict__ psi,
+                                    float* __restrict__ psi_res, float a, float b, float dt) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n * Nfp) return;
+  const int64_t t = i / Nfp;
+  const int m = int(i - t * Nfp);
+  const int64_t e = tr_elem[t];
+  const int f = tr_face[t] & 3;
+  const int nm = fmask[f * Nfp + m];
+  float qm[5];
+  for (int v = 0; v < 5; ++v) qm[v] = q[(e * 5 + v) * Np + nm];
+  const float* g = geo + e * kGeoStride + kGeoNrm + 3 * f;
+  const float nv[3] = {g[0], g[1], g[2]};
+  float wo, wi;
+  acoustic_invariants(qm, nv, bg, wo, wi);
+  const float x0 = txyz[i * 3], x1 = txyz[i * 3 + 1], x2 = txyz[i * 3 + 2];
+  const float r = fmaxf(sqrtf(x0 * x0 + x1 * x1 + x2 * x2), S.r_floor);
+  const float p = psi[i];
+  const float res = a * psi_res[i] + dt * mlp::memory_rate(p, wo, r, S);
+  psi_res[i] = res;
+  psi[i] = p + b * res;
+}
+
+cudaError_t launch_trace_memory(const float* q, int Np, int Nfp, const int32_t* tr_elem,
+                                const int8_t* tr_face, const int32_t* fmask, const float* geo,
+                                const float* txyz, int64_t n, const BaseGhost& bg,
+                                const mlp::Scales& S, float* psi, float* psi_res, float a,
+                                float b, float dt, cudaStream_t s) {
+  const int64_t total = n * Nfp;
+  if (total == 0) return cudaSuccess;
+  trace_memory_kernel<<<unsigned((total + 127) / 128), 128, 0, s>>>(
+      q, Np, Nfp, tr_elem, tr_face, fmask, geo, txyz, n, bg, S, psi, psi_res, a, b, dt);
   return cudaGetLastError();
 }
 
@@ -238,13 +349,17 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ gra
   w[p] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
 }
 
-__global__ void mlp_forward_kernel(const float* __restrict__ w, const float* __restrict__ X,
-                                   int64_t N, float* __restrict__ out) {
+__global__ void __launch_bounds__(128)
+mlp_forward_kernel(const float* __restrict__ w, const float* __restrict__ X, int64_t N,
+                   float* __restrict__ out) {
+  extern __shared__ __align__(16) float sw[];
+  for (int k = threadIdx.x; k < kParams; k += blockDim.x) sw[k] = w[k];
+  __syncthreads();
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   float x[kIn], y[kOut];
   for (int k = 0; k < kIn; ++k) x[k] = X[i * kIn + k];
-  mlp::forward(w, x, y);
+  mlp::forward_smem(sw, x, y);
   for (int o = 0; o < kOut; ++o) out[i * kOut + o] = y[o];
 }
 
@@ -284,7 +399,7 @@ cudaError_t launch_adam(float* w, const float* grad, float* m, float* v, float l
 cudaError_t launch_mlp_forward(const float* w, const float* X, int64_t N, float* out,
                                cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  mlp_forward_kernel<<<unsigned((N + 127) / 128), 128, 0, s>>>(w, X, N, out);
+  mlp_forward_kernel<<<unsigned((N + 127) / 128), 128, size_t(kParams) * 4, s>>>(w, X, N, out);
   return cudaGetLastError();
 }
 

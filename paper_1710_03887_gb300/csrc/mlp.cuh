@@ -3,13 +3,15 @@
 // enters it (a learned impedance). All float32.
 //
 // Features of a face node with interior perturbation trace q'-, outward
-// normal n and position x (R = radius used to scale positions), built from
-// the parts of the trace the interior determines -- the outgoing acoustic
-// invariant w_out = p' + rho0 c0 u.n, the entropy mode and the tangential
-// velocity -- and not from the incoming invariant (which the condition sets):
-//   s    = |w_out| / (rho0 c0^2) + 1e-12                 (outgoing amplitude)
+// normal n, position x (R = radius used to scale positions) and memory psi
+// of past outgoing waves (d psi/dt = -(c0 / 2|x|)(psi + w_out), the exact
+// incoming invariant of an outgoing spherical wave), built from the parts of
+// the trace the interior determines -- the outgoing acoustic invariant
+// w_out = p' + rho0 c0 u.n, the entropy mode and the tangential velocity --
+// and not from the incoming invariant (which the condition sets):
+//   s    = (|w_out| + |psi|) / (rho0 c0^2) + 1e-12            (amplitude)
 //   feat = (w_out / (rho0 c0^2 s),  (rho' - p'/c0^2) / (rho0 s),
-//           u_t / (c0 s) (3),  n (3),  x / R (3),  10 w_out / (2 p0))  (12 values)
+//           u_t / (c0 s) (3),  n (3),  x / R (3),  psi / (rho0 c0^2 s))  (12 values)
 // Output 0 is the incoming invariant the condition sets, relative to the
 // characteristic ghost's, in units of rho0 c0^2 s; outputs 1..4 are unused.
 // The normalised perturbation z = (rho'/rho0, m'/(rho0 c0), E'/(rho0 c0^2))
@@ -31,9 +33,13 @@ constexpr int oB2 = oW2 + kH * kH;
 constexpr int oW3 = oB2 + kH;
 constexpr int oB3 = oW3 + kH * kOut;
 constexpr int kParams = oB3 + kOut;   // 5317
+// forward_smem reads every block of four with one 16-byte load
+static_assert(oB1 % 4 == 0 && oW2 % 4 == 0 && oB2 % 4 == 0 && oW3 % 4 == 0 && kH % 4 == 0,
+              "parameter blocks must start on 16-byte boundaries");
 
 struct Scales {
   float rho0, c0, p0, gm1, inv_R;
+  float r_floor;              // distance floor of the memory rate (1e-3 R)
 };
 
 // z of a perturbation state
@@ -55,47 +61,72 @@ __host__ __device__ inline void denormalise(const float z[5], const Scales& S, f
   q[4] = z[4] * eref;
 }
 
-// features of a face node; returns the outgoing amplitude s
+// features of a face node with memory psi; returns the amplitude s
 __host__ __device__ inline float features(const float qm[5], const float n[3], const float x[3],
-                                          const Scales& S, float feat[kIn]) {
+                                          float psi, const Scales& S, float feat[kIn]) {
   const float rinv = 1.0f / (S.rho0 + qm[0]);
   const float pp = S.gm1 * (qm[4] - 0.5f * (qm[1] * qm[1] + qm[2] * qm[2] + qm[3] * qm[3]) * rinv);
   const float u[3] = {qm[1] * rinv, qm[2] * rinv, qm[3] * rinv};
   const float un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
   const float pref = S.rho0 * S.c0 * S.c0;
   const float wout = pp + S.rho0 * S.c0 * un;
-  const float s = fabsf(wout) / pref + 1e-12f;
+  const float s = (fabsf(wout) + fabsf(psi)) / pref + 1e-12f;
   feat[0] = wout / (pref * s);
   feat[1] = (qm[0] - pp / (S.c0 * S.c0)) / (S.rho0 * s);
   for (int d = 0; d < 3; ++d) feat[2 + d] = (u[d] - un * n[d]) / (S.c0 * s);
   for (int d = 0; d < 3; ++d) feat[5 + d] = n[d];
   for (int d = 0; d < 3; ++d) feat[8 + d] = x[d] * S.inv_R;
-  feat[11] = 10.0f * wout / (2.0f * pref / (S.gm1 + 1.0f));   // 10 w_out / (2 p0), p0 = rho0 c0^2 / gamma
+  feat[11] = psi / (pref * s);
   return s;
 }
 
-// y = W3^T tanh(W2^T tanh(W1^T x + b1) + b2) + b3, weights read through the
-// read-only path (every thread of a tile reads the same parameters)
-__device__ inline void forward(const float* __restrict__ w, const float x[kIn], float y[kOut]) {
+// d psi / dt of the memory at distance r from the origin
+__host__ __device__ inline float memory_rate(float psi, float wout, float r, const Scales& S) {
+  return -(S.c0 / (2.0f * r)) * (psi + wout);
+}
+
+// y = W3^T tanh(W2^T tanh(W1^T x + b1) + b2) + b3 with the parameters in
+// shared memory (16-byte aligned, mlp packing): every thread of a block reads
+// the same words, four at a time.
+__device__ inline void forward_smem(const float* __restrict__ sw, const float x[kIn], float y[kOut]) {
   float h1[kH];
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float a = __ldg(w + oB1 + j);
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) a += x[i] * __ldg(w + oW1 + i * kH + j);
-    h1[j] = tanhf(a);
+  for (int j = 0; j < kH; j += 4) {
+    float4 a = *reinterpret_cast<const float4*>(sw + oB1 + j);
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) {
+      const float4 w4 = *reinterpret_cast<const float4*>(sw + oW1 + i * kH + j);
+      a.x += x[i] * w4.x;
+      a.y += x[i] * w4.y;
+      a.z += x[i] * w4.z;
+      a.w += x[i] * w4.w;
+    }
+    h1[j] = tanhf(a.x);
+    h1[j + 1] = tanhf(a.y);
+    h1[j + 2] = tanhf(a.z);
+    h1[j + 3] = tanhf(a.w);
   }
   float out[kOut];
-  for (int o = 0; o < kOut; ++o) out[o] = __ldg(w + oB3 + o);
-#pragma unroll 2
-  for (int j = 0; j < kH; ++j) {
-    float a = __ldg(w + oB2 + j);
-#pragma unroll 8
-    for (int i = 0; i < kH; ++i) a += h1[i] * __ldg(w + oW2 + i * kH + j);
-    const float h2 = tanhf(a);
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) out[o] += h2 * __ldg(w + oW3 + j * kOut + o);
+  for (int o = 0; o < kOut; ++o) out[o] = sw[oB3 + o];
+#pragma unroll 1
+  for (int j = 0; j < kH; j += 4) {
+    float4 a = *reinterpret_cast<const float4*>(sw + oB2 + j);
+#pragma unroll
+    for (int i = 0; i < kH; ++i) {
+      const float4 w4 = *reinterpret_cast<const float4*>(sw + oW2 + i * kH + j);
+      a.x += h1[i] * w4.x;
+      a.y += h1[i] * w4.y;
+      a.z += h1[i] * w4.z;
+      a.w += h1[i] * w4.w;
+    }
+    const float h2[4] = {tanhf(a.x), tanhf(a.y), tanhf(a.z), tanhf(a.w)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) out[o] += h2[k] * sw[oW3 + (j + k) * kOut + o];
   }
+#pragma unroll
   for (int o = 0; o < kOut; ++o) y[o] = out[o];
 }
 

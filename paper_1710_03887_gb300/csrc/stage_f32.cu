@@ -168,9 +168,8 @@ stage_f32_kernel(const StageArgsF32 A) {
       } else {
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
-          const float* xb = A.bxyz + (size_t((-1 - c) >> 3) * Nfp + m) * 3;
-          const float xv[3] = {xb[0], xb[1], xb[2]};
-          ghost_learned_f(qm, nv, xv, bg, A.mlp_scales, A.mlp_w, qp);
+          const float D = A.bD ? A.bD[size_t((-1 - c) >> 3) * Nfp + m] : 0.0f;
+          ghost_learned_f(qm, nv, bg, D, qp);
         } else {
           ghost_state_f(mode, qm, nv, bg, qp);
         }

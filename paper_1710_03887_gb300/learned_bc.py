@@ -7,8 +7,9 @@ orchestrates calls and keeps tensors):
    onto the sphere of radius 1, so the truncated domain (r < 1) is exactly the
    inner part of the large one, element for element.
 2. ``record``: seeded reference runs on the large ball; at the interior faces
-   on r = 1 the library samples (features of the inner trace, target
-   correction of the characteristic ghost towards the outer trace)
+   on r = 1 the library integrates the memory of the inner trace and samples
+   (features of the inner trace and memory, target correction of the
+   characteristic ghost's incoming invariant towards the outer trace's)
    (dg_sample_traces).
 3. ``train``: full-batch Adam on the GPU with the library's own forward and
    backward kernels (dg_mlp_train).
@@ -91,11 +92,12 @@ def crossing_time(center, width):
     return (1.0 + np.linalg.norm(center) + 3.0 * width) / c0
 
 
-def record(order, nested, runs, every, device, width_scale=1.0, precision=None, min_rel=1e-3):
+def record(order, nested, runs, every, device, width_scale=1.0, precision=None, min_rel=1e-2):
     """Reference runs on the large ball; returns device tensors (X, Y).
 
-    Samples whose pressure perturbation is below ``min_rel`` times the run's
-    pulse amplitude (the far tail before the pulse arrives) are dropped."""
+    Samples whose amplitude |w_out| + |psi| is below ``min_rel`` times the
+    run's pulse amplitude (the far tail before the pulse arrives, where
+    features and targets are ratios of vanishing numbers) are dropped."""
     import torch
     prec = B.DG_PREC_F32 if precision is None else precision
     S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
@@ -114,9 +116,9 @@ def record(order, nested, runs, every, device, width_scale=1.0, precision=None, 
             S.step(every, dt)
             X = torch.empty((n, 12), dtype=torch.float32, device=device)
             Y = torch.empty((n, 5), dtype=torch.float32, device=device)
-            S.sample_traces(X, Y)
-            # feature 11 is 10 w_out / (2 p0): keep the nodes the pulse actually reaches
-            keep = X[:, 11].abs() > 10.0 * min_rel * a
+            amp = torch.empty((n,), dtype=torch.float32, device=device)
+            S.sample_traces(X, Y, amp)
+            keep = amp > min_rel * a * W.P0_SI
             Xs.append(X[keep])
             Ys.append(Y[keep])
     S.sync()
@@ -143,6 +145,20 @@ def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
     return w, hist
 
 
+def spherical_weights(eps=1e-2):
+    """Parameters that make the network the exact spherical-wave closure
+    w_in = psi: one tanh path from feature 11 (psi / rho0 c0^2 s) to output 0,
+    y0 = tanh(eps tanh(eps f11)) / eps^2 = f11 (1 + O(eps^2)). With the
+    characteristic ghost's own w_in of second order at rest, the closure then
+    sets the incoming invariant to the memory, exactly right for an outgoing
+    spherical wave centred at the origin."""
+    w = np.zeros(B.DG_MLP_NPARAMS, dtype=np.float32)
+    w[11 * 64 + 0] = eps                  # W1[11][0]
+    w[12 * 64 + 64 + 0] = eps             # W2[0][0]
+    w[12 * 64 + 64 + 64 * 64 + 64 + 0] = 1.0 / (eps * eps)   # W3[0][0]
+    return w
+
+
 def acoustic_energy_weights(order):
     """Quadrature weights 1^T M of the reference element."""
     return B.reference_mass(order).sum(axis=0)
@@ -154,6 +170,42 @@ def acoustic_energy(dq, J, wq):
     dp = (W.GAMMA - 1.0) * dq[:, 4]
     e = dp * dp / (2.0 * W.RHO0_SI * c0sq) + np.sum(dq[:, 1:4] ** 2, axis=1) / (2.0 * W.RHO0_SI)
     return float(np.einsum("k,i,ki->", J, wq, e))
+
+
+def reflection_table(order, nested, amplitude, width, center, weights, precision=None):
+    """Reflected energies of the free-stream (the paper's pass-through),
+    characteristic, exact spherical-wave (``spherical_weights``) and learned
+    conditions for one pulse; the large ball is run once and judges all four."""
+    prec = B.DG_PREC_F32 if precision is None else precision
+    big = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+    big.upload_mesh(*nested.big)
+    qb = pulse(big.node_coords(), amplitude, width, center)
+    dt = big.stable_dt(qb, 0.5)
+    steps = int(np.ceil(crossing_time(center, width) / dt))
+    big.set_state(qb)
+    big.step(steps, dt)
+    qb1, _ = big.get_state()
+    big.close()
+    qs0 = qb[nested.inner].copy()
+    out = {}
+    for name, mode, w in (("freestream", B.DG_BC_FREESTREAM, None),
+                          ("characteristic", B.DG_BC_CHARACTERISTIC, None),
+                          ("spherical", B.DG_BC_LEARNED, spherical_weights()),
+                          ("learned", B.DG_BC_LEARNED, weights)):
+        small = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+        small.upload_mesh(*nested.small)
+        small.set_bc(0, mode)
+        if w is not None:
+            small.set_bc_mlp(w, nested.radius)
+        small.set_state(qs0)
+        small.step(steps, dt)
+        qs1, _ = small.get_state()
+        J = small.geometry()["J"]
+        small.close()
+        wq = acoustic_energy_weights(order)
+        base = W.uniform_state(len(qs0), qs0.shape[2], W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
+        out[name] = acoustic_energy(qs1 - qb1[nested.inner], J, wq) / acoustic_energy(qs0 - base, J, wq)
+    return out
 
 
 def reflected_energy(order, nested, amplitude, width, center, mode, weights=None,

@@ -13,7 +13,6 @@ import pytest
 from oracle import mlp as OM
 from oracle.euler_dg import LEARNED, Gas
 from oracle.euler_dg import Solver as OSolver
-from oracle.euler_dg import learned_target
 from oracle.geometry import Geometry
 from oracle.reference_element import ReferenceElement
 from paper_1710_03887_gb300 import binding as B
@@ -99,6 +98,39 @@ def test_learned_closure_rhs_matches_oracle(cuda_device):
     assert np.abs(orc_c.rhs(q) - ro).max() > 1e-3 * np.abs(ro).max()
 
 
+@pytest.mark.parametrize("prec", [B.DG_PREC_F32, B.DG_PREC_F32_TC])
+def test_learned_closure_run_matches_oracle(cuda_device, prec):
+    """Twenty steps with the closure and its memory against the float64 oracle:
+    the memory grows from zero with the outgoing waves and feeds the network."""
+    p = 2
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=8)
+    gas = Gas(SI["gamma"], SI["rho0"], SI["p0"])
+    geom = Geometry(ReferenceElement(p), xyz, EToV)
+    w = _weights(9, out_scale=0.2)
+    w[11 * 64:12 * 64] *= 20.0                  # make the memory feature matter
+    orc = OSolver(geom, gas, bc_mode={0: LEARNED}, mlp=(w, 1.0))
+    q0 = W.gaussian_pulse_state(geom.x, SI["gamma"], SI["rho0"], SI["p0"], 0.02, 0.3,
+                                center=(0.2, -0.1, 0.1))
+    dt = orc.stable_dt(q0, 0.5)
+    qo, _, _, _ = orc.run(q0, dt, 20)
+    assert np.abs(orc.psi).max() > 1e-3 * 0.02 * SI["p0"]      # the memory is in play
+    S = B.Solver(p, precision=prec, **SI)
+    S.upload_mesh(xyz, EToV)
+    S.set_bc(0, B.DG_BC_LEARNED)
+    S.set_bc_mlp(w.astype(np.float32), 1.0)
+    S.set_state(q0)
+    S.step(20, dt)
+    qg, _ = S.get_state()
+    base = W.uniform_state(geom.K, geom.ref.Np, SI["rho0"], (0, 0, 0), SI["p0"], SI["gamma"])
+    num = np.abs(qg - qo).max(axis=(0, 2))
+    den = np.abs(qo - base).max(axis=(0, 2))
+    assert np.all(num <= 2e-4 * den), num / den
+    # the same run with the characteristic condition ends elsewhere
+    oc = OSolver(geom, gas)
+    qc, _, _, _ = oc.run(q0, dt, 20)
+    assert np.abs(qc - qo).max(axis=(0, 2))[4] > 1e-3 * den[4]     # 5x the tolerance
+
+
 def test_trace_samples_match_oracle(cuda_device):
     import torch
     p = 2
@@ -108,29 +140,46 @@ def test_trace_samples_match_oracle(cuda_device):
     elem, face = L.trace_faces(S, nested)
     assert len(elem) == 12 * 4 ** 2                 # the r = 1 sphere: 2 triangles per lattice square
     S.set_trace_faces(elem, face)
-    ref = ReferenceElement(p)
-    geom = Geometry(ref, *nested.big)
+    geom = Geometry(ReferenceElement(p), *nested.big)
     gas = Gas(SI["gamma"], SI["rho0"], SI["p0"])
-    q = W.random_smooth_state(geom.x, SI["gamma"], SI["rho0"], SI["p0"], 0.05, seed=7)
-    S.set_state(q)
+    q0 = W.gaussian_pulse_state(geom.x, SI["gamma"], SI["rho0"], SI["p0"], 0.05, 0.3,
+                                center=(0.3, 0.2, -0.1))
+    orc = OSolver(geom, gas)
+    orc.set_trace_faces(elem, face)
+    dt = orc.stable_dt(q0, 0.5)
+    steps = 40                                       # the pulse reaches r = 1
+    qo, _, _, _ = orc.run(q0, dt, steps)
+    fo, yo, so = orc.trace_samples(qo)
+    S.set_state(q0)
+    S.step(steps, dt)
     n = len(elem) * S.Nfp
     X = torch.empty((n, 12), dtype=torch.float32, device=cuda_device)
     Y = torch.empty((n, 5), dtype=torch.float32, device=cuda_device)
-    S.sample_traces(X, Y)
+    amp = torch.empty((n,), dtype=torch.float32, device=cuda_device)
+    S.sample_traces(X, Y, amp)
     S.sync()
-    # the same samples in float64 from the oracle's own pairing
-    flat = np.transpose(q, (0, 2, 1)).reshape(-1, 5)
-    qm = flat[geom.vmapM[elem, face]]                # [nf, Nfp, 5]
-    qo = flat[geom.vmapP[elem, face]]
-    nv = np.broadcast_to(geom.nrm[elem, face][:, None, :], qm.shape[:2] + (3,))
-    xf = geom.x[elem[:, None], ref.Fmask[face]]
-    q0 = gas.freestream()
-    fo, s = OM.features(qm - q0, nv, xf, gas, 1.0)
-    yo = learned_target(qm, qo, nv, gas)
-    # features and targets are divided by the outgoing amplitude s, itself a
-    # float32 sum p' + rho0 c0 u_n that partly cancels: relative tolerance
-    np.testing.assert_allclose(X.cpu().numpy(), fo.reshape(-1, 12), rtol=1e-3, atol=2e-5)
-    np.testing.assert_allclose(Y.cpu().numpy(), yo.reshape(-1, 5), rtol=1e-3, atol=2e-4)
+    Xg, Yg, ag = X.cpu().numpy(), Y.cpu().numpy(), amp.cpu().numpy()
+    fo, yo, so = fo.reshape(-1, 12), yo.reshape(-1, 5), so.reshape(-1)
+    assert np.abs(orc.psi).max() > 1e-3 * 0.05 * SI["p0"]     # the memory has filled
+    # compare where the wave has arrived (s above 1e-3 of its largest value):
+    # features and targets are ratios by s, a float32 sum that partly cancels
+    live = so > 1e-3 * so.max()
+    assert live.mean() > 0.5
+    np.testing.assert_allclose(Xg[live], fo[live], rtol=2e-3, atol=2e-3)
+    np.testing.assert_allclose(Yg[live], yo[live], rtol=2e-3, atol=2e-3)
+    np.testing.assert_allclose(ag, so * gas.rho0 * gas.c0 ** 2, rtol=2e-3, atol=1e-3 * ag.max())
+
+
+def test_spherical_closure_absorbs_a_centred_pulse(cuda_device):
+    """The memory on its own, through a network that realises w_in = psi:
+    on the truncated ball a centred pulse leaves with far less reflected
+    energy than under the characteristic condition (the large ball judges)."""
+    nested = L.nested_ball(16)
+    rc, _ = L.reflected_energy(3, nested, 0.01, 0.3, (0.0, 0.0, 0.0), B.DG_BC_CHARACTERISTIC)
+    rs, _ = L.reflected_energy(3, nested, 0.01, 0.3, (0.0, 0.0, 0.0), B.DG_BC_LEARNED,
+                               weights=L.spherical_weights())
+    print("reflected energy, characteristic / spherical:", rc, rs)
+    assert rs < 0.2 * rc
 
 
 def test_learned_closure_beats_characteristic(cuda_device):
@@ -150,4 +199,4 @@ def test_learned_closure_beats_characteristic(cuda_device):
         rl, _ = L.reflected_energy(p, nested, amp, width, centre, B.DG_BC_LEARNED, weights=w)
         gains.append(rc / rl)
     print("reflected energy, characteristic / learned:", gains, "loss", hist[0], hist[-1])
-    assert all(g > 1.05 for g in gains), gains
+    assert all(g > 5.0 for g in gains), gains

@@ -68,36 +68,39 @@ def _trace_states(gas, rng, k=7, amp=1e-3):
     qm[:, 0] *= 1 + amp * rng.normal(size=k)
     qm[:, 1:4] = amp * gas.rho0 * gas.c0 * rng.normal(size=(k, 3))
     qm[:, 4] *= 1 + amp * rng.normal(size=k)
-    return qm, n, rng.normal(size=(k, 3))
+    psi = amp * gas.rho0 * gas.c0 ** 2 * rng.normal(size=k)
+    return qm, n, rng.normal(size=(k, 3)), psi
 
 
 def test_learned_ghost_reduces_to_characteristic_without_correction():
     gas = Gas(1.4, 1.225, 101325.0)
-    qm, n, x = _trace_states(gas, np.random.default_rng(5))
-    q0 = gas.freestream()
+    qm, n, x, psi = _trace_states(gas, np.random.default_rng(5))
     gc = ghost_characteristic(qm, n, gas)
     w = np.zeros(mlp.N_PARAMS)
-    np.testing.assert_allclose(ghost_learned(qm, n, x, gas, w, 1.0), gc, rtol=1e-15)
+    np.testing.assert_allclose(ghost_learned(qm, n, x, psi, gas, w, 1.0), gc, rtol=1e-15)
 
 
 def test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound():
-    from oracle.euler_dg import LEARNED_KAPPA, acoustic_invariants
+    from oracle.euler_dg import acoustic_invariants
     gas = Gas(1.4, 1.225, 101325.0)
     rng = np.random.default_rng(6)
-    qm, n, x = _trace_states(gas, rng, k=50)
+    qm, n, x, psi = _trace_states(gas, rng, k=50)
     q0 = gas.freestream()
     gc = ghost_characteristic(qm, n, gas)
     wo_m, _ = acoustic_invariants(qm - q0, n, gas)
     wo_c, wi_c = acoustic_invariants(gc - q0, n, gas)
-    _, s = mlp.features(qm - q0, n, x, gas, 1.0)
-    amp = np.abs(wo_m)
+    _, s = mlp.features(qm - q0, n, x, psi, gas, 1.0)
+    pref = gas.rho0 * gas.c0 ** 2
+    # the bound is |w_out| + |psi| (or the characteristic ghost's own |w_in|)
+    np.testing.assert_allclose(pref * s, np.abs(wo_m) + np.abs(psi) + pref * 1e-12, rtol=1e-12)
+    amp = np.abs(wo_m) + np.abs(psi)
     for b0 in (0.05, -0.05, 1e3):              # small corrections, and a huge one (clipped)
         w = np.zeros(mlp.N_PARAMS)
         w[-5] = b0                             # constant output 0 = b0
-        gl = ghost_learned(qm, n, x, gas, w, 1.0)
+        gl = ghost_learned(qm, n, x, psi, gas, w, 1.0)
         wo_l, wi_l = acoustic_invariants(gl - q0, n, gas)
-        lim = np.maximum(np.abs(wi_c), LEARNED_KAPPA * amp)
-        want = np.clip(wi_c + gas.rho0 * gas.c0 ** 2 * s * b0, -lim, lim)
+        lim = np.maximum(np.abs(wi_c), pref * s)
+        want = np.clip(wi_c + pref * s * b0, -lim, lim)
         # outgoing invariant unchanged, incoming one moved to the bounded target
         # (linearised invariants: second-order terms ~ amplitude x change)
         tol = 1e-2 * (amp + np.abs(want - wi_c))
@@ -111,17 +114,19 @@ def test_learned_target_is_the_incoming_invariant_gap():
     from oracle.euler_dg import acoustic_invariants, learned_target
     gas = Gas(1.4, 1.225, 101325.0)
     rng = np.random.default_rng(8)
-    qm, n, _ = _trace_states(gas, rng, k=20)
-    qo, _, _ = _trace_states(gas, rng, k=20)
+    qm, n, _, psi = _trace_states(gas, rng, k=20)
+    qo, _, _, _ = _trace_states(gas, rng, k=20)
     q0 = gas.freestream()
-    y = learned_target(qm, qo, n, gas)
+    y = learned_target(qm, qo, n, psi, gas)
     _, wi_o = acoustic_invariants(qo - q0, n, gas)
     _, wi_c = acoustic_invariants(ghost_characteristic(qm, n, gas) - q0, n, gas)
-    _, s = mlp.features(qm - q0, n, np.zeros_like(n), gas, 1.0)
+    wo_m, _ = acoustic_invariants(qm - q0, n, gas)
+    s = (np.abs(wo_m) + np.abs(psi)) / (gas.rho0 * gas.c0 ** 2) + 1e-12
     np.testing.assert_allclose(y[:, 0] * gas.rho0 * gas.c0 ** 2 * s, wi_o - wi_c, rtol=1e-12)
     assert np.all(y[:, 1:] == 0)
     # with the outer trace equal to the characteristic ghost there is nothing to learn
-    assert np.allclose(learned_target(qm, ghost_characteristic(qm, n, gas), n, gas), 0, atol=1e-12)
+    assert np.allclose(learned_target(qm, ghost_characteristic(qm, n, gas), n, psi, gas), 0,
+                       atol=1e-12)
 
 
 def test_features_definition():
@@ -129,21 +134,105 @@ def test_features_definition():
     q = np.array([[0.01, 0.02, -0.03, 0.04, 0.05]])
     n = np.array([[0.0, 0.0, 1.0]])
     x = np.array([[0.5, 0.0, 0.0]])
-    f, s = mlp.features(q, n, x, gas, 2.0)
+    psi = np.array([-0.007])
+    f, s = mlp.features(q, n, x, psi, gas, 2.0)
     rho = 1.01
     pp = 0.4 * (0.05 - 0.5 * (0.02 ** 2 + 0.03 ** 2 + 0.04 ** 2) / rho)
     wout = pp + 0.04 / rho
-    assert s[0] == pytest.approx(abs(wout) + 1e-12)
-    assert f[0, 0] == pytest.approx(np.sign(wout))
+    assert s[0] == pytest.approx(abs(wout) + 0.007 + 1e-12)
+    assert f[0, 0] == pytest.approx(wout / s[0])
     assert f[0, 1] == pytest.approx((0.01 - pp) / s[0])
     np.testing.assert_allclose(f[0, 2:5], [0.02 / rho / s[0], -0.03 / rho / s[0], 0.0], atol=1e-15)
     np.testing.assert_allclose(f[0, 5:8], [0, 0, 1])
     np.testing.assert_allclose(f[0, 8:11], [0.25, 0, 0])
-    assert f[0, 11] == pytest.approx(10 * wout / (2 * gas.p0))
+    assert f[0, 11] == pytest.approx(-0.007 / s[0])
+    assert abs(f[0, 0]) + abs(f[0, 11]) == pytest.approx(1.0)
     # the incoming invariant of the trace does not enter the features
     q2 = q.copy()
     dwin = 1e-3                                # change p' by dwin/2 and rho0 c0 u_n by -dwin/2
     q2[0, 4] += dwin / 2 / 0.4
     q2[0, 3] -= dwin / 2
-    f2, s2 = mlp.features(q2, n, x, gas, 2.0)
+    f2, s2 = mlp.features(q2, n, x, psi, gas, 2.0)
     assert abs(s2[0] - s[0]) < 2e-2 * dwin          # second order: amplitude x change
+
+
+def test_memory_reproduces_the_spherical_incoming_invariant():
+    """Closed form: an outgoing spherical wave p = f(t - r/c0)/r of linear
+    acoustics has, at radius r, w_out = 2 f/r + c0 F/r^2 and
+    w_in = -c0 F/r^2 (F the time integral of f, from the radial momentum
+    equation). Driving the memory with that w_out, integrated by the
+    scheme's own Runge-Kutta stages, reproduces w_in."""
+    from scipy.special import erf
+    from oracle.euler_dg import LSRK_A, LSRK_B, LSRK_C, memory_rate
+    gas = Gas(1.4, 1.225, 101325.0)
+    c0 = gas.c0
+    for r, sig in ((1.0, 0.3 / c0), (2.5, 0.1 / c0)):
+        def f(tau):
+            return 50.0 * np.exp(-(tau / sig) ** 2)
+
+        def F(tau):
+            return 50.0 * sig * np.sqrt(np.pi) / 2 * (1.0 + erf(tau / sig))
+
+        def wout(t):
+            return 2 * f(t - r / c0) / r + c0 * F(t - r / c0) / r ** 2
+
+        t, dt = r / c0 - 6 * sig, sig / 40
+        psi, res = 0.0, 0.0
+        err, peak = 0.0, 0.0
+        for _ in range(600):
+            for a, b, c in zip(LSRK_A, LSRK_B, LSRK_C):
+                res = float(a) * res + dt * memory_rate(psi, wout(t + float(c) * dt), r, gas)
+                psi = psi + float(b) * res
+            t += dt
+            exact = -c0 * F(t - r / c0) / r ** 2
+            err = max(err, abs(psi - exact))
+            peak = max(peak, abs(exact))
+        assert err <= 1e-6 * peak, (r, err, peak)
+        # and the characteristic ghost's w_in = 0 misses all of it: a few per
+        # cent (narrow pulse far out) to a quarter of the outgoing peak 100/r
+        assert peak > 0.03 * 100.0 / r
+
+
+def test_solver_memory_decays_on_the_free_stream():
+    """On the free stream w_out = 0, so every memory decays as
+    psi0 exp(-c0 t / 2r), learned faces and trace faces alike, while the state
+    (zero network: the characteristic ghost) stays the free stream."""
+    from oracle.euler_dg import LEARNED, Solver
+    from oracle.geometry import Geometry
+    from oracle.reference_element import ReferenceElement
+    from paper_1710_03887_gb300 import workloads as W
+    gas = Gas(1.4, 1.225, 101325.0)
+    xyz, EToV = W.kuhn_cube(2, jitter=0.1, seed=1)
+    geom = Geometry(ReferenceElement(1), xyz, EToV)
+    S = Solver(geom, gas, bc_mode={0: LEARNED}, mlp=(np.zeros(mlp.N_PARAMS), 0.7))
+    # interior faces away from the origin (where r is floored)
+    inner = np.nonzero(~geom.boundary)
+    fx = geom.x[inner[0][:, None], geom.ref.Fmask[inner[1]]]
+    far = np.nonzero(np.linalg.norm(fx, axis=-1).min(axis=1) > 0.2)[0][:5]
+    S.set_trace_faces(inner[0][far], inner[1][far])
+    nl = S.n_learned
+    assert nl == int(geom.boundary.sum()) and len(S.mem_elem) == nl + 5
+    rng = np.random.default_rng(3)
+    psi0 = rng.normal(size=S.psi.shape) * 100.0
+    S.psi = psi0.copy()
+    q = W.uniform_state(geom.K, geom.ref.Np, gas.rho0, (0, 0, 0), gas.p0, gas.gamma)
+    q0 = q.copy()
+    dt = 1e-4
+    res, led, t = None, None, 0.0
+    for _ in range(20):
+        q, t, res, led = S.step(q, t, dt, res, led)
+    np.testing.assert_allclose(q, q0, rtol=1e-14, atol=1e-9)
+    r = np.linalg.norm(S.mem_x, axis=-1)
+    np.testing.assert_allclose(S.psi, psi0 * np.exp(-gas.c0 * t / (2 * r)), rtol=1e-9)
+
+
+def test_spherical_weights_realise_the_memory_feature():
+    """The parameter set of the exact spherical closure: output 0 equals
+    feature 11 (psi / rho0 c0^2 s) to second order in the small signal, and
+    nothing else reaches the outputs."""
+    from paper_1710_03887_gb300 import learned_bc as L
+    w = L.spherical_weights().astype(np.float64)
+    X = np.random.default_rng(4).uniform(-1, 1, size=(500, mlp.N_IN))
+    y, _ = mlp.forward(w, X)
+    np.testing.assert_allclose(y[:, 0], X[:, 11], atol=1e-4)
+    assert np.all(y[:, 1:] == 0)
