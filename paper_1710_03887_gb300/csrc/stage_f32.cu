@@ -10,40 +10,18 @@
 //   n.F(q-) - F* = ((n.F')(q'-) - (n.F')(q'+)) / 2 + lambda (q'+ - q'-) / 2,
 // and outer-face ghost states follow the same rules as the float64 path,
 // rewritten in perturbation quantities (ghost_state_f). Fused like the
-// float64 kernel: one launch per stage, operators in shared memory, every
-// face evaluated from both sides, no atomics; GB300's float64 pipe is left
-// idle except for the per-tile boundary-flux sums.
+// float64 kernel: one launch per stage, every face evaluated from both
+// sides, no atomics; GB300's float64 pipe is left idle except for the
+// per-tile boundary-flux sums. The Dr/Ds/Dt contraction and the lift, three
+// quarters of the arithmetic, are one product per (variable, element) row
+// with the operator columns broadcast from shared memory (see OrderF).
 #include <cmath>
+#include <cstdint>
 
 #include "dg_device.cuh"
 #include "ghost_f32.cuh"
 
 namespace dgk {
-
-template <int P>
-struct OrderF {
-  static constexpr int Np = (P + 1) * (P + 2) * (P + 3) / 6;
-  static constexpr int Nfp = (P + 1) * (P + 2) / 2;
-  static constexpr int NF = 4 * Nfp;
-  static constexpr int ET = P == 1 ? 64 : P == 2 ? 32 : P == 3 ? 16 : 8;
-  static constexpr int NT = (ET * Np + 31) / 32 * 32;
-  static constexpr int kOps = 3 * Np * Np + NF * Np + NF;
-  static constexpr int kTbl = 4 * 4 * 6 * Nfp;
-  // shared memory, in floats
-  static constexpr int oOps = 0;
-  static constexpr int oQ = oOps + kOps;
-  static constexpr int oF = oQ + ET * 5 * Np;
-  static constexpr int oDF = oF + ET * 15 * Np;
-  static constexpr int oGeo = oDF + ET * 5 * NF;
-  static constexpr int oEnd = oGeo + ET * kGeoStride;
-  static constexpr int nWarps = NT / 32;
-  // doubles for the ledger reduction, then integers
-  static constexpr size_t oRedB = (size_t(oEnd) * 4 + 15) / 16 * 16;
-  static constexpr size_t oConnB = oRedB + size_t(nWarps) * 5 * 8;
-  static constexpr size_t oFmaskB = oConnB + size_t(ET) * 4 * 4;
-  static constexpr size_t oTblB = oFmaskB + size_t(4) * Nfp * 4;
-  static constexpr size_t bytes = (oTblB + kTbl + 15) / 16 * 16;
-};
 
 struct BaseF {
   float rho0, p0, gamma, gm1, H0;
@@ -52,7 +30,7 @@ struct BaseF {
 // velocity, pressure perturbation and 1/rho of a perturbation state
 __device__ __forceinline__ void prim_f(const float q[5], const BaseF& b, float& rinv, float u[3],
                                        float& pp) {
-  rinv = 1.0f / (b.rho0 + q[0]);
+  rinv = __fdividef(1.0f, b.rho0 + q[0]);          // 2 ulp: far below the form's tolerance
   u[0] = q[1] * rinv;
   u[1] = q[2] * rinv;
   u[2] = q[3] * rinv;
@@ -70,33 +48,105 @@ __device__ __forceinline__ void normal_flux_f(const float q[5], const float n[3]
   fn[2] = q[2] * un + pp * n[1];
   fn[3] = q[3] * un + pp * n[2];
   fn[4] = un * (b.H0 + q[4] + pp);
-  lam = fabsf(un) + sqrtf(b.gamma * (b.p0 + pp) * rinv);
+  const float c2 = b.gamma * (b.p0 + pp) * rinv;
+  lam = fabsf(un) + (c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f);
 }
+
+// 4-byte asynchronous global -> shared copy and its completion
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(int32_t* dst, const int32_t* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group1() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// acc += a * b on two packed float32 lanes (one instruction for two FMAs)
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+// Tile of ET = 32 elements. The node and face phases map threads to
+// (element, node) and (element, face node) items and write one row per
+// (variable, element) of
+//   X = [F_r (Np) | F_s (Np) | F_t (Np) | Fscale (n.F - F*) (NF)],
+// F_a the metric-folded fluxes; the stage's right-hand side is then the
+// product of X with OT = [-Dr | -Ds | -Dt | LIFT]^T (K = 3 Np + NF rows,
+// NP4 = Np rounded up to 4 columns), staged in shared memory. In the product
+// a thread owns one (variable, element) row and one half of K and keeps all
+// Np outputs in registers: per k one load of X (consecutive lanes read
+// consecutive rows of odd stride, no bank conflicts) and NP4/4 warp-uniform
+// 16-byte loads of OT (broadcasts) feed Np FMAs. The two halves' partial
+// sums meet in the Runge-Kutta pass.
+template <int P>
+struct OrderF {
+  static constexpr int Np = (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int Nfp = (P + 1) * (P + 2) / 2;
+  static constexpr int NF = 4 * Nfp;
+  static constexpr int ET = 32;
+  static constexpr int NT = 5 * ET * 2;                     // (variable, element, K half)
+  static constexpr int K = 3 * Np + NF;
+  static constexpr int KH = (K + 1) / 2;
+  static constexpr int SX = K % 2 ? K : K + 1;              // odd row stride of X
+  static constexpr int NP4 = (Np + 3) / 4 * 4;
+  static constexpr int SO = Np % 2 ? Np : Np + 1;           // odd row stride of the partials
+  static constexpr int kTbl = 4 * 4 * 6 * Nfp;
+  // shared memory, in floats: OT [K][NP4] (16-byte aligned rows), two
+  // buffers of the state [le][v][n] (global layout), X [v*ET + le][SX]
+  // (after the product: the two partials [h][v*ET + le][SO]), two buffers of
+  // geometry records, face weights. The second state / geometry /
+  // connection buffer receives the next tile while this one is computed.
+  static constexpr int kQT = ET * 5 * Np;
+  static constexpr int oOT = 0;
+  static constexpr int oQ = oOT + K * NP4;
+  static constexpr int oX = oQ + 2 * kQT;
+  static constexpr int oGeo = oX + 5 * ET * SX;
+  static constexpr int oW = oGeo + 2 * ET * kGeoStride;
+  static constexpr int oEnd = oW + NF;
+  static_assert(2 * 5 * ET * SO <= 5 * ET * SX, "partials fit in the X rows");
+  static constexpr int nWarps = NT / 32;
+  static constexpr size_t oRedB = (size_t(oEnd) * 4 + 15) / 16 * 16;
+  static constexpr size_t oConnB = oRedB + size_t(nWarps) * 5 * 8;
+  static constexpr size_t oFmaskB = oConnB + 2 * size_t(ET) * 4 * 4;
+  static constexpr size_t oTblB = oFmaskB + size_t(4) * Nfp * 4;
+  static constexpr size_t bytes = (oTblB + kTbl + 15) / 16 * 16;
+};
 
 template <int P>
 __global__ void __launch_bounds__(OrderF<P>::NT)
 stage_f32_kernel(const StageArgsF32 A) {
   using O = OrderF<P>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
+  constexpr int K = O::K, KH = O::KH, SX = O::SX, NP4 = O::NP4, SO = O::SO;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
-  float* sOps = sm + O::oOps;
-  float* sQ = sm + O::oQ;
-  float* sF = sm + O::oF;
-  float* sDF = sm + O::oDF;
-  float* sGeo = sm + O::oGeo;
+  float* sOT = sm + O::oOT;
+  float* sX = sm + O::oX;
+  float* faceW = sm + O::oW;
   double* sRed = reinterpret_cast<double*>(smem_raw + O::oRedB);
-  int32_t* sConn = reinterpret_cast<int32_t*>(smem_raw + O::oConnB);
   int32_t* sFmask = reinterpret_cast<int32_t*>(smem_raw + O::oFmaskB);
   uint8_t* sTbl = smem_raw + O::oTblB;
-  const float* DrT = sOps;
-  const float* DsT = sOps + Np * Np;
-  const float* DtT = sOps + 2 * Np * Np;
-  const float* LiftT = sOps + 3 * Np * Np;
-  const float* faceW = LiftT + NF * Np;
   const int tid = threadIdx.x;
 
-  for (int i = tid; i < O::kOps; i += NT) sOps[i] = A.ops[i];
+  // OT from the transposed operators in A.ops ([DrT | DsT | DtT] [j][n] and
+  // LiftT [m][n]), volume rows negated; then the face weights
+  for (int i = tid; i < K * NP4; i += NT) {
+    const int k = i / NP4, n = i - (i / NP4) * NP4;
+    float v = 0.0f;
+    if (n < Np) v = (k < 3 * Np) ? -A.ops[k * Np + n] : A.ops[3 * Np * Np + (k - 3 * Np) * Np + n];
+    sOT[i] = v;
+  }
+  for (int i = tid; i < NF; i += NT) faceW[i] = A.ops[3 * Np * Np + NF * Np + i];
   for (int i = tid; i < O::kTbl; i += NT) sTbl[i] = A.nbr_tbl[i];
   for (int i = tid; i < 4 * Nfp; i += NT) sFmask[i] = A.fmask[i];
   const BaseF b{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
@@ -104,48 +154,89 @@ stage_f32_kernel(const StageArgsF32 A) {
   const BaseGhost bg{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
                      float(A.gas.c0)};
 
-  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+  // asynchronous copy of tile t's state, geometry and connections into buffer bf
+  auto prefetch = [&](int t, int bf) {
+    if (t >= A.ntiles) return;
+    const int64_t f0 = int64_t(t) * ET;
+    const int n = int((A.K - f0) < ET ? (A.K - f0) : int64_t(ET));
+    float* dq = sm + O::oQ + bf * O::kQT;
+    const float* gq = A.q_in + f0 * 5 * Np;
+    if constexpr ((5 * Np) % 4 == 0) {              // 16-byte rows of the state
+      for (int i = tid; i < n * 5 * Np / 4; i += NT) cp_async16(dq + 4 * i, gq + 4 * i);
+    } else {
+      for (int i = tid; i < n * 5 * Np; i += NT) cp_async4(dq + i, gq + i);
+    }
+    float* dg = sm + O::oGeo + bf * ET * kGeoStride;
+    const float* gg = A.geo + f0 * kGeoStride;
+    for (int i = tid; i < n * kGeoStride / 4; i += NT) cp_async16(dg + 4 * i, gg + 4 * i);
+    int32_t* dc = reinterpret_cast<int32_t*>(smem_raw + O::oConnB) + bf * ET * 4;
+    const int32_t* gc = A.conn + f0 * 4;
+    for (int i = tid; i < n; i += NT) cp_async16(dc + 4 * i, gc + 4 * i);
+  };
+  prefetch(blockIdx.x, 0);
+  cp_async_commit();
+
+  int iter = 0;
+  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
-    __syncthreads();
-    {
-      const float* gq = A.q_in + e0 * 5 * Np;
-      for (int i = tid; i < nE * 5 * Np; i += NT) sQ[i] = gq[i];
-      const float* gg = A.geo + e0 * kGeoStride;
-      for (int i = tid; i < nE * kGeoStride; i += NT) sGeo[i] = gg[i];
-      const int32_t* gc = A.conn + e0 * 4;
-      for (int i = tid; i < nE * 4; i += NT) sConn[i] = gc[i];
-    }
-    __syncthreads();
+    const int buf = iter & 1;
+    const float* sQ = sm + O::oQ + buf * O::kQT;
+    const float* sGeo = sm + O::oGeo + buf * ET * kGeoStride;
+    const int32_t* sConn = reinterpret_cast<const int32_t*>(smem_raw + O::oConnB) + buf * ET * 4;
+    cp_async_wait_all();
+    __syncthreads();   // this tile's data is in; the previous tile is finished
 
-    // ---- volume fluxes (perturbation form) at nodes
-    {
-      const int le = tid / Np, n = tid - (tid / Np) * Np;
-      if (le < nE) {
-        float q[5];
-        for (int v = 0; v < 5; ++v) q[v] = sQ[(le * 5 + v) * Np + n];
-        float rinv, u[3], pp;
-        prim_f(q, b, rinv, u, pp);
-        if (!(b.rho0 + q[0] > 0.0f) || !(b.p0 + pp > 0.0f) || !isfinite(q[4]) || !isfinite(pp))
-          atomicOr(A.status, kStatusBadState);
-        const float H = b.H0 + q[4] + pp;
-        float F[3][5];
-        for (int d = 0; d < 3; ++d) {
-          F[d][0] = q[1 + d];
-          F[d][1] = q[1] * u[d];
-          F[d][2] = q[2] * u[d];
-          F[d][3] = q[3] * u[d];
-          F[d][1 + d] += pp;
-          F[d][4] = u[d] * H;
-        }
-        const float* dr = sGeo + le * kGeoStride + kGeoDrdx;
-        for (int a = 0; a < 3; ++a) {
-          const float m0 = dr[a * 3], m1 = dr[a * 3 + 1], m2 = dr[a * 3 + 2];
-          for (int v = 0; v < 5; ++v)
-            sF[(le * 15 + a * 5 + v) * Np + n] = m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v];
-        }
+    // ---- neighbour traces of interior face nodes, copied asynchronously into
+    // the face columns of X (row v, element le, column 3 Np + fm), where the
+    // face phase reads them and then writes the jump; the copies fly while
+    // the node phase computes
+    for (int it = tid; it < nE * NF; it += NT) {
+      const int le = it / NF, fm = it - (it / NF) * NF;
+      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+      const int32_t c = sConn[le * 4 + f];
+      if (c >= 0) {
+        const int64_t e2 = c >> 5;
+        const int f2 = (c >> 3) & 3, o = c & 7;
+        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+        const float* src = A.q_in + e2 * 5 * Np + n2;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async4(sX + (v * ET + le) * SX + 3 * Np + fm, src + v * Np);
       }
     }
+    cp_async_commit();
+    prefetch(tile + gridDim.x, buf ^ 1);
+    cp_async_commit();
+
+    // ---- volume fluxes (perturbation form) at nodes, folded with the metric
+    for (int it = tid; it < nE * Np; it += NT) {
+      const int le = it / Np, n = it - (it / Np) * Np;
+      float q[5];
+      for (int v = 0; v < 5; ++v) q[v] = sQ[(le * 5 + v) * Np + n];
+      float rinv, u[3], pp;
+      prim_f(q, b, rinv, u, pp);
+      if (!(b.rho0 + q[0] > 0.0f) || !(b.p0 + pp > 0.0f) || !isfinite(q[4]) || !isfinite(pp))
+        atomicOr(A.status, kStatusBadState);
+      const float H = b.H0 + q[4] + pp;
+      float F[3][5];
+      for (int d = 0; d < 3; ++d) {
+        F[d][0] = q[1 + d];
+        F[d][1] = q[1] * u[d];
+        F[d][2] = q[2] * u[d];
+        F[d][3] = q[3] * u[d];
+        F[d][1 + d] += pp;
+        F[d][4] = u[d] * H;
+      }
+      const float* dr = sGeo + le * kGeoStride + kGeoDrdx;
+      for (int a = 0; a < 3; ++a) {
+        const float m0 = dr[a * 3], m1 = dr[a * 3 + 1], m2 = dr[a * 3 + 2];
+        for (int v = 0; v < 5; ++v)
+          sX[(v * ET + le) * SX + a * Np + n] = m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v];
+      }
+    }
+
+    cp_async_wait_group1();            // the gathers; the next tile may still fly
+    __syncthreads();
 
     // ---- face fluxes at face nodes
     float led[5] = {0, 0, 0, 0, 0};   // float32 within the tile, float64 across tiles
@@ -155,16 +246,15 @@ stage_f32_kernel(const StageArgsF32 A) {
       const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
       const int n = sFmask[f * Nfp + m];
       float qm[5], qp[5];
+#pragma unroll
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
       const float* geo = sGeo + le * kGeoStride;
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       const int32_t c = sConn[le * 4 + f];
+      float* xf = sX + le * SX + 3 * Np + fm;        // + v * ET * SX
       if (c >= 0) {
-        const int64_t e2 = c >> 5;
-        const int f2 = (c >> 3) & 3, o = c & 7;
-        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-        const float* src = A.q_in + e2 * 5 * Np + n2;
-        for (int v = 0; v < 5; ++v) qp[v] = __ldg(src + v * Np);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qp[v] = xf[v * ET * SX];
       } else {
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
@@ -179,9 +269,10 @@ stage_f32_kernel(const StageArgsF32 A) {
       normal_flux_f(qp, nv, b, fnp, lp);
       const float lam = fmaxf(lm, lp);
       const float fs = geo[kGeoFscale + f];
+#pragma unroll
       for (int v = 0; v < 5; ++v) {
         const float jump = 0.5f * (fnm[v] - fnp[v]) + 0.5f * lam * (qp[v] - qm[v]);
-        sDF[(le * 5 + v) * NF + fm] = fs * jump;
+        xf[v * ET * SX] = fs * jump;
         if (c < 0) {
           const float fstar = 0.5f * (fnm[v] + fnp[v]) - 0.5f * lam * (qp[v] - qm[v]);
           led[v] += faceW[fm] * geo[kGeoSJ + f] * fstar;
@@ -206,37 +297,62 @@ stage_f32_kernel(const StageArgsF32 A) {
     }
     __syncthreads();
 
-    // ---- per node: contraction, lift, Runge-Kutta update
+    // the residuals the Runge-Kutta pass will read, loaded before the product
+    constexpr int RI = (ET * 5 * Np + NT - 1) / NT;
+    const int64_t base = e0 * 5 * Np;
+    float rres[RI];
+#pragma unroll
+    for (int s = 0; s < RI; ++s) {
+      const int i = tid + s * NT;
+      rres[s] = (A.a != 0.0f && i < nE * 5 * Np) ? A.res[base + i] : 0.0f;
+    }
+
+    // ---- X OT: thread = (variable, element, half of K), lane = element;
+    // accumulators hold two output nodes each (packed float32 FMAs)
     {
-      const int le = tid / Np, n = tid - (tid / Np) * Np;
+      const int le = tid & 31, row = tid >> 5;       // row = v + 5 h
+      const int v = row % 5, h = row / 5;
+      const int k0 = h * KH, k1 = (h + 1) * KH < K ? (h + 1) * KH : K;
+      uint64_t acc[NP4 / 2];
+#pragma unroll
+      for (int j = 0; j < NP4 / 2; ++j) acc[j] = 0;
       if (le < nE) {
-        float acc[5] = {0, 0, 0, 0, 0};
-        const float* Fr = sF + (le * 15) * Np;
-        const float* Fs = Fr + 5 * Np;
-        const float* Ft = Fr + 10 * Np;
-#pragma unroll 4
-        for (int j = 0; j < Np; ++j) {
-          const float dr = DrT[j * Np + n], ds = DsT[j * Np + n], dt = DtT[j * Np + n];
+        const float* x = sX + (v * ET + le) * SX;
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+          uint64_t xx;
+          asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(x[k]));
+          const ulonglong2* col = reinterpret_cast<const ulonglong2*>(sOT + k * NP4);
 #pragma unroll
-          for (int v = 0; v < 5; ++v)
-            acc[v] += dr * Fr[v * Np + j] + ds * Fs[v * Np + j] + dt * Ft[v * Np + j];
+          for (int n4 = 0; n4 < NP4 / 4; ++n4) {
+            const ulonglong2 o = col[n4];
+            fma2(acc[2 * n4], o.x, xx);
+            fma2(acc[2 * n4 + 1], o.y, xx);
+          }
         }
-        float out[5];
-        for (int v = 0; v < 5; ++v) out[v] = -acc[v];
-        const float* dF = sDF + (le * 5) * NF;
-#pragma unroll 4
-        for (int m = 0; m < NF; ++m) {
-          const float l = LiftT[m * Np + n];
+      }
+      __syncthreads();                 // every thread has read its X row
+      if (le < nE) {
+        float* o = sX + (h * 5 * ET + v * ET + le) * SO;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) out[v] += l * dF[v * NF + m];
-        }
-        const int64_t base = (e0 + le) * 5 * Np + n;
-        for (int v = 0; v < 5; ++v) {
-          const int64_t ix = base + int64_t(v) * Np;
-          const float r = (A.a != 0.0f) ? A.a * A.res[ix] + A.dt * out[v] : A.dt * out[v];
-          A.res[ix] = r;
-          A.q_out[ix] = sQ[(le * 5 + v) * Np + n] + A.b * r;
-        }
+        for (int n = 0; n < Np; ++n)
+          o[n] = __uint_as_float(uint32_t(n % 2 ? acc[n / 2] >> 32 : acc[n / 2]));
+      }
+    }
+    __syncthreads();
+
+    // ---- Runge-Kutta update, coalesced over the tile's state
+#pragma unroll
+    for (int s = 0; s < RI; ++s) {
+      const int i = tid + s * NT;
+      if (i < nE * 5 * Np) {
+        const int le = i / (5 * Np), r = i - le * 5 * Np;
+        const int v = r / Np, n = r - (r / Np) * Np;
+        const int ro = (v * ET + le) * SO + n;
+        const float rhs = sX[ro] + sX[5 * ET * SO + ro];
+        const float res = A.a * rres[s] + A.dt * rhs;
+        A.res[base + i] = res;
+        A.q_out[base + i] = sQ[i] + A.b * res;
       }
     }
   }
