@@ -81,39 +81,49 @@ __device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
 // (variable, element) of
 //   X = [F_r (Np) | F_s (Np) | F_t (Np) | Fscale (n.F - F*) (NF)],
 // F_a the metric-folded fluxes; the stage's right-hand side is then the
-// product of X with OT = [-Dr | -Ds | -Dt | LIFT]^T (K = 3 Np + NF rows,
-// NP4 = Np rounded up to 4 columns), staged in shared memory. In the product
-// a thread owns one (variable, element) row and one half of K and keeps all
-// Np outputs in registers: per k one load of X (consecutive lanes read
-// consecutive rows of odd stride, no bank conflicts) and NP4/4 warp-uniform
-// 16-byte loads of OT (broadcasts) feed Np FMAs. The two halves' partial
-// sums meet in the Runge-Kutta pass.
+// product of X with OT = [-Dr | -Ds | -Dt | LIFT]^T (K = 3 Np + NF rows),
+// staged in shared memory with its Np columns split into NQ parts of NPQ,
+// each padded to NPQ4 (16-byte aligned). In the product a warp owns one
+// K part (of NK) and one output part, lane = element: per k it loads the
+// five X rows of its element (consecutive lanes read rows of odd stride,
+// no bank conflicts) and the part's OT entries once (warp-uniform 16-byte
+// broadcasts), which feed 5 x NPQ FMAs in packed float32x2 accumulators.
+// The NK partial sums, stored [part][v][n][ET+1] (conflict-free both ways),
+// meet in the Runge-Kutta pass.
 template <int P>
 struct OrderF {
   static constexpr int Np = (P + 1) * (P + 2) * (P + 3) / 6;
   static constexpr int Nfp = (P + 1) * (P + 2) / 2;
   static constexpr int NF = 4 * Nfp;
   static constexpr int ET = 32;
-  static constexpr int NT = 5 * ET * 2;                     // (variable, element, K half)
+  static constexpr int NQ = P == 4 ? 4 : 2;                 // output parts
+  static constexpr int NK = 5;                              // K parts
+  static constexpr int NT = 32 * NQ * NK;
   static constexpr int K = 3 * Np + NF;
-  static constexpr int KH = (K + 1) / 2;
-  static constexpr int SX = K % 2 ? K : K + 1;              // odd row stride of X
-  static constexpr int NP4 = (Np + 3) / 4 * 4;
-  static constexpr int SO = Np % 2 ? Np : Np + 1;           // odd row stride of the partials
+  static constexpr int KP = (K + NK - 1) / NK;
+  static constexpr int NPQ = (Np + NQ - 1) / NQ;
+  static constexpr int NPQ2 = (NPQ + 1) / 2 * 2;
+  static constexpr int NPQ4 = (NPQ + 3) / 4 * 4;
+  static constexpr int OTW = NQ * NPQ4;
+  static constexpr int kPart = 5 * Np * (ET + 1);           // floats of one K part's sums
+  static constexpr int SXmin = (NK * kPart + 5 * ET - 1) / (5 * ET);
+  static constexpr int SX0 = K > SXmin ? K : SXmin;
+  static constexpr int SX = SX0 % 2 ? SX0 : SX0 + 1;        // odd row stride of X
+  static_assert(NK * kPart <= 5 * ET * SX, "partial sums fit in the X rows");
   static constexpr int kTbl = 4 * 4 * 6 * Nfp;
-  // shared memory, in floats: OT [K][NP4] (16-byte aligned rows), two
-  // buffers of the state [le][v][n] (global layout), X [v*ET + le][SX]
-  // (after the product: the two partials [h][v*ET + le][SO]), two buffers of
-  // geometry records, face weights. The second state / geometry /
-  // connection buffer receives the next tile while this one is computed.
+  static constexpr int minBlocks = P == 4 ? 1 : 2;          // CTAs per SM
+  // shared memory, in floats: OT [K][OTW], two buffers of the state
+  // [le][v][n] (global layout), X [v*ET + le][SX] (after the product: the
+  // partial sums), two buffers of geometry records, face weights. The second
+  // state / geometry / connection buffer receives the next tile while this
+  // one is computed.
   static constexpr int kQT = ET * 5 * Np;
   static constexpr int oOT = 0;
-  static constexpr int oQ = oOT + K * NP4;
+  static constexpr int oQ = oOT + K * OTW;
   static constexpr int oX = oQ + 2 * kQT;
   static constexpr int oGeo = oX + 5 * ET * SX;
   static constexpr int oW = oGeo + 2 * ET * kGeoStride;
   static constexpr int oEnd = oW + NF;
-  static_assert(2 * 5 * ET * SO <= 5 * ET * SX, "partials fit in the X rows");
   static constexpr int nWarps = NT / 32;
   static constexpr size_t oRedB = (size_t(oEnd) * 4 + 15) / 16 * 16;
   static constexpr size_t oConnB = oRedB + size_t(nWarps) * 5 * 8;
@@ -123,11 +133,11 @@ struct OrderF {
 };
 
 template <int P>
-__global__ void __launch_bounds__(OrderF<P>::NT)
+__global__ void __launch_bounds__(OrderF<P>::NT, OrderF<P>::minBlocks)
 stage_f32_kernel(const StageArgsF32 A) {
   using O = OrderF<P>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
-  constexpr int K = O::K, KH = O::KH, SX = O::SX, NP4 = O::NP4, SO = O::SO;
+  constexpr int K = O::K, SX = O::SX, NPQ = O::NPQ, NPQ2 = O::NPQ2, NPQ4 = O::NPQ4, OTW = O::OTW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   float* sOT = sm + O::oOT;
@@ -140,10 +150,12 @@ stage_f32_kernel(const StageArgsF32 A) {
 
   // OT from the transposed operators in A.ops ([DrT | DsT | DtT] [j][n] and
   // LiftT [m][n]), volume rows negated; then the face weights
-  for (int i = tid; i < K * NP4; i += NT) {
-    const int k = i / NP4, n = i - (i / NP4) * NP4;
+  for (int i = tid; i < K * OTW; i += NT) {
+    const int k = i / OTW, c = i - (i / OTW) * OTW;
+    const int q = c / NPQ4, j = c - (c / NPQ4) * NPQ4, n = q * NPQ + j;
     float v = 0.0f;
-    if (n < Np) v = (k < 3 * Np) ? -A.ops[k * Np + n] : A.ops[3 * Np * Np + (k - 3 * Np) * Np + n];
+    if (j < NPQ && n < Np)
+      v = (k < 3 * Np) ? -A.ops[k * Np + n] : A.ops[3 * Np * Np + (k - 3 * Np) * Np + n];
     sOT[i] = v;
   }
   for (int i = tid; i < NF; i += NT) faceW[i] = A.ops[3 * Np * Np + NF * Np + i];
@@ -307,36 +319,51 @@ stage_f32_kernel(const StageArgsF32 A) {
       rres[s] = (A.a != 0.0f && i < nE * 5 * Np) ? A.res[base + i] : 0.0f;
     }
 
-    // ---- X OT: thread = (variable, element, half of K), lane = element;
-    // accumulators hold two output nodes each (packed float32 FMAs)
+    // ---- X OT: warp = (K part, output part), lane = element
     {
-      const int le = tid & 31, row = tid >> 5;       // row = v + 5 h
-      const int v = row % 5, h = row / 5;
-      const int k0 = h * KH, k1 = (h + 1) * KH < K ? (h + 1) * KH : K;
-      uint64_t acc[NP4 / 2];
+      const int le = tid & 31, w = tid >> 5;
+      const int kq = w % O::NK, h = w / O::NK;
+      const int k0 = kq * O::KP, k1 = (kq + 1) * O::KP < K ? (kq + 1) * O::KP : K;
+      uint64_t acc[5][NPQ2 / 2];
 #pragma unroll
-      for (int j = 0; j < NP4 / 2; ++j) acc[j] = 0;
+      for (int v = 0; v < 5; ++v)
+#pragma unroll
+        for (int j = 0; j < NPQ2 / 2; ++j) acc[v][j] = 0;
       if (le < nE) {
-        const float* x = sX + (v * ET + le) * SX;
-#pragma unroll 2
+        const float* x = sX + le * SX;                // row v at + v * ET * SX
+        const float* ot = sOT + h * NPQ4;
+#pragma unroll 1
         for (int k = k0; k < k1; ++k) {
-          uint64_t xx;
-          asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(x[k]));
-          const ulonglong2* col = reinterpret_cast<const ulonglong2*>(sOT + k * NP4);
+          uint64_t op[NPQ2 / 2];
 #pragma unroll
-          for (int n4 = 0; n4 < NP4 / 4; ++n4) {
-            const ulonglong2 o = col[n4];
-            fma2(acc[2 * n4], o.x, xx);
-            fma2(acc[2 * n4 + 1], o.y, xx);
+          for (int j = 0; j + 1 < NPQ2 / 2; j += 2) {
+            const ulonglong2 o = *reinterpret_cast<const ulonglong2*>(ot + k * OTW + 2 * j);
+            op[j] = o.x;
+            op[j + 1] = o.y;
+          }
+          if constexpr ((NPQ2 / 2) % 2)
+            op[NPQ2 / 2 - 1] = *reinterpret_cast<const uint64_t*>(ot + k * OTW + NPQ2 - 2);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            uint64_t xx;
+            asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(x[v * ET * SX + k]));
+#pragma unroll
+            for (int j = 0; j < NPQ2 / 2; ++j) fma2(acc[v][j], op[j], xx);
           }
         }
       }
-      __syncthreads();                 // every thread has read its X row
+      __syncthreads();                 // every thread has read its X rows
       if (le < nE) {
-        float* o = sX + (h * 5 * ET + v * ET + le) * SO;
+        float* part = sX + kq * O::kPart + le;        // [v][n][ET + 1]
 #pragma unroll
-        for (int n = 0; n < Np; ++n)
-          o[n] = __uint_as_float(uint32_t(n % 2 ? acc[n / 2] >> 32 : acc[n / 2]));
+        for (int v = 0; v < 5; ++v)
+#pragma unroll
+          for (int j = 0; j < NPQ; ++j) {
+            const int n = h * NPQ + j;
+            if (n < Np)
+              part[(v * Np + n) * (ET + 1)] =
+                  __uint_as_float(uint32_t(j % 2 ? acc[v][j / 2] >> 32 : acc[v][j / 2]));
+          }
       }
     }
     __syncthreads();
@@ -348,8 +375,10 @@ stage_f32_kernel(const StageArgsF32 A) {
       if (i < nE * 5 * Np) {
         const int le = i / (5 * Np), r = i - le * 5 * Np;
         const int v = r / Np, n = r - (r / Np) * Np;
-        const int ro = (v * ET + le) * SO + n;
-        const float rhs = sX[ro] + sX[5 * ET * SO + ro];
+        const float* part = sX + (v * Np + n) * (ET + 1) + le;
+        float rhs = 0.0f;
+#pragma unroll
+        for (int kq = 0; kq < O::NK; ++kq) rhs += part[kq * O::kPart];
         const float res = A.a * rres[s] + A.dt * rhs;
         A.res[base + i] = res;
         A.q_out[base + i] = sQ[i] + A.b * res;
