@@ -12,10 +12,10 @@ five-stage low-storage RK4 time step of the whole mesh.
   e2e        same metric through the C ABI with host buffers: dg_set_state
              from pinned host memory, dg_step, sensor read-back and
              dg_get_state to host, all inside the timed region (wall clock)
-  roofline   stage kernel of the headline form: algorithmic bytes (float32
-             forms, HBM bound) or float64 flops (float64 form, ALU bound) per
-             launch / average launch time (CUDA event pairs around every stage
-             launch on the solver's stream)
+  roofline   stage kernel of the headline form: algorithmic flops (float32
+             and float64 forms, ALU bound) or bytes (tensor-core form, HBM
+             bound) per launch / average launch time (CUDA event pairs around
+             every stage launch on the solver's stream)
   forms      every arithmetic form (float32 perturbation, its tensor-core
              variant, float64) timed the same way, with the float32 forms'
              error against float64 after the timed steps
@@ -71,6 +71,11 @@ def fp64_peak_gflops(sm_mhz=2070.0):
     """Nominal GB300 float64 rate: 1.25 TFLOP/s at the 2070 MHz boost clock over
     152 SMs, i.e. 4 flops per SM per clock; scaled to the given clock."""
     return 152 * 4 * sm_mhz * 1e-3
+
+
+def fp32_peak_tflops(sm_mhz=2070.0):
+    """GB300 float32 FMA rate: 152 SMs x 128 lanes x 2 flop per clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e-6
 
 
 def profiled_traffic(summary, source):
@@ -317,19 +322,32 @@ def roofline_for(m, order):
                 "avg_launch_ms": avg_launch_s * 1e3, "launches": m["klaunch"]}
     peaks = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "of measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "of fallback"
     bytes_per_elem = stage_bytes_per_element(order, 4)
-    achieved = bytes_per_elem * K / avg_launch_s * 1e-9
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm,
-            "traffic": (profiled_traffic("stage_tc_p3_ball.md", "stage_tc.cu")
-                        if m["precision"] == "f32_tc"
-                        else profiled_traffic("stage_f32_p3_ball.md", "stage_f32.cu")),
-            "kernel": "stage_tc_kernel<3>" if m["precision"] == "f32_tc" else "stage_f32_kernel<3>",
+    hbm_achieved = bytes_per_elem * K / avg_launch_s * 1e-9
+    flops = stage_flops_per_element(order) * K / avg_launch_s * 1e-12
+    if m["precision"] == "f32":
+        # 26,600 flop / 1,744 B = 15 flop/B at p=3, above the float32 ridge
+        # (80.5 TFLOP/s / 6.78 TB/s = 12 flop/B): bound by the float32 ALUs
+        peak = fp32_peak_tflops(2070.0)
+        return {"bound": "alu", "achieved": flops, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / peak,
+                "traffic": profiled_traffic("stage_f32_p3_ball.md", "stage_f32.cu"),
+                "kernel": "stage_f32_kernel<3>",
+                "note": ("algorithmic float32 flops per stage (1 FMA = 2); peak = 152 SMs x 128 "
+                         "FMA lanes x 2 flop x 2070 MHz (recipe's unit counts and clock)"),
+                "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": hbm_achieved / hbm, "peak_source": hbm_src},
+                "avg_launch_ms": avg_launch_s * 1e3, "launches": m["klaunch"]}
+    # tensor-core form: the contractions leave the ALUs; the rest (6.6 kflop /
+    # 1,744 B per element) is below the ridge: bound by HBM
+    return {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+            "frac": hbm_achieved / hbm,
+            "traffic": profiled_traffic("stage_tc_p3_ball.md", "stage_tc.cu"),
+            "kernel": "stage_tc_kernel<3>",
             "note": ("algorithmic bytes per stage: q, res read + q, res written (float32), "
-                     "geometry record 128 B, connections 16 B; peak = measured copy bandwidth "
-                     + ("(MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "(fallback)")),
-            "flops_frac_fp32": stage_flops_per_element(order) * K / avg_launch_s
-            / (152 * 256 * 2.07e9),
+                     "geometry record 128 B, connections 16 B; peak " + hbm_src),
+            "flops_frac_fp32": flops / fp32_peak_tflops(2070.0),
             "avg_launch_ms": avg_launch_s * 1e3, "launches": m["klaunch"]}
 
 
