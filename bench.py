@@ -435,7 +435,7 @@ def run_gpu(args, rank, world):
                           f"{state_bytes / (2 if head['precision'] == 'f32' else 1) / 1e6:.0f} MB each); no flush")},
         "e2e": {"value": head["e2e"], "unit": UNIT, "h2d_bytes_per_step": state_bytes / args.steps,
                 "d2h_bytes_per_step": (state_bytes + head["nprobe"] * 5 * 8 * args.steps) / args.steps},
-        "gpu_launches": args.steps * 11,
+        "gpu_launches": args.steps * 6,     # 5 stage kernels (ledger inside) + 1 probe kernel per step
         "roofline": roofline_for(head, w["order"]),
         "clocks": head["clocks"],
     }

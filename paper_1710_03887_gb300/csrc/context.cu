@@ -46,7 +46,7 @@ struct dg_ctx {
   bool have_mesh = false, dev_ready = false, have_state = false;
   double t = 0.0;
   int cur = 0;
-  int ntiles = 0, nslots = 0, grid = 0, sms = 0;
+  int ntiles = 0, grid = 0, sms = 0;
   dgk::Gas gas{};
   // device buffers
   int prec = DG_PREC_FP64;
@@ -64,8 +64,8 @@ struct dg_ctx {
   double* ops = nullptr;
   uint8_t* tbl = nullptr;
   int32_t* fmask = nullptr;
-  int32_t* slot = nullptr;
-  double* ledger_part = nullptr;
+  double* ledger_part = nullptr;   // [grid][5] per-CTA ledger sums
+  unsigned long long* ticket = nullptr;
   double* ledger = nullptr;        // L[5], Lres[5]
   double* mass_w = nullptr;
   double* totals_part = nullptr;   // [kTotalsBlocks*5 + 5]
@@ -121,7 +121,7 @@ struct dg_ctx {
     if (dev_ready) cudaStreamSynchronize(stream);
     clear_events();
     dfree(q[0]); dfree(q[1]); dfree(res); dfree(scratch); dfree(geo); dfree(conn);
-    dfree(ops); dfree(tbl); dfree(fmask); dfree(slot); dfree(ledger_part); dfree(ledger);
+    dfree(ops); dfree(tbl); dfree(fmask); dfree(ticket); dfree(ledger_part); dfree(ledger);
     dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
     dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
     dfree(bxyz); dfree(bface); dfree(bpsi); dfree(bpsi_res); dfree(bD);
@@ -210,11 +210,9 @@ int ensure_device(dg_ctx* c) {
     DG_CUDA(cudaMalloc(&c->geo32, g32.size() * 4));
     DG_CUDA(cudaMemcpy(c->geo32, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice));
   }
-  // face connection words and ledger slots of tiles that own boundary faces
+  // face connection words; boundary faces get a slot (their index in bfaces)
   std::vector<int32_t> conn(size_t(K) * 4);
-  std::vector<int32_t> slot(c->ntiles, -1);
   std::vector<int64_t> bfaces;
-  int nslots = 0;
   for (int64_t e = 0; e < K; ++e)
     for (int f = 0; f < 4; ++f) {
       const size_t i = size_t(e) * 4 + f;
@@ -224,11 +222,8 @@ int ensure_device(dg_ctx* c) {
         // boundary id in the low 3 bits, boundary-face slot above them
         conn[i] = -1 - (c->mesh.bc[i] + 8 * int32_t(bfaces.size()));
         bfaces.push_back(int64_t(i));
-        const int tile = int(e / ET);
-        if (slot[tile] < 0) slot[tile] = nslots++;
       }
     }
-  c->nslots = std::max(nslots, 1);
   // node positions of every boundary face (features of the learned closure)
   if (f32 && !bfaces.empty()) {
     std::vector<float> bx(bfaces.size() * size_t(Nfp) * 3);
@@ -257,10 +252,10 @@ int ensure_device(dg_ctx* c) {
   }
   DG_CUDA(cudaMalloc(&c->conn, conn.size() * 4));
   DG_CUDA(cudaMemcpy(c->conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice));
-  DG_CUDA(cudaMalloc(&c->slot, slot.size() * 4));
-  DG_CUDA(cudaMemcpy(c->slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice));
-  DG_CUDA(cudaMalloc(&c->ledger_part, size_t(c->nslots) * 5 * 8));
-  DG_CUDA(cudaMemset(c->ledger_part, 0, size_t(c->nslots) * 5 * 8));
+  DG_CUDA(cudaMalloc(&c->ledger_part, size_t(c->grid) * 5 * 8));
+  DG_CUDA(cudaMemset(c->ledger_part, 0, size_t(c->grid) * 5 * 8));
+  DG_CUDA(cudaMalloc(&c->ticket, sizeof(unsigned long long)));
+  DG_CUDA(cudaMemset(c->ticket, 0, sizeof(unsigned long long)));
   DG_CUDA(cudaMalloc(&c->ledger, 10 * 8));
   DG_CUDA(cudaMemset(c->ledger, 0, 10 * 8));
   // operators, transposed so that consecutive nodes are consecutive words
@@ -304,8 +299,12 @@ int ensure_device(dg_ctx* c) {
   return DG_OK;
 }
 
+dgk::LedgerArgs ledger_args(dg_ctx* c, bool update, double a, double b, double dt) {
+  return dgk::LedgerArgs{c->ledger_part, c->ledger, c->ticket, a, b, dt, update ? 1 : 0};
+}
+
 dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* res, double a,
-                          double b, double dt) {
+                          double b, double dt, bool update) {
   dgk::StageArgs A{};
   A.q_in = qin;
   A.q_out = qout;
@@ -315,8 +314,7 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
   A.ops = c->ops;
   A.nbr_tbl = c->tbl;
   A.fmask = c->fmask;
-  A.ledger_slot = c->slot;
-  A.ledger_part = c->ledger_part;
+  A.led = ledger_args(c, update, a, b, dt);
   A.status = c->status;
   A.K = c->mesh.K;
   A.ntiles = c->ntiles;
@@ -384,8 +382,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     A.ops = c->ops32;
     A.nbr_tbl = c->tbl;
     A.fmask = c->fmask;
-    A.ledger_slot = c->slot;
-    A.ledger_part = c->ledger_part;
+    A.led = ledger_args(c, !to_scratch, a, b, dt);
     A.status = c->status;
     A.K = c->mesh.K;
     A.ntiles = c->ntiles;
@@ -403,7 +400,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
       DG_CUDA(dgk::launch_stage_f32(c->ref.p, A, c->grid, c->stream));
   } else {
     dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], to_scratch ? c->scratch : c->res,
-                                  a, b, dt);
+                                  a, b, dt, !to_scratch);
     DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
   }
   return DG_OK;
@@ -702,8 +699,6 @@ int dg_step(dg_ctx* c, int n, double dt) {
       if (rc) return rc;
       rc = record_event(c);
       if (rc) return rc;
-      DG_CUDA(dgk::launch_ledger_update(c->ledger_part, c->nslots, c->ledger, kRkA[k], kRkB[k], dt,
-                                        c->stream));
       c->cur = 1 - c->cur;
     }
     c->t += dt;
@@ -725,8 +720,8 @@ int dg_step(dg_ctx* c, int n, double dt) {
 int dg_eval_rhs(dg_ctx* c, double* rhs) {
   if (!c || !rhs) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
-  // one stage with a = b = 0, dt = 1 writes f(q) into the scratch residual;
-  // the ledger slots it touches are rewritten by the next real stage
+  // one stage with a = b = 0, dt = 1 writes f(q) into the scratch residual
+  // and leaves the ledger alone
   int rc = run_stage(c, true, 0.0, 0.0, 1.0);
   if (rc) return rc;
   if (c->prec != DG_PREC_FP64)

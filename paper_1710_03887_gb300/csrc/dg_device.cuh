@@ -29,6 +29,50 @@ struct Gas {
   double gamma, gm1, rho0, p0, u0[3], c0, E0, s_inf;
 };
 
+// Boundary-flux ledger, advanced inside the stage kernels: every CTA writes
+// the sum of its tiles' contributions (in its own fixed tile order) to
+// part[blockIdx.x]; the CTA that takes the last ticket of the launch adds
+// the partials in CTA order and advances ledger = [L(5), Lres(5)] by the
+// same Runge-Kutta stage as the state (res = a res + dt f, L += b res).
+// The ticket counter only grows, so it needs no reset between launches;
+// every CTA of every launch takes exactly one ticket, and all launches of a
+// context use the same grid.
+struct LedgerArgs {
+  double* part;                // [gridDim.x][5]
+  double* ledger;              // [10]
+  unsigned long long* ticket;  // monotone counter
+  double a, b, dt;
+  int update;                  // 0: leave the ledger alone (dg_eval_rhs)
+};
+
+// Called by every thread of every CTA after the tile loop; threads 0..4
+// hold the CTA's sums. Needs at least 160 threads per CTA.
+__device__ inline void ledger_finish(const LedgerArgs& L, double cta_sum) {
+  __shared__ double s_sum[5];
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+  if (tid < 5) s_sum[tid] = cta_sum;
+  __syncthreads();
+  if (tid == 0) {
+    for (int v = 0; v < 5; ++v) L.part[size_t(blockIdx.x) * 5 + v] = s_sum[v];
+    __threadfence();
+    s_last = ((atomicAdd(L.ticket, 1ull) + 1ull) % gridDim.x) == 0ull;
+  }
+  __syncthreads();
+  if (s_last && tid < 160) {       // warp v adds variable v over the CTAs, in a fixed order
+    __threadfence();
+    const int v = tid >> 5, lane = tid & 31;
+    double x = 0.0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) x += __ldcg(L.part + size_t(b) * 5 + v);
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0 && L.update) {
+      const double r = (L.a != 0.0) ? L.a * L.ledger[5 + v] + L.dt * x : L.dt * x;
+      L.ledger[5 + v] = r;
+      L.ledger[v] += L.b * r;
+    }
+  }
+}
+
 struct StageArgs {
   const double* q_in;
   double* q_out;
@@ -38,8 +82,7 @@ struct StageArgs {
   const double* ops;         // DrT | DsT | DtT ([j][i], Np*Np each) | LIFTT ([m][i], NF*Np) | face_w [NF]
   const uint8_t* nbr_tbl;    // [4][4][6][Nfp]: neighbour volume node
   const int32_t* fmask;      // [4][Nfp]
-  const int32_t* ledger_slot;  // [ntiles]: slot in ledger_part, or -1 (no boundary face)
-  double* ledger_part;       // [nslots][5]
+  LedgerArgs led;
   int* status;
   int64_t K;
   int ntiles;
@@ -58,8 +101,7 @@ struct StageArgsF32 {
   const float* ops;          // same packing as StageArgs::ops, float32
   const uint8_t* nbr_tbl;
   const int32_t* fmask;
-  const int32_t* ledger_slot;
-  double* ledger_part;
+  LedgerArgs led;
   int* status;
   int64_t K;
   int ntiles;
@@ -145,8 +187,6 @@ size_t stage_smem_bytes(int p);
 cudaError_t stage_prepare(int p, int* blocks_per_sm);
 cudaError_t launch_stage(int p, const StageArgs& a, int grid, cudaStream_t s);
 
-cudaError_t launch_ledger_update(const double* part, int nslots, double* ledger, double a,
-                                 double b, double dt, cudaStream_t s);
 cudaError_t launch_probe_sample(const double* q, int Np, int n, const int32_t* elem,
                                 const double* rows, double* out, cudaStream_t s);
 cudaError_t launch_totals(const double* q, const double* geo, const double* mass_w, int64_t K,

@@ -189,6 +189,7 @@ stage_f32_kernel(const StageArgsF32 A) {
   cp_async_commit();
 
   int iter = 0;
+  double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
@@ -303,8 +304,7 @@ stage_f32_kernel(const StageArgsF32 A) {
       if (tid < 5) {
         double acc = 0.0;
         for (int w = 0; w < O::nWarps; ++w) acc += sRed[w * 5 + tid];
-        const int slot = A.ledger_slot[tile];
-        if (slot >= 0) A.ledger_part[size_t(slot) * 5 + tid] = acc;
+        cled += acc;
       }
     }
     __syncthreads();
@@ -385,6 +385,7 @@ stage_f32_kernel(const StageArgsF32 A) {
       }
     }
   }
+  ledger_finish(A.led, cled);
 }
 
 int stage_f32_tile_elems(int p) {

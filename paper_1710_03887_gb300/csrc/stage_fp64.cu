@@ -82,6 +82,7 @@ stage_fp64_kernel(const StageArgs A) {
   for (int i = tid; i < 4 * Nfp; i += NT) sFmask[i] = A.fmask[i];
   const Gas g = A.gas;
 
+  double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
@@ -169,8 +170,7 @@ stage_fp64_kernel(const StageArgs A) {
       if (tid < 5) {
         double acc = 0.0;
         for (int w = 0; w < O::nWarps; ++w) acc += sRed[w * 5 + tid];
-        const int slot = A.ledger_slot[tile];
-        if (slot >= 0) A.ledger_part[size_t(slot) * 5 + tid] = acc;
+        cled += acc;
       }
     }
     __syncthreads();
@@ -209,6 +209,7 @@ stage_fp64_kernel(const StageArgs A) {
       }
     }
   }
+  ledger_finish(A.led, cled);
 }
 
 int stage_tile_elems(int p) {
@@ -259,36 +260,6 @@ cudaError_t launch_stage(int p, const StageArgs& a, int grid, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------- small kernels
-
-// Sum the tiles' ledger contributions in a fixed order and advance the ledger
-// by the same Runge-Kutta stage as the state: ledger = [L(5), Lres(5)].
-__global__ void ledger_update_kernel(const double* part, int nslots, double* ledger, double a,
-                                     double b, double dt) {
-  __shared__ double red[256 * 5];
-  const int tid = threadIdx.x;
-  double acc[5] = {0, 0, 0, 0, 0};
-  for (int i = tid; i < nslots; i += blockDim.x)
-    for (int v = 0; v < 5; ++v) acc[v] += part[size_t(i) * 5 + v];
-  for (int v = 0; v < 5; ++v) red[tid * 5 + v] = acc[v];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (tid < w)
-      for (int v = 0; v < 5; ++v) red[tid * 5 + v] += red[(tid + w) * 5 + v];
-    __syncthreads();
-  }
-  if (tid < 5) {
-    const double f = red[tid];
-    const double r = (a != 0.0) ? a * ledger[5 + tid] + dt * f : dt * f;
-    ledger[5 + tid] = r;
-    ledger[tid] += b * r;
-  }
-}
-
-cudaError_t launch_ledger_update(const double* part, int nslots, double* ledger, double a,
-                                 double b, double dt, cudaStream_t s) {
-  ledger_update_kernel<<<1, 256, 0, s>>>(part, nslots, ledger, a, b, dt);
-  return cudaGetLastError();
-}
 
 // Sensor values: out[probe][v] = sum_n row[probe][n] q[elem][v][n]
 __global__ void probe_kernel(const double* q, int Np, int n, const int32_t* elem,

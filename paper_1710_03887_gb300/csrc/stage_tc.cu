@@ -147,6 +147,7 @@ stage_tc_kernel(const StageArgsF32 A) {
   constexpr uint32_t idesc = tc::idesc_tf32(O::M, O::N);
   uint32_t phase = 0;
 
+  double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
@@ -273,8 +274,7 @@ stage_tc_kernel(const StageArgsF32 A) {
       if (tid < 5) {
         double acc = 0.0;
         for (int w = 0; w < NT / 32; ++w) acc += sRed[w * 5 + tid];
-        const int slot = A.ledger_slot[tile];
-        if (slot >= 0) A.ledger_part[size_t(slot) * 5 + tid] = acc;
+        cled += acc;
       }
     }
 
@@ -315,6 +315,7 @@ stage_tc_kernel(const StageArgsF32 A) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, 32);
   }
+  ledger_finish(A.led, cled);
 }
 
 size_t stage_tc_ops_bytes(int p) {
