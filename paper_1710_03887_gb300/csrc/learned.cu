@@ -122,9 +122,9 @@ closure_kernel(ClosureArgs A, BaseGhost bg) {
   if (net) {
     ghost_state_f(1, qm, nv, bg, qc);
     acoustic_invariants(qc, nv, bg, wo_c, wi_c);
-    float feat[mlp::kIn], y[mlp::kOut];
+    float feat[mlp::kIn], y[1];
     const float s = mlp::features(qm, nv, xv, psi, A.S, feat);
-    mlp::forward_smem(sw, feat, y);
+    mlp::forward_smem<1>(sw, feat, y);              // output 0 only
     const float pref = bg.rho0 * bg.c0 * bg.c0;
     // bounded by the characteristic ghost's own |w_in| or |w_out| + |psi|
     // (= rho0 c0^2 s), which holds the spherical-wave value psi
@@ -359,7 +359,7 @@ mlp_forward_kernel(const float* __restrict__ w, const float* __restrict__ X, int
   if (i >= N) return;
   float x[kIn], y[kOut];
   for (int k = 0; k < kIn; ++k) x[k] = X[i * kIn + k];
-  mlp::forward_smem(sw, x, y);
+  mlp::forward_smem<kOut>(sw, x, y);
   for (int o = 0; o < kOut; ++o) out[i * kOut + o] = y[o];
 }
 

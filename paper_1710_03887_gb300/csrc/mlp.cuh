@@ -85,49 +85,80 @@ __host__ __device__ inline float memory_rate(float psi, float wout, float r, con
   return -(S.c0 / (2.0f * r)) * (psi + wout);
 }
 
+// acc += a * b on two packed float32 lanes (one instruction for two FMAs)
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ uint64_t dup2(float x) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lo2(uint64_t v) { return __uint_as_float(uint32_t(v)); }
+__device__ __forceinline__ float hi2(uint64_t v) { return __uint_as_float(uint32_t(v >> 32)); }
+
 // y = W3^T tanh(W2^T tanh(W1^T x + b1) + b2) + b3 with the parameters in
-// shared memory (16-byte aligned, mlp packing): every thread of a block reads
-// the same words, four at a time.
-__device__ inline void forward_smem(const float* __restrict__ sw, const float x[kIn], float y[kOut]) {
+// shared memory (16-byte aligned, mlp packing): every thread of a block
+// reads the same words. Hidden units go in groups of eight, two per packed
+// float32x2 FMA; outputs [0, NOUT) are formed (NOUT = 1: the closure's only
+// output).
+template <int NOUT>
+__device__ inline void forward_smem(const float* __restrict__ sw, const float x[kIn],
+                                    float y[NOUT]) {
+  uint64_t xx[kIn];
+#pragma unroll
+  for (int i = 0; i < kIn; ++i) xx[i] = dup2(x[i]);
   float h1[kH];
 #pragma unroll
-  for (int j = 0; j < kH; j += 4) {
-    float4 a = *reinterpret_cast<const float4*>(sw + oB1 + j);
+  for (int j = 0; j < kH; j += 8) {
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(sw + oB1 + j);
+    const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(sw + oB1 + j + 4);
+    uint64_t a[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
     for (int i = 0; i < kIn; ++i) {
-      const float4 w4 = *reinterpret_cast<const float4*>(sw + oW1 + i * kH + j);
-      a.x += x[i] * w4.x;
-      a.y += x[i] * w4.y;
-      a.z += x[i] * w4.z;
-      a.w += x[i] * w4.w;
+      const ulonglong2 w0 = *reinterpret_cast<const ulonglong2*>(sw + oW1 + i * kH + j);
+      const ulonglong2 w1 = *reinterpret_cast<const ulonglong2*>(sw + oW1 + i * kH + j + 4);
+      fma2(a[0], w0.x, xx[i]);
+      fma2(a[1], w0.y, xx[i]);
+      fma2(a[2], w1.x, xx[i]);
+      fma2(a[3], w1.y, xx[i]);
     }
-    h1[j] = tanhf(a.x);
-    h1[j + 1] = tanhf(a.y);
-    h1[j + 2] = tanhf(a.z);
-    h1[j + 3] = tanhf(a.w);
-  }
-  float out[kOut];
 #pragma unroll
-  for (int o = 0; o < kOut; ++o) out[o] = sw[oB3 + o];
+    for (int k = 0; k < 4; ++k) {
+      h1[j + 2 * k] = tanhf(lo2(a[k]));
+      h1[j + 2 * k + 1] = tanhf(hi2(a[k]));
+    }
+  }
+  float out[NOUT];
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) out[o] = sw[oB3 + o];
 #pragma unroll 1
-  for (int j = 0; j < kH; j += 4) {
-    float4 a = *reinterpret_cast<const float4*>(sw + oB2 + j);
+  for (int j = 0; j < kH; j += 8) {
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(sw + oB2 + j);
+    const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(sw + oB2 + j + 4);
+    uint64_t a[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
     for (int i = 0; i < kH; ++i) {
-      const float4 w4 = *reinterpret_cast<const float4*>(sw + oW2 + i * kH + j);
-      a.x += h1[i] * w4.x;
-      a.y += h1[i] * w4.y;
-      a.z += h1[i] * w4.z;
-      a.w += h1[i] * w4.w;
+      const uint64_t hh = dup2(h1[i]);
+      const ulonglong2 w0 = *reinterpret_cast<const ulonglong2*>(sw + oW2 + i * kH + j);
+      const ulonglong2 w1 = *reinterpret_cast<const ulonglong2*>(sw + oW2 + i * kH + j + 4);
+      fma2(a[0], w0.x, hh);
+      fma2(a[1], w0.y, hh);
+      fma2(a[2], w1.x, hh);
+      fma2(a[3], w1.y, hh);
     }
-    const float h2[4] = {tanhf(a.x), tanhf(a.y), tanhf(a.z), tanhf(a.w)};
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 4; ++k) {
+      const float h2a = tanhf(lo2(a[k])), h2b = tanhf(hi2(a[k]));
 #pragma unroll
-      for (int o = 0; o < kOut; ++o) out[o] += h2[k] * sw[oW3 + (j + k) * kOut + o];
+      for (int o = 0; o < NOUT; ++o) {
+        out[o] += h2a * sw[oW3 + (j + 2 * k) * kOut + o];
+        out[o] += h2b * sw[oW3 + (j + 2 * k + 1) * kOut + o];
+      }
+    }
   }
 #pragma unroll
-  for (int o = 0; o < kOut; ++o) y[o] = out[o];
+  for (int o = 0; o < NOUT; ++o) y[o] = out[o];
 }
 
 }  // namespace mlp
