@@ -328,8 +328,18 @@ class Solver:
         out, ledger, _ = self.rhs_full(q, t, self.psi)
         return (out, ledger) if want_ledger else out
 
+    def rhs_parts(self, q):
+        """The inputs of the two contractions of Eq. 10 at state q: the
+        metric-folded fluxes Ft [K, 3, 5, Np] (F~_r, F~_s, F~_t) and the face
+        terms dF [K, 5, 4 Nfp], so that
+        rhs = -(Dr Ft_r + Ds Ft_s + Dt Ft_t) + LIFT dF."""
+        return self._rhs(q, self.psi, parts=True)
+
     def rhs_full(self, q, t, psi):
         """(dq/dt, boundary flux integral, d psi/dt) at state q with memory psi."""
+        return self._rhs(q, psi)
+
+    def _rhs(self, q, psi, parts=False):
         g, ref, gas = self.g, self.ref, self.gas
         gam = gas.gamma
         K, Np, Nfp = g.K, ref.Np, ref.Nfp
@@ -342,6 +352,9 @@ class Solver:
             for b in range(3):
                 dab = np.einsum("ij,kvj->kvi", D[a], flux[b])
                 div += g.drdx[:, a, b][:, None, None] * dab
+        if parts:
+            Ft = np.stack([sum(g.drdx[:, a, b][:, None, None] * flux[b] for b in range(3))
+                           for a in range(3)], axis=1)
         # face traces
         flat = qn.reshape(K * Np, 5)
         qm = flat[g.vmapM]                                    # [K, 4, Nfp, 5]
@@ -357,6 +370,8 @@ class Solver:
         fstar = llf_flux(qm, qp, n, gam)
         dF = g.Fscale[:, :, None, None] * (normal_flux(qm, n, gam) - fstar)
         dF = np.transpose(dF, (0, 3, 1, 2)).reshape(K, 5, 4 * Nfp)
+        if parts:
+            return Ft, dF
         lift = np.einsum("ij,kvj->kvi", ref.LIFT, dF)
         out = -div + lift
         w = g.sJ[:, :, None] * self.face_w[None, :, :]        # [K, 4, Nfp]

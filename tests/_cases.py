@@ -82,3 +82,26 @@ class Case:
 
 __all__ = ["Case", "rel_err", "state_err", "direction_tags", "SI", "SCALED", "CHARACTERISTIC", "FREESTREAM",
            "SLIP_WALL", "Probes"]
+
+
+U32 = 2.0 ** -24          # unit roundoff of float32, round to nearest
+
+
+def f32_contraction_bound(osol, q, gas):
+    """Rounding bound of the float32 stage at each node and variable:
+    (K + 10) u (sum_a |D_a| |F~'_a| + |LIFT| |dF|), the standard bound of a
+    K-term float32 dot product (K = 3 Np + 4 Nfp) applied to Eq. 10's two
+    contractions, with ten more roundings for forming the inputs; F~' are the
+    metric-folded fluxes minus the base state's (what the perturbation form
+    contracts), dF the face terms. Computed in float64 by the oracle."""
+    ref = osol.ref
+    Ft, dF = osol.rhs_parts(q)
+    base = np.zeros_like(q)
+    base[:, 0] = gas.rho0
+    base[:, 4] = gas.p0 / (gas.gamma - 1.0)
+    Ft0, _ = osol.rhs_parts(base)
+    D = (ref.Dr, ref.Ds, ref.Dt)
+    A = sum(np.einsum("ij,kvj->kvi", np.abs(D[a]), np.abs(Ft[:, a] - Ft0[:, a])) for a in range(3))
+    A = A + np.einsum("ij,kvj->kvi", np.abs(ref.LIFT), np.abs(dF))
+    K = 3 * ref.Np + 4 * ref.Nfp
+    return (K + 10) * U32 * A

@@ -375,3 +375,26 @@ def test_probes_interpolate_linear_fields():
     np.testing.assert_allclose(P.sample(q), np.outer(lin(pts), np.arange(1, 6)), rtol=1e-13)
     with pytest.raises(ValueError):
         Probes(geom, [[2.0, 0.0, 0.0]])
+
+
+def test_rhs_parts_recombine_to_the_rhs():
+    """The contraction inputs the oracle exposes (metric-folded fluxes, face
+    terms) give back its right-hand side through Eq. 10's two products, with
+    every boundary mode in play."""
+    from oracle.euler_dg import CHARACTERISTIC, FREESTREAM, SLIP_WALL
+    gas = Gas(1.4, 1.4, 1.0)
+    xyz, EToV = W.kuhn_cube(2, jitter=0.15, seed=9)
+    for p in (1, 3):
+        ref = ReferenceElement(p)
+        geom = Geometry(ref, xyz, EToV)
+        bc_id = np.zeros((geom.K, 4), dtype=np.int64)
+        cen = geom.x.mean(axis=1)
+        bc_id[cen[:, 0] > 0] = 1
+        bc_id[cen[:, 1] > 0.3] = 2
+        S = Solver(geom, gas, bc_id=bc_id, bc_mode={0: CHARACTERISTIC, 1: FREESTREAM, 2: SLIP_WALL})
+        q = W.random_smooth_state(geom.x, gas.gamma, gas.rho0, gas.p0, 0.05, seed=p)
+        Ft, dF = S.rhs_parts(q)
+        D = (ref.Dr, ref.Ds, ref.Dt)
+        rebuilt = -sum(np.einsum("ij,kvj->kvi", D[a], Ft[:, a]) for a in range(3))
+        rebuilt += np.einsum("ij,kvj->kvi", ref.LIFT, dF)
+        np.testing.assert_allclose(rebuilt, S.rhs(q), rtol=0, atol=1e-12 * np.abs(S.rhs(q)).max())
