@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "cp_async.cuh"
 #include "dg_device.cuh"
 #include "ghost_f32.cuh"
 
@@ -50,25 +51,6 @@ __device__ __forceinline__ void normal_flux_f(const float q[5], const float n[3]
   fn[4] = un * (b.H0 + q[4] + pp);
   const float c2 = b.gamma * (b.p0 + pp) * rinv;
   lam = fabsf(un) + (c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f);
-}
-
-// 4-byte asynchronous global -> shared copy and its completion
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(int32_t* dst, const int32_t* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_group1() {
-  asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
 // acc += a * b on two packed float32 lanes (one instruction for two FMAs)

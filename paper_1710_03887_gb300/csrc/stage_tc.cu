@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "cp_async.cuh"
 #include "dg_device.cuh"
 #include "ghost_f32.cuh"
 #include "tc_ptx.cuh"
@@ -35,23 +36,30 @@ struct OrderTC {
   static constexpr int KU = 3 * Np + NF;               // used columns
   static constexpr int K = (KU + 7) / 8 * 8;
   static constexpr int NT = 512;
+  static constexpr int SX = KU % 2 ? KU : KU + 1;      // odd row stride of X
+  static constexpr int SO = Np % 2 ? Np : Np + 1;      // odd row stride of the results
+  static constexpr int kQT = ET * 5 * Np;
+  static_assert(M * SO <= 5 * ET * SX, "the results fit in the X rows");
   static constexpr uint32_t SBO = uint32_t(K / 4) * 128u;
   static constexpr uint32_t kABytes = uint32_t(M / 8) * SBO;
   static constexpr uint32_t kBBytes = uint32_t(N / 8) * SBO;
-  // shared memory (bytes): A_hi, A_lo, B_hi, B_lo, then the tile data
+  // shared memory (bytes): A_hi, A_lo, B_hi, B_lo (operand layouts), X
+  // [row = 5 le + v][SX] (then the results [row][SO]), two buffers of state,
+  // geometry and connections, face weights, reduction space, tables, barrier
+  static constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
   static constexpr size_t oAhi = 0;
   static constexpr size_t oAlo = oAhi + kABytes;
   static constexpr size_t oBhi = oAlo + kABytes;
   static constexpr size_t oBlo = oBhi + kBBytes;
-  static constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
-  static constexpr size_t oQ = oBlo + kBBytes;                             // ET*5*Np floats
-  static constexpr size_t oGeo = al16(oQ + size_t(ET) * 5 * Np * 4);      // ET*32 floats
-  static constexpr size_t oW = al16(oGeo + size_t(ET) * kGeoStride * 4);  // NF floats
-  static constexpr size_t oRed = (oW + size_t(NF) * 4 + 15) / 16 * 16;   // 16 warps x 5 doubles
-  static constexpr size_t oConn = oRed + 16 * 5 * 8;                 // ET*4 ints
-  static constexpr size_t oFmask = oConn + size_t(ET) * 16;          // 4*Nfp ints
+  static constexpr size_t oX = al16(oBlo + kBBytes);
+  static constexpr size_t oQ = al16(oX + size_t(5 * ET) * SX * 4);
+  static constexpr size_t oGeo = al16(oQ + 2 * size_t(kQT) * 4);
+  static constexpr size_t oW = al16(oGeo + 2 * size_t(ET) * kGeoStride * 4);
+  static constexpr size_t oRed = al16(oW + size_t(NF) * 4);         // 16 warps x 5 doubles
+  static constexpr size_t oConn = oRed + 16 * 5 * 8;                 // 2 x ET*4 ints
+  static constexpr size_t oFmask = oConn + 2 * size_t(ET) * 16;      // 4*Nfp ints
   static constexpr size_t oTbl = oFmask + size_t(NF) * 4;            // 96*Nfp bytes
-  static constexpr size_t oBar = (oTbl + 96 * Nfp + 15) / 16 * 16;   // mbarrier, tmem slot, flag
+  static constexpr size_t oBar = al16(oTbl + 96 * Nfp);              // mbarrier, tmem slot, flag
   static constexpr size_t bytes = oBar + 32;
   static constexpr size_t kOpsBytes = 2 * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
 };
@@ -62,7 +70,7 @@ struct BaseF2 {
 
 __device__ __forceinline__ void prim_tc(const float q[5], const BaseF2& b, float& rinv, float u[3],
                                         float& pp) {
-  rinv = 1.0f / (b.rho0 + q[0]);
+  rinv = __fdividef(1.0f, b.rho0 + q[0]);          // 2 ulp: far below the form's tolerance
   u[0] = q[1] * rinv;
   u[1] = q[2] * rinv;
   u[2] = q[3] * rinv;
@@ -79,34 +87,37 @@ __device__ __forceinline__ void normal_flux_tc(const float q[5], const float n[3
   fn[2] = q[2] * un + pp * n[1];
   fn[3] = q[3] * un + pp * n[2];
   fn[4] = un * (b.H0 + q[4] + pp);
-  lam = fabsf(un) + sqrtf(b.gamma * (b.p0 + pp) * rinv);
-}
-
-// Store x into the A operand (hi and lo tf32 parts) at (row, k).
-template <uint32_t SBO>
-__device__ __forceinline__ void put_split(unsigned char* ahi, unsigned char* alo, int row, int k,
-                                          float x) {
-  const uint32_t off = tc::kmajor_offset(row, k, SBO);
-  const float hi = tc::to_tf32(x);
-  *reinterpret_cast<float*>(ahi + off) = hi;
-  *reinterpret_cast<float*>(alo + off) = tc::to_tf32(x - hi);
+  const float c2 = b.gamma * (b.p0 + pp) * rinv;
+  lam = fabsf(un) + (c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f);
 }
 
 constexpr uint32_t kWaitTries = 1u << 24;   // bounded MMA completion wait
 
+// Per tile of 25 elements:
+//  1. state, geometry and connections arrived by cp.async during the
+//     previous tile; neighbour traces are gathered by cp.async into the face
+//     columns of X while
+//  2. the flux phase writes the metric-folded fluxes into X (row-major, odd
+//     stride: conflict-free);
+//  3. the face phase replaces the gathered traces by Fscale (n.F - F*);
+//  4. X is split into the tf32 head and tail of the A operand, one warp per
+//     8 x 4 core matrix (128 contiguous bytes, conflict-free);
+//  5. one thread issues the MMAs (A_hi B_hi + A_hi B_lo + A_lo B_hi, K/8
+//     steps) and commits them to the mbarrier;
+//  6. warps 0..3 move their rows of the accumulator from tensor memory into
+//     the X space, and all threads update q and res with coalesced accesses.
 template <int P>
 __global__ void __launch_bounds__(OrderTC<P>::NT, 1)
 stage_tc_kernel(const StageArgsF32 A) {
   using O = OrderTC<P>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
+  constexpr int KU = O::KU, K = O::K, SX = O::SX, SO = O::SO;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* sAhi = smem + O::oAhi;
   unsigned char* sAlo = smem + O::oAlo;
-  float* sQ = reinterpret_cast<float*>(smem + O::oQ);
-  float* sGeo = reinterpret_cast<float*>(smem + O::oGeo);
+  float* sX = reinterpret_cast<float*>(smem + O::oX);
   float* sW = reinterpret_cast<float*>(smem + O::oW);
   double* sRed = reinterpret_cast<double*>(smem + O::oRed);
-  int32_t* sConn = reinterpret_cast<int32_t*>(smem + O::oConn);
   int32_t* sFmask = reinterpret_cast<int32_t*>(smem + O::oFmask);
   uint8_t* sTbl = smem + O::oTbl;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + O::oBar);
@@ -115,7 +126,7 @@ stage_tc_kernel(const StageArgsF32 A) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // constant operand B (host-built images in the operand layout), face
-  // weights, tables; zero A once so its padding rows/columns stay finite
+  // weights, tables
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.ops);
     uint4* dst = reinterpret_cast<uint4*>(smem + O::oBhi);
@@ -123,8 +134,6 @@ stage_tc_kernel(const StageArgsF32 A) {
     const float* w = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(A.ops) +
                                                     2 * O::kBBytes);
     for (int i = tid; i < NF; i += NT) sW[i] = w[i];
-    uint4* a = reinterpret_cast<uint4*>(smem + O::oAhi);
-    for (int i = tid; i < int(2 * O::kABytes / 16); i += NT) a[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < 96 * Nfp; i += NT) sTbl[i] = A.nbr_tbl[i];
     for (int i = tid; i < NF; i += NT) sFmask[i] = A.fmask[i];
   }
@@ -147,33 +156,62 @@ stage_tc_kernel(const StageArgsF32 A) {
   constexpr uint32_t idesc = tc::idesc_tf32(O::M, O::N);
   uint32_t phase = 0;
 
+  // asynchronous copy of tile t's state, geometry and connections into buffer bf
+  auto prefetch = [&](int t, int bf) {
+    if (t >= A.ntiles) return;
+    const int64_t f0 = int64_t(t) * ET;
+    const int n = int((A.K - f0) < ET ? (A.K - f0) : int64_t(ET));
+    float* dq = reinterpret_cast<float*>(smem + O::oQ) + bf * O::kQT;
+    const float* gq = A.q_in + f0 * 5 * Np;
+    if constexpr ((5 * Np) % 4 == 0) {
+      for (int i = tid; i < n * 5 * Np / 4; i += NT) cp_async16(dq + 4 * i, gq + 4 * i);
+    } else {
+      for (int i = tid; i < n * 5 * Np; i += NT) cp_async4(dq + i, gq + i);
+    }
+    float* dg = reinterpret_cast<float*>(smem + O::oGeo) + bf * ET * kGeoStride;
+    const float* gg = A.geo + f0 * kGeoStride;
+    for (int i = tid; i < n * kGeoStride / 4; i += NT) cp_async16(dg + 4 * i, gg + 4 * i);
+    int32_t* dc = reinterpret_cast<int32_t*>(smem + O::oConn) + bf * ET * 4;
+    const int32_t* gc = A.conn + f0 * 4;
+    for (int i = tid; i < n; i += NT) cp_async16(dc + 4 * i, gc + 4 * i);
+  };
+  prefetch(blockIdx.x, 0);
+  cp_async_commit();
+
   double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
-  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+  int iter = 0;
+  for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
+    const int buf = iter & 1;
+    const float* sQ = reinterpret_cast<const float*>(smem + O::oQ) + buf * O::kQT;
+    const float* sGeo = reinterpret_cast<const float*>(smem + O::oGeo) + buf * ET * kGeoStride;
+    const int32_t* sConn = reinterpret_cast<const int32_t*>(smem + O::oConn) + buf * ET * 4;
+    cp_async_wait_all();
     tc::fence_before_sync();
-    __syncthreads();   // previous epilogue done with sQ and with tensor memory
+    __syncthreads();   // this tile's data is in; the previous tile is finished
     if (*sAbort) break;
     tc::fence_after_sync();
-    {
-      const int nq = nE * 5 * Np;
-      if constexpr ((5 * Np) % 4 == 0) {        // rows of 16-byte multiples: vector loads
-        const float4* gq = reinterpret_cast<const float4*>(A.q_in + e0 * 5 * Np);
-        float4* q4 = reinterpret_cast<float4*>(sQ);
-        for (int i = tid; i < nq / 4; i += NT) q4[i] = gq[i];
-      } else {
-        const float* gq = A.q_in + e0 * 5 * Np;
-        for (int i = tid; i < nq; i += NT) sQ[i] = gq[i];
-      }
-      const float4* gg = reinterpret_cast<const float4*>(A.geo + e0 * kGeoStride);
-      float4* g4 = reinterpret_cast<float4*>(sGeo);
-      for (int i = tid; i < nE * kGeoStride / 4; i += NT) g4[i] = gg[i];
-      const int32_t* gc = A.conn + e0 * 4;
-      for (int i = tid; i < nE * 4; i += NT) sConn[i] = gc[i];
-    }
-    __syncthreads();
 
-    // ---- volume: reference-direction fluxes into A columns [0, 3 Np)
+    // neighbour traces into the face columns of X (row 5 le + v, column 3 Np + fm)
+    for (int it = tid; it < nE * NF; it += NT) {
+      const int le = it / NF, fm = it - (it / NF) * NF;
+      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+      const int32_t c = sConn[le * 4 + f];
+      if (c >= 0) {
+        const int64_t e2 = c >> 5;
+        const int f2 = (c >> 3) & 3, o = c & 7;
+        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+        const float* src = A.q_in + e2 * 5 * Np + n2;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async4(sX + (le * 5 + v) * SX + 3 * Np + fm, src + v * Np);
+      }
+    }
+    cp_async_commit();
+    prefetch(tile + gridDim.x, buf ^ 1);
+    cp_async_commit();
+
+    // ---- volume: reference-direction fluxes into X columns [0, 3 Np)
     for (int it = tid; it < nE * Np; it += NT) {
       const int le = it / Np, n = it - (it / Np) * Np;
       float q[5];
@@ -196,12 +234,13 @@ stage_tc_kernel(const StageArgsF32 A) {
       for (int a = 0; a < 3; ++a) {
         const float m0 = dr[a * 3], m1 = dr[a * 3 + 1], m2 = dr[a * 3 + 2];
         for (int v = 0; v < 5; ++v)
-          put_split<O::SBO>(sAhi, sAlo, le * 5 + v, a * Np + n,
-                            m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v]);
+          sX[(le * 5 + v) * SX + a * Np + n] = m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v];
       }
     }
+    cp_async_wait_group1();            // the gathers; the next tile may still fly
+    __syncthreads();
 
-    // ---- faces: jumps Fscale (n.F(q-) - F*) into A columns [3 Np, 3 Np + 4 Nfp)
+    // ---- faces: jumps Fscale (n.F(q-) - F*) into X columns [3 Np, 3 Np + 4 Nfp)
     float led[5] = {0, 0, 0, 0, 0};
     bool any_bdry = false;
     for (int it = tid; it < nE * NF; it += NT) {
@@ -213,12 +252,9 @@ stage_tc_kernel(const StageArgsF32 A) {
       const float* geo = sGeo + le * kGeoStride;
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       const int32_t c = sConn[le * 4 + f];
+      float* xf = sX + le * 5 * SX + 3 * Np + fm;     // row v at + v * SX
       if (c >= 0) {
-        const int64_t e2 = c >> 5;
-        const int f2 = (c >> 3) & 3, o = c & 7;
-        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-        const float* src = A.q_in + e2 * 5 * Np + n2;
-        for (int v = 0; v < 5; ++v) qp[v] = __ldg(src + v * Np);
+        for (int v = 0; v < 5; ++v) qp[v] = xf[v * SX];
       } else {
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
@@ -235,7 +271,7 @@ stage_tc_kernel(const StageArgsF32 A) {
       const float fs = geo[kGeoFscale + f];
       for (int v = 0; v < 5; ++v) {
         const float jump = 0.5f * (fnm[v] - fnp[v]) + 0.5f * lam * (qp[v] - qm[v]);
-        put_split<O::SBO>(sAhi, sAlo, le * 5 + v, 3 * Np + fm, fs * jump);
+        xf[v * SX] = fs * jump;
         if (c < 0) {
           const float fstar = 0.5f * (fnm[v] + fnp[v]) - 0.5f * lam * (qp[v] - qm[v]);
           led[v] += sW[fm] * geo[kGeoSJ + f] * fstar;
@@ -243,27 +279,7 @@ stage_tc_kernel(const StageArgsF32 A) {
       }
       any_bdry |= (c < 0);
     }
-    // operand writes become visible to the tensor cores
-    tc::fence_smem_to_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t ahi = tc::smem_addr(sAhi), alo = tc::smem_addr(sAlo);
-      const uint32_t bhi = tc::smem_addr(smem + O::oBhi), blo = tc::smem_addr(smem + O::oBlo);
-#pragma unroll 1
-      for (int s = 0; s < O::K / 8; ++s) {
-        const uint32_t off = 256u * s;
-        const uint64_t dAhi = tc::smem_desc(ahi + off, 128u, O::SBO);
-        const uint64_t dAlo = tc::smem_desc(alo + off, 128u, O::SBO);
-        const uint64_t dBhi = tc::smem_desc(bhi + off, 128u, O::SBO);
-        const uint64_t dBlo = tc::smem_desc(blo + off, 128u, O::SBO);
-        tc::mma_tf32(tmem, dAhi, dBhi, idesc, s > 0 ? 1u : 0u);
-        tc::mma_tf32(tmem, dAhi, dBlo, idesc, 1u);
-        tc::mma_tf32(tmem, dAlo, dBhi, idesc, 1u);
-      }
-      tc::mma_commit(mbar);
-    }
-    // boundary-flux ledger of this tile (overlaps the MMAs)
+    // boundary-flux ledger of this tile (the barrier also publishes X)
     if (__syncthreads_or(any_bdry)) {
       for (int v = 0; v < 5; ++v) {
         float x = led[v];
@@ -278,7 +294,47 @@ stage_tc_kernel(const StageArgsF32 A) {
       }
     }
 
-    // ---- epilogue: rows of tensor memory -> Runge-Kutta update
+    // ---- X -> tf32 head and tail of A: warp = one 8 x 4 core matrix at a time
+    for (int blk = warp; blk < (O::M / 8) * (K / 4); blk += NT / 32) {
+      const int g = blk / (K / 4), cch = blk - (blk / (K / 4)) * (K / 4);
+      const int r = 8 * g + (lane >> 2), k = 4 * cch + (lane & 3);
+      const float x = (r < 5 * nE && k < KU) ? sX[r * SX + k] : 0.0f;
+      const float hi = tc::to_tf32(x);
+      const uint32_t off = uint32_t(g) * O::SBO + uint32_t(cch) * 128u + uint32_t(lane) * 4u;
+      *reinterpret_cast<float*>(sAhi + off) = hi;
+      *reinterpret_cast<float*>(sAlo + off) = tc::to_tf32(x - hi);
+    }
+    // operand writes become visible to the tensor cores
+    tc::fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ahi = tc::smem_addr(sAhi), alo = tc::smem_addr(sAlo);
+      const uint32_t bhi = tc::smem_addr(smem + O::oBhi), blo = tc::smem_addr(smem + O::oBlo);
+#pragma unroll 1
+      for (int s = 0; s < K / 8; ++s) {
+        const uint32_t off = 256u * s;
+        const uint64_t dAhi = tc::smem_desc(ahi + off, 128u, O::SBO);
+        const uint64_t dAlo = tc::smem_desc(alo + off, 128u, O::SBO);
+        const uint64_t dBhi = tc::smem_desc(bhi + off, 128u, O::SBO);
+        const uint64_t dBlo = tc::smem_desc(blo + off, 128u, O::SBO);
+        tc::mma_tf32(tmem, dAhi, dBhi, idesc, s > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, dAhi, dBlo, idesc, 1u);
+        tc::mma_tf32(tmem, dAlo, dBhi, idesc, 1u);
+      }
+      tc::mma_commit(mbar);
+    }
+    // the residuals the Runge-Kutta pass will read, loaded while the MMAs run
+    constexpr int RI = (O::kQT + NT - 1) / NT;
+    const int64_t base = e0 * 5 * Np;
+    float rres[RI];
+#pragma unroll
+    for (int s = 0; s < RI; ++s) {
+      const int i = tid + s * NT;
+      rres[s] = (A.a != 0.0f && i < nE * 5 * Np) ? A.res[base + i] : 0.0f;
+    }
+
+    // ---- accumulator rows -> X space [row][SO] (warps 0..3: lanes 32w .. 32w+31)
     if (warp < 4) {
       const bool done = tc::mbar_wait(mbar, phase, kWaitTries);
       if (!done) {
@@ -291,21 +347,28 @@ stage_tc_kernel(const StageArgsF32 A) {
         float d[32];
         tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16), d);
         const int row = 32 * warp + lane;
-        if (row < nE * 5) {
-          const int le = row / 5, v = row - (row / 5) * 5;
-          const int64_t base = ((e0 + le) * 5 + v) * Np;
-          const float* qs = sQ + (le * 5 + v) * Np;
+        if (row < 5 * nE) {
 #pragma unroll
-          for (int j = 0; j < Np; ++j) {
-            const float r = (A.a != 0.0f) ? A.a * A.res[base + j] + A.dt * d[j] : A.dt * d[j];
-            A.res[base + j] = r;
-            A.q_out[base + j] = qs[j] + A.b * r;
-          }
+          for (int j = 0; j < Np; ++j) sX[row * SO + j] = d[j];
         }
       }
     }
     phase ^= 1u;
+    __syncthreads();
+
+    // ---- Runge-Kutta update, coalesced over the tile's state
+#pragma unroll
+    for (int s = 0; s < RI; ++s) {
+      const int i = tid + s * NT;
+      if (i < nE * 5 * Np) {
+        const int row = i / Np, n = i - (i / Np) * Np;
+        const float res = A.a * rres[s] + A.dt * sX[row * SO + n];
+        A.res[base + i] = res;
+        A.q_out[base + i] = sQ[i] + A.b * res;
+      }
+    }
   }
+  cp_async_wait_all();
   // a wait that gave up may leave MMAs in flight: give them a bounded chance
   // to finish before the tensor memory is released
   if (*sAbort && tid == 0) tc::mbar_wait(mbar, phase, kWaitTries);
