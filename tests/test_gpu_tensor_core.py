@@ -55,3 +55,38 @@ def test_tf32_mma_matches_host(cuda_device, probe, N, K):
     got = dD.cpu().numpy()
     scale = np.abs(tf32_round(A)).astype(np.float64) @ np.abs(tf32_round(B)).astype(np.float64).T
     assert np.all(np.abs(got - ref) <= 1e-6 * scale + 1e-30), np.abs(got - ref).max()
+
+
+def test_tf32_mma_m64_rows_in_tensor_memory(cuda_device, probe):
+    """M = 64: the same product, with every lane of the accumulator read back;
+    each of the 64 result rows must appear, whole and correct, in exactly one
+    tensor-memory lane (the stage kernel's M = 64 tiles rely on the mapping
+    this test prints and pins)."""
+    import torch
+    probe.tc_gemm_probe_m64.restype = ctypes.c_int
+    probe.tc_gemm_probe_m64.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int,
+                                                               ctypes.c_void_p]
+    N, K = 24, 104
+    rng = np.random.default_rng(64)
+    A = rng.normal(size=(64, K)).astype(np.float32)
+    B = rng.normal(size=(N, K)).astype(np.float32)
+    dA = torch.from_numpy(A).to(cuda_device)
+    dB = torch.from_numpy(B).to(cuda_device)
+    dD = torch.full((128, 32), float("nan"), dtype=torch.float32, device=cuda_device)
+    st = torch.zeros(1, dtype=torch.int32, device=cuda_device)
+    rc = probe.tc_gemm_probe_m64(dA.data_ptr(), dB.data_ptr(), dD.data_ptr(), N, K, st.data_ptr())
+    assert rc == 0
+    assert int(st.item()) == 0, "MMA completion wait timed out"
+    ref = tf32_round(A).astype(np.float64) @ tf32_round(B).astype(np.float64).T
+    scale = np.abs(tf32_round(A)).astype(np.float64) @ np.abs(tf32_round(B)).astype(np.float64).T
+    got = dD.cpu().numpy()[:, :N].astype(np.float64)
+    lanes = []
+    for r in range(64):
+        hit = [L for L in range(128)
+               if np.all(np.abs(got[L] - ref[r]) <= 1e-6 * scale[r] + 1e-30)]
+        lanes.append(hit)
+    print("M=64 row -> tensor-memory lanes:", [h[0] if len(h) == 1 else h for h in lanes])
+    assert all(len(h) == 1 for h in lanes)
+    # row r sits in lane 32 (r // 16) + r % 16: the first 16 lanes of each
+    # warp's quarter of tensor memory
+    assert [h[0] for h in lanes] == [32 * (r // 16) + r % 16 for r in range(64)]
