@@ -118,6 +118,34 @@ int dg_set_stream(dg_ctx* ctx, void* cuda_stream);
 int dg_upload_mesh(dg_ctx* ctx, int64_t nvert, const double* xyz, int64_t K,
                    const int32_t* EToV, const int8_t* face_tag,
                    const int64_t* vert_class);
+/* A mesh given directly by its geometric factors and connectivity instead
+ * of vertices (Appendix A, Eq. 9: the per-element affine maps and the shared
+ * faces; e.g. factors computed by another program for parity checks). Host
+ * arrays, copied:
+ *   drdx[K][3][3]  d r_a / d x_b of element e's affine map (J > 0)
+ *   J[K]           determinant of dx/d(r,s,t)
+ *   nrm[K][4][3]   outward unit normals of faces 0..3 (t=-1, s=-1,
+ *                  r+s+t=-1, r=-1)
+ *   Fscale[K][4]   face area / (2 J) (half the area: the surface Jacobian
+ *                  over the volume Jacobian)
+ *   EToE[K][4]     neighbour element or -1 (boundary face)
+ *   EToF[K][4]     neighbour's face (0..3) on interior faces
+ *   orient[K][4]   orientation code o (0..5) on interior faces: face vertex c
+ *                  of face f of e is face vertex P[o][c] of face EToF of
+ *                  EToE, with face f's vertices V[f] = {0,1,2}, {0,1,3},
+ *                  {1,2,3}, {0,2,3} (element vertices in the order of the
+ *                  affine map) and P = {0,1,2}, {0,2,1}, {1,0,2}, {1,2,0},
+ *                  {2,0,1}, {2,1,0}
+ *   bc[K][4]       boundary id (0..7) on boundary faces (nullable: 0)
+ * Errors (DG_ERR_MESH): J <= 0, normals not of unit length, Fscale <= 0,
+ * neighbour links that are not mutual, orientation codes that are not
+ * inverse permutations of each other, interior normals not back to back.
+ * Without vertex coordinates, dg_node_coords, dg_set_probes, the learned
+ * closure and trace recording report DG_ERR_ORDER. Replaces any previous
+ * mesh and invalidates the state. */
+int dg_upload_geometry(dg_ctx* ctx, int64_t K, const double* drdx, const double* J,
+                       const double* nrm, const double* Fscale, const int32_t* EToE,
+                       const int8_t* EToF, const int8_t* orient, const int8_t* bc);
 /* Ghost rule of boundary id bc_id (0..7). */
 int dg_set_bc(dg_ctx* ctx, int bc_id, int mode);
 /* Sizes: number of elements, nodes per element, nodes per face. */

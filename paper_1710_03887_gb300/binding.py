@@ -73,6 +73,7 @@ _SIGS = {
     "dg_get_bc_mlp": (C.c_int, [_P, _P]),
     "dg_set_trace_faces": (C.c_int, [_P, C.c_int64, _P, _P]),
     "dg_sample_traces": (C.c_int, [_P, _P, _P, _P]),
+    "dg_upload_geometry": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "dg_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _D, _P]),
     "dg_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_double, _P]),
     "dg_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P]),
@@ -287,6 +288,18 @@ class Solver:
         w = np.zeros(DG_MLP_NPARAMS, dtype=np.float32)
         self._check(self.lib.dg_get_bc_mlp(self.h, _ptr(w)))
         return w
+
+    def upload_geometry(self, drdx, J, nrm, Fscale, EToE, EToF, orient, bc=None):
+        """Mesh given by its geometric factors and connectivity (see the header)."""
+        K = int(np.asarray(J).shape[0])
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (drdx, J, nrm, Fscale)]
+        e2e = np.ascontiguousarray(EToE, dtype=np.int32)
+        e2f = np.ascontiguousarray(EToF, dtype=np.int8)
+        ori = np.ascontiguousarray(orient, dtype=np.int8)
+        b = None if bc is None else np.ascontiguousarray(bc, dtype=np.int8)
+        self._check(self.lib.dg_upload_geometry(self.h, K, *(_ptr(x) for x in a), _ptr(e2e), _ptr(e2f),
+                                                _ptr(ori), None if b is None else _ptr(b)))
+        self.K = K
 
     def set_trace_faces(self, elem, face):
         elem = np.ascontiguousarray(elem, dtype=np.int32)

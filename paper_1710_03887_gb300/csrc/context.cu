@@ -227,7 +227,7 @@ int ensure_device(dg_ctx* c) {
   // node positions of every boundary face (features of the learned closure)
   if (f32 && !bfaces.empty()) {
     std::vector<float> bx(bfaces.size() * size_t(Nfp) * 3);
-    for (size_t b = 0; b < bfaces.size(); ++b) {
+    for (size_t b = 0; b < bfaces.size() && !c->mesh.verts.empty(); ++b) {
       const int64_t e = bfaces[b] / 4;
       const int f = int(bfaces[b] % 4);
       for (int m = 0; m < Nfp; ++m) {
@@ -338,6 +338,8 @@ dgk::BaseGhost base_ghost(const dg_ctx* c) {
 int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
   bool learned = false;
   for (int i = 0; i < 8; ++i) learned = learned || c->bc_mode[i] == DG_BC_LEARNED;
+  if (learned && c->nbf > 0 && c->mesh.verts.empty())
+    return c->fail(DG_ERR_ORDER, "the learned closure needs vertex coordinates (dg_upload_mesh)");
   const dgk::BaseGhost bg = base_ghost(c);
   if (learned && c->nbf > 0) {
     dgk::ClosureArgs C{};
@@ -546,6 +548,71 @@ int dg_upload_mesh(dg_ctx* c, int64_t nvert, const double* xyz, int64_t K, const
   return DG_OK;
 }
 
+int dg_upload_geometry(dg_ctx* c, int64_t K, const double* drdx, const double* J,
+                       const double* nrm, const double* Fscale, const int32_t* EToE,
+                       const int8_t* EToF, const int8_t* orient, const int8_t* bc) {
+  if (!c) return DG_ERR_ARG;
+  if (K <= 0 || !drdx || !J || !nrm || !Fscale || !EToE || !EToF || !orient)
+    return c->fail(DG_ERR_ARG, "empty mesh or null array");
+  if (K > (int64_t(1) << 26)) return c->fail(DG_ERR_ARG, "too many elements (max 2^26)");
+  c->free_device();
+  c->have_mesh = false;
+  dg::Mesh m;
+  m.K = K;
+  m.drdx.assign(drdx, drdx + size_t(K) * 9);
+  m.J.assign(J, J + K);
+  m.nrm.assign(nrm, nrm + size_t(K) * 12);
+  m.Fscale.assign(Fscale, Fscale + size_t(K) * 4);
+  m.EToE.assign(EToE, EToE + size_t(K) * 4);
+  m.EToF.assign(size_t(K) * 4, 0);
+  m.orient.assign(size_t(K) * 4, 0);
+  m.bc.assign(size_t(K) * 4, -1);
+  m.sJ.resize(size_t(K) * 4);
+  m.rin.resize(K);
+  for (int64_t e = 0; e < K; ++e) {
+    if (!(J[e] > 0.0) || !std::isfinite(J[e]))
+      return c->fail(DG_ERR_MESH, "J <= 0 at element " + std::to_string(e));
+    double fsum = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      const size_t i = size_t(e) * 4 + f;
+      const double* n = nrm + i * 3;
+      const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      if (!(std::fabs(len - 1.0) < 1e-6))
+        return c->fail(DG_ERR_MESH, "normal not of unit length at element " + std::to_string(e));
+      if (!(Fscale[i] > 0.0) || !std::isfinite(Fscale[i]))
+        return c->fail(DG_ERR_MESH, "Fscale <= 0 at element " + std::to_string(e));
+      m.sJ[i] = Fscale[i] * J[e];
+      fsum += Fscale[i];
+      const int32_t e2 = EToE[i];
+      if (e2 < 0) {
+        const int8_t tag = bc ? bc[i] : int8_t(0);
+        if (tag < 0 || tag > 7) return c->fail(DG_ERR_MESH, "boundary id out of 0..7");
+        m.bc[i] = tag;
+        continue;
+      }
+      const int f2 = EToF[i], o = orient[i];
+      if (e2 >= K || f2 < 0 || f2 > 3 || o < 0 || o > 5)
+        return c->fail(DG_ERR_MESH, "neighbour, face or orientation out of range at element " +
+                                        std::to_string(e));
+      const size_t j = size_t(e2) * 4 + f2;
+      if (EToE[j] != e || EToF[j] != f || orient[j] < 0 || orient[j] > 5)
+        return c->fail(DG_ERR_MESH, "neighbour links not mutual at element " + std::to_string(e));
+      for (int q = 0; q < 3; ++q)
+        if (dg::kPerm[orient[j]][dg::kPerm[o][q]] != q)
+          return c->fail(DG_ERR_MESH, "orientation codes not inverse at element " + std::to_string(e));
+      const double* n2 = nrm + j * 3;
+      if (n[0] * n2[0] + n[1] * n2[1] + n[2] * n2[2] > -1.0 + 1e-6)
+        return c->fail(DG_ERR_MESH, "matched faces not back to back at element " + std::to_string(e));
+      m.EToF[i] = int8_t(f2);
+      m.orient[i] = int8_t(o);
+    }
+    m.rin[e] = 2.0 / fsum;            // 3 V / total area with V = 4 J / 3, area_f = 2 Fscale_f J
+  }
+  c->mesh = std::move(m);
+  c->have_mesh = true;
+  return DG_OK;
+}
+
 int dg_set_bc(dg_ctx* c, int bc_id, int mode) {
   if (!c) return DG_ERR_ARG;
   if (bc_id < 0 || bc_id > 7) return c->fail(DG_ERR_ARG, "boundary id must be 0..7");
@@ -566,7 +633,7 @@ int dg_sizes(const dg_ctx* c, int64_t* K, int32_t* Np, int32_t* Nfp) {
 
 int dg_node_coords(const dg_ctx* c, double* xyz) {
   if (!c || !xyz) return DG_ERR_ARG;
-  if (!c->have_mesh) return DG_ERR_ORDER;
+  if (!c->have_mesh || c->mesh.verts.empty()) return DG_ERR_ORDER;
   const int Np = c->ref.Np;
   for (int64_t e = 0; e < c->mesh.K; ++e) {
     const double* v = &c->mesh.verts[size_t(e) * 12];
@@ -733,6 +800,8 @@ int dg_eval_rhs(dg_ctx* c, double* rhs) {
 int dg_set_probes(dg_ctx* c, int n, const double* xyz, int capacity) {
   if (!c) return DG_ERR_ARG;
   if (n < 0 || n > 4096 || (n > 0 && (!xyz || capacity < 1))) return c->fail(DG_ERR_ARG, "bad probe arguments");
+  if (n > 0 && (!c->have_mesh || c->mesh.verts.empty()))
+    return c->fail(DG_ERR_ORDER, "probes need a mesh with vertex coordinates");
   int rc = ensure_device(c);
   if (rc) return rc;
   DG_CUDA(cudaStreamSynchronize(c->stream));
@@ -915,6 +984,8 @@ int dg_get_bc_mlp(dg_ctx* c, float* w) {
 int dg_set_trace_faces(dg_ctx* c, int64_t n, const int32_t* elem, const int8_t* face) {
   if (!c || n < 0 || (n > 0 && (!elem || !face))) return DG_ERR_ARG;
   if (c->prec == DG_PREC_FP64) return c->fail(DG_ERR_UNSUPPORTED, "traces are sampled in the float32 forms");
+  if (c->have_mesh && c->mesh.verts.empty())
+    return c->fail(DG_ERR_ORDER, "trace recording needs vertex coordinates (dg_upload_mesh)");
   int rc = ensure_device(c);
   if (rc) return rc;
   const int Nfp = c->ref.Nfp;

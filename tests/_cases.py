@@ -105,3 +105,28 @@ def f32_contraction_bound(osol, q, gas):
     A = A + np.einsum("ij,kvj->kvi", np.abs(ref.LIFT), np.abs(dF))
     K = 3 * ref.Np + 4 * ref.Nfp
     return (K + 10) * U32 * A
+
+
+# Orientation convention of dg_upload_geometry (include/dg_euler.h): face
+# vertex c of face f of element e is face vertex PERMS[o][c] of the
+# neighbour's face.
+FACE_VERTS = ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3))
+PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def orientation_codes(EToV, EToE, EToF):
+    K = len(EToV)
+    ori = np.zeros((K, 4), dtype=np.int8)
+    for e in range(K):
+        for f in range(4):
+            e2 = int(EToE[e, f])
+            if e2 < 0:
+                continue
+            f2 = int(EToF[e, f])
+            for o, P in enumerate(PERMS):
+                if all(EToV[e][FACE_VERTS[f][c]] == EToV[e2][FACE_VERTS[f2][P[c]]] for c in range(3)):
+                    ori[e, f] = o
+                    break
+            else:
+                raise ValueError("faces do not match")
+    return ori

@@ -112,3 +112,48 @@ def test_calls_out_of_order_fail_cleanly():
     lib = B.load()
     assert lib.dg_node_coords(S.h, None) == B.DG_ERR_ARG
     assert lib.dg_destroy(None) == B.DG_OK
+
+
+def test_upload_geometry_round_trip_and_errors():
+    """A mesh re-uploaded through its geometric factors (dg_upload_geometry)
+    has the same geometry and stable time step; malformed factors are
+    rejected, and calls that need vertices say so."""
+    from paper_1710_03887_gb300 import workloads as W
+    from ._cases import orientation_codes
+    xyz, EToV = W.kuhn_cube(2, jitter=0.1, seed=2)
+    S1 = B.Solver(2)
+    S1.upload_mesh(xyz, EToV)
+    g = S1.geometry()
+    ori = orientation_codes(EToV, g["EToE"], g["EToF"])
+    Fs = g["sJ"] / g["J"][:, None]
+    S2 = B.Solver(2)
+    S2.upload_geometry(g["drdx"], g["J"], g["nrm"], Fs, g["EToE"], g["EToF"], ori)
+    g2 = S2.geometry()
+    for k in ("J", "drdx", "nrm", "EToE", "EToF", "bc"):
+        np.testing.assert_array_equal(g2[k], g[k])
+    np.testing.assert_allclose(g2["sJ"], g["sJ"], rtol=1e-15)
+    q = W.uniform_state(S1.K, S1.Np, 1.225, (0, 0, 0), 101325.0, 1.4)
+    assert S2.stable_dt(q) == pytest.approx(S1.stable_dt(q), rel=1e-13)
+    with pytest.raises(B.DGError) as ei:
+        S2.node_coords()
+    assert ei.value.code == B.DG_ERR_ORDER
+    with pytest.raises(B.DGError) as ei:
+        S2.set_probes([[0.0, 0.0, 0.0]])
+    assert ei.value.code == B.DG_ERR_ORDER
+    # malformed inputs
+    e, f = np.argwhere(g["EToE"] >= 0)[0]
+    bad = g["EToE"].copy()
+    bad[e, f] = (bad[e, f] + 1) % S1.K
+    with pytest.raises(B.DGError) as ei:
+        S2.upload_geometry(g["drdx"], g["J"], g["nrm"], Fs, bad, g["EToF"], ori)
+    assert ei.value.code == B.DG_ERR_MESH
+    bad_o = ori.copy()
+    bad_o[e, f] = (bad_o[e, f] + 1) % 6
+    with pytest.raises(B.DGError) as ei:
+        S2.upload_geometry(g["drdx"], g["J"], g["nrm"], Fs, g["EToE"], g["EToF"], bad_o)
+    assert ei.value.code == B.DG_ERR_MESH
+    bad_J = g["J"].copy()
+    bad_J[3] = -1.0
+    with pytest.raises(B.DGError) as ei:
+        S2.upload_geometry(g["drdx"], bad_J, g["nrm"], Fs, g["EToE"], g["EToF"], ori)
+    assert ei.value.code == B.DG_ERR_MESH
