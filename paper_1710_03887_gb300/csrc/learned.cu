@@ -245,7 +245,7 @@ mlp_grad_kernel(const float* __restrict__ w, const float* __restrict__ X,
       const int s = i / kH, j = i - (i / kH) * kH;
       float a = sW[oB1 + j];
       for (int k = 0; k < kIn; ++k) a += sX[s * kIn + k] * sW[oW1 + k * kH + j];
-      H1[i] = tanhf(a);
+      H1[i] = tanh_fast(a);
     }
     __syncthreads();
     // H2 = tanh(H1 W2 + b2)
@@ -253,7 +253,7 @@ mlp_grad_kernel(const float* __restrict__ w, const float* __restrict__ X,
       const int s = i / kH, j = i - (i / kH) * kH;
       float a = sW[oB2 + j];
       for (int k = 0; k < kH; ++k) a += H1[s * kH + k] * sW[oW2 + k * kH + j];
-      H2[i] = tanhf(a);
+      H2[i] = tanh_fast(a);
     }
     __syncthreads();
     // output, its error and the loss; dL/dout = 2 (out - y) / N

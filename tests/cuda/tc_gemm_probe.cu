@@ -154,3 +154,20 @@ extern "C" int tc_gemm_probe_m64(const float* A, const float* B, float* Dfull, i
   if (cudaGetLastError() != cudaSuccess) return -3;
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : -4;
 }
+
+// ---- the network's tanh against CUDA's tanhf, elementwise
+#include "../../paper_1710_03887_gb300/csrc/mlp.cuh"
+
+__global__ void tanh_probe_kernel(const float* x, float* fast, float* ref, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  fast[i] = dgk::mlp::tanh_fast(x[i]);
+  ref[i] = tanhf(x[i]);
+}
+
+extern "C" int tanh_probe(const float* x, float* fast, float* ref, int n) {
+  if (n <= 0) return -1;
+  tanh_probe_kernel<<<(n + 255) / 256, 256>>>(x, fast, ref, n);
+  if (cudaGetLastError() != cudaSuccess) return -3;
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -4;
+}

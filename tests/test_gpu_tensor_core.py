@@ -90,3 +90,22 @@ def test_tf32_mma_m64_rows_in_tensor_memory(cuda_device, probe):
     # row r sits in lane 32 (r // 16) + r % 16: the first 16 lanes of each
     # warp's quarter of tensor memory
     assert [h[0] for h in lanes] == [32 * (r // 16) + r % 16 for r in range(64)]
+
+
+def test_network_tanh_against_tanhf(cuda_device, probe):
+    """The closure network's tanh (1 - 2 / (1 + e^{2x}) with hardware exp2 and
+    reciprocal) stays within 3e-7 of CUDA's tanhf everywhere, including the
+    saturated tails and x = 0."""
+    import torch
+    probe.tanh_probe.restype = ctypes.c_int
+    probe.tanh_probe.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int]
+    x = np.concatenate([np.linspace(-30.0, 30.0, 200001), [0.0, -0.0, 1e-30, -1e-30, 1e-6, 88.0, -88.0,
+                                                           1e30, -1e30]]).astype(np.float32)
+    dx = torch.from_numpy(x).to(cuda_device)
+    fast = torch.empty_like(dx)
+    ref = torch.empty_like(dx)
+    assert probe.tanh_probe(dx.data_ptr(), fast.data_ptr(), ref.data_ptr(), x.size) == 0
+    f, r = fast.cpu().numpy(), ref.cpu().numpy()
+    assert np.all(np.isfinite(f))
+    assert np.abs(f - r).max() <= 3e-7, np.abs(f - r).max()
+    assert np.abs(f - np.tanh(x.astype(np.float64))).max() <= 3e-7
