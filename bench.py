@@ -383,6 +383,20 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     # a source off the centre, where the spherical memory is no longer exact
     table["2% p0 off-centre (0.3,0.1,-0.2)"] = L.reflection_table(
         WORKLOAD["order"], nested, 0.02, 0.25, (0.3, 0.1, -0.2), w)
+    # plain float64 DG on the same pulse: the float32 form's reflected energy
+    # and state against it (at 2 % p0)
+    from paper_1710_03887_gb300 import binding as B
+    centre = (0.0, 0.0, 0.0)
+    r64, d64 = L.reflected_energy(WORKLOAD["order"], nested, 0.02, 0.3, centre,
+                                  B.DG_BC_CHARACTERISTIC, precision=B.DG_PREC_FP64)
+    r32, d32 = L.reflected_energy(WORKLOAD["order"], nested, 0.02, 0.3, centre,
+                                  B.DG_BC_CHARACTERISTIC, precision=B.DG_PREC_F32)
+    fp64_check = {
+        "pulse": "2% p0, width 0.3, centred; characteristic condition on the truncated ball",
+        "reflected_energy_fp64": r64, "reflected_energy_f32": r32,
+        "f32_minus_fp64_rel": (r32 - r64) / r64,
+        "max_state_diff_rel_to_pulse_amplitude": L.max_state_difference(d32, d64, 0.02),
+    }
     t_judge = time.perf_counter() - t0 - t_rec - t_train
     m = measure_form(args, "f32", xyz, EToV, dev, stream, dist, world, sample_clocks=False,
                      mlp=(w, WORKLOAD["radius"]))
@@ -397,6 +411,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
         "loss_last": float(hist[-1]),
         "reflected_energy_rel": table,
         "gain_vs_characteristic": {k: v["characteristic"] / v["learned"] for k, v in table.items()},
+        "vs_plain_fp64": fp64_check,
         "seconds": {"record": t_rec, "train": t_train, "judge": t_judge},
         "bench_workload_learned_bc": {"value": m["value"], "unit": UNIT,
                                       "ms_per_step": m["ms"] / args.steps,

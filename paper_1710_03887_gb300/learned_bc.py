@@ -240,4 +240,16 @@ def reflected_energy(order, nested, amplitude, width, center, mode, weights=None
     big.close()
     small.close()
     return er / e0, {"E0": e0, "E_reflected": er, "E_left_in_reference": left, "dt": dt,
-                     "steps": steps}
+                     "steps": steps, "q_small": qs1}
+
+
+def max_state_difference(d_a, d_b, amplitude):
+    """Largest difference of two truncated-ball end states (details of
+    ``reflected_energy``) per conserved variable, in units of the pulse's
+    own scale in that variable: rho0 A / gamma for density, rho0 c0 A / gamma
+    for momentum, p0 A / (gamma - 1) for energy."""
+    c0 = np.sqrt(W.GAMMA * W.P0_SI / W.RHO0_SI)
+    scale = np.array([W.RHO0_SI / W.GAMMA] + [W.RHO0_SI * c0 / W.GAMMA] * 3
+                     + [W.P0_SI / (W.GAMMA - 1.0)]) * amplitude
+    diff = np.abs(d_a["q_small"] - d_b["q_small"]).max(axis=(0, 2))
+    return (diff / scale).tolist()
