@@ -84,6 +84,7 @@ struct dg_ctx {
   float* bpsi = nullptr;           // memory of the boundary face nodes [slot][Nfp]
   float* bpsi_res = nullptr;
   float* bD = nullptr;             // incoming-invariant increments [slot][Nfp]
+  uint8_t* face_list = nullptr;    // float32 stage: faces each tile evaluates
   float* mlp_w = nullptr;          // network parameters (device), null until set
   float* mlp_m = nullptr;          // Adam moments
   float* mlp_v = nullptr;
@@ -124,7 +125,7 @@ struct dg_ctx {
     dfree(ops); dfree(tbl); dfree(fmask); dfree(ticket); dfree(ledger_part); dfree(ledger);
     dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
     dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
-    dfree(bxyz); dfree(bface); dfree(bpsi); dfree(bpsi_res); dfree(bD);
+    dfree(bxyz); dfree(bface); dfree(bpsi); dfree(bpsi_res); dfree(bD); dfree(face_list);
     dfree(tr_elem); dfree(tr_face); dfree(txyz); dfree(tr_psi); dfree(tr_res);
     ntrace = 0;
     nbf = 0;
@@ -250,6 +251,25 @@ int ensure_device(dg_ctx* c) {
     DG_CUDA(cudaMemset(c->bpsi_res, 0, nb));
     DG_CUDA(cudaMemset(c->bD, 0, nb));
   }
+  if (f32 && !tcf) {
+    // faces each tile evaluates: a face shared by two elements of the tile
+    // once, under the lower element (the float32 stage writes both jumps)
+    const size_t row = 16 + 4 * size_t(ET);
+    std::vector<uint8_t> fl(size_t(c->ntiles) * row, 0);
+    for (int t = 0; t < c->ntiles; ++t) {
+      const int64_t e0 = int64_t(t) * ET, e1 = std::min<int64_t>(K, e0 + ET);
+      int32_t cnt = 0;
+      for (int64_t e = e0; e < e1; ++e)
+        for (int f = 0; f < 4; ++f) {
+          const int64_t e2 = c->mesh.EToE[size_t(e) * 4 + f];
+          if (e2 >= e0 && e2 < e1 && e2 < e) continue;
+          fl[size_t(t) * row + 16 + cnt++] = uint8_t(((e - e0) << 2) | f);
+        }
+      std::memcpy(&fl[size_t(t) * row], &cnt, 4);
+    }
+    DG_CUDA(cudaMalloc(&c->face_list, fl.size()));
+    DG_CUDA(cudaMemcpy(c->face_list, fl.data(), fl.size(), cudaMemcpyHostToDevice));
+  }
   DG_CUDA(cudaMalloc(&c->conn, conn.size() * 4));
   DG_CUDA(cudaMemcpy(c->conn, conn.data(), conn.size() * 4, cudaMemcpyHostToDevice));
   DG_CUDA(cudaMalloc(&c->ledger_part, size_t(c->grid) * 5 * 8));
@@ -284,8 +304,22 @@ int ensure_device(dg_ctx* c) {
     DG_CUDA(cudaMalloc(&c->ops32, o32.size() * 4));
     DG_CUDA(cudaMemcpy(c->ops32, o32.data(), o32.size() * 4, cudaMemcpyHostToDevice));
   }
-  DG_CUDA(cudaMalloc(&c->tbl, c->ref.nbr_node.size()));
-  DG_CUDA(cudaMemcpy(c->tbl, c->ref.nbr_node.data(), c->ref.nbr_node.size(),
+  // face-node tables [4][4][6][Nfp], one after the other: the neighbour's
+  // volume node of face node m, then the neighbour's face node (its index in
+  // the neighbour face's node list)
+  std::vector<uint8_t> tbl2(c->ref.nbr_node);
+  tbl2.resize(2 * c->ref.nbr_node.size(), 0xFF);
+  for (int f = 0; f < 4; ++f)
+    for (int f2 = 0; f2 < 4; ++f2)
+      for (int o = 0; o < 6; ++o)
+        for (int m = 0; m < Nfp; ++m) {
+          const size_t i = ((size_t(f) * 4 + f2) * 6 + o) * Nfp + m;
+          for (int m2 = 0; m2 < Nfp; ++m2)
+            if (c->ref.Fmask[f2 * Nfp + m2] == c->ref.nbr_node[i])
+              tbl2[c->ref.nbr_node.size() + i] = uint8_t(m2);
+        }
+  DG_CUDA(cudaMalloc(&c->tbl, tbl2.size()));
+  DG_CUDA(cudaMemcpy(c->tbl, tbl2.data(), tbl2.size(),
                      cudaMemcpyHostToDevice));
   std::vector<int32_t> fm(c->ref.Fmask.begin(), c->ref.Fmask.end());
   DG_CUDA(cudaMalloc(&c->fmask, fm.size() * 4));
@@ -394,6 +428,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     A.dt = float(dt);
     A.gas = c->gas;
     A.bD = c->bD;
+    A.face_list = c->face_list;
     int rc = run_memory(c, to_scratch, a, b, dt);
     if (rc) return rc;
     if (c->prec == DG_PREC_F32_TC)

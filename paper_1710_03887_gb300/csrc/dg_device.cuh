@@ -80,7 +80,8 @@ struct StageArgs {
   const double* geo;         // [K][kGeoStride]
   const int32_t* conn;       // [K][4]
   const double* ops;         // DrT | DsT | DtT ([j][i], Np*Np each) | LIFTT ([m][i], NF*Np) | face_w [NF]
-  const uint8_t* nbr_tbl;    // [4][4][6][Nfp]: neighbour volume node
+  const uint8_t* nbr_tbl;    // [4][4][6][Nfp]: neighbour volume node; then the same
+                             // shape: neighbour face node (index in its face's list)
   const int32_t* fmask;      // [4][Nfp]
   LedgerArgs led;
   int* status;
@@ -111,6 +112,10 @@ struct StageArgsF32 {
   // learned closure (boundary mode 3): incoming-invariant increments
   // [boundary face slot][Nfp] from launch_closure, or null (characteristic)
   const float* bD;
+  // float32 stage: per tile, a 16-byte header (int32 count) then the faces it
+  // evaluates, one byte each (element in tile << 2 | face); a face between
+  // two elements of the tile appears once, under its lower element
+  const uint8_t* face_list;  // [ntiles][16 + 4 ET]
 };
 
 int stage_f32_tile_elems(int p);

@@ -109,9 +109,11 @@ struct OrderF {
   static constexpr int nWarps = NT / 32;
   static constexpr size_t oRedB = (size_t(oEnd) * 4 + 15) / 16 * 16;
   static constexpr size_t oConnB = oRedB + size_t(nWarps) * 5 * 8;
-  static constexpr size_t oFmaskB = oConnB + 2 * size_t(ET) * 4 * 4;
+  static constexpr size_t kFL = 16 + 4 * size_t(ET);                // face list row (bytes)
+  static constexpr size_t oFLB = oConnB + 2 * size_t(ET) * 4 * 4;   // two face-list buffers
+  static constexpr size_t oFmaskB = oFLB + 2 * kFL;
   static constexpr size_t oTblB = oFmaskB + size_t(4) * Nfp * 4;
-  static constexpr size_t bytes = (oTblB + kTbl + 15) / 16 * 16;
+  static constexpr size_t bytes = (oTblB + 2 * kTbl + 15) / 16 * 16;
 };
 
 template <int P>
@@ -141,7 +143,7 @@ stage_f32_kernel(const StageArgsF32 A) {
     sOT[i] = v;
   }
   for (int i = tid; i < NF; i += NT) faceW[i] = A.ops[3 * Np * Np + NF * Np + i];
-  for (int i = tid; i < O::kTbl; i += NT) sTbl[i] = A.nbr_tbl[i];
+  for (int i = tid; i < 2 * O::kTbl; i += NT) sTbl[i] = A.nbr_tbl[i];   // volume-node and face-node tables
   for (int i = tid; i < 4 * Nfp; i += NT) sFmask[i] = A.fmask[i];
   const BaseF b{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
                 float(A.gas.E0 + A.gas.p0)};
@@ -166,6 +168,9 @@ stage_f32_kernel(const StageArgsF32 A) {
     int32_t* dc = reinterpret_cast<int32_t*>(smem_raw + O::oConnB) + bf * ET * 4;
     const int32_t* gc = A.conn + f0 * 4;
     for (int i = tid; i < n; i += NT) cp_async16(dc + 4 * i, gc + 4 * i);
+    unsigned char* dl = smem_raw + O::oFLB + bf * O::kFL;
+    const uint8_t* gl = A.face_list + size_t(t) * O::kFL;
+    for (int i = tid; i < int(O::kFL / 16); i += NT) cp_async16(dl + 16 * i, gl + 16 * i);
   };
   prefetch(blockIdx.x, 0);
   cp_async_commit();
@@ -179,18 +184,20 @@ stage_f32_kernel(const StageArgsF32 A) {
     const float* sQ = sm + O::oQ + buf * O::kQT;
     const float* sGeo = sm + O::oGeo + buf * ET * kGeoStride;
     const int32_t* sConn = reinterpret_cast<const int32_t*>(smem_raw + O::oConnB) + buf * ET * 4;
+    const uint8_t* sFL = smem_raw + O::oFLB + buf * O::kFL;   // count, then (le << 2 | f)
     cp_async_wait_all();
     __syncthreads();   // this tile's data is in; the previous tile is finished
 
-    // ---- neighbour traces of interior face nodes, copied asynchronously into
-    // the face columns of X (row v, element le, column 3 Np + fm), where the
-    // face phase reads them and then writes the jump; the copies fly while
-    // the node phase computes
-    for (int it = tid; it < nE * NF; it += NT) {
-      const int le = it / NF, fm = it - (it / NF) * NF;
-      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+    // ---- neighbour traces of face nodes whose neighbour lies outside the
+    // tile, copied asynchronously into the face columns of X (row v, element
+    // le, column 3 Np + fm), where the face phase reads them and then writes
+    // the jump; the copies fly while the node phase computes
+    const int nF = *reinterpret_cast<const int32_t*>(sFL);
+    for (int it = tid; it < nF * Nfp; it += NT) {
+      const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
+      const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      if (c >= 0) {
+      if (c >= 0 && ((c >> 5) < e0 || (c >> 5) >= e0 + nE)) {
         const int64_t e2 = c >> 5;
         const int f2 = (c >> 3) & 3, o = c & 7;
         const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
@@ -233,21 +240,34 @@ stage_f32_kernel(const StageArgsF32 A) {
     cp_async_wait_group1();            // the gathers; the next tile may still fly
     __syncthreads();
 
-    // ---- face fluxes at face nodes
+    // ---- face fluxes at the nodes of the tile's listed faces. A face between
+    // two elements of the tile is listed once, under its lower element, which
+    // writes both jumps: with A = (n.F(q-) - n.F(q+)) / 2 and
+    // B = lambda (q+ - q-) / 2 the own jump is Fscale (A + B) and the
+    // neighbour's (normal -n, traces swapped) Fscale' (A - B).
     float led[5] = {0, 0, 0, 0, 0};   // float32 within the tile, float64 across tiles
     bool any_bdry = false;
-    for (int it = tid; it < nE * NF; it += NT) {
-      const int le = it / NF, fm = it - (it / NF) * NF;
-      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+    for (int it = tid; it < nF * Nfp; it += NT) {
+      const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
+      const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
+      const int32_t c = sConn[le * 4 + f];
+      const int le2 = (c >= 0) ? int((c >> 5) - e0) : -1;   // neighbour's tile slot
+      const bool inside = c >= 0 && le2 >= 0 && le2 < nE;   // then le2 > le (face list)
       const int n = sFmask[f * Nfp + m];
       float qm[5], qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
       const float* geo = sGeo + le * kGeoStride;
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
-      const int32_t c = sConn[le * 4 + f];
       float* xf = sX + le * SX + 3 * Np + fm;        // + v * ET * SX
-      if (c >= 0) {
+      int f2 = 0, o = 0;
+      if (inside) {
+        f2 = (c >> 3) & 3;
+        o = c & 7;
+        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qp[v] = sQ[(le2 * 5 + v) * Np + n2];
+      } else if (c >= 0) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) qp[v] = xf[v * ET * SX];
       } else {
@@ -264,12 +284,20 @@ stage_f32_kernel(const StageArgsF32 A) {
       normal_flux_f(qp, nv, b, fnp, lp);
       const float lam = fmaxf(lm, lp);
       const float fs = geo[kGeoFscale + f];
+      float* xf2 = xf;
+      float fs2 = 0.0f;
+      if (inside) {
+        const int m2 = sTbl[O::kTbl + ((f * 4 + f2) * 6 + o) * Nfp + m];
+        xf2 = sX + le2 * SX + 3 * Np + f2 * Nfp + m2;
+        fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const float jump = 0.5f * (fnm[v] - fnp[v]) + 0.5f * lam * (qp[v] - qm[v]);
-        xf[v * ET * SX] = fs * jump;
+        const float hA = 0.5f * (fnm[v] - fnp[v]), hB = 0.5f * lam * (qp[v] - qm[v]);
+        xf[v * ET * SX] = fs * (hA + hB);
+        if (inside) xf2[v * ET * SX] = fs2 * (hA - hB);
         if (c < 0) {
-          const float fstar = 0.5f * (fnm[v] + fnp[v]) - 0.5f * lam * (qp[v] - qm[v]);
+          const float fstar = 0.5f * (fnm[v] + fnp[v]) - hB;
           led[v] += faceW[fm] * geo[kGeoSJ + f] * fstar;
         }
       }
