@@ -66,6 +66,9 @@ extern "C" {
                                 /* invariant (float32 forms; see dg_set_bc_mlp); falls   */
                                 /* back to the characteristic ghost where the result is  */
                                 /* not finite or has rho <= 0 or p <= 0                  */
+#define DG_BC_INFLOW_PULSE 4    /* mouthpiece inflow (section 2.4, Eqs. 5-7): a one-     */
+                                /* period pressure pulse entering as a plane wave; see   */
+                                /* dg_set_inflow                                         */
 
 /* Arithmetic of the time step (dg_params.precision) */
 #define DG_PREC_FP64 0          /* float64 state, fluxes and contractions               */
@@ -148,6 +151,14 @@ int dg_upload_geometry(dg_ctx* ctx, int64_t K, const double* drdx, const double*
                        const int8_t* EToF, const int8_t* orient, const int8_t* bc);
 /* Ghost rule of boundary id bc_id (0..7). */
 int dg_set_bc(dg_ctx* ctx, int bc_id, int mode);
+/* Inflow pulse of DG_BC_INFLOW_PULSE (section 2.4): at stage time t the ghost
+ * is p = p0 (1 + A (1 - cos(alpha t))) while 0 <= t < 2 pi / alpha (p0
+ * afterwards), rho = rho0 (p/p0)^(1/gamma) (Eq. 6), velocity
+ * (p - p0)/(rho0 c0) along the inward normal (Eq. 5; the paper's bore axis),
+ * E from Eq. 2. The paper's pulse is A = 0.05 (a 10 % p0 peak) with
+ * alpha = 565 in its time unit (the defaults). DG_ERR_ARG unless alpha > 0
+ * and A > -1/2. */
+int dg_set_inflow(dg_ctx* ctx, double amplitude, double alpha);
 /* Sizes: number of elements, nodes per element, nodes per face. */
 int dg_sizes(const dg_ctx* ctx, int64_t* K, int32_t* Np, int32_t* Nfp);
 /* Physical node coordinates xyz[K][Np][3] (host). */

@@ -27,6 +27,8 @@ What is computed, with the passage it follows:
                     entropy p/rho^g and tangential velocity from inside when
                     that normal velocity is >= 0 (outflow), else from the
                     free stream;
+    INFLOW_PULSE    the mouthpiece inflow of section 2.4 (Eqs. 5-7): a
+                    time-dependent ghost (``ghost_inflow``);
     SLIP_WALL       reflective wall (section 2.3, Eq. 4): normal velocity
                     mirrored, rho and p unchanged. Eq. 4 as printed mixes
                     components (u - 2 u n_x, ...); the oracle mirrors the
@@ -62,6 +64,7 @@ FREESTREAM = 0
 CHARACTERISTIC = 1
 SLIP_WALL = 2
 LEARNED = 3        # characteristic ghost + network correction (oracle/mlp.py)
+INFLOW_PULSE = 4   # the mouthpiece pulse of section 2.4 (Eqs. 5-7)
 
 # Carpenter & Kennedy (1994), NASA TM-109112, five-stage 2N-storage RK4
 LSRK_A = [Fraction(0), Fraction(-567301805773, 1357537059087),
@@ -181,6 +184,30 @@ def ghost_characteristic(qm, n, gas):
     return qp
 
 
+def inflow_pressure(t, gas, amplitude, alpha):
+    """Mouthpiece pressure of section 2.4: p0 (1 + A (1 - cos(alpha t))) while
+    t < 2 pi / alpha (one unipolar pulse), p0 afterwards."""
+    t = np.asarray(t, dtype=np.float64)
+    on = (t >= 0.0) & (t < 2.0 * np.pi / alpha)
+    return gas.p0 * (1.0 + np.where(on, amplitude * (1.0 - np.cos(alpha * t)), 0.0))
+
+
+def ghost_inflow(qm, n, gas, t, amplitude, alpha):
+    """Inflow ghost of section 2.4 (Eq. 7): the pulse pressure p(t), density
+    from the adiabatic relation (Eq. 6) rho = rho0 (p/p0)^(1/gamma), and the
+    velocity of a plane wave entering through the face (Eq. 5),
+    (p - p0) / (rho0 c0) along the inward normal -n; E from Eq. 2. The paper
+    states it for the bore's left end, where -n is +x."""
+    p = inflow_pressure(t, gas, amplitude, alpha)
+    rho = gas.rho0 * (p / gas.p0) ** (1.0 / gas.gamma)
+    un = (p - gas.p0) / (gas.rho0 * gas.c0)
+    q = np.zeros(qm.shape)
+    q[..., 0] = rho
+    q[..., 1:4] = -np.asarray(rho * un)[..., None] * n
+    q[..., 4] = p / (gas.gamma - 1.0) + 0.5 * rho * un * un
+    return q
+
+
 GHOSTS = {FREESTREAM: ghost_freestream, CHARACTERISTIC: ghost_characteristic,
           SLIP_WALL: ghost_slip_wall}
 
@@ -273,8 +300,10 @@ class Solver:
     and ``reset_memory`` (called by ``run``) zeroes it.
     """
 
-    def __init__(self, geom: Geometry, gas: Gas, bc_id=None, bc_mode=None, mlp=None):
+    def __init__(self, geom: Geometry, gas: Gas, bc_id=None, bc_mode=None, mlp=None,
+                 inflow=(0.05, 565.0)):
         self.g = geom
+        self.inflow = inflow                # (amplitude A, rate alpha) of the mouthpiece pulse
         self.ref = geom.ref
         self.gas = gas
         self.mlp = mlp                      # (parameters, radius) of the learned closure
@@ -333,13 +362,13 @@ class Solver:
         metric-folded fluxes Ft [K, 3, 5, Np] (F~_r, F~_s, F~_t) and the face
         terms dF [K, 5, 4 Nfp], so that
         rhs = -(Dr Ft_r + Ds Ft_s + Dt Ft_t) + LIFT dF."""
-        return self._rhs(q, self.psi, parts=True)
+        return self._rhs(q, self.psi, 0.0, parts=True)
 
     def rhs_full(self, q, t, psi):
-        """(dq/dt, boundary flux integral, d psi/dt) at state q with memory psi."""
-        return self._rhs(q, psi)
+        """(dq/dt, boundary flux integral, d psi/dt) at state q, time t, memory psi."""
+        return self._rhs(q, psi, t)
 
-    def _rhs(self, q, psi, parts=False):
+    def _rhs(self, q, psi, t, parts=False):
         g, ref, gas = self.g, self.ref, self.gas
         gam = gas.gamma
         K, Np, Nfp = g.K, ref.Np, ref.Nfp
@@ -365,6 +394,8 @@ class Solver:
                 rows = slice(row, row + len(sel[0]))
                 qp[sel] = ghost_learned(qm[sel], n[sel], self.mem_x[rows], psi[rows], gas,
                                         self.mlp[0], self.radius)
+            elif mode == INFLOW_PULSE:
+                qp[sel] = ghost_inflow(qm[sel], n[sel], gas, t, *self.inflow)
             else:
                 qp[sel] = GHOSTS[mode](qm[sel], n[sel], gas)
         fstar = llf_flux(qm, qp, n, gam)

@@ -28,6 +28,7 @@ DG_BC_FREESTREAM = 0
 DG_BC_CHARACTERISTIC = 1
 DG_BC_SLIP_WALL = 2
 DG_BC_LEARNED = 3
+DG_BC_INFLOW_PULSE = 4
 DG_MLP_NPARAMS = 5317
 
 DG_PREC_FP64 = 0
@@ -74,6 +75,7 @@ _SIGS = {
     "dg_set_trace_faces": (C.c_int, [_P, C.c_int64, _P, _P]),
     "dg_sample_traces": (C.c_int, [_P, _P, _P, _P]),
     "dg_upload_geometry": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dg_set_inflow": (C.c_int, [_P, C.c_double, C.c_double]),
     "dg_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _D, _P]),
     "dg_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_double, _P]),
     "dg_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P]),
@@ -197,6 +199,9 @@ class Solver:
 
     def set_bc(self, bc_id, mode):
         self._check(self.lib.dg_set_bc(self.h, bc_id, mode))
+
+    def set_inflow(self, amplitude, alpha):
+        self._check(self.lib.dg_set_inflow(self.h, float(amplitude), float(alpha)))
 
     def node_coords(self):
         out = np.zeros((self.K, self.Np, 3))

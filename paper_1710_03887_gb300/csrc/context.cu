@@ -22,7 +22,7 @@ const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
 const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                         2277821191437.0 / 14882151754819.0};
-[[maybe_unused]] const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0,
                         2526269341429.0 / 6820363962896.0, 2006345519317.0 / 3224310063776.0,
                         2802321613138.0 / 2924317926251.0};
 
@@ -41,6 +41,7 @@ struct dg_ctx {
   dg::Mesh mesh;
   dg_params prm{};
   int bc_mode[8];
+  double inflow_amp = 0.05, inflow_alpha = 565.0;   // mouthpiece pulse (section 2.4)
   std::string err;
   cudaStream_t stream = nullptr;
   bool have_mesh = false, dev_ready = false, have_state = false;
@@ -407,7 +408,31 @@ int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
 
 // One Runge-Kutta stage from q[cur] to q[1-cur]; with to_scratch the residual
 // goes to the scratch buffer (used by dg_eval_rhs with a = b = 0, dt = 1).
-int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
+// Inflow ghost (section 2.4, Eqs. 5-7) at time t: pressure p0 (1 + A (1 -
+// cos(alpha t))) during one period, rho = rho0 (p/p0)^(1/gamma), speed
+// (p - p0)/(rho0 c0) into the domain; as {rho, rho u_in, E} and, for the
+// float32 forms, as {rho - rho0, rho u_in, E - E0} formed without cancellation.
+void inflow_state(const dg_ctx* c, double t, double full[3], float pert[3]) {
+  const dgk::Gas& g = c->gas;
+  const double kTwoPi = 6.283185307179586;
+  const bool on = t >= 0.0 && t < kTwoPi / c->inflow_alpha;
+  const double dp = on ? g.p0 * c->inflow_amp * (1.0 - std::cos(c->inflow_alpha * t)) : 0.0;
+  const double drho = g.rho0 * std::expm1(std::log1p(dp / g.p0) / g.gamma);
+  const double rho = g.rho0 + drho;
+  const double un = dp / (g.rho0 * g.c0);
+  const double dE = dp / g.gm1 + 0.5 * rho * un * un;
+  full[0] = rho;
+  full[1] = rho * un;
+  full[2] = (g.p0 + dp) / g.gm1 + 0.5 * rho * un * un;
+  pert[0] = float(drho);
+  pert[1] = float(rho * un);
+  pert[2] = float(dE);
+}
+
+int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double ts) {
+  double in_full[3];
+  float in_pert[3];
+  inflow_state(c, ts, in_full, in_pert);
   if (c->prec != DG_PREC_FP64) {
     dgk::StageArgsF32 A{};
     A.q_in = c->q32[c->cur];
@@ -427,6 +452,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     A.b = float(b);
     A.dt = float(dt);
     A.gas = c->gas;
+    for (int i = 0; i < 3; ++i) A.inflow[i] = in_pert[i];
     A.bD = c->bD;
     A.face_list = c->face_list;
     int rc = run_memory(c, to_scratch, a, b, dt);
@@ -438,6 +464,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
   } else {
     dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], to_scratch ? c->scratch : c->res,
                                   a, b, dt, !to_scratch);
+    for (int i = 0; i < 3; ++i) A.inflow[i] = in_full[i];
     DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
   }
   return DG_OK;
@@ -648,10 +675,19 @@ int dg_upload_geometry(dg_ctx* c, int64_t K, const double* drdx, const double* J
   return DG_OK;
 }
 
+int dg_set_inflow(dg_ctx* c, double amplitude, double alpha) {
+  if (!c) return DG_ERR_ARG;
+  if (!std::isfinite(amplitude) || !(alpha > 0.0) || !std::isfinite(alpha) || amplitude <= -0.5)
+    return c->fail(DG_ERR_ARG, "need alpha > 0 and amplitude > -1/2");
+  c->inflow_amp = amplitude;
+  c->inflow_alpha = alpha;
+  return DG_OK;
+}
+
 int dg_set_bc(dg_ctx* c, int bc_id, int mode) {
   if (!c) return DG_ERR_ARG;
   if (bc_id < 0 || bc_id > 7) return c->fail(DG_ERR_ARG, "boundary id must be 0..7");
-  if (mode < 0 || mode > 3) return c->fail(DG_ERR_ARG, "unknown boundary mode");
+  if (mode < 0 || mode > 4) return c->fail(DG_ERR_ARG, "unknown boundary mode");
   if (mode == DG_BC_LEARNED && c->prec == DG_PREC_FP64)
     return c->fail(DG_ERR_UNSUPPORTED, "the learned closure runs in the float32 forms");
   c->bc_mode[bc_id] = mode;
@@ -797,7 +833,7 @@ int dg_step(dg_ctx* c, int n, double dt) {
     for (int k = 0; k < 5; ++k) {
       int rc = record_event(c);
       if (rc) return rc;
-      rc = run_stage(c, false, kRkA[k], kRkB[k], dt);
+      rc = run_stage(c, false, kRkA[k], kRkB[k], dt, c->t + kRkC[k] * dt);
       if (rc) return rc;
       rc = record_event(c);
       if (rc) return rc;
@@ -824,7 +860,7 @@ int dg_eval_rhs(dg_ctx* c, double* rhs) {
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   // one stage with a = b = 0, dt = 1 writes f(q) into the scratch residual
   // and leaves the ledger alone
-  int rc = run_stage(c, true, 0.0, 0.0, 1.0);
+  int rc = run_stage(c, true, 0.0, 0.0, 1.0, c->t);
   if (rc) return rc;
   if (c->prec != DG_PREC_FP64)
     DG_CUDA(dgk::launch_widen(c->scratch32, c->scratch, int64_t(c->state_elems()), c->stream));

@@ -90,6 +90,7 @@ struct StageArgs {
   int bc_mode[8];
   double a, b, dt;
   Gas gas;
+  double inflow[3];          // mode 4 ghost at the stage time: rho, rho u_in, E
 };
 
 // Float32 perturbation-form stage (stage_f32.cu)
@@ -109,6 +110,8 @@ struct StageArgsF32 {
   int bc_mode[8];
   float a, b, dt;
   Gas gas;
+  float inflow[3];           // mode 4 ghost at the stage time, perturbation form:
+                             // rho - rho0, rho u_in, E - E0
   // learned closure (boundary mode 3): incoming-invariant increments
   // [boundary face slot][Nfp] from launch_closure, or null (characteristic)
   const float* bD;

@@ -34,7 +34,15 @@ __device__ __forceinline__ void normal_flux(const double q[5], const double n[3]
 
 // Ghost state of an outer face node.
 __device__ inline void ghost_state(int mode, const double qm[5], const double n[3], const Gas& g,
-                            double qp[5]) {
+                            const double inflow[3], double qp[5]) {
+  if (mode == 4) {  // inflow pulse (section 2.4, Eq. 7): rho, rho u_in along -n, E
+    qp[0] = inflow[0];
+    qp[1] = -inflow[1] * n[0];
+    qp[2] = -inflow[1] * n[1];
+    qp[3] = -inflow[1] * n[2];
+    qp[4] = inflow[2];
+    return;
+  }
   if (mode == 0) {  // free stream (the paper's pass-through ghost)
     qp[0] = g.rho0;
     qp[1] = g.rho0 * g.u0[0];

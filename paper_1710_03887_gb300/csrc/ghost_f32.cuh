@@ -19,12 +19,23 @@ namespace dgk {
 
 struct BaseGhost {
   float rho0, p0, gamma, gm1, c0;
+  // mode 4 (inflow pulse) at the stage time: rho - rho0, rho u_in (speed along
+  // the inward normal), E - E0, formed on the host in float64
+  float in_drho = 0.0f, in_m = 0.0f, in_dE = 0.0f;
 };
 
 __host__ __device__ inline void ghost_state_f(int mode, const float qm[5], const float n[3],
                                               const BaseGhost& g, float qp[5]) {
   if (mode == 0) {  // free stream: zero perturbation
     for (int v = 0; v < 5; ++v) qp[v] = 0.0f;
+    return;
+  }
+  if (mode == 4) {  // inflow pulse (section 2.4, Eq. 7): the same state on every face
+    qp[0] = g.in_drho;
+    qp[1] = -g.in_m * n[0];
+    qp[2] = -g.in_m * n[1];
+    qp[3] = -g.in_m * n[2];
+    qp[4] = g.in_dE;
     return;
   }
   if (mode == 2) {  // reflective wall

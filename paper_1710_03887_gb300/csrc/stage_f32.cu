@@ -148,7 +148,7 @@ stage_f32_kernel(const StageArgsF32 A) {
   const BaseF b{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
                 float(A.gas.E0 + A.gas.p0)};
   const BaseGhost bg{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
-                     float(A.gas.c0)};
+                     float(A.gas.c0), A.inflow[0], A.inflow[1], A.inflow[2]};
 
   // asynchronous copy of tile t's state, geometry and connections into buffer bf
   auto prefetch = [&](int t, int bf) {

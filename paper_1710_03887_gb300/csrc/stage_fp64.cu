@@ -144,7 +144,7 @@ stage_fp64_kernel(const StageArgs A) {
         const double* src = A.q_in + e2 * 5 * Np + n2;
         for (int v = 0; v < 5; ++v) qp[v] = __ldg(src + v * Np);
       } else {
-        ghost_state(A.bc_mode[(-1 - c) & 7], qm, nv, g, qp);
+        ghost_state(A.bc_mode[(-1 - c) & 7], qm, nv, g, A.inflow, qp);
       }
       double fnm[5], fnp[5], lm, lp;
       normal_flux(qm, nv, g, fnm, lm);

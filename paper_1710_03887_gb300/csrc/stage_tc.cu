@@ -152,7 +152,7 @@ stage_tc_kernel(const StageArgsF32 A) {
   const uint32_t tmem = *tslot;
   const BaseF2 b{float(A.gas.rho0), float(A.gas.p0), float(A.gas.gamma), float(A.gas.gm1),
                  float(A.gas.E0 + A.gas.p0), float(A.gas.c0)};
-  const BaseGhost bg{b.rho0, b.p0, b.gamma, b.gm1, b.c0};
+  const BaseGhost bg{b.rho0, b.p0, b.gamma, b.gm1, b.c0, A.inflow[0], A.inflow[1], A.inflow[2]};
   constexpr uint32_t idesc = tc::idesc_tf32(O::M, O::N);
   uint32_t phase = 0;
 

@@ -130,3 +130,16 @@ def orientation_codes(EToV, EToE, EToF):
             else:
                 raise ValueError("faces do not match")
     return ori
+
+
+def inflow_case(p, seed=13):
+    """Kuhn cube with the faces on x = -1 tagged 1 (the inflow pulse of
+    section 2.4) and every other boundary face tagged 0."""
+    from oracle.geometry import Geometry
+    from oracle.reference_element import ReferenceElement
+    from paper_1710_03887_gb300 import workloads as W
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=seed)
+    geom = Geometry(ReferenceElement(p), xyz, EToV)
+    fx = geom.x[:, geom.ref.Fmask].mean(axis=2)[..., 0]          # face centroids' x, [K, 4]
+    tag = np.where(geom.boundary, np.where(fx < -1.0 + 1e-9, 1, 0), -1).astype(np.int8)
+    return xyz, EToV, geom, tag

@@ -134,3 +134,32 @@ def test_f32_full_size_ball_rhs_sample(cuda_device, prec):
     den = np.abs(rhs).max(axis=(0, 2))
     den = np.where(den > 0, den, 1.0)
     assert np.all(num / den < RHS_TOL), num / den
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_f32_inflow_pulse_run(cuda_device, prec):
+    """The inflow pulse of section 2.4 in the float32 forms against the
+    float64 oracle (one whole pulse within 20 steps)."""
+    from oracle.euler_dg import CHARACTERISTIC, INFLOW_PULSE, Gas
+    from oracle.euler_dg import Solver as OSolver
+    from ._cases import inflow_case
+    xyz, EToV, geom, tag = inflow_case(2)
+    gas = Gas(SI["gamma"], SI["rho0"], SI["p0"])
+    q0 = W.uniform_state(geom.K, geom.ref.Np, SI["rho0"], (0, 0, 0), SI["p0"], SI["gamma"])
+    bc_id = np.where(tag < 0, 0, tag).astype(np.int64)
+    orc = OSolver(geom, gas, bc_id=bc_id, bc_mode={0: CHARACTERISTIC, 1: INFLOW_PULSE})
+    dt = orc.stable_dt(q0, 0.5)
+    alpha = 2 * np.pi / (12 * dt)
+    orc.inflow = (0.05, alpha)
+    qo, _, _, _ = orc.run(q0, dt, 20)
+    from paper_1710_03887_gb300 import binding as B
+    S = B.Solver(2, precision=prec_code(prec), **SI)
+    S.upload_mesh(xyz, EToV, face_tag=tag)
+    S.set_bc(0, B.DG_BC_CHARACTERISTIC)
+    S.set_bc(1, B.DG_BC_INFLOW_PULSE)
+    S.set_inflow(0.05, alpha)
+    S.set_state(q0)
+    S.step(20, dt)
+    qg, _ = S.get_state()
+    err = perturbation_err(qg, qo, q0)
+    assert np.all(err < RUN_TOL), err

@@ -211,3 +211,37 @@ def test_rhs_with_oracle_geometric_factors(cuda_device):
     S.set_state(q)
     err = rel_err(S.eval_rhs(), ro)
     assert np.all(err < TOL), err
+
+
+def test_inflow_pulse_run_matches_oracle(cuda_device):
+    """The mouthpiece inflow of section 2.4 on the x = -1 faces (characteristic
+    elsewhere), one whole pulse within 20 steps: float64 run against the
+    oracle, and the ledger balance of the mass it injects."""
+    from oracle.euler_dg import CHARACTERISTIC, INFLOW_PULSE, Gas
+    from oracle.euler_dg import Solver as OSolver
+    from paper_1710_03887_gb300 import binding as B
+    from ._cases import inflow_case
+    xyz, EToV, geom, tag = inflow_case(2)
+    gas = Gas(SI["gamma"], SI["rho0"], SI["p0"])
+    q0 = W.uniform_state(geom.K, geom.ref.Np, SI["rho0"], (0, 0, 0), SI["p0"], SI["gamma"])
+    bc_id = np.where(tag < 0, 0, tag).astype(np.int64)
+    orc = OSolver(geom, gas, bc_id=bc_id, bc_mode={0: CHARACTERISTIC, 1: INFLOW_PULSE})
+    dt = orc.stable_dt(q0, 0.5)
+    alpha = 2 * np.pi / (12 * dt)                    # the pulse lasts 12 steps
+    orc.inflow = (0.05, alpha)
+    qo, to, ledger_o, _ = orc.run(q0, dt, 20)
+    assert np.abs(qo - q0).max(axis=(0, 2))[4] > 1e-3 * SI["p0"]       # it came in
+    S = B.Solver(2, **SI)
+    S.upload_mesh(xyz, EToV, face_tag=tag)
+    S.set_bc(0, B.DG_BC_CHARACTERISTIC)
+    S.set_bc(1, B.DG_BC_INFLOW_PULSE)
+    S.set_inflow(0.05, alpha)
+    S.set_state(q0)
+    S.step(20, dt)
+    qg, _ = S.get_state()
+    err = state_err(qg, qo, gas)
+    assert np.all(err < TOL), err
+    led = S.boundary_flux()
+    assert np.allclose(led, ledger_o, rtol=1e-9, atol=1e-12 * np.abs(orc.totals(q0)).max())
+    bal = S.totals() - orc.totals(q0) + led
+    assert np.all(np.abs(bal) <= 1e-12 * np.maximum(np.abs(orc.totals(q0)), 1.0)), bal

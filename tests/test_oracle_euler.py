@@ -398,3 +398,49 @@ def test_rhs_parts_recombine_to_the_rhs():
         rebuilt = -sum(np.einsum("ij,kvj->kvi", D[a], Ft[:, a]) for a in range(3))
         rebuilt += np.einsum("ij,kvj->kvi", ref.LIFT, dF)
         np.testing.assert_allclose(rebuilt, S.rhs(q), rtol=0, atol=1e-12 * np.abs(S.rhs(q)).max())
+
+
+def test_inflow_ghost_is_the_free_stream_outside_the_pulse():
+    from oracle.euler_dg import INFLOW_PULSE, ghost_inflow, inflow_pressure
+    gas = Gas(1.4, 1.4, 1.0)
+    n = np.array([[-1.0, 0.0, 0.0], [0.0, 0.6, -0.8]])
+    qm = np.tile(gas.freestream(), (2, 1))
+    alpha = 565.0
+    for t in (0.0, 2 * np.pi / alpha, 1.0, -1e-3):
+        np.testing.assert_array_equal(ghost_inflow(qm, n, gas, t, 0.05, alpha), qm)
+    # the pulse's peak is p0 (1 + 2 A) at half its length
+    assert inflow_pressure(np.pi / alpha, gas, 0.05, alpha) == pytest.approx(1.1)
+    # free-stream preservation with inflow faces when no pulse is on
+    xyz, EToV = W.kuhn_cube(2, jitter=0.1, seed=3)
+    geom = Geometry(ReferenceElement(2), xyz, EToV)
+    bc_id = (geom.x.mean(axis=1)[:, 0] < 0).astype(np.int64)[:, None].repeat(4, 1)
+    S = Solver(geom, gas, bc_id=bc_id, bc_mode={0: CHARACTERISTIC, 1: INFLOW_PULSE})
+    q = W.uniform_state(geom.K, geom.ref.Np, gas.rho0, (0, 0, 0), gas.p0, gas.gamma)
+    assert np.abs(S.rhs(q, t=2 * np.pi / alpha)).max() < 1e-12
+
+
+def test_inflow_ghost_injects_the_planar_wave():
+    """With the interior at rest, the local Lax-Friedrichs flux through an
+    inflow face equals the flux of the plane acoustic wave entering through it
+    (p' = p(t) - p0, velocity p'/(rho0 c0) along -n, rho' = p'/c0^2): mass
+    -p'/c0, momentum (p0 + p') n, energy -(E0 + p0) p'/(rho0 c0), to first
+    order in the amplitude."""
+    from oracle.euler_dg import ghost_inflow, inflow_pressure, llf_flux
+    gas = Gas(1.4, 1.225, 101325.0)
+    rng = np.random.default_rng(11)
+    n = rng.normal(size=(16, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    qm = np.tile(gas.freestream(), (16, 1))
+    A, alpha = 1e-6, 565.0
+    t = rng.uniform(0, 2 * np.pi / alpha, size=16)
+    qg = ghost_inflow(qm, n, gas, t, A, alpha)
+    F = llf_flux(qm, qg, n, gas.gamma)
+    pp = inflow_pressure(t, gas, A, alpha) - gas.p0
+    want = np.zeros_like(F)
+    want[:, 0] = -pp / gas.c0
+    want[:, 1:4] = (gas.p0 + pp)[:, None] * n
+    want[:, 4] = -(gas.freestream()[4] + gas.p0) * pp / (gas.rho0 * gas.c0)
+    scale = np.abs(pp)[:, None] * np.array([1 / gas.c0, 1, 1, 1, gas.c0 / 0.4])
+    err = np.abs(F - want)
+    err[:, 1:4] = np.abs((F - want)[:, 1:4])
+    assert np.all(err <= 1e-5 * scale + 1e-9 * np.abs(want) * (np.arange(5) >= 1)[None, :])
