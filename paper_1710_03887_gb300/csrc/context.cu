@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dg_euler.h"
 #include "dg_device.cuh"
 #include "dg_host.hpp"
@@ -829,6 +831,11 @@ int dg_step(dg_ctx* c, int n, double dt) {
   if (!c) return DG_ERR_ARG;
   if (n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return c->fail(DG_ERR_ARG, "need n >= 0 and dt > 0");
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  // a named range per call for timeline tools (no cost without one attached)
+  struct Range {
+    Range() { nvtxRangePushA("dg_step"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
   for (int s = 0; s < n; ++s) {
     for (int k = 0; k < 5; ++k) {
       int rc = record_event(c);
@@ -1135,6 +1142,10 @@ int dg_mlp_train(dg_ctx* c, const float* X, const float* Y, int64_t N, int iters
                  double* loss_history) {
   if (!c || !X || !Y || N <= 0 || iters < 0 || !(lr > 0.0)) return DG_ERR_ARG;
   if (!c->mlp_w) return c->fail(DG_ERR_ORDER, "no network set");
+  nvtxRangePushA("dg_mlp_train");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   for (int it = 0; it < iters; ++it) {
     int rc = mlp_grad_dev(c, X, Y, N);
     if (rc) return rc;

@@ -171,3 +171,38 @@ extern "C" int tanh_probe(const float* x, float* fast, float* ref, int n) {
   if (cudaGetLastError() != cudaSuccess) return -3;
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : -4;
 }
+
+// ---- bounded completion wait: an mbarrier nothing arrives at (no MMA is
+// issued or committed) must give up after max_tries, report it in status,
+// and still release its tensor memory
+__global__ void tc_wait_timeout_kernel(uint32_t max_tries, int* status) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&slot, 32);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = slot;
+  const bool ok = tc::mbar_wait(&mbar, 0, max_tries);
+  if (!ok && tid == 0) atomicOr(status, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 32);
+  }
+}
+
+extern "C" int tc_wait_timeout_probe(unsigned max_tries, int* status) {
+  tc_wait_timeout_kernel<<<1, 128>>>(max_tries, status);
+  if (cudaGetLastError() != cudaSuccess) return -3;
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -4;
+}

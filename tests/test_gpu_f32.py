@@ -163,3 +163,35 @@ def test_f32_inflow_pulse_run(cuda_device, prec):
     qg, _ = S.get_state()
     err = perturbation_err(qg, qo, q0)
     assert np.all(err < RUN_TOL), err
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_f32_runs_are_bitwise_repeatable_and_bad_states_reported(cuda_device, prec):
+    """Two runs from the same state give the same bits (no atomics in the
+    stage; the ledger's partial sums are added in a fixed order), and a
+    non-physical state is reported without spoiling the context."""
+    from paper_1710_03887_gb300 import binding as B
+    xyz, EToV = W.kuhn_cube(4, jitter=0.1, seed=17)
+    case = Case(3, xyz, EToV)
+    q0 = case.pulse(0.05, 0.3)
+    dt = case.oracle.stable_dt(q0, 0.5)
+    S = f32_library(case, prec)
+    runs = []
+    for _ in range(2):
+        S.set_state(q0)
+        S.step(15, dt)
+        q, _ = S.get_state()
+        runs.append((q, S.boundary_flux()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+    bad = q0.copy()
+    bad[5, 4, 2] = 0.0                       # zero energy: negative pressure
+    S.set_state(bad)
+    with pytest.raises(B.DGError) as e:
+        S.step(1, dt)
+        S.get_state()
+    assert e.value.code == B.DG_ERR_NONFINITE
+    S.set_state(q0)                          # usable again
+    S.step(15, dt)
+    q, _ = S.get_state()
+    assert np.array_equal(q, runs[0][0])

@@ -109,3 +109,20 @@ def test_network_tanh_against_tanhf(cuda_device, probe):
     assert np.all(np.isfinite(f))
     assert np.abs(f - r).max() <= 3e-7, np.abs(f - r).max()
     assert np.abs(f - np.tanh(x.astype(np.float64))).max() <= 3e-7
+
+
+def test_bounded_completion_wait_gives_up_and_the_device_stays_usable(cuda_device, probe):
+    """The stage kernel's tensor-core completion wait is bounded: here nothing
+    ever arrives at the barrier, so the wait gives up after its tries, sets
+    the status word and frees its tensor memory; the same process then runs
+    a normal product."""
+    import time
+    import torch
+    probe.tc_wait_timeout_probe.restype = ctypes.c_int
+    probe.tc_wait_timeout_probe.argtypes = [ctypes.c_uint, ctypes.c_void_p]
+    st = torch.zeros(1, dtype=torch.int32, device=cuda_device)
+    t0 = time.perf_counter()
+    assert probe.tc_wait_timeout_probe(1 << 12, st.data_ptr()) == 0
+    assert time.perf_counter() - t0 < 10.0
+    assert int(st.item()) == 1
+    test_tf32_mma_matches_host(cuda_device, probe, 16, 8)
