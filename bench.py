@@ -367,11 +367,11 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     characteristic and learned conditions on the truncated ball, and the
     trained closure is timed on the bench workload."""
     from paper_1710_03887_gb300 import learned_bc as L
-    n, runs, every, iters = args.learned_n, 8, 10, 600
+    n, runs, every, iters = args.learned_n, 8, args.learned_every, 600
     t0 = time.perf_counter()
     nested = L.nested_ball(n)
     X, Y = L.record(WORKLOAD["order"], nested, L.run_seeds(0, runs), every=every, device=dev,
-                    width_scale=2.0)
+                    width_scale=2.0, node_fraction=args.learned_fraction)
     t_rec = time.perf_counter() - t0
     w, hist = L.train(X, Y, iters=iters, lr=3e-3, seed=0, radius=nested.radius,
                       order=WORKLOAD["order"])
@@ -404,7 +404,8 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
         "config": (f"radius-2 ball on the n={n} lattice ({len(nested.big[1])} tets), truncated at "
                    f"r=1 ({len(nested.small[1])} tets); p=3 float32; {runs} seeded pulse runs "
                    f"(centre |x|<0.5, width 0.2-0.4, amplitude 0.1-10% p0) sampled every "
-                   f"{every} steps at r=1; judged with centred pulses of width 0.3 and one "
+                   f"{every} steps at r=1 (fraction {args.learned_fraction:g} of the trace nodes); "
+                   "judged with centred pulses of width 0.3 and one "
                    "off-centre pulse of width 0.25; 'spherical' is the memory closure w_in = psi "
                    "without training"),
         "samples": int(X.shape[0]), "iters": iters, "loss_first": float(hist[0]),
@@ -495,7 +496,11 @@ def main():
                     help="arithmetic form of the headline number (the other is measured beside it)")
     ap.add_argument("--one-form", action="store_true", help="measure only --precision")
     ap.add_argument("--learned-n", type=int, default=16,
-                    help="lattice of the learned-closure experiment's radius-2 ball (0 = skip)")
+                    help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
+                         "64 gives the ~200k-element truncated ball of the configuration)")
+    ap.add_argument("--learned-every", type=int, default=10, help="steps between trace samples")
+    ap.add_argument("--learned-fraction", type=float, default=1.0,
+                    help="fraction of trace nodes kept per sample (seeded)")
     ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],
                     help="lattice size of the ball (32 = the benchmark; smaller for profiling)")
     args = ap.parse_args()

@@ -92,13 +92,18 @@ def crossing_time(center, width):
     return (1.0 + np.linalg.norm(center) + 3.0 * width) / c0
 
 
-def record(order, nested, runs, every, device, width_scale=1.0, precision=None, min_rel=1e-2):
+def record(order, nested, runs, every, device, width_scale=1.0, precision=None, min_rel=1e-2,
+           node_fraction=1.0, seed=0):
     """Reference runs on the large ball; returns device tensors (X, Y).
 
     Samples whose amplitude |w_out| + |psi| is below ``min_rel`` times the
     run's pulse amplitude (the far tail before the pulse arrives, where
-    features and targets are ratios of vanishing numbers) are dropped."""
+    features and targets are ratios of vanishing numbers) are dropped; with
+    ``node_fraction`` < 1 a seeded random subset of the trace nodes is kept
+    at each sampling time (large meshes)."""
     import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
     prec = B.DG_PREC_F32 if precision is None else precision
     S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.upload_mesh(*nested.big)
@@ -119,6 +124,8 @@ def record(order, nested, runs, every, device, width_scale=1.0, precision=None, 
             amp = torch.empty((n,), dtype=torch.float32, device=device)
             S.sample_traces(X, Y, amp)
             keep = amp > min_rel * a * W.P0_SI
+            if node_fraction < 1.0:
+                keep &= torch.rand(n, generator=gen, device=device) < node_fraction
             Xs.append(X[keep])
             Ys.append(Y[keep])
     S.sync()
