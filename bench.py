@@ -20,7 +20,7 @@ five-stage low-storage RK4 time step of the whole mesh.
              variant, float64) timed the same way, with the float32 forms'
              error against float64 after the timed steps
   learned_bc the learned boundary closure: traces recorded, network trained
-             and reflected energies judged on the GPU, and the closure timed on
+             and reflected energies measured on the GPU, and the closure timed on
              the bench workload
   cpu_baseline  the float64 CPU oracle on a bounded sample of the workload
 
@@ -363,7 +363,7 @@ LEARNED_AMPLITUDES = (0.001, 0.005, 0.02, 0.1)
 def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     """The learned closure end to end on the GPU: seeded reference runs on the
     radius-2 ball record traces at r = 1, the library trains the network,
-    the large ball judges the reflected energy of the free-stream,
+    the large ball is the reference for the reflected energy of the free-stream,
     characteristic and learned conditions on the truncated ball, and the
     trained closure is timed on the bench workload."""
     from paper_1710_03887_gb300 import learned_bc as L
@@ -399,7 +399,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
         "f32_minus_fp64_rel": (r32 - r64) / r64,
         "max_state_diff_rel_to_pulse_amplitude": L.max_state_difference(d32, d64, 0.02),
     }
-    t_judge = time.perf_counter() - t0 - t_rec - t_train
+    t_eval = time.perf_counter() - t0 - t_rec - t_train
     m = measure_form(args, "f32", xyz, EToV, dev, stream, dist, world, sample_clocks=False,
                      mlp=(w, WORKLOAD["radius"]))
     return {
@@ -407,7 +407,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
                    f"r=1 ({len(nested.small[1])} tets); p=3 float32; {runs} seeded pulse runs "
                    f"(centre |x|<0.5, width 0.2-0.4, amplitude 0.1-10% p0) sampled every "
                    f"{every} steps at r=1 (fraction {args.learned_fraction:g} of the trace nodes); "
-                   "judged with centred pulses of width 0.3 and one "
+                   "measured with centred pulses of width 0.3 and one "
                    "off-centre pulse of width 0.25; 'spherical' is the memory closure w_in = psi "
                    "without training"),
         "samples": int(X.shape[0]), "iters": iters, "loss_first": float(hist[0]),
@@ -415,7 +415,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
         "reflected_energy_rel": table,
         "gain_vs_characteristic": {k: v["characteristic"] / v["learned"] for k, v in table.items()},
         "vs_plain_fp64": fp64_check,
-        "seconds": {"record": t_rec, "train": t_train, "judge": t_judge},
+        "seconds": {"record": t_rec, "train": t_train, "evaluate": t_eval},
         "bench_workload_learned_bc": {"value": m["value"], "unit": UNIT,
                                       "ms_per_step": m["ms"] / args.steps,
                                       "avg_stage_launch_ms": m["kms"] / max(m["klaunch"], 1)},

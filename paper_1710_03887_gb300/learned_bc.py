@@ -13,7 +13,7 @@ orchestrates calls and keeps tensors):
    (dg_sample_traces).
 3. ``train``: full-batch Adam on the GPU with the library's own forward and
    backward kernels (dg_mlp_train).
-4. ``reflected_energy``: the judge. The truncated ball with a given outer
+4. ``reflected_energy``: the measure. The truncated ball with a given outer
    condition and the large ball start from the same pulse; after the pulse
    has left r < 1 in the large ball, the acoustic energy of their difference
    inside r < 1, relative to the initial acoustic energy, is the reflection
@@ -182,7 +182,8 @@ def acoustic_energy(dq, J, wq):
 def reflection_table(order, nested, amplitude, width, center, weights, precision=None):
     """Reflected energies of the free-stream (the paper's pass-through),
     characteristic, exact spherical-wave (``spherical_weights``) and learned
-    conditions for one pulse; the large ball is run once and judges all four."""
+    conditions for one pulse; the large ball is run once as the reference
+    for all four."""
     prec = B.DG_PREC_F32 if precision is None else precision
     big = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     big.upload_mesh(*nested.big)

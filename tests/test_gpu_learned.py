@@ -173,7 +173,7 @@ def test_trace_samples_match_oracle(cuda_device):
 def test_spherical_closure_absorbs_a_centred_pulse(cuda_device):
     """The memory on its own, through a network that realises w_in = psi:
     on the truncated ball a centred pulse leaves with far less reflected
-    energy than under the characteristic condition (the large ball judges)."""
+    energy than under the characteristic condition (the large ball is the reference)."""
     nested = L.nested_ball(16)
     rc, _ = L.reflected_energy(3, nested, 0.01, 0.3, (0.0, 0.0, 0.0), B.DG_BC_CHARACTERISTIC)
     rs, _ = L.reflected_energy(3, nested, 0.01, 0.3, (0.0, 0.0, 0.0), B.DG_BC_LEARNED,
@@ -184,7 +184,7 @@ def test_spherical_closure_absorbs_a_centred_pulse(cuda_device):
 
 def test_learned_closure_beats_characteristic(cuda_device):
     """Train on the method's own traces at r = 1 inside the radius-2 ball and
-    compare reflected energies on the truncated ball (the large ball judges)."""
+    compare reflected energies on the truncated ball (the large ball is the reference)."""
     p, n = 3, 16
     nested = L.nested_ball(n)
     runs = L.run_seeds(0, 6)
