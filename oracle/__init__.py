@@ -11,8 +11,13 @@ Modules:
                      (Appendix A, Eqs. 10-11), built from a monomial basis with
                      exact integrals
   geometry           affine maps, normals, face matching by coordinates
-  euler_dg           Euler fluxes (Eqs. 1-2), boundary ghost states (section
-                     2.2, Eq. 4), local Lax-Friedrichs flux, semi-discrete
-                     right-hand side (Eqs. 10, 12), low-storage RK4, probes,
+  euler_dg           Euler fluxes (Eqs. 1-2), boundary ghost states (free
+                     stream, characteristic, wall: sections 2.2-2.3, Eq. 4;
+                     inflow pulse: section 2.4, Eqs. 5-7; the learned closure
+                     and its spherical-wave memory), local Lax-Friedrichs
+                     flux, semi-discrete right-hand side (Eqs. 10, 12) and its
+                     contraction inputs, low-storage RK4, probes,
                      boundary-flux ledger and conserved totals
+  mlp                the closure's network (forward, loss gradient, Adam) and
+                     its features
 """

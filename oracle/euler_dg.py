@@ -50,7 +50,12 @@ What is computed, with the passage it follows:
 Parity status: pinned (tests/test_oracle_euler.py: flux consistency and
 antisymmetry, free-stream preservation, discrete conservation, p+1
 convergence against exact solutions, axis-permutation and inversion
-symmetry, LSRK order conditions, the characteristic ghost on 1D states).
+symmetry, LSRK order conditions, the characteristic ghost on 1D states, the
+inflow ghost's free stream outside the pulse and its first-order plane-wave
+flux, the contraction inputs recombining to the right-hand side;
+tests/test_oracle_mlp.py: the learned ghost's reduction to the
+characteristic one and its bound, the memory against the closed form of an
+outgoing spherical wave and its decay on the free stream).
 """
 from __future__ import annotations
 
