@@ -13,10 +13,16 @@
  *   - local Lax-Friedrichs numerical flux on every face (section 1.1);
  *   - outer-boundary ghost states: the paper's free-stream pass-through
  *     condition (section 2.2), a characteristic (Riemann-invariant)
- *     far-field ghost (section 1) and the reflective wall of section 2.3 Eq. 4;
+ *     far-field ghost (section 1), the reflective wall of section 2.3 Eq. 4,
+ *     the mouthpiece inflow pulse of section 2.4 (Eqs. 5-7), and a learned
+ *     closure (a network trained on the method's own traces, with a
+ *     spherical-wave memory after the asymptotic conditions section 1 names);
  *   - time integration of the ODE system of Eq. 12 with the five-stage
  *     2N-storage fourth-order Runge-Kutta scheme of Carpenter & Kennedy (1994);
- *   - sensors (section 3) and the time-integrated boundary flux.
+ *   - sensors (section 3) and the time-integrated boundary flux;
+ *   - three arithmetic forms of the time step: float64, a float32
+ *     perturbation form, and the float32 form with tensor-core (tcgen05,
+ *     TF32x3) contractions.
  *
  * Conventions
  *   - Every function returns an int status: DG_OK (0) or a negative DG_ERR_*.
@@ -30,15 +36,17 @@
  *     freed by dg_destroy). Device work is enqueued on the stream given by
  *     dg_set_stream (default: the legacy default stream); calls that return
  *     host data synchronise that stream.
- *   - State layout everywhere: q[K][5][Np] (element-major, then variable,
- *     then node), float64. Node order: lattice (i,j,k), i+j+k <= p, with k
+ *   - State layout at the interface: q[K][5][Np] (element-major, then
+ *     variable, then node), float64, total (not perturbation) state; the
+ *     float32 forms convert inside. Node order: lattice (i,j,k), i+j+k <= p, with k
  *     outermost and i innermost; reference tetrahedron vertices v1=(-1,-1,-1),
  *     v2=(1,-1,-1), v3=(-1,1,-1), v4=(-1,-1,1) map to element vertices
  *     EToV[e][0..3].
- *   - A device error (non-finite state, non-positive density or pressure) is
- *     latched in a status word on the device and reported as
- *     DG_ERR_NONFINITE by the next call that synchronises (dg_sync,
- *     dg_get_state, dg_read_*), which also clears it.
+ *   - A device error (non-finite state, non-positive density or pressure; a
+ *     tensor-core completion wait that gave up) is latched in a status word
+ *     on the device and reported as DG_ERR_NONFINITE (DG_ERR_TIMEOUT) by the
+ *     next call that synchronises (dg_sync, dg_get_state, dg_read_*), which
+ *     also clears it; the context stays usable.
  */
 #ifndef DG_EULER_H
 #define DG_EULER_H
@@ -73,10 +81,12 @@ extern "C" {
 /* Arithmetic of the time step (dg_params.precision) */
 #define DG_PREC_FP64 0          /* float64 state, fluxes and contractions               */
 #define DG_PREC_F32 1           /* float32 perturbation state q - q0 about the resting   */
-                                /* free stream (u0 must be 0); fluxes, contractions and  */
-                                /* update in float32; ghost states, geometry record and  */
-                                /* the ledger / totals accumulate in float64. The state  */
-                                /* still crosses the ABI as total float64 q[K][5][Np].   */
+                                /* free stream (u0 must be 0); fluxes, ghost states      */
+                                /* (written without cancellation against p0, c0),        */
+                                /* contractions and update in float32; geometry and      */
+                                /* operators formed in float64 on the host; the ledger   */
+                                /* and totals add in float64. The state still crosses    */
+                                /* the ABI as total float64 q[K][5][Np].                 */
 #define DG_PREC_F32_TC 2        /* DG_PREC_F32 with both contractions (volume and LIFT,  */
                                 /* Eq. 10) as one tcgen05 tensor-core GEMM per tile of   */
                                 /* 25 elements, tf32 operands split in head + tail,      */

@@ -9,9 +9,35 @@
 
 namespace dgk {
 
+// 1/x by Newton-Raphson on f(y) = 1/y - x (y <- y + y (1 - x y)) from the
+// hardware's approximate reciprocal: each step squares the relative error,
+// so two steps take the estimate below double precision rounding (tested
+// against the correctly rounded division to 2 ulp).
+__device__ __forceinline__ double recip_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  y = fma(y, fma(-x, y, 1.0), y);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return y;
+}
+
+// sqrt(x), x > 0: Newton-Raphson on 1/sqrt(x) (y <- y (3 - x y^2) / 2) from
+// the hardware estimate, then s = x y and one Newton step on s
+// (s <- s + (x - s^2) y / 2); 0 for x <= 0 (a non-physical state, which the
+// kernels report separately). Tested against sqrt to 2 ulp.
+__device__ __forceinline__ double sqrt_nr(double x) {
+  if (!(x > 0.0)) return 0.0;
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  const double s = x * y;
+  return fma(fma(-s, s, x), 0.5 * y, s);
+}
+
 __device__ __forceinline__ void pressure_and_velocity(const double q[5], double gm1, double& rinv,
                                                       double u[3], double& p) {
-  rinv = 1.0 / q[0];
+  rinv = recip_nr(q[0]);
   u[0] = q[1] * rinv;
   u[1] = q[2] * rinv;
   u[2] = q[3] * rinv;
@@ -29,7 +55,7 @@ __device__ __forceinline__ void normal_flux(const double q[5], const double n[3]
   fn[2] = q[2] * un + p * n[1];
   fn[3] = q[3] * un + p * n[2];
   fn[4] = (q[4] + p) * un;
-  lam = fabs(un) + sqrt(g.gamma * p * rinv);
+  lam = fabs(un) + sqrt_nr(g.gamma * p * rinv);
 }
 
 // Ghost state of an outer face node.

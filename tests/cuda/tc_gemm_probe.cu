@@ -206,3 +206,24 @@ extern "C" int tc_wait_timeout_probe(unsigned max_tries, int* status) {
   if (cudaGetLastError() != cudaSuccess) return -3;
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : -4;
 }
+
+// ---- float64 reciprocal and square root of the float64 stage kernel
+#include "../../paper_1710_03887_gb300/csrc/dg_physics.cuh"
+
+__global__ void fp64_nr_probe_kernel(const double* x, double* rcp, double* rcp_ref, double* sq,
+                                     double* sq_ref, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rcp[i] = dgk::recip_nr(x[i]);
+  rcp_ref[i] = 1.0 / x[i];
+  sq[i] = dgk::sqrt_nr(x[i]);
+  sq_ref[i] = sqrt(x[i]);
+}
+
+extern "C" int fp64_nr_probe(const double* x, double* rcp, double* rcp_ref, double* sq,
+                             double* sq_ref, int n) {
+  if (n <= 0) return -1;
+  fp64_nr_probe_kernel<<<(n + 255) / 256, 256>>>(x, rcp, rcp_ref, sq, sq_ref, n);
+  if (cudaGetLastError() != cudaSuccess) return -3;
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -4;
+}

@@ -126,3 +126,24 @@ def test_bounded_completion_wait_gives_up_and_the_device_stays_usable(cuda_devic
     assert time.perf_counter() - t0 < 10.0
     assert int(st.item()) == 1
     test_tf32_mma_matches_host(cuda_device, probe, 16, 8)
+
+
+def test_float64_newton_reciprocal_and_sqrt(cuda_device, probe):
+    """The float64 stage's reciprocal and square root (Newton-Raphson from
+    the hardware estimates) stay within 2 ulp of the correctly rounded
+    division and sqrt over the range a state can reach."""
+    import torch
+    probe.fp64_nr_probe.restype = ctypes.c_int
+    probe.fp64_nr_probe.argtypes = [ctypes.c_void_p] * 5 + [ctypes.c_int]
+    rng = np.random.default_rng(5)
+    x = np.concatenate([10.0 ** rng.uniform(-8, 12, size=200000),
+                        [1.0, 2.0, 0.5, 1.225, 101325.0, 1.4, 3.0, 1e-300, 1e300]])
+    dx = torch.from_numpy(x).to(cuda_device)
+    outs = [torch.empty_like(dx) for _ in range(4)]
+    assert probe.fp64_nr_probe(dx.data_ptr(), *(o.data_ptr() for o in outs), x.size) == 0
+    rcp, rcp_ref, sq, sq_ref = (o.cpu().numpy() for o in outs)
+    ok = (x > 1e-290) & (x < 1e290)
+    ulp = np.spacing(np.abs(rcp_ref))
+    assert np.all(np.abs(rcp - rcp_ref)[ok] <= 2 * ulp[ok])
+    ulp = np.spacing(sq_ref)
+    assert np.all(np.abs(sq - sq_ref)[ok] <= 2 * ulp[ok])
