@@ -254,10 +254,10 @@ int ensure_device(dg_ctx* c) {
     DG_CUDA(cudaMemset(c->bpsi_res, 0, nb));
     DG_CUDA(cudaMemset(c->bD, 0, nb));
   }
-  if (f32 && !tcf) {
+  {
     // faces each tile evaluates: a face shared by two elements of the tile
-    // once, under the lower element (the float32 stage writes both jumps)
-    const size_t row = 16 + 4 * size_t(ET);
+    // once, under the lower element (the stage writes both jumps)
+    const size_t row = 16 + (4 * size_t(ET) + 15) / 16 * 16;   // rows start on 16-byte boundaries
     std::vector<uint8_t> fl(size_t(c->ntiles) * row, 0);
     for (int t = 0; t < c->ntiles; ++t) {
       const int64_t e0 = int64_t(t) * ET, e1 = std::min<int64_t>(K, e0 + ET);
@@ -351,6 +351,7 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
   A.ops = c->ops;
   A.nbr_tbl = c->tbl;
   A.fmask = c->fmask;
+  A.face_list = c->face_list;
   A.led = ledger_args(c, update, a, b, dt);
   A.status = c->status;
   A.K = c->mesh.K;

@@ -83,6 +83,7 @@ struct StageArgs {
   const uint8_t* nbr_tbl;    // [4][4][6][Nfp]: neighbour volume node; then the same
                              // shape: neighbour face node (index in its face's list)
   const int32_t* fmask;      // [4][Nfp]
+  const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]: count, then (le << 2 | f)
   LedgerArgs led;
   int* status;
   int64_t K;
@@ -118,7 +119,7 @@ struct StageArgsF32 {
   // float32 stage: per tile, a 16-byte header (int32 count) then the faces it
   // evaluates, one byte each (element in tile << 2 | face); a face between
   // two elements of the tile appears once, under its lower element
-  const uint8_t* face_list;  // [ntiles][16 + 4 ET]
+  const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]
 };
 
 int stage_f32_tile_elems(int p);

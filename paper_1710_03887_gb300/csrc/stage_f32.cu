@@ -109,7 +109,8 @@ struct OrderF {
   static constexpr int nWarps = NT / 32;
   static constexpr size_t oRedB = (size_t(oEnd) * 4 + 15) / 16 * 16;
   static constexpr size_t oConnB = oRedB + size_t(nWarps) * 5 * 8;
-  static constexpr size_t kFL = 16 + 4 * size_t(ET);                // face list row (bytes)
+  static constexpr size_t kFL = 16 + (4 * size_t(ET) + 15) / 16 * 16;   // face list row (16-byte multiple)
+  static_assert(kFL % 16 == 0, "face-list rows are copied in 16-byte pieces");
   static constexpr size_t oFLB = oConnB + 2 * size_t(ET) * 4 * 4;   // two face-list buffers
   static constexpr size_t oFmaskB = oFLB + 2 * kFL;
   static constexpr size_t oTblB = oFmaskB + size_t(4) * Nfp * 4;

@@ -50,8 +50,10 @@ struct Order {
   static constexpr size_t bytes_double = size_t(oEnd) * 8;
   static constexpr size_t oConnB = bytes_double;                       // ET*4 int32
   static constexpr size_t oFmaskB = oConnB + size_t(ET) * 4 * 4;       // 4*Nfp int32
-  static constexpr size_t oTblB = oFmaskB + size_t(4) * Nfp * 4;       // kTbl bytes
-  static constexpr size_t bytes = (oTblB + kTbl + 15) / 16 * 16;
+  static constexpr size_t oTblB = oFmaskB + size_t(4) * Nfp * 4;       // 2 kTbl bytes
+  static constexpr size_t kFL = 16 + (4 * size_t(ET) + 15) / 16 * 16;   // face list row
+  static constexpr size_t oFLB = (oTblB + 2 * kTbl + 15) / 16 * 16;
+  static constexpr size_t bytes = (oFLB + kFL + 15) / 16 * 16;
 };
 
 template <int P>
@@ -78,7 +80,8 @@ stage_fp64_kernel(const StageArgs A) {
   const int tid = threadIdx.x;
 
   for (int i = tid; i < O::kOps; i += NT) sOps[i] = A.ops[i];
-  for (int i = tid; i < O::kTbl; i += NT) sTbl[i] = A.nbr_tbl[i];
+  for (int i = tid; i < 2 * O::kTbl; i += NT) sTbl[i] = A.nbr_tbl[i];   // volume- and face-node tables
+  uint8_t* sFL = smem_raw + O::oFLB;
   for (int i = tid; i < 4 * Nfp; i += NT) sFmask[i] = A.fmask[i];
   const Gas g = A.gas;
 
@@ -94,6 +97,8 @@ stage_fp64_kernel(const StageArgs A) {
       for (int i = tid; i < nE * kGeoStride; i += NT) sGeo[i] = gg[i];
       const int32_t* gc = A.conn + e0 * 4;
       for (int i = tid; i < nE * 4; i += NT) sConn[i] = gc[i];
+      const uint8_t* gl = A.face_list + size_t(tile) * O::kFL;
+      for (int i = tid; i < int(O::kFL); i += NT) sFL[i] = gl[i];
     }
     __syncthreads();
 
@@ -125,19 +130,33 @@ stage_fp64_kernel(const StageArgs A) {
       }
     }
 
-    // ---- face fluxes at face nodes
+    // ---- face fluxes at the nodes of the tile's listed faces. A face between
+    // two elements of the tile is listed once, under its lower element, which
+    // writes both jumps: with A = (n.F(q-) - n.F(q+)) / 2 and
+    // B = lambda (q+ - q-) / 2, Fscale (A + B) for itself and Fscale' (A - B)
+    // for the neighbour (normal -n, traces swapped).
     double led[5] = {0, 0, 0, 0, 0};
     bool any_bdry = false;
-    for (int it = tid; it < nE * NF; it += NT) {
-      const int le = it / NF, fm = it - (it / NF) * NF;
-      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+    const int nF = *reinterpret_cast<const int32_t*>(sFL);
+    for (int it = tid; it < nF * Nfp; it += NT) {
+      const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
+      const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int n = sFmask[f * Nfp + m];
       double qm[5], qp[5];
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
       const double* geo = sGeo + le * kGeoStride;
       const double nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       const int32_t c = sConn[le * 4 + f];
-      if (c >= 0) {
+      const int le2 = (c >= 0) ? int((c >> 5) - e0) : -1;
+      const bool inside = c >= 0 && le2 >= 0 && le2 < nE;   // then le2 > le (face list)
+      int f2 = 0, m2 = 0;
+      if (inside) {
+        f2 = (c >> 3) & 3;
+        const int o = c & 7;
+        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+        m2 = sTbl[O::kTbl + ((f * 4 + f2) * 6 + o) * Nfp + m];
+        for (int v = 0; v < 5; ++v) qp[v] = sQ[(le2 * 5 + v) * Np + n2];
+      } else if (c >= 0) {
         const int64_t e2 = c >> 5;
         const int f2 = (c >> 3) & 3, o = c & 7;
         const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
@@ -151,10 +170,12 @@ stage_fp64_kernel(const StageArgs A) {
       normal_flux(qp, nv, g, fnp, lp);
       const double lam = fmax(lm, lp);
       const double fs = geo[kGeoFscale + f];
+      const double fs2 = inside ? sGeo[le2 * kGeoStride + kGeoFscale + f2] : 0.0;
       for (int v = 0; v < 5; ++v) {
-        const double fstar = 0.5 * (fnm[v] + fnp[v]) - 0.5 * lam * (qp[v] - qm[v]);
-        sDF[(le * 5 + v) * NF + fm] = fs * (fnm[v] - fstar);
-        if (c < 0) led[v] += faceW[fm] * geo[kGeoSJ + f] * fstar;
+        const double hA = 0.5 * (fnm[v] - fnp[v]), hB = 0.5 * lam * (qp[v] - qm[v]);
+        sDF[(le * 5 + v) * NF + fm] = fs * (hA + hB);
+        if (inside) sDF[(le2 * 5 + v) * NF + f2 * Nfp + m2] = fs2 * (hA - hB);
+        if (c < 0) led[v] += faceW[fm] * geo[kGeoSJ + f] * (0.5 * (fnm[v] + fnp[v]) - hB);
       }
       any_bdry |= (c < 0);
     }

@@ -58,8 +58,11 @@ struct OrderTC {
   static constexpr size_t oRed = al16(oW + size_t(NF) * 4);         // 16 warps x 5 doubles
   static constexpr size_t oConn = oRed + 16 * 5 * 8;                 // 2 x ET*4 ints
   static constexpr size_t oFmask = oConn + 2 * size_t(ET) * 16;      // 4*Nfp ints
-  static constexpr size_t oTbl = oFmask + size_t(NF) * 4;            // 96*Nfp bytes
-  static constexpr size_t oBar = al16(oTbl + 96 * Nfp);              // mbarrier, tmem slot, flag
+  static constexpr size_t oTbl = oFmask + size_t(NF) * 4;            // 2 x 96*Nfp bytes
+  static constexpr size_t kFL = 16 + (4 * size_t(ET) + 15) / 16 * 16;   // face list row (16-byte multiple)
+  static_assert(kFL % 16 == 0, "face-list rows are copied in 16-byte pieces");
+  static constexpr size_t oFL = al16(oTbl + 2 * 96 * Nfp);           // 2 face-list buffers
+  static constexpr size_t oBar = al16(oFL + 2 * kFL);                // mbarrier, tmem slot, flag
   static constexpr size_t bytes = oBar + 32;
   static constexpr size_t kOpsBytes = 2 * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
 };
@@ -134,7 +137,7 @@ stage_tc_kernel(const StageArgsF32 A) {
     const float* w = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(A.ops) +
                                                     2 * O::kBBytes);
     for (int i = tid; i < NF; i += NT) sW[i] = w[i];
-    for (int i = tid; i < 96 * Nfp; i += NT) sTbl[i] = A.nbr_tbl[i];
+    for (int i = tid; i < 2 * 96 * Nfp; i += NT) sTbl[i] = A.nbr_tbl[i];   // volume- and face-node tables
     for (int i = tid; i < NF; i += NT) sFmask[i] = A.fmask[i];
   }
   if (tid == 0) {
@@ -174,6 +177,9 @@ stage_tc_kernel(const StageArgsF32 A) {
     int32_t* dc = reinterpret_cast<int32_t*>(smem + O::oConn) + bf * ET * 4;
     const int32_t* gc = A.conn + f0 * 4;
     for (int i = tid; i < n; i += NT) cp_async16(dc + 4 * i, gc + 4 * i);
+    unsigned char* dl = smem + O::oFL + bf * O::kFL;
+    const uint8_t* gl = A.face_list + size_t(t) * O::kFL;
+    for (int i = tid; i < int(O::kFL / 16); i += NT) cp_async16(dl + 16 * i, gl + 16 * i);
   };
   prefetch(blockIdx.x, 0);
   cp_async_commit();
@@ -187,18 +193,21 @@ stage_tc_kernel(const StageArgsF32 A) {
     const float* sQ = reinterpret_cast<const float*>(smem + O::oQ) + buf * O::kQT;
     const float* sGeo = reinterpret_cast<const float*>(smem + O::oGeo) + buf * ET * kGeoStride;
     const int32_t* sConn = reinterpret_cast<const int32_t*>(smem + O::oConn) + buf * ET * 4;
+    const uint8_t* sFL = smem + O::oFL + buf * O::kFL;      // count, then (le << 2 | f)
     cp_async_wait_all();
     tc::fence_before_sync();
     __syncthreads();   // this tile's data is in; the previous tile is finished
     if (*sAbort) break;
     tc::fence_after_sync();
 
-    // neighbour traces into the face columns of X (row 5 le + v, column 3 Np + fm)
-    for (int it = tid; it < nE * NF; it += NT) {
-      const int le = it / NF, fm = it - (it / NF) * NF;
-      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+    // neighbour traces of faces whose neighbour lies outside the tile, into
+    // the face columns of X (row 5 le + v, column 3 Np + fm)
+    const int nF = *reinterpret_cast<const int32_t*>(sFL);
+    for (int it = tid; it < nF * Nfp; it += NT) {
+      const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
+      const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      if (c >= 0) {
+      if (c >= 0 && ((c >> 5) < e0 || (c >> 5) >= e0 + nE)) {
         const int64_t e2 = c >> 5;
         const int f2 = (c >> 3) & 3, o = c & 7;
         const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
@@ -240,12 +249,14 @@ stage_tc_kernel(const StageArgsF32 A) {
     cp_async_wait_group1();            // the gathers; the next tile may still fly
     __syncthreads();
 
-    // ---- faces: jumps Fscale (n.F(q-) - F*) into X columns [3 Np, 3 Np + 4 Nfp)
+    // ---- faces: jumps Fscale (n.F(q-) - F*) into X columns [3 Np, 3 Np + 4 Nfp),
+    // a face between two elements of the tile once (both jumps: Fscale (A + B)
+    // and Fscale' (A - B), A = (n.F(q-) - n.F(q+)) / 2, B = lambda (q+ - q-) / 2)
     float led[5] = {0, 0, 0, 0, 0};
     bool any_bdry = false;
-    for (int it = tid; it < nE * NF; it += NT) {
-      const int le = it / NF, fm = it - (it / NF) * NF;
-      const int f = fm / Nfp, m = fm - (fm / Nfp) * Nfp;
+    for (int it = tid; it < nF * Nfp; it += NT) {
+      const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
+      const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int n = sFmask[f * Nfp + m];
       float qm[5], qp[5];
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
@@ -253,7 +264,18 @@ stage_tc_kernel(const StageArgsF32 A) {
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       const int32_t c = sConn[le * 4 + f];
       float* xf = sX + le * 5 * SX + 3 * Np + fm;     // row v at + v * SX
-      if (c >= 0) {
+      const int le2 = (c >= 0) ? int((c >> 5) - e0) : -1;
+      const bool inside = c >= 0 && le2 >= 0 && le2 < nE;   // then le2 > le (face list)
+      float* xf2 = xf;
+      float fs2 = 0.0f;
+      if (inside) {
+        const int f2 = (c >> 3) & 3, o = c & 7;
+        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+        const int m2 = sTbl[96 * Nfp + ((f * 4 + f2) * 6 + o) * Nfp + m];
+        for (int v = 0; v < 5; ++v) qp[v] = sQ[(le2 * 5 + v) * Np + n2];
+        xf2 = sX + le2 * 5 * SX + 3 * Np + f2 * Nfp + m2;
+        fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
+      } else if (c >= 0) {
         for (int v = 0; v < 5; ++v) qp[v] = xf[v * SX];
       } else {
         const int mode = A.bc_mode[(-1 - c) & 7];
@@ -270,12 +292,10 @@ stage_tc_kernel(const StageArgsF32 A) {
       const float lam = fmaxf(lm, lp);
       const float fs = geo[kGeoFscale + f];
       for (int v = 0; v < 5; ++v) {
-        const float jump = 0.5f * (fnm[v] - fnp[v]) + 0.5f * lam * (qp[v] - qm[v]);
-        xf[v * SX] = fs * jump;
-        if (c < 0) {
-          const float fstar = 0.5f * (fnm[v] + fnp[v]) - 0.5f * lam * (qp[v] - qm[v]);
-          led[v] += sW[fm] * geo[kGeoSJ + f] * fstar;
-        }
+        const float hA = 0.5f * (fnm[v] - fnp[v]), hB = 0.5f * lam * (qp[v] - qm[v]);
+        xf[v * SX] = fs * (hA + hB);
+        if (inside) xf2[v * SX] = fs2 * (hA - hB);
+        if (c < 0) led[v] += sW[fm] * geo[kGeoSJ + f] * (0.5f * (fnm[v] + fnp[v]) - hB);
       }
       any_bdry |= (c < 0);
     }
