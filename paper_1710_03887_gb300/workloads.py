@@ -213,3 +213,175 @@ def random_smooth_state(nodes, gamma, rho0, p0, amplitude, seed=0):
 GAMMA = 1.4
 RHO0_SI = 1.225
 P0_SI = 101325.0
+
+
+# ---------------------------------------------------------------- horn workload
+# Boundary ids of ``horn_in_room``'s face tags
+HORN_OUTER, HORN_WALL, HORN_MOUTHPIECE = 0, 1, 2
+
+
+def horn_radius(x, bore=0.006, bell=0.06, x0=1.05, m=0.7):
+    """Bessel-flared horn profile r(x) = bore (x0 - x)^-m, clamped to
+    [bore, bell]: a short cylindrical bore (x < x0 - 1) and then the flare,
+    r(1) = 0.0488 for the defaults. The horn's axis is the x axis and its
+    mouthpiece the plane x = 0 (section 1.2 builds the paper's trumpet the same
+    way: a straight bore, a flare, rotated about the axis)."""
+    x = np.asarray(x, dtype=np.float64)
+    r = bore * np.power(np.maximum(x0 - x, 1e-300), -m)
+    return np.clip(r, bore, bell)
+
+
+def _graded(h0, length, growth):
+    """Positions 0 = y_0 < ... < y_n = length whose spacings grow geometrically
+    from about h0 by the factor ``growth`` (all scaled to end at ``length``)."""
+    if growth <= 1.0:
+        n = max(1, int(round(length / h0)))
+        return np.linspace(0.0, length, n + 1)
+    n = max(1, int(np.ceil(np.log1p(length * (growth - 1.0) / h0) / np.log(growth))))
+    y = np.concatenate([[0.0], np.cumsum(h0 * growth ** np.arange(n))])
+    return y * (length / y[-1])
+
+
+def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12,
+                 horn_length=1.0, wall=0.002, aspect=1.0, profile=horn_radius):
+    """A flared horn opening into a room in front of its bell: the
+    bell-front domains of section 1.2 (Table 1's half domains, where the region
+    behind the bell plane is left out), meshed without a mesh generator.
+
+    Logical lattice: planes ix along the axis, and a square lattice
+    (i, j) in [-m, m]^2 across it. The inner block max(|i|, |j|) <= m1 maps onto
+    the disc of radius ``profile(x)`` (the horn's interior; the same
+    square-to-disc blend as ``ball``), the rings outside it onto annuli whose
+    widths grow from ``wall`` by ``growth`` out to the room's side wall (a
+    square of half-width ``room_half`` for ``shape="box"``, a circle of that
+    radius for ``"cylinder"``). Horn planes are spaced ``aspect`` times the
+    local cross-section cell (r(x) / m1); room planes grow from ``wall`` by
+    ``growth`` out to ``horn_length + room_length``. Horn cells are the inner
+    block of the planes up to the bell, room cells the whole lattice after it;
+    every cell is split into six tetrahedra (the Kuhn chains of ``kuhn_cube``,
+    mirrored across the axis planes so the four quadrants are mirror images).
+
+    Face tags: HORN_MOUTHPIECE on the plane x = 0 (the inflow pulse of section
+    2.4), HORN_WALL on the horn's lateral surface and on the first ring of the
+    bell plane (the bell's rim, one wall thickness wide; slip walls, Eq. 4),
+    HORN_OUTER on the rest of the room's boundary (pass-through).
+
+    Returns ``(xyz, EToV, face_tag, info)``; ``info`` has the bell plane,
+    the element counts of horn and room, and the sensor analogues of Table 2.
+    """
+    if shape not in ("box", "cylinder"):
+        raise ValueError("shape must be 'box' or 'cylinder'")
+    m1 = int(m1)
+    if m1 < 1:
+        raise ValueError("m1 must be >= 1")
+    # planes along the axis
+    xs = [0.0]
+    while xs[-1] < horn_length:
+        xs.append(xs[-1] + aspect * float(profile(xs[-1])) / m1)
+    xs = np.asarray(xs) * (horn_length / xs[-1])
+    nh = len(xs) - 1
+    xs = np.concatenate([xs, horn_length + _graded(wall, room_length, growth)[1:]])
+    NX = len(xs) - 1
+    # rings of the room's cross-section
+    R_in = float(profile(horn_length))
+    if room_half <= R_in + wall:
+        raise ValueError("the room must be wider than the bell and its rim")
+    rho = R_in + _graded(wall, room_half - R_in, growth)
+    m = m1 + len(rho) - 1
+    beta = 1.0 if shape == "box" else 0.0
+
+    # vertex positions on the full logical lattice
+    g = np.arange(-m, m + 1)
+    IX, I, J = np.meshgrid(np.arange(NX + 1), g, g, indexing="ij")
+    IX, I, J = IX.ravel(), I.ravel(), J.ravel()
+    S = np.maximum(np.abs(I), np.abs(J))
+    L2 = np.hypot(I, J).astype(np.float64)
+    safe = np.where(L2 > 0, L2, 1.0)
+    x = xs[IX]
+    R = profile(np.minimum(x, horn_length))
+    yz = np.zeros((IX.size, 2))
+    inner = S <= m1
+    v = np.stack([I, J], axis=1) / m1
+    linf = S / m1
+    gfac = 1.0 - linf * (1.0 - np.where(L2 > 0, S / safe, 1.0))
+    yz[inner] = (R[:, None] * v * gfac[:, None])[inner]
+    outer = ~inner
+    k = np.clip(S - m1, 0, len(rho) - 1)
+    phi = (rho[k] - R_in) / (room_half - R_in)
+    dir_c = np.stack([I, J], axis=1) / safe[:, None]
+    dir_s = np.stack([I, J], axis=1) / np.where(S > 0, S, 1)[:, None]
+    far = room_half * ((1.0 - beta) * dir_c + beta * dir_s)
+    yz_o = (1.0 - phi)[:, None] * R_in * dir_c + phi[:, None] * far
+    yz[outer] = yz_o[outer]
+    xyz_all = np.column_stack([x, yz])
+
+    # cells: the inner block up to the bell plane, everything after it
+    W = 2 * m + 1
+
+    def vid(a, b, c):
+        return (a * W + (b + m)) * W + (c + m)
+
+    cx, ci, cj = np.meshgrid(np.arange(NX), np.arange(-m, m), np.arange(-m, m), indexing="ij")
+    cx, ci, cj = cx.ravel(), ci.ravel(), cj.ravel()
+    keep = (cx >= nh) | ((ci >= -m1) & (ci + 1 <= m1) & (cj >= -m1) & (cj + 1 <= m1))
+    cx, ci, cj = cx[keep], ci[keep], cj[keep]
+    cells = np.stack([cx, ci, cj], axis=1)
+    step = np.stack([np.ones_like(cx), np.where(ci >= 0, 1, -1), np.where(cj >= 0, 1, -1)], axis=1)
+    start = cells + (step < 0)
+    tets = []
+    for perm in _PERMS:
+        corner = start.copy()
+        chain = [corner.copy()]
+        for axis in perm:
+            corner = corner.copy()
+            corner[:, axis] += step[:, axis]
+            chain.append(corner)
+        tets.append(np.stack([vid(q[:, 0], q[:, 1], q[:, 2]) for q in chain], axis=1))
+    EToV = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int64)
+    # orientation from the logical lattice; the map must agree with it everywhere
+    lat = np.column_stack([IX, I, J]).astype(np.float64)
+
+    def signed(P):
+        p = P[EToV]
+        return np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])
+
+    neg = signed(lat) < 0
+    EToV[neg, 1], EToV[neg, 2] = EToV[neg, 2].copy(), EToV[neg, 1].copy()
+    if np.any(signed(xyz_all) <= 0):
+        raise ValueError("horn map folded a cell: lower growth or aspect")
+    used, inv = np.unique(EToV.ravel(), return_inverse=True)
+    EToV = inv.reshape(EToV.shape).astype(np.int32)
+    xyz = xyz_all[used].copy()
+    lix, ls = IX[used], S[used]
+
+    # boundary faces (faces met once) and their tags
+    fv = np.array([(0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3)])
+    faces = np.sort(EToV[:, fv], axis=2).reshape(-1, 3).astype(np.int64)
+    key = (faces[:, 0] * len(used) + faces[:, 1]) * len(used) + faces[:, 2]
+    _, first, count = np.unique(key, return_inverse=True, return_counts=True)
+    bnd = count[first] == 1
+    fx, fs = lix[faces], ls[faces]
+    tag = np.full(faces.shape[0], -1, dtype=np.int8)
+    mouth = np.all(fx == 0, axis=1)
+    rim = np.all(fx == nh, axis=1) & (fs.max(axis=1) <= m1 + 1)
+    side = np.all(fx <= nh, axis=1) & np.all(fs == m1, axis=1)
+    tag[bnd] = HORN_OUTER
+    tag[bnd & (rim | side)] = HORN_WALL
+    tag[bnd & mouth] = HORN_MOUTHPIECE
+    face_tag = tag.reshape(-1, 4)
+    _fix_orientation(xyz, EToV)
+    n_horn = int(6 * np.count_nonzero(cx < nh))
+    info = {
+        "bell_x": horn_length,
+        "bell_radius": R_in,
+        "n_horn": n_horn,
+        "n_room": int(EToV.shape[0]) - n_horn,
+        "planes": (nh, NX - nh),
+        "rings": m - m1,
+        # Table 2 positions relative to the bell and the room's walls
+        "sensors": np.array([[horn_length + 0.01, room_half - 0.01, 0.0],
+                             [horn_length + 1.00, 0.0, 0.0],
+                             [horn_length + 1.01, 0.0, 0.0],
+                             [horn_length + 0.37, 0.57, 0.0]]),
+    }
+    return xyz, EToV, face_tag, info

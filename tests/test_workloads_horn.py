@@ -1,0 +1,110 @@
+"""The horn-in-room workload (bell-front domain of section 1.2, Table 1's
+half domains): a lattice-mapped mesh of a flared horn and the room in front
+of its bell. Checked here against what geometry alone fixes: exact volumes of
+the flat-walled room, convergence of the horn's volume to the solid of
+revolution, the face tags, the mirror symmetries of the construction, and
+free-stream preservation of the oracle with every boundary kind of the
+workload at once."""
+import numpy as np
+import pytest
+
+from oracle.euler_dg import CHARACTERISTIC, INFLOW_PULSE, SLIP_WALL, Gas
+from oracle.euler_dg import Solver as OSolver
+from oracle.geometry import Geometry
+from oracle.reference_element import ReferenceElement
+from paper_1710_03887_gb300 import workloads as W
+
+SMALL = dict(m1=1, room_length=0.03, room_half=0.03, growth=1.8, horn_length=0.1, aspect=3.0)
+
+
+def _volumes(p, xyz, EToV):
+    g = Geometry(ReferenceElement(p), xyz, EToV)
+    J = g.J.reshape(g.J.shape[0], -1)[:, 0]
+    return g, J * 4.0 / 3.0
+
+
+def test_profile_is_a_clamped_bessel_flare():
+    x = np.array([0.0, 0.04, 0.5, 1.0])
+    r = W.horn_radius(x)
+    assert r[0] == r[1] == 0.006                       # the cylindrical bore
+    assert r[2] == pytest.approx(0.006 * 0.55 ** -0.7)
+    assert r[3] == pytest.approx(0.006 * 0.05 ** -0.7)
+    assert np.all(np.diff(W.horn_radius(np.linspace(0, 1, 101))) >= 0)
+
+
+def test_tags_and_boundary_agree_with_the_oracle_connectivity():
+    xyz, EToV, tag, info = W.horn_in_room(**SMALL)
+    g, vol = _volumes(1, xyz, EToV)
+    assert np.array_equal(g.boundary, tag >= 0)
+    m1 = SMALL["m1"]
+    counts = np.bincount(tag[tag >= 0], minlength=3)
+    assert counts[W.HORN_MOUTHPIECE] == 2 * (2 * m1) ** 2
+    nh = info["planes"][0]
+    lateral = nh * 4 * (2 * m1) * 2                    # horn planes x perimeter cells x 2 triangles
+    rim = ((2 * m1 + 2) ** 2 - (2 * m1) ** 2) * 2
+    assert counts[W.HORN_WALL] == lateral + rim
+    # the mouthpiece lies on x = 0 with outward normal -x; walls face away from the axis
+    fx = g.x[:, g.ref.Fmask].mean(axis=2)              # face centroids [K, 4, 3]
+    mouth = tag == W.HORN_MOUTHPIECE
+    assert np.allclose(fx[mouth][:, 0], 0.0) and np.allclose(g.nrm[mouth][:, 0], -1.0)
+    side = (tag == W.HORN_WALL) & (fx[..., 0] < info["bell_x"] - 1e-12)
+    radial = np.einsum("fd,fd->f", g.nrm[side][:, 1:], fx[side][:, 1:])
+    assert np.all(radial > 0)
+
+
+@pytest.mark.parametrize("shape", ["box", "cylinder"])
+def test_room_and_horn_volumes(shape):
+    kw = dict(SMALL, shape=shape)
+    xyz, EToV, tag, info = W.horn_in_room(**kw)
+    _, vol = _volumes(1, xyz, EToV)
+    assert np.all(vol > 0)
+    room = vol[info["n_horn"]:].sum()
+    L, h = kw["room_length"], kw["room_half"]
+    if shape == "box":                                 # flat walls: exact
+        assert room == pytest.approx((2 * h) ** 2 * L, rel=1e-12)
+    else:                                              # inscribed polygon of the circle
+        assert 0.95 * np.pi * h * h * L < room < np.pi * h * h * L
+    # the horn's polygonal cross-sections converge to the disc at second order
+    xs = np.linspace(0.0, kw["horn_length"], 20001)
+    exact = np.pi * np.trapezoid(W.horn_radius(xs) ** 2, xs)
+    errs = []
+    for m1 in (1, 2, 4):
+        xyz, EToV, _, info = W.horn_in_room(**dict(kw, m1=m1))
+        _, vol = _volumes(1, xyz, EToV)
+        errs.append(abs(vol[:info["n_horn"]].sum() - exact) / exact)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.02 and errs[1] / errs[2] > 3.0
+
+
+def test_mirror_symmetries_of_the_mesh():
+    xyz, EToV, _, _ = W.horn_in_room(**dict(SMALL, m1=2))
+    c = xyz[EToV].mean(axis=1)
+
+    def canon(a):
+        return a[np.lexsort(np.round(a, 12).T[::-1])]
+
+    ref = canon(c)
+    for M in (np.diag([1, -1, 1]), np.diag([1, 1, -1]), np.array([[1, 0, 0], [0, 0, 1], [0, 1, 0]])):
+        assert np.allclose(canon(c @ M.T), ref, atol=1e-12)
+
+
+def test_rest_state_is_preserved_with_every_boundary_of_the_workload():
+    """Walls reflect a state at rest into itself, the characteristic
+    condition returns the free stream, and the inflow pulse at t = 0 is the
+    base state: the right-hand side vanishes to rounding."""
+    xyz, EToV, tag, _ = W.horn_in_room(**SMALL)
+    g = Geometry(ReferenceElement(2), xyz, EToV)
+    gas = Gas(W.GAMMA, W.RHO0_SI, W.P0_SI)
+    bc_id = np.where(tag < 0, 0, tag).astype(np.int64)
+    orc = OSolver(g, gas, bc_id=bc_id, bc_mode={W.HORN_OUTER: CHARACTERISTIC,
+                                                 W.HORN_WALL: SLIP_WALL,
+                                                 W.HORN_MOUTHPIECE: INFLOW_PULSE})
+    orc.inflow = (0.1, 2 * np.pi * 500.0)
+    q = W.uniform_state(g.K, g.ref.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
+    r = orc.rhs(q, 0.0)
+    scale = W.P0_SI * np.abs(g.Fscale).max()
+    assert np.abs(r).max() <= 1e-12 * scale
+    # a quarter period later the pulse drives the mouthpiece only
+    r = orc.rhs(q, 0.25 * 2 * np.pi / orc.inflow[1])
+    moved = np.abs(r).max(axis=(1, 2)) > 1e-9 * scale
+    assert moved.any() and np.all(np.any(tag[moved] == W.HORN_MOUTHPIECE, axis=1))
