@@ -22,6 +22,9 @@ five-stage low-storage RK4 time step of the whole mesh.
   learned_bc the learned boundary closure: traces recorded, network trained
              and reflected energies measured on the GPU, and the closure timed on
              the bench workload
+  horn       the horn-in-room workload (1,419,552 tets, p=3: a flared horn with
+             slip walls, the inflow pulse at its mouthpiece, a pass-through
+             room in front of the bell), both float32 forms timed the same way
   cpu_baseline  the float64 CPU oracle on a bounded sample of the workload
 
 ``--impl reference`` times the CPU oracle itself on that sample instead.
@@ -422,6 +425,72 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     }
 
 
+def horn_section(args, dev, stream):
+    """Both float32 forms on the horn-in-room workload: the mixed-precision
+    configuration's geometry (a flared horn with slip walls inside a room in
+    front of its bell, ~1.4 M tets, p = 3, the inflow pulse of 10 % p0 at the
+    mouthpiece), timed like the bench workload (device-resident state, CUDA
+    events on the solver's stream), with the sensor analogues recorded."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    t0 = time.perf_counter()
+    xyz, EToV, tag, info = W.horn_in_room()
+    t_mesh = time.perf_counter() - t0
+    out = {"workload": ("horn in a box room: bore 0.006, Bessel flare 0.006 (1.05 - x)^-0.7 to "
+                        "x = 1, room 1.02 x 2 x 2 in front of the bell; %d tets (horn %d, room %d); "
+                        "p=3; slip walls, inflow pulse A = 0.05 (peak 10%% p0), alpha = 565 /s, "
+                        "characteristic BC on the room" % (len(EToV), info["n_horn"], info["n_room"])),
+           "elements": int(len(EToV)), "mesh_seconds": t_mesh}
+    for precision, code in (("f32", B.DG_PREC_F32), ("f32_tc", B.DG_PREC_F32_TC)):
+        S = B.Solver(3, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=code)
+        S.set_stream(stream.cuda_stream)
+        S.upload_mesh(xyz, EToV, face_tag=tag)
+        S.set_bc(W.HORN_OUTER, B.DG_BC_CHARACTERISTIC)
+        S.set_bc(W.HORN_WALL, B.DG_BC_SLIP_WALL)
+        S.set_bc(W.HORN_MOUTHPIECE, B.DG_BC_INFLOW_PULSE)
+        S.set_inflow(0.05, 565.0)
+        q0 = torch.empty((S.K, 5, S.Np), dtype=torch.float64, device=dev)
+        base = W.uniform_state(1, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
+        q0[:] = torch.from_numpy(base).to(dev)
+        dt = horn_dt(S)
+        S.set_probes(info["sensors"], capacity=max(args.horn_steps, 1))
+        S.set_state(q0)
+        S.step(args.warmup, dt)
+        S.read_probes()
+        S.set_state(q0)
+        torch.cuda.synchronize(dev)
+        S.set_kernel_timing(True)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        S.step(args.horn_steps, dt)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = start.elapsed_time(stop)
+        kms, klaunch = S.read_kernel_timing()
+        S.set_kernel_timing(False)
+        series = S.read_probes(args.horn_steps)
+        S.sync()
+        dof = 5 * S.Np * S.K
+        avg = kms / max(klaunch, 1)
+        out[precision] = {
+            "value": dof * args.horn_steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / args.horn_steps, "steps": args.horn_steps, "dt": dt,
+            "avg_stage_launch_ms": avg,
+            "stage_tflops": stage_flops_per_element(3) * S.K / (avg * 1e-3) / 1e12,
+            "sensor_max_abs_dp_rel_p0": float(np.abs(series[..., 4] - series[:1, :, 4]).max()
+                                              * (W.GAMMA - 1.0) / W.P0_SI)}
+        S.close()
+    return out
+
+
+def horn_dt(S):
+    """The solver's CFL 0.5 time step for the gas at rest."""
+    from paper_1710_03887_gb300 import workloads as W
+    return S.stable_dt(W.uniform_state(S.K, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA), 0.5)
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -480,6 +549,8 @@ def run_gpu(args, rank, world):
         lb["bench_workload_learned_bc"]["vs_characteristic"] = (
             lb["bench_workload_learned_bc"]["value"] / res["f32"]["value"] if "f32" in res else None)
         line["learned_bc"] = lb
+    if args.horn_steps > 0:
+        line["horn"] = horn_section(args, dev, stream)
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -500,6 +571,8 @@ def main():
     ap.add_argument("--learned-n", type=int, default=16,
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")
+    ap.add_argument("--horn-steps", type=int, default=20,
+                    help="steps timed on the horn-in-room workload (0: skip it)")
     ap.add_argument("--learned-every", type=int, default=10, help="steps between trace samples")
     ap.add_argument("--learned-fraction", type=float, default=1.0,
                     help="fraction of trace nodes kept per sample (seeded)")

@@ -87,14 +87,26 @@ __all__ = ["Case", "rel_err", "state_err", "direction_tags", "SI", "SCALED", "CH
 U32 = 2.0 ** -24          # unit roundoff of float32, round to nearest
 
 
-def f32_contraction_bound(osol, q, gas):
-    """Rounding bound of the float32 stage at each node and variable:
-    (K + 10) u (sum_a |D_a| |F~'_a| + |LIFT| |dF|), the standard bound of a
-    K-term float32 dot product (K = 3 Np + 4 Nfp) applied to Eq. 10's two
-    contractions, with ten more roundings for forming the inputs; F~' are the
-    metric-folded fluxes minus the base state's (what the perturbation form
-    contracts), dF the face terms. Computed in float64 by the oracle."""
-    ref = osol.ref
+def f32_contraction_bound(osol, q, gas, parts=False):
+    """Rounding bound of the float32 stage at each node and variable, two parts.
+
+    Arithmetic: (K + 10) u (sum_a |D_a| |F~'_a| + |LIFT| |dF|), the standard
+    bound of a K-term float32 dot product (K = 3 Np + 4 Nfp) applied to Eq.
+    10's two contractions, with ten more roundings for forming the inputs; F~'
+    are the metric-folded fluxes minus the base state's (what the perturbation
+    form contracts), dF the face terms.
+
+    Input: the state enters as q' = q - q0 rounded to float32, so each face
+    node's dissipation term lambda (q'+ - q'-) / 2 of the LLF flux may move by
+    up to lambda u (|q'-| + |q'+|) / 2 even where the exact term vanishes
+    (continuous fields: float64 traces that differ in their last bits round
+    to the same float32); lifted with Fscale and |LIFT|. Per element the
+    largest |q'| of the element and of the face's neighbour, and the largest
+    |u| + c of the whole state, stand in for the node values.
+
+    Computed in float64 from the oracle's parts; ``parts=True`` returns the
+    arithmetic and the input term separately."""
+    ref, g = osol.ref, osol.g
     Ft, dF = osol.rhs_parts(q)
     base = np.zeros_like(q)
     base[:, 0] = gas.rho0
@@ -104,7 +116,58 @@ def f32_contraction_bound(osol, q, gas):
     A = sum(np.einsum("ij,kvj->kvi", np.abs(D[a]), np.abs(Ft[:, a] - Ft0[:, a])) for a in range(3))
     A = A + np.einsum("ij,kvj->kvi", np.abs(ref.LIFT), np.abs(dF))
     K = 3 * ref.Np + 4 * ref.Nfp
-    return (K + 10) * U32 * A
+    # input rounding of the LLF dissipation term
+    rho = q[:, 0]
+    u = q[:, 1:4] / rho[:, None]
+    pr = (gas.gamma - 1.0) * (q[:, 4] - 0.5 * rho * np.sum(u * u, axis=1))
+    lam = np.max(np.sqrt(np.sum(u * u, axis=1)) + np.sqrt(gas.gamma * np.abs(pr) / rho))
+    qp = np.abs(q - base).max(axis=2)                                   # [K, 5]
+    jump = 0.5 * lam * U32 * (qp[:, None, :] + qp[g.EToE])              # [K, 4, 5]
+    dF_in = np.repeat((g.Fscale[:, :, None] * jump).transpose(0, 2, 1), ref.Nfp, axis=2)
+    arith = (K + 10) * U32 * A
+    inp = np.einsum("ij,kvj->kvi", np.abs(ref.LIFT), dF_in)
+    return (arith, inp) if parts else arith + inp
+
+
+U64 = 2.0 ** -53          # unit roundoff of float64
+
+
+def f64_oracle_bound(osol, q, gas):
+    """Rounding bound of the float64 oracle's own right-hand side, which works
+    on the total state (base state included):
+    (K + 10) u64 (sum_a |D_a| |F~_a| + |LIFT| |dF|) for the contractions, plus
+    64 u64 |LIFT| Fscale M for the face terms, M = (|n.F-| + |n.F+|) / 2 +
+    lambda (|q-| + |q+|) / 2 bounded by element maxima: traces, characteristic
+    ghosts (square roots and powers) and fluxes carry a few tens of roundings
+    of quantities of that size before they cancel. The float32 perturbation
+    form does not see these roundings (at rest it computes exact zeros), so
+    a comparison of the two must allow them."""
+    ref, g = osol.ref, osol.g
+    Ft, dF = osol.rhs_parts(q)
+    D = (ref.Dr, ref.Ds, ref.Dt)
+    A = sum(np.einsum("ij,kvj->kvi", np.abs(D[a]), np.abs(Ft[:, a])) for a in range(3))
+    A = A + np.einsum("ij,kvj->kvi", np.abs(ref.LIFT), np.abs(dF))
+    K = 3 * ref.Np + 4 * ref.Nfp
+    rho = q[:, 0]
+    u = q[:, 1:4] / rho[:, None]
+    pr = (gas.gamma - 1.0) * (q[:, 4] - 0.5 * rho * np.sum(u * u, axis=1))
+    lam = np.max(np.sqrt(np.sum(u * u, axis=1)) + np.sqrt(gas.gamma * np.abs(pr) / rho))
+    fl = np.stack([q[:, 1:4],                                             # [K, 5, 3, Np]
+                   q[:, 1:2] * u + pr[:, None] * np.eye(3)[0][:, None],
+                   q[:, 2:3] * u + pr[:, None] * np.eye(3)[1][:, None],
+                   q[:, 3:4] * u + pr[:, None] * np.eye(3)[2][:, None],
+                   u * (q[:, 4] + pr)[:, None]], axis=1)
+    fmax = np.abs(fl).max(axis=(2, 3))                                    # [K, 5]
+    qabs = np.abs(q).max(axis=2)
+    M = 0.5 * (fmax[:, None, :] + fmax[g.EToE]) + 0.5 * lam * (qabs[:, None, :] + qabs[g.EToE])
+    dF_in = np.repeat((g.Fscale[:, :, None] * M).transpose(0, 2, 1), ref.Nfp, axis=2)
+    return (K + 10) * U64 * A + 64 * U64 * np.einsum("ij,kvj->kvi", np.abs(ref.LIFT), dF_in)
+
+
+def f32_parity_bound(osol, q, gas):
+    """What a float32-form result may differ from the float64 oracle by:
+    the float32 form's rounding plus the oracle's own."""
+    return f32_contraction_bound(osol, q, gas) + f64_oracle_bound(osol, q, gas)
 
 
 # Orientation convention of dg_upload_geometry (include/dg_euler.h): face

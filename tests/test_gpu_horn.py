@@ -9,7 +9,9 @@ pass-through room in front of its bell (the bell-front domains of section
   other run tests, same reasoning);
 * full size (1,419,552 elements, p = 3, float32): sampled right-hand sides
   against the oracle on the patch around them (walls, rim, mouthpiece and
-  room elements included), each node held to its float32 dot-product bound;
+  room elements included), each node held to the float32 form's rounding
+  bound plus the oracle's own (at rest the float32 form computes exact
+  zeros where the float64 oracle leaves rounding of the base state);
   then a run with the inflow pulse, mass balanced against the boundary-flux
   ledger, and the sensor analogues of Table 2 located and read."""
 import numpy as np
@@ -22,7 +24,7 @@ from oracle.reference_element import ReferenceElement
 from paper_1710_03887_gb300 import binding as B
 from paper_1710_03887_gb300 import workloads as W
 
-from ._cases import SI, f32_contraction_bound
+from ._cases import SI, f32_parity_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -64,11 +66,12 @@ def test_small_horn_inflow_run_matches_oracle(cuda_device, prec):
     S.step(16, dt)
     qg, _ = S.get_state()
     pert = np.abs(qo - q0).max(axis=(0, 2))
-    assert np.all(pert > 0)                             # the pulse entered
+    assert np.all(pert[[0, 1, 4]] > 0)                  # the pulse entered
     if prec == "fp64":
         err = np.abs(qg - qo).max(axis=(0, 2)) / np.abs(qo).max(axis=(0, 2))
         assert np.all(err < 1e-11), err
     else:
+        pert[1:4] = pert[1:4].max()                     # momentum: relative to its largest component
         err = np.abs(qg - qo).max(axis=(0, 2)) / pert
         assert np.all(err < 2e-4), err
     # mass entered through the mouthpiece only (walls carry no mass flux)
@@ -118,10 +121,16 @@ def test_full_size_horn_sampled_parity_run_and_sensors(cuda_device):
     assert np.array_equal(orc.g.boundary[local], tag[sample] >= 0)
     qp = q[torch.as_tensor(patch, device=q.device)].cpu().numpy()
     ro = orc.rhs(qp, 0.0)
-    bound = f32_contraction_bound(orc, qp, GAS)[local]
+    bound = f32_parity_bound(orc, qp, GAS)[local]
     err = np.abs(rhs[sample] - ro[local])
     floor = 1e-7 * np.abs(ro[local]).max(axis=(0, 2))[None, :, None]
     ratio = err / (bound + floor)
+    worst = np.argsort(-ratio.max(axis=(1, 2)))[:6]
+    for i in worst:
+        e = sample[i]
+        print("element", e, "tags", tag[e], "centroid", np.round(cent[e], 4),
+              "ratio", ratio[i].max(axis=1), "lib", np.abs(rhs[e]).max(axis=1),
+              "oracle", np.abs(ro[local[i]]).max(axis=1), "bound", bound[i].max(axis=1))
     assert np.all(ratio <= 1.0), ratio.max(axis=(0, 2))
     # run: the inflow pulse enters, the bell pulse spreads; mass balances the ledger
     S.set_probes(info["sensors"], capacity=64)

@@ -9,7 +9,8 @@ Tolerance: on fine meshes the float32 rounding of the contractions is
 relative to the terms before they cancel, sum |D| |F~'|, which grows like 1/h
 against the derivative itself, so a fixed fraction of max |rhs| is not a
 mesh-independent bound. Each node and variable is held to the dot-product
-bound of its two float32 contractions (tests/_cases.f32_contraction_bound)."""
+bound of its two float32 contractions plus the input rounding of the face
+jumps, and the float64 oracle's own rounding (tests/_cases.f32_parity_bound)."""
 import numpy as np
 import pytest
 
@@ -20,7 +21,7 @@ from oracle.reference_element import ReferenceElement
 from paper_1710_03887_gb300 import binding as B
 from paper_1710_03887_gb300 import workloads as W
 
-from ._cases import SI, f32_contraction_bound
+from ._cases import SI, f32_parity_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +63,7 @@ def _sampled_parity(S, xyz, EToV, order, q_dev, w, seed):
     local = np.searchsorted(patch, sample)
     assert np.array_equal(geom.boundary[local], g["EToE"][sample] < 0)
     qp = q_dev[torch.as_tensor(patch, device=q_dev.device)].cpu().numpy()
-    bound = f32_contraction_bound(osol, qp, Gas(SI["gamma"], SI["rho0"], SI["p0"]))[local]
+    bound = f32_parity_bound(osol, qp, Gas(SI["gamma"], SI["rho0"], SI["p0"]))[local]
     err = np.abs(rhs[sample] - ro[local])
     floor = 1e-7 * np.abs(ro[local]).max(axis=(0, 2))[None, :, None]
     ratio = err / (bound + floor)
