@@ -22,7 +22,7 @@ five-stage low-storage RK4 time step of the whole mesh.
   learned_bc the learned boundary closure: traces recorded, network trained
              and reflected energies measured on the GPU, and the closure timed on
              the bench workload
-  horn       the horn-in-room workload (1,419,552 tets, p=3: a flared horn with
+  horn       the horn-in-room workload (1,489,704 tets, p=3: a flared horn with
              slip walls, the inflow pulse at its mouthpiece, a pass-through
              room in front of the bell), both float32 forms timed the same way
   cpu_baseline  the float64 CPU oracle on a bounded sample of the workload
@@ -428,7 +428,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
 def horn_section(args, dev, stream):
     """Both float32 forms on the horn-in-room workload: the mixed-precision
     configuration's geometry (a flared horn with slip walls inside a room in
-    front of its bell, ~1.4 M tets, p = 3, the inflow pulse of 10 % p0 at the
+    front of its bell, ~1.5 M tets, p = 3, the inflow pulse of 10 % p0 at the
     mouthpiece), timed like the bench workload (device-resident state, CUDA
     events on the solver's stream), with the sensor analogues recorded."""
     import torch

@@ -232,62 +232,76 @@ def horn_radius(x, bore=0.006, bell=0.06, x0=1.05, m=0.7):
 
 
 def _graded(h0, length, growth):
-    """Positions 0 = y_0 < ... < y_n = length whose spacings grow geometrically
-    from about h0 by the factor ``growth`` (all scaled to end at ``length``)."""
+    """Positions 0 = y_0 < ... < y_n = length: the first spacing is exactly h0
+    (a wall thickness, a cap), the following ones grow geometrically by about
+    ``growth`` (scaled together so the last position is ``length``)."""
+    if length <= h0:
+        return np.array([0.0, length])
     if growth <= 1.0:
-        n = max(1, int(round(length / h0)))
-        return np.linspace(0.0, length, n + 1)
-    n = max(1, int(np.ceil(np.log1p(length * (growth - 1.0) / h0) / np.log(growth))))
-    y = np.concatenate([[0.0], np.cumsum(h0 * growth ** np.arange(n))])
-    return y * (length / y[-1])
+        n = max(1, int(round((length - h0) / h0)))
+        return np.concatenate([[0.0], h0 + np.linspace(0.0, length - h0, n + 1)])
+    n = max(1, int(np.ceil(np.log1p((length - h0) * (growth - 1.0) / (h0 * growth)) / np.log(growth))))
+    rest = np.cumsum(h0 * growth ** np.arange(1, n + 1))
+    return np.concatenate([[0.0, h0], h0 + rest * ((length - h0) / rest[-1])])
 
 
 def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12,
-                 horn_length=1.0, wall=0.002, aspect=1.0, profile=horn_radius):
-    """A flared horn opening into a room in front of its bell: the
-    bell-front domains of section 1.2 (Table 1's half domains, where the region
-    behind the bell plane is left out), meshed without a mesh generator.
+                 horn_length=1.0, wall=0.002, aspect=1.0, behind=0.0, profile=horn_radius):
+    """A flared horn and the room around it, meshed without a mesh generator.
 
-    Logical lattice: planes ix along the axis, and a square lattice
-    (i, j) in [-m, m]^2 across it. The inner block max(|i|, |j|) <= m1 maps onto
-    the disc of radius ``profile(x)`` (the horn's interior; the same
-    square-to-disc blend as ``ball``), the rings outside it onto annuli whose
-    widths grow from ``wall`` by ``growth`` out to the room's side wall (a
-    square of half-width ``room_half`` for ``shape="box"``, a circle of that
-    radius for ``"cylinder"``). Horn planes are spaced ``aspect`` times the
-    local cross-section cell (r(x) / m1); room planes grow from ``wall`` by
-    ``growth`` out to ``horn_length + room_length``. Horn cells are the inner
-    block of the planes up to the bell, room cells the whole lattice after it;
-    every cell is split into six tetrahedra (the Kuhn chains of ``kuhn_cube``,
-    mirrored across the axis planes so the four quadrants are mirror images).
+    Two domain types of section 1.2 (Table 1): with ``behind = 0`` the room
+    lies in front of the bell only (type B, the bell-front domains: nothing
+    behind the bell plane); with ``behind > 0`` the room encloses the whole
+    horn and reaches ``behind`` past its mouthpiece plane (type A): the horn's
+    wall (thickness ``wall``) and a cap of the same thickness behind the
+    mouthpiece are solid.
 
-    Face tags: HORN_MOUTHPIECE on the plane x = 0 (the inflow pulse of section
-    2.4), HORN_WALL on the horn's lateral surface and on the first ring of the
-    bell plane (the bell's rim, one wall thickness wide; slip walls, Eq. 4),
-    HORN_OUTER on the rest of the room's boundary (pass-through).
+    Logical lattice: planes ix along the axis, and a square lattice (i, j) in
+    [-m, m]^2 across it. The inner block max(|i|, |j|) <= m1 maps onto the
+    disc of radius r(x) = ``profile(x)`` (the horn's interior, continued
+    behind the mouthpiece and in front of the bell with the end radii; the
+    same square-to-disc blend as ``ball``); ring 1 onto the annulus of width
+    ``wall`` around it (the wall, or on the bell plane its rim); rings 2..
+    onto annuli whose widths grow by ``growth`` out to the room's side wall,
+    blending from circles to the square of half-width ``room_half``
+    (``shape="box"``) or staying circles of that radius (``"cylinder"``).
+    Horn planes are spaced ``aspect`` times the local cross-section cell
+    r(x)/m1; room planes grow from ``wall`` by ``growth`` away from the bell
+    (and from the mouthpiece). Every kept cell is split into six tetrahedra
+    (the Kuhn chains of ``kuhn_cube``, mirrored across the axis planes so
+    the four quadrants are mirror images).
+
+    Face tags: HORN_MOUTHPIECE on the horn's end disc at x = 0 (the inflow
+    pulse of section 2.4), HORN_WALL on every face of the solid (the horn's
+    inner and outer surfaces, the bell rim, the cap; slip walls, Eq. 4),
+    HORN_OUTER on the room's outer boundary (pass-through).
 
     Returns ``(xyz, EToV, face_tag, info)``; ``info`` has the bell plane,
-    the element counts of horn and room, and the sensor analogues of Table 2.
+    element counts, and the sensor analogues of Table 2.
     """
     if shape not in ("box", "cylinder"):
         raise ValueError("shape must be 'box' or 'cylinder'")
     m1 = int(m1)
     if m1 < 1:
         raise ValueError("m1 must be >= 1")
-    # planes along the axis
-    xs = [0.0]
-    while xs[-1] < horn_length:
-        xs.append(xs[-1] + aspect * float(profile(xs[-1])) / m1)
-    xs = np.asarray(xs) * (horn_length / xs[-1])
-    nh = len(xs) - 1
-    xs = np.concatenate([xs, horn_length + _graded(wall, room_length, growth)[1:]])
+    enclose = behind > 0.0
+    # planes along the axis: behind the mouthpiece, along the horn, in front
+    xh = [0.0]
+    while xh[-1] < horn_length:
+        xh.append(xh[-1] + aspect * float(profile(xh[-1])) / m1)
+    xh = np.asarray(xh) * (horn_length / xh[-1])
+    back = -_graded(wall, behind, growth)[:0:-1] if enclose else np.zeros(0)
+    i0 = len(back)                       # plane of the mouthpiece
+    i1 = i0 + len(xh) - 1                # plane of the bell
+    xs = np.concatenate([back, xh, horn_length + _graded(wall, room_length, growth)[1:]])
     NX = len(xs) - 1
-    # rings of the room's cross-section
-    R_in = float(profile(horn_length))
-    if room_half <= R_in + wall:
+    r_max = float(profile(np.asarray(horn_length)))
+    if room_half <= r_max + 2 * wall:
         raise ValueError("the room must be wider than the bell and its rim")
-    rho = R_in + _graded(wall, room_half - R_in, growth)
-    m = m1 + len(rho) - 1
+    # ring fractions beyond the wall (from the bell's cross-section)
+    rho = (r_max + wall) + _graded(wall, room_half - r_max - wall, growth)
+    psi = (rho - rho[0]) / (rho[-1] - rho[0])          # 0 at ring 1 .. 1 at the side wall
+    m = m1 + len(rho)
     beta = 1.0 if shape == "box" else 0.0
 
     # vertex positions on the full logical lattice
@@ -298,7 +312,7 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
     L2 = np.hypot(I, J).astype(np.float64)
     safe = np.where(L2 > 0, L2, 1.0)
     x = xs[IX]
-    R = profile(np.minimum(x, horn_length))
+    R = profile(np.clip(x, 0.0, horn_length))
     yz = np.zeros((IX.size, 2))
     inner = S <= m1
     v = np.stack([I, J], axis=1) / m1
@@ -306,16 +320,17 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
     gfac = 1.0 - linf * (1.0 - np.where(L2 > 0, S / safe, 1.0))
     yz[inner] = (R[:, None] * v * gfac[:, None])[inner]
     outer = ~inner
-    k = np.clip(S - m1, 0, len(rho) - 1)
-    phi = (rho[k] - R_in) / (room_half - R_in)
+    kr = np.clip(S - m1 - 1, 0, len(psi) - 1)          # ring index beyond the wall
+    rad1 = R + wall
+    radk = rad1 + (room_half - rad1) * psi[kr]
+    bk = beta * psi[kr]
     dir_c = np.stack([I, J], axis=1) / safe[:, None]
     dir_s = np.stack([I, J], axis=1) / np.where(S > 0, S, 1)[:, None]
-    far = room_half * ((1.0 - beta) * dir_c + beta * dir_s)
-    yz_o = (1.0 - phi)[:, None] * R_in * dir_c + phi[:, None] * far
+    yz_o = radk[:, None] * ((1.0 - bk)[:, None] * dir_c + bk[:, None] * dir_s)
     yz[outer] = yz_o[outer]
     xyz_all = np.column_stack([x, yz])
 
-    # cells: the inner block up to the bell plane, everything after it
+    # cells
     W = 2 * m + 1
 
     def vid(a, b, c):
@@ -323,7 +338,13 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
 
     cx, ci, cj = np.meshgrid(np.arange(NX), np.arange(-m, m), np.arange(-m, m), indexing="ij")
     cx, ci, cj = cx.ravel(), ci.ravel(), cj.ravel()
-    keep = (cx >= nh) | ((ci >= -m1) & (ci + 1 <= m1) & (cj >= -m1) & (cj + 1 <= m1))
+    smax = np.maximum(np.maximum(np.abs(ci), np.abs(ci + 1)), np.maximum(np.abs(cj), np.abs(cj + 1)))
+    in_horn = (cx >= i0) & (cx < i1)
+    if enclose:
+        solid = (in_horn & (smax == m1 + 1)) | ((cx == i0 - 1) & (smax <= m1 + 1))
+        keep = ~solid
+    else:
+        keep = (cx >= i1) | (in_horn & (smax <= m1))
     cx, ci, cj = cx[keep], ci[keep], cj[keep]
     cells = np.stack([cx, ci, cj], axis=1)
     step = np.stack([np.ones_like(cx), np.where(ci >= 0, 1, -1), np.where(cj >= 0, 1, -1)], axis=1)
@@ -338,6 +359,7 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
             chain.append(corner)
         tets.append(np.stack([vid(q[:, 0], q[:, 1], q[:, 2]) for q in chain], axis=1))
     EToV = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int64)
+    tet_cx = np.repeat(cx, 6)
     # orientation from the logical lattice; the map must agree with it everywhere
     lat = np.column_stack([IX, I, J]).astype(np.float64)
 
@@ -361,22 +383,29 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
     _, first, count = np.unique(key, return_inverse=True, return_counts=True)
     bnd = count[first] == 1
     fx, fs = lix[faces], ls[faces]
+    fcx = np.repeat(tet_cx, 4)
+    outer_f = np.all(fs == m, axis=1) | np.all(fx == NX, axis=1)
+    if enclose:
+        outer_f |= np.all(fx == 0, axis=1)
+    else:
+        outer_f |= np.all(fx == i1, axis=1) & (fs.max(axis=1) > m1 + 1)
+    mouth = np.all(fx == i0, axis=1) & (fs.max(axis=1) <= m1) & (fcx >= i0)
     tag = np.full(faces.shape[0], -1, dtype=np.int8)
-    mouth = np.all(fx == 0, axis=1)
-    rim = np.all(fx == nh, axis=1) & (fs.max(axis=1) <= m1 + 1)
-    side = np.all(fx <= nh, axis=1) & np.all(fs == m1, axis=1)
-    tag[bnd] = HORN_OUTER
-    tag[bnd & (rim | side)] = HORN_WALL
+    tag[bnd] = HORN_WALL
+    tag[bnd & outer_f] = HORN_OUTER
     tag[bnd & mouth] = HORN_MOUTHPIECE
     face_tag = tag.reshape(-1, 4)
     _fix_orientation(xyz, EToV)
-    n_horn = int(6 * np.count_nonzero(cx < nh))
+    horn_cells = (cx >= i0) & (cx < i1) & (np.maximum(np.maximum(np.abs(ci), np.abs(ci + 1)),
+                                                        np.maximum(np.abs(cj), np.abs(cj + 1))) <= m1)
     info = {
         "bell_x": horn_length,
-        "bell_radius": R_in,
-        "n_horn": n_horn,
-        "n_room": int(EToV.shape[0]) - n_horn,
-        "planes": (nh, NX - nh),
+        "bell_radius": r_max,
+        "type": "A" if enclose else "B",
+        "n_horn": int(6 * np.count_nonzero(horn_cells)),
+        "n_room": int(EToV.shape[0] - 6 * np.count_nonzero(horn_cells)),
+        "horn_elements": np.repeat(horn_cells, 6),
+        "planes": (i0, i1 - i0, NX - i1),
         "rings": m - m1,
         # Table 2 positions relative to the bell and the room's walls
         "sensors": np.array([[horn_length + 0.01, room_half - 0.01, 0.0],

@@ -1,19 +1,22 @@
 """The horn-in-room workload on the GPU (GPU): a flared horn with slip walls,
-driven by the inflow pulse of section 2.4 at its mouthpiece, opening into a
-pass-through room in front of its bell (the bell-front domains of section
-1.2, at the mixed-precision configuration's size of ~1.4 M elements).
+driven by the inflow pulse of section 2.4 at its mouthpiece, inside a
+pass-through room (the domain types of section 1.2: a room in front of the
+bell only, at the mixed-precision configuration's size of ~1.5 M elements,
+or a room enclosing the whole horn).
 
-* small horn (4,464 elements, p = 2): every form against the oracle over 16
-  steps in which one whole inflow pulse enters: float64 to 1e-11 per
-  variable, float32 forms to 2e-4 of the perturbation (the tolerances of the
-  other run tests, same reasoning);
-* full size (1,419,552 elements, p = 3, float32): sampled right-hand sides
+* small horns (4,464 elements in front of the bell, 12,432 enclosing; p = 2):
+  every form against the oracle over 16 steps in which one whole inflow
+  pulse enters: float64 to 1e-11 per variable, float32 forms to 2e-4 of the
+  perturbation (the tolerances of the other run tests, same reasoning);
+* full size (1,489,704 elements, p = 3, float32): sampled right-hand sides
   against the oracle on the patch around them (walls, rim, mouthpiece and
   room elements included), each node held to the float32 form's rounding
   bound plus the oracle's own (at rest the float32 form computes exact
   zeros where the float64 oracle leaves rounding of the base state);
   then a run with the inflow pulse, mass balanced against the boundary-flux
   ledger, and the sensor analogues of Table 2 located and read."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -29,6 +32,7 @@ from ._cases import SI, f32_parity_bound
 pytestmark = pytest.mark.gpu
 
 SMALL = dict(m1=1, room_length=0.03, room_half=0.03, growth=1.8, horn_length=0.1, aspect=3.0)
+DOMAINS = {"bell-front": SMALL, "enclosing": dict(SMALL, behind=0.02)}
 MODES = {W.HORN_OUTER: CHARACTERISTIC, W.HORN_WALL: SLIP_WALL, W.HORN_MOUTHPIECE: INFLOW_PULSE}
 LIB_MODES = {W.HORN_OUTER: B.DG_BC_CHARACTERISTIC, W.HORN_WALL: B.DG_BC_SLIP_WALL,
              W.HORN_MOUTHPIECE: B.DG_BC_INFLOW_PULSE}
@@ -50,16 +54,24 @@ def _library(p, prec, xyz, EToV, tag, amp, alpha):
     return S
 
 
-@pytest.mark.parametrize("prec", list(PRECS))
-def test_small_horn_inflow_run_matches_oracle(cuda_device, prec):
-    xyz, EToV, tag, _ = W.horn_in_room(**SMALL)
-    p = 2
-    orc = _oracle(p, xyz, EToV, tag)
+@functools.lru_cache(maxsize=None)
+def _oracle_run(domain):
+    """16 oracle steps from rest with one whole inflow pulse (shared by the forms)."""
+    xyz, EToV, tag, _ = W.horn_in_room(**DOMAINS[domain])
+    orc = _oracle(2, xyz, EToV, tag)
     q0 = W.uniform_state(orc.g.K, orc.ref.Np, SI["rho0"], (0, 0, 0), SI["p0"], SI["gamma"])
     dt = orc.stable_dt(q0, 0.5)
-    alpha = 2 * np.pi / (12 * dt)                       # one whole pulse within the run
+    alpha = 2 * np.pi / (12 * dt)
     orc.inflow = (0.1, alpha)
     qo, _, ledger_o, _ = orc.run(q0, dt, 16)
+    return xyz, EToV, tag, q0, dt, alpha, qo, ledger_o
+
+
+@pytest.mark.parametrize("domain", list(DOMAINS))
+@pytest.mark.parametrize("prec", list(PRECS))
+def test_small_horn_inflow_run_matches_oracle(cuda_device, prec, domain):
+    xyz, EToV, tag, q0, dt, alpha, qo, ledger_o = _oracle_run(domain)
+    p = 2
     S = _library(p, prec, xyz, EToV, tag, 0.1, alpha)
     S.set_state(q0)
     tot0 = S.totals()
@@ -100,7 +112,7 @@ def test_full_size_horn_sampled_parity_run_and_sensors(cuda_device):
     import torch
     xyz, EToV, tag, info = W.horn_in_room()
     K = EToV.shape[0]
-    assert K == 1_419_552
+    assert K == 1_489_704
     S = _library(3, "f32", xyz, EToV, tag, 0.1, 2 * np.pi * 2000.0)
     # a pulse straddling the bell plane: horn, rim and room elements all see it
     q = _device_pulse(S, xyz, EToV, 3, cuda_device, (info["bell_x"], 0.02, 0.0), 0.03, 0.05)

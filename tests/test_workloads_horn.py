@@ -1,10 +1,10 @@
-"""The horn-in-room workload (bell-front domain of section 1.2, Table 1's
-half domains): a lattice-mapped mesh of a flared horn and the room in front
-of its bell. Checked here against what geometry alone fixes: exact volumes of
-the flat-walled room, convergence of the horn's volume to the solid of
-revolution, the face tags, the mirror symmetries of the construction, and
-free-stream preservation of the oracle with every boundary kind of the
-workload at once."""
+"""The horn-in-room workload (the two domain types of section 1.2, Table 1:
+a room in front of the bell only, or a room enclosing the whole horn): a
+lattice-mapped mesh of a flared horn and its room. Checked here against what
+geometry alone fixes: exact volumes of the flat-walled room, convergence of
+the horn's and the wall's volumes to the solids of revolution, the face tags
+counted from the construction, the mirror symmetries, and free-stream
+preservation of the oracle with every boundary kind of the workload."""
 import numpy as np
 import pytest
 
@@ -15,6 +15,7 @@ from oracle.reference_element import ReferenceElement
 from paper_1710_03887_gb300 import workloads as W
 
 SMALL = dict(m1=1, room_length=0.03, room_half=0.03, growth=1.8, horn_length=0.1, aspect=3.0)
+ENCLOSED = dict(SMALL, behind=0.02)
 
 
 def _volumes(p, xyz, EToV):
@@ -32,24 +33,33 @@ def test_profile_is_a_clamped_bessel_flare():
     assert np.all(np.diff(W.horn_radius(np.linspace(0, 1, 101))) >= 0)
 
 
-def test_tags_and_boundary_agree_with_the_oracle_connectivity():
-    xyz, EToV, tag, info = W.horn_in_room(**SMALL)
+@pytest.mark.parametrize("kw", [SMALL, ENCLOSED], ids=["bell-front", "enclosing"])
+def test_tags_and_boundary_agree_with_the_oracle_connectivity(kw):
+    xyz, EToV, tag, info = W.horn_in_room(**kw)
     g, vol = _volumes(1, xyz, EToV)
     assert np.array_equal(g.boundary, tag >= 0)
-    m1 = SMALL["m1"]
+    m1 = kw["m1"]
     counts = np.bincount(tag[tag >= 0], minlength=3)
     assert counts[W.HORN_MOUTHPIECE] == 2 * (2 * m1) ** 2
-    nh = info["planes"][0]
-    lateral = nh * 4 * (2 * m1) * 2                    # horn planes x perimeter cells x 2 triangles
-    rim = ((2 * m1 + 2) ** 2 - (2 * m1) ** 2) * 2
-    assert counts[W.HORN_WALL] == lateral + rim
-    # the mouthpiece lies on x = 0 with outward normal -x; walls face away from the axis
+    nh = info["planes"][1]
+    inside = nh * 4 * (2 * m1) * 2                     # horn planes x perimeter cells x 2 triangles
+    ring = ((2 * m1 + 2) ** 2 - (2 * m1) ** 2) * 2    # the bell rim / the wall's front end
+    if info["type"] == "B":
+        assert counts[W.HORN_WALL] == inside + ring
+    else:
+        outside = nh * 4 * (2 * m1 + 2) * 2            # the wall's outer surface
+        cap = (2 * m1 + 2) ** 2 * 2 + 4 * (2 * m1 + 2) * 2
+        assert counts[W.HORN_WALL] == inside + outside + ring + cap
+    # the mouthpiece lies on x = 0 with outward normal -x; inner walls face away from the axis
     fx = g.x[:, g.ref.Fmask].mean(axis=2)              # face centroids [K, 4, 3]
     mouth = tag == W.HORN_MOUTHPIECE
     assert np.allclose(fx[mouth][:, 0], 0.0) and np.allclose(g.nrm[mouth][:, 0], -1.0)
-    side = (tag == W.HORN_WALL) & (fx[..., 0] < info["bell_x"] - 1e-12)
-    radial = np.einsum("fd,fd->f", g.nrm[side][:, 1:], fx[side][:, 1:])
-    assert np.all(radial > 0)
+    horn = info["horn_elements"][:, None] & (tag == W.HORN_WALL) & (fx[..., 0] < info["bell_x"] - 1e-12)
+    assert np.all(np.einsum("fd,fd->f", g.nrm[horn][:, 1:], fx[horn][:, 1:]) > 0)
+    if info["type"] == "A":                            # the wall's outer surface faces the axis
+        out = ~info["horn_elements"][:, None] & (tag == W.HORN_WALL) & (fx[..., 0] > 1e-9) \
+            & (fx[..., 0] < info["bell_x"] - 1e-12)
+        assert out.any() and np.all(np.einsum("fd,fd->f", g.nrm[out][:, 1:], fx[out][:, 1:]) < 0)
 
 
 @pytest.mark.parametrize("shape", ["box", "cylinder"])
@@ -76,8 +86,27 @@ def test_room_and_horn_volumes(shape):
     assert errs[2] < 0.02 and errs[1] / errs[2] > 3.0
 
 
-def test_mirror_symmetries_of_the_mesh():
-    xyz, EToV, _, _ = W.horn_in_room(**dict(SMALL, m1=2))
+def test_enclosing_room_volume_is_the_box_minus_the_solid():
+    """Type A: flat outer walls, so the mesh volume is the box minus the
+    horn's wall (thickness 0.002) and the mouthpiece cap; the polygonal
+    annuli converge to the solid of revolution."""
+    kw = dict(ENCLOSED)
+    box = (2 * kw["room_half"]) ** 2 * (kw["room_length"] + kw["horn_length"] + kw["behind"])
+    xs = np.linspace(0.0, kw["horn_length"], 20001)
+    r = W.horn_radius(xs)
+    solid = np.pi * np.trapezoid((r + 0.002) ** 2 - r * r, xs) + np.pi * (0.006 + 0.002) ** 2 * 0.002
+    errs = []
+    for m1 in (1, 2, 4):
+        xyz, EToV, _, _ = W.horn_in_room(**dict(kw, m1=m1))
+        _, vol = _volumes(1, xyz, EToV)
+        assert np.all(vol > 0)
+        errs.append(abs(box - vol.sum() - solid) / solid)
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.005
+
+
+@pytest.mark.parametrize("kw", [SMALL, ENCLOSED], ids=["bell-front", "enclosing"])
+def test_mirror_symmetries_of_the_mesh(kw):
+    xyz, EToV, _, _ = W.horn_in_room(**dict(kw, m1=2))
     c = xyz[EToV].mean(axis=1)
 
     def canon(a):
@@ -88,11 +117,12 @@ def test_mirror_symmetries_of_the_mesh():
         assert np.allclose(canon(c @ M.T), ref, atol=1e-12)
 
 
-def test_rest_state_is_preserved_with_every_boundary_of_the_workload():
+@pytest.mark.parametrize("kw", [SMALL, ENCLOSED], ids=["bell-front", "enclosing"])
+def test_rest_state_is_preserved_with_every_boundary_of_the_workload(kw):
     """Walls reflect a state at rest into itself, the characteristic
     condition returns the free stream, and the inflow pulse at t = 0 is the
     base state: the right-hand side vanishes to rounding."""
-    xyz, EToV, tag, _ = W.horn_in_room(**SMALL)
+    xyz, EToV, tag, _ = W.horn_in_room(**kw)
     g = Geometry(ReferenceElement(2), xyz, EToV)
     gas = Gas(W.GAMMA, W.RHO0_SI, W.P0_SI)
     bc_id = np.where(tag < 0, 0, tag).astype(np.int64)
