@@ -70,6 +70,23 @@ def stage_flops_per_element(p):
     return Np * (103 + 25) + 30 * Np * Np + 4 * Nfp * 101 + 40 * Np * Nfp
 
 
+def modal_stage_flops_per_element(p):
+    """Algorithmic float64 flops of one stage of the paper's discretisation
+    (Gauss rules of degree 2p and 2p+1: Nq = (p+1)^3 volume and Nfq = (p+1)^2
+    points per face) per element (1 FMA = 2 flops).
+
+    volume point: state from the nodes (5 x Np FMAs), Euler flux + metric fold (103)
+    volume sums:  3 directions x 5 variables x Np x Nq FMAs
+    face point:   own and neighbour trace (2 x 5 x Nfp FMAs), LLF (101),
+                  surface sum (5 x Np FMAs)
+    node:         RK update (25)
+    """
+    Np = (p + 1) * (p + 2) * (p + 3) // 6
+    Nfp = (p + 1) * (p + 2) // 2
+    Nq, Nfq = (p + 1) ** 3, (p + 1) ** 2
+    return Nq * (10 * Np + 103) + 30 * Np * Nq + 4 * Nfq * (20 * Nfp + 101 + 10 * Np) + 25 * Np
+
+
 def fp64_peak_gflops(sm_mhz=2070.0):
     """Nominal GB300 float64 rate: 1.25 TFLOP/s at the 2070 MHz boost clock over
     152 SMs, i.e. 4 flops per SM per clock; scaled to the given clock."""
@@ -246,7 +263,8 @@ def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_cl
     from paper_1710_03887_gb300 import binding as B
     from paper_1710_03887_gb300 import workloads as W
     w = WORKLOAD
-    prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC, "fp64": B.DG_PREC_FP64}[precision]
+    prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC, "fp64": B.DG_PREC_FP64,
+            "modal": B.DG_PREC_MODAL}[precision]
     S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.set_stream(stream.cuda_stream)
     S.upload_mesh(xyz, EToV)
@@ -313,6 +331,15 @@ def roofline_for(m, order):
     """Roofline object of the stage kernel of one measured form."""
     K = m["K"]
     avg_launch_s = (m["kms"] * 1e-3) / max(m["klaunch"], 1)
+    if m["precision"] == "modal":
+        achieved = modal_stage_flops_per_element(order) * K / avg_launch_s * 1e-12
+        peak = fp64_peak_gflops(2070.0) * 1e-3
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "stage_modal_kernel<3>",
+                "note": ("the paper's discretisation (Gauss rules of degree 2p, 2p+1; two Heun "
+                         "stages per step); algorithmic float64 flops per stage; float64 pipe "
+                         "peak as for the float64 nodal form"),
+                "avg_launch_ms": avg_launch_s * 1e3, "launches": m["klaunch"]}
     if m["precision"] == "fp64":
         achieved = stage_flops_per_element(order) * K / avg_launch_s * 1e-12
         peak = fp64_peak_gflops(2070.0) * 1e-3
@@ -503,7 +530,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     w = WORKLOAD
     xyz, EToV = build_workload()
-    forms = [args.precision] + [f for f in ("f32_tc", "f32", "fp64")
+    forms = [args.precision] + [f for f in ("f32_tc", "f32", "fp64", "modal")
                                 if f != args.precision and not args.one_form]
     res = {f: measure_form(args, f, xyz, EToV, dev, stream, dist, world, sample_clocks=(f == args.precision))
            for f in forms}
@@ -522,7 +549,8 @@ def run_gpu(args, rank, world):
                           f"{state_bytes / (2 if head['precision'] == 'f32' else 1) / 1e6:.0f} MB each); no flush")},
         "e2e": {"value": head["e2e"], "unit": UNIT, "h2d_bytes_per_step": state_bytes / args.steps,
                 "d2h_bytes_per_step": (state_bytes + head["nprobe"] * 5 * 8 * args.steps) / args.steps},
-        "gpu_launches": args.steps * 6,     # 5 stage kernels (ledger inside) + 1 probe kernel per step
+        # 5 stage kernels (ledger inside) + 1 probe kernel per step; 2 + 1 for Heun's RK2
+        "gpu_launches": args.steps * (3 if head["precision"] == "modal" else 6),
         "roofline": roofline_for(head, w["order"]),
         "clocks": head["clocks"],
     }
@@ -542,6 +570,18 @@ def run_gpu(args, rank, world):
                 "max_err_per_var_rel_to_perturbation": (num / den).tolist(),
                 "after_steps": args.steps,
                 "speedup": a["value"] / b["value"]}
+    if "modal" in res and "fp64" in res:
+        # the two discretisations side by side (same pulse, same dt, same steps):
+        # their difference is the discretisation difference (quadrature vs
+        # collocation, RK2 vs RK4), measured against the perturbation
+        a, b = res["modal"], res["fp64"]
+        base = W.uniform_state(a["q0"].shape[0], a["q0"].shape[2], W.RHO0_SI, (0, 0, 0),
+                               W.P0_SI, W.GAMMA)
+        num = np.abs(a["q_end"] - b["q_end"]).max(axis=(0, 2))
+        den = np.abs(b["q_end"] - base).max(axis=(0, 2))
+        forms_out["modal_vs_nodal_fp64"] = {
+            "max_diff_per_var_rel_to_perturbation": (num / den).tolist(), "after_steps": args.steps,
+            "speedup_per_step": a["value"] / b["value"]}
     line["forms"] = forms_out
     if args.learned_n > 0:
         # rank 0 only, after the replicas' timed regions: no barrier inside
@@ -565,7 +605,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64"],
+    ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64", "modal"],
                     help="arithmetic form of the headline number (the other is measured beside it)")
     ap.add_argument("--one-form", action="store_true", help="measure only --precision")
     ap.add_argument("--learned-n", type=int, default=16,

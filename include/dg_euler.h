@@ -91,6 +91,16 @@ extern "C" {
                                 /* Eq. 10) as one tcgen05 tensor-core GEMM per tile of   */
                                 /* 25 elements, tf32 operands split in head + tail,      */
                                 /* float32 accumulation; orders 1..3                     */
+#define DG_PREC_MODAL 3         /* the paper's own discretisation (Appendix A): the weak */
+                                /* form of Eq. 10 in the orthonormal basis of Eq. 11,    */
+                                /* volume integral by a Gauss rule of degree 2p, surface */
+                                /* integrals by one of degree 2p+1 (collapsed Gauss-     */
+                                /* Jacobi products, one point set per face: the rule of  */
+                                /* its lower-numbered element), LLF flux, Heun's second- */
+                                /* order Runge-Kutta (section 1.1) in dg_step; float64.  */
+                                /* The state crosses the ABI as nodal values of the same */
+                                /* polynomials (the nodes of the other forms), so probes,*/
+                                /* totals and dg_stable_dt work unchanged.               */
 
 /* Free-stream gas and defaults of a context. */
 typedef struct dg_params {
@@ -188,6 +198,24 @@ int dg_stable_dt(const dg_ctx* ctx, const double* q, double cfl, double* dt);
  * NULL. */
 int dg_reference_operators(int order, double* rst, double* Dr, double* Ds,
                            double* Dt, double* LIFT, int32_t* Fmask);
+
+/* Gauss rules of DG_PREC_MODAL at order 1..4 (host only, no context):
+ * vol[Nq][4] = (r, s, t, weight) on the reference tetrahedron, exact to
+ * degree 2p; face[Nfq][3] = (u, v, weight) on the triangle (-1,-1), (1,-1),
+ * (-1,1), exact to degree 2p+1; Nq = (p+1)^3, Nfq = (p+1)^2 (Appendix A's
+ * 2p / 2p+1 rules as collapsed Gauss-Jacobi products). Either array may be
+ * NULL; nq/nfq (nullable) receive the counts. */
+int dg_modal_quadrature(int order, double* vol, double* face, int32_t* nq, int32_t* nfq);
+/* Operators of DG_PREC_MODAL on nodal values (host only, no context), with
+ * Nq, Nfq as above (Appendix A's weak form, Eq. 10, in the orthonormal
+ * basis, Eq. 11):
+ *   du_n/dt = sum_a sum_q Sv[a][n][q] G_a(x_q) - sum_f Fscale_f sum_q Sf[f][v_f][n][q] F*_q
+ * Iq[Nq][Np]: nodal values -> volume points; Sv[3][Np][Nq]; Ifn[4][7][Nfq][Nfp]:
+ * face-node values (Fmask order) -> face points; Sf[4][7][Np][Nfq]; wf[Nfq]
+ * face weights. Face variant v_f = 0 when the element's index is not above
+ * its neighbour's (and on outer faces), else 1 + the face's orientation
+ * code. Any output may be NULL. */
+int dg_modal_operators(int order, double* Iq, double* Sv, double* Ifn, double* Sf, double* wf);
 
 /* State q[K][5][Np] from host memory at time t; resets the Runge-Kutta
  * residual, the boundary-flux ledger and the probe buffer. */

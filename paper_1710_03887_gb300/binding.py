@@ -34,6 +34,7 @@ DG_MLP_NPARAMS = 5317
 DG_PREC_FP64 = 0
 DG_PREC_F32 = 1
 DG_PREC_F32_TC = 2
+DG_PREC_MODAL = 3
 
 
 class dg_params(C.Structure):
@@ -70,6 +71,8 @@ _SIGS = {
     "dg_read_kernel_timing": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
     "dg_weighted_totals_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, _P, _P]),
     "dg_reference_mass": (C.c_int, [C.c_int, _P]),
+    "dg_modal_quadrature": (C.c_int, [C.c_int, _P, _P, _P, _P]),
+    "dg_modal_operators": (C.c_int, [C.c_int, _P, _P, _P, _P, _P]),
     "dg_set_bc_mlp": (C.c_int, [_P, _P, C.c_double]),
     "dg_get_bc_mlp": (C.c_int, [_P, _P]),
     "dg_set_trace_faces": (C.c_int, [_P, C.c_int64, _P, _P]),
@@ -151,6 +154,36 @@ def reference_operators(order):
     if rc != DG_OK:
         raise DGError(rc, "dg_reference_operators failed")
     return dict(r=rst[0], s=rst[1], t=rst[2], Dr=Dr, Ds=Ds, Dt=Dt, LIFT=LIFT, Fmask=Fmask)
+
+
+def modal_quadrature(order):
+    """Gauss rules of the paper's discretisation (host only): volume points
+    and weights [Nq, 4] (r, s, t, w), face points and weights [Nfq, 3] (u, v, w)."""
+    lib = load()
+    nq, nfq = C.c_int32(), C.c_int32()
+    rc = lib.dg_modal_quadrature(order, None, None, C.byref(nq), C.byref(nfq))
+    if rc != DG_OK:
+        raise DGError(rc, "dg_modal_quadrature failed")
+    vol, face = np.zeros((nq.value, 4)), np.zeros((nfq.value, 3))
+    rc = lib.dg_modal_quadrature(order, _ptr(vol), _ptr(face), None, None)
+    if rc != DG_OK:
+        raise DGError(rc, "dg_modal_quadrature failed")
+    return vol, face
+
+
+def modal_operators(order):
+    """Operators of the paper's discretisation on nodal values (host only):
+    dict with Iq [Nq, Np], Sv [3, Np, Nq], Ifn [4, 7, Nfq, Nfp], Sf [4, 7, Np, Nfq], wf [Nfq]."""
+    lib = load()
+    Np = (order + 1) * (order + 2) * (order + 3) // 6
+    Nfp = (order + 1) * (order + 2) // 2
+    Nq, Nfq = (order + 1) ** 3, (order + 1) ** 2
+    out = dict(Iq=np.zeros((Nq, Np)), Sv=np.zeros((3, Np, Nq)), Ifn=np.zeros((4, 7, Nfq, Nfp)),
+               Sf=np.zeros((4, 7, Np, Nfq)), wf=np.zeros(Nfq))
+    rc = lib.dg_modal_operators(order, *(_ptr(out[k]) for k in ("Iq", "Sv", "Ifn", "Sf", "wf")))
+    if rc != DG_OK:
+        raise DGError(rc, "dg_modal_operators failed")
+    return out
 
 
 class Solver:

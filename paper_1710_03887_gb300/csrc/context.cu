@@ -28,6 +28,13 @@ const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0,
                         2526269341429.0 / 6820363962896.0, 2006345519317.0 / 3224310063776.0,
                         2802321613138.0 / 2924317926251.0};
 
+// Heun's method (the paper's second-order Runge-Kutta, section 1.1) in the
+// same 2N-storage form: res = dt f(q); q1 = q + res; res = -res + dt f(q1);
+// q2 = q1 + res/2 = (q + q1 + dt f(q1))/2.
+const double kHeunA[2] = {0.0, -1.0};
+const double kHeunB[2] = {1.0, 0.5};
+const double kHeunC[2] = {0.0, 1.0};
+
 constexpr int kTotalsBlocks = 256;
 
 template <typename T>
@@ -65,6 +72,7 @@ struct dg_ctx {
   double* geo = nullptr;
   int32_t* conn = nullptr;
   double* ops = nullptr;
+  double* mops = nullptr;          // operators of the paper's discretisation (DG_PREC_MODAL)
   uint8_t* tbl = nullptr;
   int32_t* fmask = nullptr;
   double* ledger_part = nullptr;   // [grid][5] per-CTA ledger sums
@@ -125,7 +133,7 @@ struct dg_ctx {
     if (dev_ready) cudaStreamSynchronize(stream);
     clear_events();
     dfree(q[0]); dfree(q[1]); dfree(res); dfree(scratch); dfree(geo); dfree(conn);
-    dfree(ops); dfree(tbl); dfree(fmask); dfree(ticket); dfree(ledger_part); dfree(ledger);
+    dfree(ops); dfree(mops); dfree(tbl); dfree(fmask); dfree(ticket); dfree(ledger_part); dfree(ledger);
     dfree(mass_w); dfree(totals_part); dfree(status); dfree(pelem); dfree(prow); dfree(pring);
     dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
     dfree(bxyz); dfree(bface); dfree(bpsi); dfree(bpsi_res); dfree(bD); dfree(face_list);
@@ -137,6 +145,7 @@ struct dg_ctx {
     nprobe = 0;
   }
   size_t state_elems() const { return size_t(mesh.K) * 5 * ref.Np; }
+  bool f32() const { return prec == DG_PREC_F32 || prec == DG_PREC_F32_TC; }
 };
 
 namespace {
@@ -169,18 +178,22 @@ int ensure_device(dg_ctx* c) {
   int dev = 0;
   DG_CUDA(cudaGetDevice(&dev));
   DG_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
-  const bool f32 = c->prec != DG_PREC_FP64;
+  const bool f32 = c->f32();
   const bool tcf = c->prec == DG_PREC_F32_TC;
+  const bool modal = c->prec == DG_PREC_MODAL;
   int bps = 0;
   if (tcf)
     DG_CUDA(dgk::stage_tc_prepare(p, &bps));
   else if (f32)
     DG_CUDA(dgk::stage_f32_prepare(p, &bps));
+  else if (modal)
+    DG_CUDA(dgk::stage_modal_prepare(p, &bps));
   else
     DG_CUDA(dgk::stage_prepare(p, &bps));
   if (bps < 1) return c->fail(DG_ERR_CUDA, "stage kernel does not fit on an SM");
   const int ET = tcf ? dgk::stage_tc_tile_elems(p)
-                     : (f32 ? dgk::stage_f32_tile_elems(p) : dgk::stage_tile_elems(p));
+                     : (f32 ? dgk::stage_f32_tile_elems(p)
+                            : (modal ? dgk::stage_modal_tile_elems(p) : dgk::stage_tile_elems(p)));
   c->ntiles = int((K + ET - 1) / ET);
   c->grid = std::min(c->ntiles, c->sms * bps);
   const size_t nq = c->state_elems();
@@ -295,6 +308,21 @@ int ensure_device(dg_ctx* c) {
   for (int m = 0; m < NF; ++m) ops[size_t(3) * Np * Np + size_t(NF) * Np + m] = c->ref.face_w[m];
   DG_CUDA(cudaMalloc(&c->ops, ops.size() * 8));
   DG_CUDA(cudaMemcpy(c->ops, ops.data(), ops.size() * 8, cudaMemcpyHostToDevice));
+  if (modal) {
+    dg::ModalOps mo;
+    std::string merr;
+    if (!dg::build_modal_ops(c->ref, mo, merr)) return c->fail(DG_ERR_ARG, merr);
+    std::vector<double> blk;
+    blk.insert(blk.end(), mo.Iq.begin(), mo.Iq.end());
+    blk.insert(blk.end(), mo.Sv.begin(), mo.Sv.end());
+    blk.insert(blk.end(), mo.Ifn.begin(), mo.Ifn.end());
+    blk.insert(blk.end(), mo.Sf.begin(), mo.Sf.end());
+    for (int q = 0; q < mo.Nfq; ++q) blk.push_back(mo.face[3 * q + 2]);
+    if (int(blk.size()) != dgk::modal_ops_len(p))
+      return c->fail(DG_ERR_ARG, "modal operator block size mismatch");
+    DG_CUDA(cudaMalloc(&c->mops, blk.size() * 8));
+    DG_CUDA(cudaMemcpy(c->mops, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice));
+  }
   if (tcf) {
     // operator matrix [-Dr | -Ds | -Dt | LIFT] as the tensor-core operand image
     std::vector<unsigned char> img(dgk::stage_tc_ops_bytes(p));
@@ -436,7 +464,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
   double in_full[3];
   float in_pert[3];
   inflow_state(c, ts, in_full, in_pert);
-  if (c->prec != DG_PREC_FP64) {
+  if (c->f32()) {
     dgk::StageArgsF32 A{};
     A.q_in = c->q32[c->cur];
     A.q_out = c->q32[1 - c->cur];
@@ -468,14 +496,19 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
     dgk::StageArgs A = stage_args(c, c->q[c->cur], c->q[1 - c->cur], to_scratch ? c->scratch : c->res,
                                   a, b, dt, !to_scratch);
     for (int i = 0; i < 3; ++i) A.inflow[i] = in_full[i];
-    DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+    if (c->prec == DG_PREC_MODAL) {
+      A.modal_ops = c->mops;
+      DG_CUDA(dgk::launch_stage_modal(c->ref.p, A, c->grid, c->stream));
+    } else {
+      DG_CUDA(dgk::launch_stage(c->ref.p, A, c->grid, c->stream));
+    }
   }
   return DG_OK;
 }
 
 // Total state (float64) of the current solution into the scratch buffer.
 int current_state_f64(dg_ctx* c, double* dst) {
-  if (c->prec != DG_PREC_FP64)
+  if (c->f32())
     DG_CUDA(dgk::launch_from_perturbation(c->q32[c->cur], dst, c->mesh.K, c->ref.Np, c->gas.rho0,
                                           c->gas.E0, c->stream));
   else if (dst != c->q[c->cur])
@@ -539,10 +572,10 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
   if (!(params->gamma > 1.0) || !(params->rho0 > 0.0) || !(params->p0 > 0.0)) return DG_ERR_ARG;
   if (params->default_bc < 0 || params->default_bc > 2) return DG_ERR_ARG;
   if (params->precision != DG_PREC_FP64 && params->precision != DG_PREC_F32 &&
-      params->precision != DG_PREC_F32_TC)
+      params->precision != DG_PREC_F32_TC && params->precision != DG_PREC_MODAL)
     return DG_ERR_UNSUPPORTED;
   if (params->precision == DG_PREC_F32_TC && order > 3) return DG_ERR_UNSUPPORTED;
-  if (params->precision != DG_PREC_FP64 &&
+  if ((params->precision == DG_PREC_F32 || params->precision == DG_PREC_F32_TC) &&
       (params->u0[0] != 0.0 || params->u0[1] != 0.0 || params->u0[2] != 0.0))
     return DG_ERR_UNSUPPORTED;   // the perturbation form is built around a resting base state
   if (order < 1 || order > dg::kMaxOrder) return DG_ERR_UNSUPPORTED;
@@ -691,7 +724,7 @@ int dg_set_bc(dg_ctx* c, int bc_id, int mode) {
   if (!c) return DG_ERR_ARG;
   if (bc_id < 0 || bc_id > 7) return c->fail(DG_ERR_ARG, "boundary id must be 0..7");
   if (mode < 0 || mode > 4) return c->fail(DG_ERR_ARG, "unknown boundary mode");
-  if (mode == DG_BC_LEARNED && c->prec == DG_PREC_FP64)
+  if (mode == DG_BC_LEARNED && !c->f32())
     return c->fail(DG_ERR_UNSUPPORTED, "the learned closure runs in the float32 forms");
   c->bc_mode[bc_id] = mode;
   return DG_OK;
@@ -779,11 +812,38 @@ int dg_reference_operators(int order, double* rst, double* Dr, double* Ds, doubl
   return DG_OK;
 }
 
+int dg_modal_quadrature(int order, double* vol, double* face, int32_t* nq, int32_t* nfq) {
+  if (order < 1 || order > dg::kMaxOrder) return DG_ERR_UNSUPPORTED;
+  std::vector<double> v, f;
+  dg::tet_rule(2 * order, v);
+  dg::tri_rule(2 * order + 1, f);
+  if (vol) std::memcpy(vol, v.data(), v.size() * 8);
+  if (face) std::memcpy(face, f.data(), f.size() * 8);
+  if (nq) *nq = int32_t(v.size() / 4);
+  if (nfq) *nfq = int32_t(f.size() / 3);
+  return DG_OK;
+}
+
+int dg_modal_operators(int order, double* Iq, double* Sv, double* Ifn, double* Sf, double* wf) {
+  dg::RefElement re;
+  std::string err;
+  if (!dg::build_ref_element(order, re, err)) return DG_ERR_UNSUPPORTED;
+  dg::ModalOps mo;
+  if (!dg::build_modal_ops(re, mo, err)) return DG_ERR_ARG;
+  if (Iq) std::memcpy(Iq, mo.Iq.data(), mo.Iq.size() * 8);
+  if (Sv) std::memcpy(Sv, mo.Sv.data(), mo.Sv.size() * 8);
+  if (Ifn) std::memcpy(Ifn, mo.Ifn.data(), mo.Ifn.size() * 8);
+  if (Sf) std::memcpy(Sf, mo.Sf.data(), mo.Sf.size() * 8);
+  if (wf)
+    for (int q = 0; q < mo.Nfq; ++q) wf[q] = mo.face[3 * q + 2];
+  return DG_OK;
+}
+
 int dg_set_state(dg_ctx* c, const double* q, double t) {
   if (!c || !q) return DG_ERR_ARG;
   int rc = ensure_device(c);
   if (rc) return rc;
-  if (c->prec != DG_PREC_FP64) {
+  if (c->f32()) {
     DG_CUDA(cudaMemcpyAsync(c->scratch, q, c->state_elems() * 8, cudaMemcpyHostToDevice, c->stream));
     DG_CUDA(dgk::launch_to_perturbation(c->scratch, c->q32[c->cur], c->mesh.K, c->ref.Np,
                                         c->gas.rho0, c->gas.E0, c->stream));
@@ -797,7 +857,7 @@ int dg_set_state_device(dg_ctx* c, const double* dq, double t) {
   if (!c || !dq) return DG_ERR_ARG;
   int rc = ensure_device(c);
   if (rc) return rc;
-  if (c->prec != DG_PREC_FP64)
+  if (c->f32())
     DG_CUDA(dgk::launch_to_perturbation(dq, c->q32[c->cur], c->mesh.K, c->ref.Np, c->gas.rho0,
                                         c->gas.E0, c->stream));
   else
@@ -809,7 +869,7 @@ int dg_get_state(dg_ctx* c, double* q, double* t) {
   if (!c || !q) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   const double* src = c->q[c->cur];
-  if (c->prec != DG_PREC_FP64) {
+  if (c->f32()) {
     int rc = current_state_f64(c, c->scratch);
     if (rc) return rc;
     src = c->scratch;
@@ -837,11 +897,16 @@ int dg_step(dg_ctx* c, int n, double dt) {
     Range() { nvtxRangePushA("dg_step"); }
     ~Range() { nvtxRangePop(); }
   } range;
+  const bool heun = c->prec == DG_PREC_MODAL;
+  const int nstage = heun ? 2 : 5;
+  const double* RA = heun ? kHeunA : kRkA;
+  const double* RB = heun ? kHeunB : kRkB;
+  const double* RC = heun ? kHeunC : kRkC;
   for (int s = 0; s < n; ++s) {
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < nstage; ++k) {
       int rc = record_event(c);
       if (rc) return rc;
-      rc = run_stage(c, false, kRkA[k], kRkB[k], dt, c->t + kRkC[k] * dt);
+      rc = run_stage(c, false, RA[k], RB[k], dt, c->t + RC[k] * dt);
       if (rc) return rc;
       rc = record_event(c);
       if (rc) return rc;
@@ -851,7 +916,7 @@ int dg_step(dg_ctx* c, int n, double dt) {
     if (c->nprobe > 0) {
       const int slotp = int(c->precorded % c->pcap);
       double* dst = c->pring + size_t(slotp) * c->nprobe * 5;
-      if (c->prec != DG_PREC_FP64)
+      if (c->f32())
         DG_CUDA(dgk::launch_probe_sample_f32(c->q32[c->cur], c->ref.Np, c->nprobe, c->pelem, c->prow,
                                              c->gas.rho0, c->gas.E0, dst, c->stream));
       else
@@ -870,7 +935,7 @@ int dg_eval_rhs(dg_ctx* c, double* rhs) {
   // and leaves the ledger alone
   int rc = run_stage(c, true, 0.0, 0.0, 1.0, c->t);
   if (rc) return rc;
-  if (c->prec != DG_PREC_FP64)
+  if (c->f32())
     DG_CUDA(dgk::launch_widen(c->scratch32, c->scratch, int64_t(c->state_elems()), c->stream));
   DG_CUDA(cudaMemcpyAsync(rhs, c->scratch, c->state_elems() * 8, cudaMemcpyDeviceToHost, c->stream));
   return check_status(c);
@@ -964,7 +1029,7 @@ int dg_conserved_totals(dg_ctx* c, double out[5]) {
   if (!c || !out) return DG_ERR_ARG;
   if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
   const double* src = c->q[c->cur];
-  if (c->prec != DG_PREC_FP64) {
+  if (c->f32()) {
     int rc = current_state_f64(c, c->scratch);
     if (rc) return rc;
     src = c->scratch;
@@ -1062,7 +1127,7 @@ int dg_get_bc_mlp(dg_ctx* c, float* w) {
 
 int dg_set_trace_faces(dg_ctx* c, int64_t n, const int32_t* elem, const int8_t* face) {
   if (!c || n < 0 || (n > 0 && (!elem || !face))) return DG_ERR_ARG;
-  if (c->prec == DG_PREC_FP64) return c->fail(DG_ERR_UNSUPPORTED, "traces are sampled in the float32 forms");
+  if (!c->f32()) return c->fail(DG_ERR_UNSUPPORTED, "traces are sampled in the float32 forms");
   if (c->have_mesh && c->mesh.verts.empty())
     return c->fail(DG_ERR_ORDER, "trace recording needs vertex coordinates (dg_upload_mesh)");
   int rc = ensure_device(c);

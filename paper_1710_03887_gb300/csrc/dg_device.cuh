@@ -92,6 +92,9 @@ struct StageArgs {
   double a, b, dt;
   Gas gas;
   double inflow[3];          // mode 4 ghost at the stage time: rho, rho u_in, E
+  // the paper's discretisation (stage_modal.cu): Iq [Nq][Np] | Sv [3][Np][Nq] |
+  // Ifn [4][7][Nfq][Nfp] | Sf [4][7][Np][Nfq] | wf [Nfq]; null for the nodal forms
+  const double* modal_ops;
 };
 
 // Float32 perturbation-form stage (stage_f32.cu)
@@ -195,6 +198,11 @@ int stage_tile_elems(int p);
 size_t stage_smem_bytes(int p);
 cudaError_t stage_prepare(int p, int* blocks_per_sm);
 cudaError_t launch_stage(int p, const StageArgs& a, int grid, cudaStream_t s);
+// The paper's discretisation (stage_modal.cu); modal_ops_len: doubles of the operator block
+int stage_modal_tile_elems(int p);
+int modal_ops_len(int p);
+cudaError_t stage_modal_prepare(int p, int* blocks_per_sm);
+cudaError_t launch_stage_modal(int p, const StageArgs& a, int grid, cudaStream_t s);
 
 cudaError_t launch_probe_sample(const double* q, int Np, int n, const int32_t* elem,
                                 const double* rows, double* out, cudaStream_t s);

@@ -65,4 +65,21 @@ bool build_mesh(const RefElement& ref, int64_t nvert, const double* xyz, int64_t
 
 bool invert_matrix(int n, std::vector<double>& a);   // in place, row-major
 
+// The paper's discretisation (modal_ops.cpp): Gauss rules and the operators
+// of the weak form on nodal values (see there for the formulas).
+struct ModalOps {
+  int Nq = 0, Nfq = 0;
+  std::vector<double> vol;                // [Nq][4]: r, s, t, weight (degree 2p)
+  std::vector<double> face;               // [Nfq][3]: u, v, weight (degree 2p + 1)
+  std::vector<double> Iq;                 // [Nq][Np] Lagrange basis at the volume points
+  std::vector<double> Sv;                 // [3][Np][Nq] volume weights of G_r, G_s, G_t
+  std::vector<double> Ifn;                // [4][7][Nfq][Nfp] face nodes -> face points
+  std::vector<double> Sf;                 // [4][7][Np][Nfq] surface weights of F*
+};
+// n-point Gauss rule for the weight (1 - x)^alpha on [-1, 1]
+void gauss_jacobi(int n, double alpha, double* x, double* w);
+void tet_rule(int degree, std::vector<double>& rstw);
+void tri_rule(int degree, std::vector<double>& uvw);
+bool build_modal_ops(const RefElement& re, ModalOps& out, std::string& err);
+
 }  // namespace dg

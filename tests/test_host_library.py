@@ -33,6 +33,23 @@ def test_reference_operators_match_oracle(p):
     np.testing.assert_array_equal(L["Fmask"], R.Fmask)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_modal_gauss_rules_match_the_oracle(p):
+    """The library's own Gauss-Jacobi rules (Newton on the Jacobi recurrence)
+    against the oracle's (a library routine), point by point: the collapsed
+    products must be the same point sets for the discretisation to agree."""
+    from oracle import modal_dg as MD
+    vol, face = B.modal_quadrature(p)
+    r, s, t, w = MD.tet_rule(2 * p)
+    assert vol.shape == (len(w), 4) and len(w) == (p + 1) ** 3
+    np.testing.assert_allclose(vol, np.stack([r, s, t, w], axis=1), rtol=0, atol=1e-14)
+    u, v, wf = MD.tri_rule(2 * p + 1)
+    assert face.shape == (len(wf), 3) and len(wf) == (p + 1) ** 2
+    np.testing.assert_allclose(face, np.stack([u, v, wf], axis=1), rtol=0, atol=1e-14)
+    with pytest.raises(B.DGError):
+        B.modal_quadrature(9)
+
+
 def test_unsupported_order_is_rejected():
     with pytest.raises(B.DGError) as e:
         B.Solver(7)
