@@ -22,6 +22,8 @@ five-stage low-storage RK4 time step of the whole mesh.
   learned_bc the learned boundary closure: traces recorded, network trained
              and reflected energies measured on the GPU, and the closure timed on
              the bench workload
+  locality   the float32 form on the bench mesh in lattice, Morton and random
+             element order (how far tiles' gathers reach)
   horn       the horn-in-room workload (1,489,704 tets, p=3: a flared horn with
              slip walls, the inflow pulse at its mouthpiece, a pass-through
              room in front of the bell), both float32 forms timed the same way
@@ -518,6 +520,56 @@ def horn_dt(S):
     return S.stable_dt(W.uniform_state(S.K, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA), 0.5)
 
 
+def locality_section(args, xyz, EToV, dev, stream):
+    """The float32 form on the bench mesh with its elements in three orders:
+    as built (lattice order), sorted along a Morton curve, and randomly
+    permuted (a mesh generator's order, at its worst). Tiles are runs of
+    consecutive elements, so the order decides how many faces a tile shares
+    internally and how far its gathers reach."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    w = WORKLOAD
+    ET = 32
+    out = {"steps": args.locality_steps, "tile_elements": ET}
+    for name, perm in (("lattice", None), ("morton", W.morton_order(xyz, EToV)),
+                       ("random", W.random_order(len(EToV), 1))):
+        E = EToV if perm is None else EToV[perm]
+        S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
+        S.set_stream(stream.cuda_stream)
+        S.upload_mesh(xyz, E)
+        EToE = S.geometry()["EToE"]
+        own = np.arange(len(E))[:, None] // ET
+        interior = EToE >= 0
+        intra = float(np.count_nonzero(interior & (EToE // ET == own)) / np.count_nonzero(interior))
+        q0 = W.gaussian_pulse_state(S.node_coords(), W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"],
+                                    w["width"])
+        dt = S.stable_dt(q0, w["cfl"])
+        q0d = torch.from_numpy(q0).to(dev)
+        S.set_state(q0d)
+        S.step(args.warmup, dt)
+        S.set_state(q0d)
+        torch.cuda.synchronize(dev)
+        S.set_kernel_timing(True)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        S.step(args.locality_steps, dt)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = start.elapsed_time(stop)
+        kms, kl = S.read_kernel_timing()
+        S.set_kernel_timing(False)
+        S.sync()
+        dof = 5 * S.Np * S.K
+        out[name] = {"value": dof * args.locality_steps / (ms * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms / args.locality_steps,
+                     "avg_stage_launch_ms": kms / max(kl, 1),
+                     "interior_faces_inside_a_tile": intra}
+        S.close()
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -591,6 +643,8 @@ def run_gpu(args, rank, world):
         line["learned_bc"] = lb
     if args.horn_steps > 0:
         line["horn"] = horn_section(args, dev, stream)
+    if args.locality_steps > 0:
+        line["locality"] = locality_section(args, xyz, EToV, dev, stream)
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -611,6 +665,8 @@ def main():
     ap.add_argument("--learned-n", type=int, default=16,
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")
+    ap.add_argument("--locality-steps", type=int, default=20,
+                    help="steps timed per element order in the locality section (0: skip it)")
     ap.add_argument("--horn-steps", type=int, default=20,
                     help="steps timed on the horn-in-room workload (0: skip it)")
     ap.add_argument("--learned-every", type=int, default=10, help="steps between trace samples")

@@ -150,6 +150,27 @@ def submesh(xyz, EToV, keep):
     return xyz[used].copy(), inv.reshape(E.shape).astype(np.int32)
 
 
+def morton_order(xyz, EToV, bits=10):
+    """Permutation of the elements that sorts their centroids along the
+    Morton (Z-order) curve of a 2^bits grid over the mesh's bounding box:
+    consecutive elements are close in space, whatever order a mesh
+    generator produced them in."""
+    c = xyz[EToV].mean(axis=1)
+    lo, hi = c.min(axis=0), c.max(axis=0)
+    g = np.clip(((c - lo) / np.maximum(hi - lo, 1e-300) * (2 ** bits - 1)).round(), 0, 2 ** bits - 1)
+    g = g.astype(np.uint64)
+    code = np.zeros(len(c), dtype=np.uint64)
+    for b in range(bits):
+        for d in range(3):
+            code |= ((g[:, d] >> np.uint64(b)) & np.uint64(1)) << np.uint64(3 * b + d)
+    return np.argsort(code, kind="stable")
+
+
+def random_order(K, seed=0):
+    """A seeded random permutation of K elements (no locality at all)."""
+    return np.random.default_rng(seed).permutation(K)
+
+
 def element_centroids(xyz, EToV):
     return xyz[EToV].mean(axis=1)
 
