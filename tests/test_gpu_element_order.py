@@ -1,8 +1,12 @@
 """Element order (GPU): the stage kernels tile runs of consecutive elements,
-evaluate faces inside a tile once and gather across tiles, so every form
-must give the same answer for any element order. A randomly permuted mesh
-(no locality: almost no face inside a tile) and a Morton-sorted one are run
-against the oracle and against the lattice-ordered run, permuted back."""
+evaluate faces inside a tile once and gather across tiles, so the nodal
+forms must give the same answer for any element order. A randomly permuted
+mesh (no locality: almost no face inside a tile) and a Morton-sorted one
+are run against the oracle and against the lattice-ordered run, permuted
+back. The paper's discretisation integrates each interior face with the
+Gauss rule of its lower-numbered element, so renumbering changes the rule
+on some faces: each order is held to the modal oracle on the same
+numbering, and the orders to each other at quadrature-error level."""
 import numpy as np
 import pytest
 
@@ -43,14 +47,22 @@ def test_any_element_order_gives_the_same_run(cuda_device, prec):
             S.set_state(q0[perm])
         S.step(10, dt)
         q, _ = S.get_state()
+        if prec == "modal":
+            from oracle.modal_dg import ModalSolver
+            qo, _, _ = ModalSolver(Case(p, xyz, EToV[perm]).geom, base.gas).run(q0[perm], dt, 10)
+            assert np.all(state_err(q, qo, base.gas) < 1e-11), name
         out = np.empty_like(q)
         out[perm] = q
         runs[name] = out
     base_q = runs["lattice"]
     for name in ("morton", "random"):
-        if prec in ("fp64", "modal"):
+        if prec == "fp64":
             err = state_err(runs[name], base_q, base.gas)
             assert np.all(err < 1e-12), (name, err)
+        elif prec == "modal":
+            pert = np.abs(base_q - q0).max(axis=(0, 2))
+            err = np.abs(runs[name] - base_q).max(axis=(0, 2)) / pert
+            assert np.all(err < 1e-3), (name, err)        # another Gauss rule on some faces
         else:
             # float32: the tile split changes the order of roundings only
             pert = np.abs(base_q - q0).max(axis=(0, 2))
