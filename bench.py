@@ -337,7 +337,10 @@ def roofline_for(m, order):
         achieved = modal_stage_flops_per_element(order) * K / avg_launch_s * 1e-12
         peak = fp64_peak_gflops(2070.0) * 1e-3
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "stage_modal_kernel<3>",
+                "frac": achieved / peak,
+                "traffic": profiled_traffic("stage_modal_p3_ball.md", "stage_modal.cu"),
+                "traffic_note": "ncu capture of a first (a = 0) stage: no residual read",
+                "kernel": "stage_modal_kernel<3>",
                 "note": ("the paper's discretisation (Gauss rules of degree 2p, 2p+1; two Heun "
                          "stages per step); algorithmic float64 flops per stage; float64 pipe "
                          "peak as for the float64 nodal form"),
