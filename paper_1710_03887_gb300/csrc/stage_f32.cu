@@ -180,6 +180,7 @@ stage_f32_kernel(const StageArgsF32 A) {
   double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
+    const int e0i = int(e0);
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
     const int buf = iter & 1;
     const float* sQ = sm + O::oQ + buf * O::kQT;
@@ -198,7 +199,7 @@ stage_f32_kernel(const StageArgsF32 A) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      if (c >= 0 && ((c >> 5) < e0 || (c >> 5) >= e0 + nE)) {
+      if (c >= 0 && ((c >> 5) < e0i || (c >> 5) >= e0i + nE)) {
         const int64_t e2 = c >> 5;
         const int f2 = (c >> 3) & 3, o = c & 7;
         const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
@@ -252,7 +253,8 @@ stage_f32_kernel(const StageArgsF32 A) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      const int le2 = (c >= 0) ? int((c >> 5) - e0) : -1;   // neighbour's tile slot
+      // neighbour's tile slot; element indices are below 2^26, so 32 bits hold them
+      const int le2 = (c >= 0) ? (c >> 5) - e0i : -1;
       const bool inside = c >= 0 && le2 >= 0 && le2 < nE;   // then le2 > le (face list)
       const int n = sFmask[f * Nfp + m];
       float qm[5], qp[5];
@@ -261,16 +263,18 @@ stage_f32_kernel(const StageArgsF32 A) {
       const float* geo = sGeo + le * kGeoStride;
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       float* xf = sX + le * SX + 3 * Np + fm;        // + v * ET * SX
-      int f2 = 0, o = 0;
-      if (inside) {
-        f2 = (c >> 3) & 3;
-        o = c & 7;
-        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+      const int f2 = (c >> 3) & 3, o = c & 7;
+      if (c >= 0) {
+        // the neighbour's trace: in the tile's state, or gathered into the face
+        // columns; one load path for both, no divergence between them
+        const float* src = xf;
+        int stride = ET * SX;
+        if (inside) {
+          src = sQ + le2 * 5 * Np + sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+          stride = Np;
+        }
 #pragma unroll
-        for (int v = 0; v < 5; ++v) qp[v] = sQ[(le2 * 5 + v) * Np + n2];
-      } else if (c >= 0) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) qp[v] = xf[v * ET * SX];
+        for (int v = 0; v < 5; ++v) qp[v] = src[v * stride];
       } else {
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
@@ -343,7 +347,9 @@ stage_f32_kernel(const StageArgsF32 A) {
       if (le < nE) {
         const float* x = sX + le * SX;                // row v at + v * ET * SX
         const float* ot = sOT + h * NPQ4;
-#pragma unroll 1
+        // two k per trip: half the loop overhead, still within 96 registers
+        // (four spill)
+#pragma unroll 2
         for (int k = k0; k < k1; ++k) {
           uint64_t op[NPQ2 / 2];
 #pragma unroll
@@ -379,20 +385,22 @@ stage_f32_kernel(const StageArgsF32 A) {
     }
     __syncthreads();
 
-    // ---- Runge-Kutta update, coalesced over the tile's state
+    // ---- Runge-Kutta update, coalesced over the tile's state; output row
+    // r = v Np + n of element le is partial-sum row r
+    float* const res_t = A.res + base;
+    float* const qout_t = A.q_out + base;
 #pragma unroll
     for (int s = 0; s < RI; ++s) {
       const int i = tid + s * NT;
       if (i < nE * 5 * Np) {
         const int le = i / (5 * Np), r = i - le * 5 * Np;
-        const int v = r / Np, n = r - (r / Np) * Np;
-        const float* part = sX + (v * Np + n) * (ET + 1) + le;
+        const float* part = sX + r * (ET + 1) + le;
         float rhs = 0.0f;
 #pragma unroll
         for (int kq = 0; kq < O::NK; ++kq) rhs += part[kq * O::kPart];
         const float res = A.a * rres[s] + A.dt * rhs;
-        A.res[base + i] = res;
-        A.q_out[base + i] = sQ[i] + A.b * res;
+        res_t[i] = res;
+        qout_t[i] = sQ[i] + A.b * res;
       }
     }
   }
