@@ -269,19 +269,28 @@ int ensure_device(dg_ctx* c) {
   }
   {
     // faces each tile evaluates: a face shared by two elements of the tile
-    // once, under the lower element (the stage writes both jumps)
+    // once, under the lower element (the stage writes both jumps). Grouped:
+    // faces inside the tile, then faces to other tiles, then outer faces;
+    // header int32 {total, inside, to other tiles, 0}
     const size_t row = 16 + (4 * size_t(ET) + 15) / 16 * 16;   // rows start on 16-byte boundaries
     std::vector<uint8_t> fl(size_t(c->ntiles) * row, 0);
+    std::vector<uint8_t> grp[3];
     for (int t = 0; t < c->ntiles; ++t) {
       const int64_t e0 = int64_t(t) * ET, e1 = std::min<int64_t>(K, e0 + ET);
-      int32_t cnt = 0;
+      for (auto& g : grp) g.clear();
       for (int64_t e = e0; e < e1; ++e)
         for (int f = 0; f < 4; ++f) {
           const int64_t e2 = c->mesh.EToE[size_t(e) * 4 + f];
-          if (e2 >= e0 && e2 < e1 && e2 < e) continue;
-          fl[size_t(t) * row + 16 + cnt++] = uint8_t(((e - e0) << 2) | f);
+          const bool inside = e2 >= e0 && e2 < e1;
+          if (inside && e2 < e) continue;
+          grp[e2 < 0 ? 2 : (inside ? 0 : 1)].push_back(uint8_t(((e - e0) << 2) | f));
         }
-      std::memcpy(&fl[size_t(t) * row], &cnt, 4);
+      int32_t hdr[4] = {int32_t(grp[0].size() + grp[1].size() + grp[2].size()), int32_t(grp[0].size()),
+                        int32_t(grp[1].size()), 0};
+      std::memcpy(&fl[size_t(t) * row], hdr, 16);
+      size_t pos = size_t(t) * row + 16;
+      for (auto& g : grp)
+        for (uint8_t b : g) fl[pos++] = b;
     }
     DG_CUDA(cudaMalloc(&c->face_list, fl.size()));
     DG_CUDA(cudaMemcpy(c->face_list, fl.data(), fl.size(), cudaMemcpyHostToDevice));

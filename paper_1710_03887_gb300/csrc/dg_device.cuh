@@ -83,7 +83,7 @@ struct StageArgs {
   const uint8_t* nbr_tbl;    // [4][4][6][Nfp]: neighbour volume node; then the same
                              // shape: neighbour face node (index in its face's list)
   const int32_t* fmask;      // [4][Nfp]
-  const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]: count, then (le << 2 | f)
+  const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]: header, then (le << 2 | f)
   LedgerArgs led;
   int* status;
   int64_t K;
@@ -119,9 +119,10 @@ struct StageArgsF32 {
   // learned closure (boundary mode 3): incoming-invariant increments
   // [boundary face slot][Nfp] from launch_closure, or null (characteristic)
   const float* bD;
-  // float32 stage: per tile, a 16-byte header (int32 count) then the faces it
-  // evaluates, one byte each (element in tile << 2 | face); a face between
-  // two elements of the tile appears once, under its lower element
+  // per tile, a 16-byte header (int32 total, inside the tile, to other
+  // tiles, 0) then the faces it evaluates, one byte each (element in tile
+  // << 2 | face), in that order: faces between two elements of the tile
+  // (once, under the lower element), faces to other tiles, outer faces
   const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]
 };
 

@@ -53,6 +53,21 @@ __device__ __forceinline__ void normal_flux_f(const float q[5], const float n[3]
   lam = fabsf(un) + (c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f);
 }
 
+// Parts of the LLF flux at a face node: n.F(q-), A = (n.F(q-) - n.F(q+)) / 2,
+// B = lambda (q+ - q-) / 2; F* = n.F(q-) - A - B, the jump n.F(q-) - F* = A + B.
+__device__ __forceinline__ void llf_parts_f(const float qm[5], const float qp[5], const float n[3],
+                                            const BaseF& b, float fnm[5], float hA[5], float hB[5]) {
+  float fnp[5], lm, lp;
+  normal_flux_f(qm, n, b, fnm, lm);
+  normal_flux_f(qp, n, b, fnp, lp);
+  const float lam = fmaxf(lm, lp);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    hA[v] = 0.5f * (fnm[v] - fnp[v]);
+    hB[v] = 0.5f * lam * (qp[v] - qm[v]);
+  }
+}
+
 // acc += a * b on two packed float32 lanes (one instruction for two FMAs)
 __device__ __forceinline__ void fma2(uint64_t& acc, uint64_t a, uint64_t b) {
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
@@ -194,19 +209,20 @@ stage_f32_kernel(const StageArgsF32 A) {
     // tile, copied asynchronously into the face columns of X (row v, element
     // le, column 3 Np + fm), where the face phase reads them and then writes
     // the jump; the copies fly while the node phase computes
-    const int nF = *reinterpret_cast<const int32_t*>(sFL);
-    for (int it = tid; it < nF * Nfp; it += NT) {
+    // face list groups: [0, aEnd) inside the tile, [aEnd, bEnd) to other
+    // tiles, [bEnd, cEnd) outer faces (items = face x face node)
+    const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
+    const int aEnd = hdr[1] * Nfp, bEnd = (hdr[1] + hdr[2]) * Nfp, cEnd = hdr[0] * Nfp;
+    for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      if (c >= 0 && ((c >> 5) < e0i || (c >> 5) >= e0i + nE)) {
-        const int64_t e2 = c >> 5;
-        const int f2 = (c >> 3) & 3, o = c & 7;
-        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-        const float* src = A.q_in + e2 * 5 * Np + n2;
+      const int64_t e2 = c >> 5;
+      const int f2 = (c >> 3) & 3, o = c & 7;
+      const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+      const float* src = A.q_in + e2 * 5 * Np + n2;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) cp_async4(sX + (v * ET + le) * SX + 3 * Np + fm, src + v * Np);
-      }
+      for (int v = 0; v < 5; ++v) cp_async4(sX + (v * ET + le) * SX + 3 * Np + fm, src + v * Np);
     }
     cp_async_commit();
     prefetch(tile + gridDim.x, buf ^ 1);
@@ -246,16 +262,15 @@ stage_f32_kernel(const StageArgsF32 A) {
     // two elements of the tile is listed once, under its lower element, which
     // writes both jumps: with A = (n.F(q-) - n.F(q+)) / 2 and
     // B = lambda (q+ - q-) / 2 the own jump is Fscale (A + B) and the
-    // neighbour's (normal -n, traces swapped) Fscale' (A - B).
+    // neighbour's (normal -n, traces swapped) Fscale' (A - B). The three
+    // groups of the list take their own branch, uniform within almost every
+    // warp: no work of one kind runs predicated off in another.
     float led[5] = {0, 0, 0, 0, 0};   // float32 within the tile, float64 across tiles
     bool any_bdry = false;
-    for (int it = tid; it < nF * Nfp; it += NT) {
+    for (int it = tid; it < cEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      // neighbour's tile slot; element indices are below 2^26, so 32 bits hold them
-      const int le2 = (c >= 0) ? (c >> 5) - e0i : -1;
-      const bool inside = c >= 0 && le2 >= 0 && le2 < nE;   // then le2 > le (face list)
       const int n = sFmask[f * Nfp + m];
       float qm[5], qp[5];
 #pragma unroll
@@ -263,19 +278,32 @@ stage_f32_kernel(const StageArgsF32 A) {
       const float* geo = sGeo + le * kGeoStride;
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       float* xf = sX + le * SX + 3 * Np + fm;        // + v * ET * SX
-      const int f2 = (c >> 3) & 3, o = c & 7;
-      if (c >= 0) {
-        // the neighbour's trace: in the tile's state, or gathered into the face
-        // columns; one load path for both, no divergence between them
-        const float* src = xf;
-        int stride = ET * SX;
-        if (inside) {
-          src = sQ + le2 * 5 * Np + sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-          stride = Np;
-        }
+      const float fs = geo[kGeoFscale + f];
+      float fnm[5], hA[5], hB[5];
+      if (it < aEnd) {
+        // both elements in the tile
+        const int le2 = (c >> 5) - e0i, f2 = (c >> 3) & 3, o = c & 7;
+        const int tb = ((f * 4 + f2) * 6 + o) * Nfp + m;
+        const float* src = sQ + le2 * 5 * Np + sTbl[tb];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) qp[v] = src[v * stride];
+        for (int v = 0; v < 5; ++v) qp[v] = src[v * Np];
+        llf_parts_f(qm, qp, nv, b, fnm, hA, hB);
+        float* xf2 = sX + le2 * SX + 3 * Np + f2 * Nfp + sTbl[O::kTbl + tb];
+        const float fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          xf[v * ET * SX] = fs * (hA[v] + hB[v]);
+          xf2[v * ET * SX] = fs2 * (hA[v] - hB[v]);
+        }
+      } else if (it < bEnd) {
+        // neighbour in another tile: its trace was gathered into the face columns
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qp[v] = xf[v * ET * SX];
+        llf_parts_f(qm, qp, nv, b, fnm, hA, hB);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) xf[v * ET * SX] = fs * (hA[v] + hB[v]);
       } else {
+        // outer face: ghost state, and the flux integral for the ledger
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
           const float D = A.bD ? A.bD[size_t((-1 - c) >> 3) * Nfp + m] : 0.0f;
@@ -283,30 +311,15 @@ stage_f32_kernel(const StageArgsF32 A) {
         } else {
           ghost_state_f(mode, qm, nv, bg, qp);
         }
-      }
-      float fnm[5], fnp[5], lm, lp;
-      normal_flux_f(qm, nv, b, fnm, lm);
-      normal_flux_f(qp, nv, b, fnp, lp);
-      const float lam = fmaxf(lm, lp);
-      const float fs = geo[kGeoFscale + f];
-      float* xf2 = xf;
-      float fs2 = 0.0f;
-      if (inside) {
-        const int m2 = sTbl[O::kTbl + ((f * 4 + f2) * 6 + o) * Nfp + m];
-        xf2 = sX + le2 * SX + 3 * Np + f2 * Nfp + m2;
-        fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
-      }
+        llf_parts_f(qm, qp, nv, b, fnm, hA, hB);
+        const float wsj = faceW[fm] * geo[kGeoSJ + f];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const float hA = 0.5f * (fnm[v] - fnp[v]), hB = 0.5f * lam * (qp[v] - qm[v]);
-        xf[v * ET * SX] = fs * (hA + hB);
-        if (inside) xf2[v * ET * SX] = fs2 * (hA - hB);
-        if (c < 0) {
-          const float fstar = 0.5f * (fnm[v] + fnp[v]) - hB;
-          led[v] += faceW[fm] * geo[kGeoSJ + f] * fstar;
+        for (int v = 0; v < 5; ++v) {
+          xf[v * ET * SX] = fs * (hA[v] + hB[v]);
+          led[v] += wsj * (fnm[v] - hA[v] - hB[v]);     // F* = n.F(q-) - A - B
         }
+        any_bdry = true;
       }
-      any_bdry |= (c < 0);
     }
     if (__syncthreads_or(any_bdry)) {
       const int lane = tid & 31, warp = tid >> 5;
