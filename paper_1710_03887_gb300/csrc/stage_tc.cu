@@ -94,6 +94,20 @@ __device__ __forceinline__ void normal_flux_tc(const float q[5], const float n[3
   lam = fabsf(un) + (c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f);
 }
 
+// Parts of the LLF flux at a face node: n.F(q-), A = (n.F(q-) - n.F(q+)) / 2,
+// B = lambda (q+ - q-) / 2; F* = n.F(q-) - A - B, the jump n.F(q-) - F* = A + B.
+__device__ __forceinline__ void llf_parts_tc(const float qm[5], const float qp[5], const float n[3],
+                                             const BaseF2& b, float fnm[5], float hA[5], float hB[5]) {
+  float fnp[5], lm, lp;
+  normal_flux_tc(qm, n, b, fnm, lm);
+  normal_flux_tc(qp, n, b, fnp, lp);
+  const float lam = fmaxf(lm, lp);
+  for (int v = 0; v < 5; ++v) {
+    hA[v] = 0.5f * (fnm[v] - fnp[v]);
+    hB[v] = 0.5f * lam * (qp[v] - qm[v]);
+  }
+}
+
 constexpr uint32_t kWaitTries = 1u << 24;   // bounded MMA completion wait
 
 // Per tile of 25 elements:
@@ -193,7 +207,7 @@ stage_tc_kernel(const StageArgsF32 A) {
     const float* sQ = reinterpret_cast<const float*>(smem + O::oQ) + buf * O::kQT;
     const float* sGeo = reinterpret_cast<const float*>(smem + O::oGeo) + buf * ET * kGeoStride;
     const int32_t* sConn = reinterpret_cast<const int32_t*>(smem + O::oConn) + buf * ET * 4;
-    const uint8_t* sFL = smem + O::oFL + buf * O::kFL;      // count, then (le << 2 | f)
+    const uint8_t* sFL = smem + O::oFL + buf * O::kFL;      // header, then (le << 2 | f)
     cp_async_wait_all();
     tc::fence_before_sync();
     __syncthreads();   // this tile's data is in; the previous tile is finished
@@ -202,19 +216,21 @@ stage_tc_kernel(const StageArgsF32 A) {
 
     // neighbour traces of faces whose neighbour lies outside the tile, into
     // the face columns of X (row 5 le + v, column 3 Np + fm)
-    const int nF = *reinterpret_cast<const int32_t*>(sFL);
-    for (int it = tid; it < nF * Nfp; it += NT) {
+    // face list groups: [0, aEnd) inside the tile, [aEnd, bEnd) to other
+    // tiles, [bEnd, cEnd) outer faces (items = face x face node)
+    const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
+    const int aEnd = hdr[1] * Nfp, bEnd = (hdr[1] + hdr[2]) * Nfp, cEnd = hdr[0] * Nfp;
+    const int e0i = int(e0);
+    for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int32_t c = sConn[le * 4 + f];
-      if (c >= 0 && ((c >> 5) < e0 || (c >> 5) >= e0 + nE)) {
-        const int64_t e2 = c >> 5;
-        const int f2 = (c >> 3) & 3, o = c & 7;
-        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-        const float* src = A.q_in + e2 * 5 * Np + n2;
+      const int64_t e2 = c >> 5;
+      const int f2 = (c >> 3) & 3, o = c & 7;
+      const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+      const float* src = A.q_in + e2 * 5 * Np + n2;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) cp_async4(sX + (le * 5 + v) * SX + 3 * Np + fm, src + v * Np);
-      }
+      for (int v = 0; v < 5; ++v) cp_async4(sX + (le * 5 + v) * SX + 3 * Np + fm, src + v * Np);
     }
     cp_async_commit();
     prefetch(tile + gridDim.x, buf ^ 1);
@@ -254,7 +270,7 @@ stage_tc_kernel(const StageArgsF32 A) {
     // and Fscale' (A - B), A = (n.F(q-) - n.F(q+)) / 2, B = lambda (q+ - q-) / 2)
     float led[5] = {0, 0, 0, 0, 0};
     bool any_bdry = false;
-    for (int it = tid; it < nF * Nfp; it += NT) {
+    for (int it = tid; it < cEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int n = sFmask[f * Nfp + m];
@@ -264,20 +280,28 @@ stage_tc_kernel(const StageArgsF32 A) {
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       const int32_t c = sConn[le * 4 + f];
       float* xf = sX + le * 5 * SX + 3 * Np + fm;     // row v at + v * SX
-      const int le2 = (c >= 0) ? int((c >> 5) - e0) : -1;
-      const bool inside = c >= 0 && le2 >= 0 && le2 < nE;   // then le2 > le (face list)
-      float* xf2 = xf;
-      float fs2 = 0.0f;
-      if (inside) {
-        const int f2 = (c >> 3) & 3, o = c & 7;
-        const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-        const int m2 = sTbl[96 * Nfp + ((f * 4 + f2) * 6 + o) * Nfp + m];
-        for (int v = 0; v < 5; ++v) qp[v] = sQ[(le2 * 5 + v) * Np + n2];
-        xf2 = sX + le2 * 5 * SX + 3 * Np + f2 * Nfp + m2;
-        fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
-      } else if (c >= 0) {
+      const float fs = geo[kGeoFscale + f];
+      float fnm[5], hA[5], hB[5];
+      if (it < aEnd) {
+        // both elements in the tile
+        const int le2 = (c >> 5) - e0i, f2 = (c >> 3) & 3, o = c & 7;
+        const int tb = ((f * 4 + f2) * 6 + o) * Nfp + m;
+        const float* src = sQ + le2 * 5 * Np + sTbl[tb];
+        for (int v = 0; v < 5; ++v) qp[v] = src[v * Np];
+        llf_parts_tc(qm, qp, nv, b, fnm, hA, hB);
+        float* xf2 = sX + le2 * 5 * SX + 3 * Np + f2 * Nfp + sTbl[96 * Nfp + tb];
+        const float fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
+        for (int v = 0; v < 5; ++v) {
+          xf[v * SX] = fs * (hA[v] + hB[v]);
+          xf2[v * SX] = fs2 * (hA[v] - hB[v]);
+        }
+      } else if (it < bEnd) {
+        // neighbour in another tile: its trace was gathered into the face columns
         for (int v = 0; v < 5; ++v) qp[v] = xf[v * SX];
+        llf_parts_tc(qm, qp, nv, b, fnm, hA, hB);
+        for (int v = 0; v < 5; ++v) xf[v * SX] = fs * (hA[v] + hB[v]);
       } else {
+        // outer face: ghost state, and the flux integral for the ledger
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
           const float D = A.bD ? A.bD[size_t((-1 - c) >> 3) * Nfp + m] : 0.0f;
@@ -285,19 +309,14 @@ stage_tc_kernel(const StageArgsF32 A) {
         } else {
           ghost_state_f(mode, qm, nv, bg, qp);
         }
+        llf_parts_tc(qm, qp, nv, b, fnm, hA, hB);
+        const float wsj = sW[fm] * geo[kGeoSJ + f];
+        for (int v = 0; v < 5; ++v) {
+          xf[v * SX] = fs * (hA[v] + hB[v]);
+          led[v] += wsj * (fnm[v] - hA[v] - hB[v]);     // F* = n.F(q-) - A - B
+        }
+        any_bdry = true;
       }
-      float fnm[5], fnp[5], lm, lp;
-      normal_flux_tc(qm, nv, b, fnm, lm);
-      normal_flux_tc(qp, nv, b, fnp, lp);
-      const float lam = fmaxf(lm, lp);
-      const float fs = geo[kGeoFscale + f];
-      for (int v = 0; v < 5; ++v) {
-        const float hA = 0.5f * (fnm[v] - fnp[v]), hB = 0.5f * lam * (qp[v] - qm[v]);
-        xf[v * SX] = fs * (hA + hB);
-        if (inside) xf2[v * SX] = fs2 * (hA - hB);
-        if (c < 0) led[v] += sW[fm] * geo[kGeoSJ + f] * (0.5f * (fnm[v] + fnp[v]) - hB);
-      }
-      any_bdry |= (c < 0);
     }
     // boundary-flux ledger of this tile (the barrier also publishes X)
     if (__syncthreads_or(any_bdry)) {
