@@ -22,6 +22,9 @@ five-stage low-storage RK4 time step of the whole mesh.
   learned_bc the learned boundary closure: traces recorded, network trained
              and reflected energies measured on the GPU, and the closure timed on
              the bench workload
+  paper_configuration  p = 1 with RK2 on the bench mesh (the paper's own setting)
+             in the paper's discretisation and the nodal forms, with device
+             memory per element
   locality   the float32 form on the bench mesh in lattice, Morton and random
              element order (how far tiles' gathers reach)
   horn       the horn-in-room workload (1,489,704 tets, p=3: a flared horn with
@@ -577,6 +580,51 @@ def locality_section(args, xyz, EToV, dev, stream):
     return out
 
 
+def paper_config_section(args, xyz, EToV, dev, stream):
+    """The paper's own configuration (section 1.1, Appendix A; Tables 1 and 3):
+    linear elements (p = 1) and RK2 on a ~200k-element mesh, in the paper's
+    discretisation (Gauss quadrature, Heun) and, beside it, the nodal float64
+    and float32 forms at p = 1; each with the device memory its context
+    holds per element (the paper's Table 3 gives ~1000 B per element)."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    w = WORKLOAD
+    out = {"order": 1, "elements": int(len(EToV)), "steps": args.paper_steps,
+           "paper_bytes_per_element": "998-1111 (Tables 1 and 3, GTX 750 Ti, precision not stated)"}
+    for name, code in (("modal", B.DG_PREC_MODAL), ("fp64", B.DG_PREC_FP64), ("f32", B.DG_PREC_F32)):
+        S = B.Solver(1, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=code)
+        S.set_stream(stream.cuda_stream)
+        S.upload_mesh(xyz, EToV)                      # host only: no device memory yet
+        q0 = W.gaussian_pulse_state(S.node_coords(), W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"],
+                                    w["width"])
+        dt = S.stable_dt(q0, w["cfl"])
+        q0d = torch.from_numpy(q0).to(dev)
+        torch.cuda.synchronize(dev)
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        S.set_state(q0d)                              # the context allocates here
+        S.step(args.warmup, dt)
+        S.set_state(q0d)
+        torch.cuda.synchronize(dev)
+        held = free0 - torch.cuda.mem_get_info(dev)[0]
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        S.step(args.paper_steps, dt)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = start.elapsed_time(stop)
+        S.sync()
+        dof = 5 * S.Np * S.K
+        out[name] = {"value": dof * args.paper_steps / (ms * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms / args.paper_steps,
+                     "stages_per_step": 2 if name == "modal" else 5,
+                     "device_bytes_per_element": held / S.K}
+        S.close()
+        del q0d
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -652,6 +700,8 @@ def run_gpu(args, rank, world):
         line["horn"] = horn_section(args, dev, stream)
     if args.locality_steps > 0:
         line["locality"] = locality_section(args, xyz, EToV, dev, stream)
+    if args.paper_steps > 0:
+        line["paper_configuration"] = paper_config_section(args, xyz, EToV, dev, stream)
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -672,6 +722,8 @@ def main():
     ap.add_argument("--learned-n", type=int, default=16,
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")
+    ap.add_argument("--paper-steps", type=int, default=50,
+                    help="steps timed per form in the paper-configuration section (0: skip it)")
     ap.add_argument("--locality-steps", type=int, default=20,
                     help="steps timed per element order in the locality section (0: skip it)")
     ap.add_argument("--horn-steps", type=int, default=20,
