@@ -128,3 +128,30 @@ def test_modal_periodic_conservation(cuda_device):
     assert np.all(state_err(qg, qo, GAS) < TOL)
     np.testing.assert_allclose(S.totals(), tot0, rtol=0, atol=1e-13 * np.abs(tot0).max())
     assert np.all(S.boundary_flux() == 0.0)
+
+
+def test_modal_full_size_p1_sampled_rhs(cuda_device):
+    """The paper's configuration: p = 1 on the 196,608-element ball. Sampled
+    elements' right-hand sides against the modal oracle on the patch made of
+    them and their neighbours (the patch keeps the elements' relative order,
+    so every face keeps the Gauss rule of its lower-numbered element)."""
+    import torch
+    xyz, EToV = W.ball(32, 1.0, jitter=0.1, seed=0)
+    K = EToV.shape[0]
+    S = _library(1, xyz, EToV)
+    q = W.random_smooth_state(S.node_coords(), SI["gamma"], SI["rho0"], SI["p0"], 0.05, seed=9)
+    S.set_state(q)
+    rhs = S.eval_rhs()
+    g = S.geometry()
+    rng = np.random.default_rng(4)
+    bdry = np.nonzero((g["EToE"] < 0).any(axis=1))[0]
+    sample = np.unique(np.concatenate([rng.choice(K, 40, replace=False), rng.choice(bdry, 12, replace=False)]))
+    patch = np.unique(np.concatenate([sample, g["EToE"][sample].ravel()]))
+    patch = patch[patch >= 0]
+    sx, sE = W.submesh(xyz, EToV, np.isin(np.arange(K), patch))
+    orc = MD.ModalSolver(Geometry(ReferenceElement(1), sx, sE), GAS)
+    local = np.searchsorted(patch, sample)
+    ro = orc.rhs_nodal(q[patch])[local]
+    # every field varies, so every variable's right-hand side is O(1)
+    err = np.abs(rhs[sample] - ro).max(axis=(0, 2)) / np.abs(ro).max(axis=(0, 2))
+    assert np.all(err < TOL), err
