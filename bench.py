@@ -625,6 +625,72 @@ def paper_config_section(args, xyz, EToV, dev, stream):
     return out
 
 
+def production_section(args, dev, stream):
+    """The production-size configuration in the float32 form: p = 4 on the
+    7,986,000-element cube lattice (n = 110, 1.4e9 DOF), a pulse at rest,
+    the characteristic condition; timed like the bench workload."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    t0 = time.perf_counter()
+    xyz, EToV = W.kuhn_cube(110, jitter=0.1, seed=5)
+    S = B.Solver(4, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
+    S.set_stream(stream.cuda_stream)
+    S.upload_mesh(xyz, EToV)
+    Np, K = S.Np, S.K
+    ops = B.reference_operators(4)
+    wv = np.stack([-0.5 * (1 + ops["r"] + ops["s"] + ops["t"]), 0.5 * (1 + ops["r"]),
+                   0.5 * (1 + ops["s"]), 0.5 * (1 + ops["t"])])
+    q = torch.empty((K, 5, Np), dtype=torch.float64, device=dev)
+    dt = None
+    for k0 in range(0, K, 1 << 20):
+        k1 = min(K, k0 + (1 << 20))
+        nodes = np.einsum("kvd,vn->knd", xyz[EToV[k0:k1]], wv)
+        qc = W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, 0.1, 0.3)
+        q[k0:k1] = torch.from_numpy(qc).to(dev)
+    # the CFL step of the library (0.5 r_in / ((p+1)^2 max(|u| + c))) from
+    # the fastest state of the run, the pulse's peak at rest, and the
+    # smallest inscribed radius 3V / (face areas), computed here in chunks
+    # rather than from the whole state on the host
+    rin = np.inf
+    for k0 in range(0, K, 1 << 20):
+        v = xyz[EToV[k0:k0 + (1 << 20)]]
+        vol = np.abs(np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]),
+                               v[:, 3] - v[:, 0])) / 6.0
+        area = sum(0.5 * np.linalg.norm(np.cross(v[:, b] - v[:, a], v[:, c] - v[:, a]), axis=1)
+                   for a, b, c in ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3)))
+        rin = min(rin, float((3.0 * vol / area).min()))
+    p_peak = 1.1 * W.P0_SI
+    rho_peak = W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA)
+    dt = 0.5 * rin / (25.0 * np.sqrt(W.GAMMA * p_peak / rho_peak))
+    setup = time.perf_counter() - t0
+    S.set_state(q)
+    S.step(1, dt)
+    S.set_state(q)
+    torch.cuda.synchronize(dev)
+    S.set_kernel_timing(True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    S.step(args.production_steps, dt)
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(stop)
+    kms, kl = S.read_kernel_timing()
+    S.set_kernel_timing(False)
+    S.sync()
+    dof = 5 * Np * K
+    avg = kms / max(kl, 1)
+    S.close()
+    return {"workload": "cube lattice n=110, 7,986,000 tets, jitter 0.1h seed 5; p=4 (Np=35); "
+                        "10% p0 pulse w=0.3; characteristic BC",
+            "elements": int(K), "dof": int(dof), "steps": args.production_steps,
+            "value": dof * args.production_steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / args.production_steps, "avg_stage_launch_ms": avg,
+            "stage_tflops": stage_flops_per_element(4) * K / (avg * 1e-3) / 1e12,
+            "setup_seconds": setup}
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -702,6 +768,8 @@ def run_gpu(args, rank, world):
         line["locality"] = locality_section(args, xyz, EToV, dev, stream)
     if args.paper_steps > 0:
         line["paper_configuration"] = paper_config_section(args, xyz, EToV, dev, stream)
+    if args.production_steps > 0:
+        line["production"] = production_section(args, dev, stream)
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -722,6 +790,9 @@ def main():
     ap.add_argument("--learned-n", type=int, default=16,
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")
+    ap.add_argument("--production-steps", type=int, default=0,
+                    help="steps timed on the p=4, 8M-element configuration (0: skip it; it "
+                         "builds the mesh on the host first, about a minute)")
     ap.add_argument("--paper-steps", type=int, default=50,
                     help="steps timed per form in the paper-configuration section (0: skip it)")
     ap.add_argument("--locality-steps", type=int, default=20,

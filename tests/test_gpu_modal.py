@@ -155,3 +155,27 @@ def test_modal_full_size_p1_sampled_rhs(cuda_device):
     # every field varies, so every variable's right-hand side is O(1)
     err = np.abs(rhs[sample] - ro).max(axis=(0, 2)) / np.abs(ro).max(axis=(0, 2))
     assert np.all(err < TOL), err
+
+
+def test_modal_bad_state_is_reported_and_the_context_stays_usable(cuda_device):
+    from paper_1710_03887_gb300 import binding as B
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=2)
+    geom = Geometry(ReferenceElement(2), xyz, EToV)
+    q0 = W.gaussian_pulse_state(geom.x, SI["gamma"], SI["rho0"], SI["p0"], 0.05, 0.3)
+    from oracle.euler_dg import Solver
+    dt = Solver(geom, GAS).stable_dt(q0, 0.3)
+    S = _library(2, xyz, EToV)
+    S.set_state(q0)
+    S.step(3, dt)
+    ref, _ = S.get_state()
+    bad = q0.copy()
+    bad[7, 4, :] = 0.0                       # zero energy: negative pressure at every point
+    S.set_state(bad)
+    with pytest.raises(B.DGError) as e:
+        S.step(1, dt)
+        S.get_state()
+    assert e.value.code == B.DG_ERR_NONFINITE
+    S.set_state(q0)
+    S.step(3, dt)
+    q, _ = S.get_state()
+    assert np.array_equal(q, ref)            # same bits as before the bad state
