@@ -141,6 +141,7 @@ class ClockSampler:
         self.index = index          # < 0: do not sample
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         if self.index < 0:
@@ -148,10 +149,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # the timed region starts once the sampler runs; its first lines
+            # (before the region) are kept apart
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
+            self.skip = len(self.lines)
         except OSError:
             self.proc = None
         return self
@@ -171,7 +178,13 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lines = self.lines[self.skip:]
+        before = 0
+        if not lines and self.skip:
+            # a region shorter than the polling interval: the last sample
+            # before it stands in, and the record says so
+            lines, before = self.lines[self.skip - 1:self.skip], 1
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -185,8 +198,11 @@ class ClockSampler:
                     reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+               "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 50}
+        if before:
+            out["note"] = "no sample fell inside the timed region; the last one before it"
+        return out
 
 
 def build_workload():
