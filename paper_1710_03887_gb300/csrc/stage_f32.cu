@@ -229,6 +229,9 @@ stage_f32_kernel(const StageArgsF32 A) {
     cp_async_commit();
 
     // ---- volume fluxes (perturbation form) at nodes, folded with the metric
+    // two items per trip (two nodes per thread for a full tile): independent
+    // load and flux chains side by side
+#pragma unroll 2
     for (int it = tid; it < nE * Np; it += NT) {
       const int le = it / Np, n = it - (it / Np) * Np;
       float q[5];
