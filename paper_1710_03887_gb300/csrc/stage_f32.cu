@@ -340,16 +340,6 @@ stage_f32_kernel(const StageArgsF32 A) {
     }
     __syncthreads();
 
-    // the residuals the Runge-Kutta pass will read, loaded before the product
-    constexpr int RI = (ET * 5 * Np + NT - 1) / NT;
-    const int64_t base = e0 * 5 * Np;
-    float rres[RI];
-#pragma unroll
-    for (int s = 0; s < RI; ++s) {
-      const int i = tid + s * NT;
-      rres[s] = (A.a != 0.0f && i < nE * 5 * Np) ? A.res[base + i] : 0.0f;
-    }
-
     // ---- X OT: warp = (K part, output part), lane = element
     {
       const int le = tid & 31, w = tid >> 5;
@@ -400,6 +390,17 @@ stage_f32_kernel(const StageArgsF32 A) {
       }
     }
     __syncthreads();
+
+    // the residuals the Runge-Kutta pass will read, loaded after the product
+    // (not held in registers through it; the other CTA on the SM covers the wait)
+    constexpr int RI = (ET * 5 * Np + NT - 1) / NT;
+    const int64_t base = e0 * 5 * Np;
+    float rres[RI];
+#pragma unroll
+    for (int s = 0; s < RI; ++s) {
+      const int i = tid + s * NT;
+      rres[s] = (A.a != 0.0f && i < nE * 5 * Np) ? A.res[base + i] : 0.0f;
+    }
 
     // ---- Runge-Kutta update, coalesced over the tile's state; output row
     // r = v Np + n of element le is partial-sum row r
