@@ -1,4 +1,4 @@
-"""Plain FP64 CPU oracle of the nodal DG Euler hot path (test infrastructure).
+"""Plain FP64 CPU oracles of the DG Euler hot path (test infrastructure).
 
 This package is the independent check of the CUDA library: slow, written for
 reading, in float64 numpy. It is used only by the tests, by the bench's CPU
@@ -20,4 +20,7 @@ Modules:
                      boundary-flux ledger and conserved totals
   mlp                the closure's network (forward, loss gradient, Adam) and
                      its features
+  modal_dg           the paper's own discretisation (Appendix A): orthonormal
+                     basis, Gauss quadrature of degree 2p / 2p+1 for Eq. 10,
+                     Heun's RK2
 """
