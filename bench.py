@@ -480,6 +480,23 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     }
 
 
+def rest_cfl_dt(xyz, EToV, order, p_fast, rho_fast, cfl=0.5):
+    """The library's CFL step, cfl r_in / ((p+1)^2 max(|u| + c)), for a gas at
+    rest whose fastest sound speed is sqrt(gamma p_fast / rho_fast), with the
+    smallest inscribed radius 3V / (face areas) computed in chunks: no
+    state-sized array on the host."""
+    from paper_1710_03887_gb300 import workloads as W
+    rin = np.inf
+    for k0 in range(0, len(EToV), 1 << 20):
+        v = xyz[EToV[k0:k0 + (1 << 20)]]
+        vol = np.abs(np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]),
+                               v[:, 3] - v[:, 0])) / 6.0
+        area = sum(0.5 * np.linalg.norm(np.cross(v[:, b] - v[:, a], v[:, c] - v[:, a]), axis=1)
+                   for a, b, c in ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3)))
+        rin = min(rin, float((3.0 * vol / area).min()))
+    return cfl * rin / ((order + 1) ** 2 * np.sqrt(W.GAMMA * p_fast / rho_fast))
+
+
 def horn_section(args, dev, stream):
     """Both float32 forms on the horn-in-room workload: the mixed-precision
     configuration's geometry (a flared horn with slip walls inside a room in
@@ -508,7 +525,7 @@ def horn_section(args, dev, stream):
         q0 = torch.empty((S.K, 5, S.Np), dtype=torch.float64, device=dev)
         base = W.uniform_state(1, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
         q0[:] = torch.from_numpy(base).to(dev)
-        dt = horn_dt(S)
+        dt = rest_cfl_dt(xyz, EToV, 3, W.P0_SI, W.RHO0_SI)
         S.set_probes(info["sensors"], capacity=max(args.horn_steps, 1))
         S.set_state(q0)
         S.step(args.warmup, dt)
@@ -538,12 +555,6 @@ def horn_section(args, dev, stream):
                                               * (W.GAMMA - 1.0) / W.P0_SI)}
         S.close()
     return out
-
-
-def horn_dt(S):
-    """The solver's CFL 0.5 time step for the gas at rest."""
-    from paper_1710_03887_gb300 import workloads as W
-    return S.stable_dt(W.uniform_state(S.K, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA), 0.5)
 
 
 def locality_section(args, xyz, EToV, dev, stream):
@@ -664,21 +675,8 @@ def production_section(args, dev, stream):
         nodes = np.einsum("kvd,vn->knd", xyz[EToV[k0:k1]], wv)
         qc = W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, 0.1, 0.3)
         q[k0:k1] = torch.from_numpy(qc).to(dev)
-    # the CFL step of the library (0.5 r_in / ((p+1)^2 max(|u| + c))) from
-    # the fastest state of the run, the pulse's peak at rest, and the
-    # smallest inscribed radius 3V / (face areas), computed here in chunks
-    # rather than from the whole state on the host
-    rin = np.inf
-    for k0 in range(0, K, 1 << 20):
-        v = xyz[EToV[k0:k0 + (1 << 20)]]
-        vol = np.abs(np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]),
-                               v[:, 3] - v[:, 0])) / 6.0
-        area = sum(0.5 * np.linalg.norm(np.cross(v[:, b] - v[:, a], v[:, c] - v[:, a]), axis=1)
-                   for a, b, c in ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3)))
-        rin = min(rin, float((3.0 * vol / area).min()))
-    p_peak = 1.1 * W.P0_SI
-    rho_peak = W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA)
-    dt = 0.5 * rin / (25.0 * np.sqrt(W.GAMMA * p_peak / rho_peak))
+    # the fastest state of the run: the pulse's peak, at rest
+    dt = rest_cfl_dt(xyz, EToV, 4, 1.1 * W.P0_SI, W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA))
     setup = time.perf_counter() - t0
     S.set_state(q)
     S.step(1, dt)
