@@ -338,7 +338,8 @@ stage_f32_kernel(const StageArgsF32 A) {
         cled += acc;
       }
     }
-    __syncthreads();
+    // (the barrier above published the face columns of X; sRed is written
+    // again only after the next tile's barriers)
 
     // ---- X OT: warp = (K part, output part), lane = element
     {
