@@ -188,6 +188,16 @@ int dg_node_coords(const dg_ctx* ctx, double* xyz);
  * EToE[K][4] (-1 on boundary faces), EToF[K][4], bc[K][4] (-1 interior). */
 int dg_get_geometry(const dg_ctx* ctx, double* J, double* drdx, double* nrm,
                     double* sJ, int32_t* EToE, int8_t* EToF, int8_t* bc);
+/* Face-node pairing the stage kernels use (host; either pointer may be
+ * NULL). Neighbours couple only through the numerical flux at the points of
+ * their shared face (section 1.1, the surface term of Eq. 10); the kernels
+ * find the other side's value at face node m of face f of element e from
+ * the face's connection word (neighbour e2, its face f2, orientation code)
+ * and the reference face-node tables. Decoded the same way here:
+ * vol_node[K][4][Nfp] = e2 * Np + n2, the neighbour's volume node at that
+ * point, and face_node[K][4][Nfp] = the position of n2 in face f2's node
+ * list; both -1 on boundary faces. DG_ERR_ORDER before a mesh upload. */
+int dg_face_pairs(const dg_ctx* ctx, int64_t* vol_node, int32_t* face_node);
 /* Stable time step  cfl * min_e r_in / ((p+1)^2 * max(|u| + c))  of a host
  * state q[K][5][Np] (host computation; r_in = 3 V / total face area). */
 int dg_stable_dt(const dg_ctx* ctx, const double* q, double cfl, double* dt);

@@ -54,6 +54,7 @@ _SIGS = {
     "dg_sizes": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "dg_node_coords": (C.c_int, [_P, _P]),
     "dg_get_geometry": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "dg_face_pairs": (C.c_int, [_P, _P, _P]),
     "dg_stable_dt": (C.c_int, [_P, _P, C.c_double, _D]),
     "dg_reference_operators": (C.c_int, [C.c_int, _P, _P, _P, _P, _P, _P]),
     "dg_set_state": (C.c_int, [_P, _P, C.c_double]),
@@ -249,6 +250,15 @@ class Solver:
         self._check(self.lib.dg_get_geometry(self.h, *(_ptr(g[k]) for k in
                                                        ("J", "drdx", "nrm", "sJ", "EToE", "EToF", "bc"))))
         return g
+
+    def face_pairs(self):
+        """(vol_node [K,4,Nfp] int64, face_node [K,4,Nfp] int32): the other
+        side's volume node (e2 * Np + n) and its face-node position for
+        every face node, as the stage kernels decode them; -1 on boundary faces."""
+        vol = np.zeros((self.K, 4, self.Nfp), dtype=np.int64)
+        fac = np.zeros((self.K, 4, self.Nfp), dtype=np.int32)
+        self._check(self.lib.dg_face_pairs(self.h, _ptr(vol), _ptr(fac)))
+        return vol, fac
 
     def stable_dt(self, q, cfl=0.5):
         q = np.ascontiguousarray(q, dtype=np.float64)

@@ -43,6 +43,26 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// Face-node tables [4][4][6][Nfp], one after the other, indexed by (own face
+// f, neighbour face f2, orientation code o, own face node m): the
+// neighbour's volume node at the same point, then that node's index in the
+// neighbour face's node list. Uploaded for the stage kernels and read back
+// by dg_face_pairs.
+std::vector<uint8_t> face_node_tables(const dg::RefElement& re) {
+  const int Nfp = re.Nfp;
+  std::vector<uint8_t> t(re.nbr_node);
+  t.resize(2 * re.nbr_node.size(), 0xFF);
+  for (int f = 0; f < 4; ++f)
+    for (int f2 = 0; f2 < 4; ++f2)
+      for (int o = 0; o < 6; ++o)
+        for (int m = 0; m < Nfp; ++m) {
+          const size_t i = ((size_t(f) * 4 + f2) * 6 + o) * Nfp + m;
+          for (int m2 = 0; m2 < Nfp; ++m2)
+            if (re.Fmask[f2 * Nfp + m2] == re.nbr_node[i]) t[re.nbr_node.size() + i] = uint8_t(m2);
+        }
+  return t;
+}
+
 }  // namespace
 
 struct dg_ctx {
@@ -344,20 +364,7 @@ int ensure_device(dg_ctx* c) {
     DG_CUDA(cudaMalloc(&c->ops32, o32.size() * 4));
     DG_CUDA(cudaMemcpy(c->ops32, o32.data(), o32.size() * 4, cudaMemcpyHostToDevice));
   }
-  // face-node tables [4][4][6][Nfp], one after the other: the neighbour's
-  // volume node of face node m, then the neighbour's face node (its index in
-  // the neighbour face's node list)
-  std::vector<uint8_t> tbl2(c->ref.nbr_node);
-  tbl2.resize(2 * c->ref.nbr_node.size(), 0xFF);
-  for (int f = 0; f < 4; ++f)
-    for (int f2 = 0; f2 < 4; ++f2)
-      for (int o = 0; o < 6; ++o)
-        for (int m = 0; m < Nfp; ++m) {
-          const size_t i = ((size_t(f) * 4 + f2) * 6 + o) * Nfp + m;
-          for (int m2 = 0; m2 < Nfp; ++m2)
-            if (c->ref.Fmask[f2 * Nfp + m2] == c->ref.nbr_node[i])
-              tbl2[c->ref.nbr_node.size() + i] = uint8_t(m2);
-        }
+  const std::vector<uint8_t> tbl2 = face_node_tables(c->ref);
   DG_CUDA(cudaMalloc(&c->tbl, tbl2.size()));
   DG_CUDA(cudaMemcpy(c->tbl, tbl2.data(), tbl2.size(),
                      cudaMemcpyHostToDevice));
@@ -776,6 +783,29 @@ int dg_get_geometry(const dg_ctx* c, double* J, double* drdx, double* nrm, doubl
   if (EToE) std::memcpy(EToE, m.EToE.data(), m.EToE.size() * 4);
   if (EToF) std::memcpy(EToF, m.EToF.data(), m.EToF.size());
   if (bc) std::memcpy(bc, m.bc.data(), m.bc.size());
+  return DG_OK;
+}
+
+int dg_face_pairs(const dg_ctx* c, int64_t* vol_node, int32_t* face_node) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->have_mesh) return DG_ERR_ORDER;
+  const int Np = c->ref.Np, Nfp = c->ref.Nfp;
+  const std::vector<uint8_t> tbl = face_node_tables(c->ref);
+  const size_t half = tbl.size() / 2;
+  for (int64_t e = 0; e < c->mesh.K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const size_t i = size_t(e) * 4 + f;
+      const bool inner = c->mesh.EToE[i] >= 0;
+      // decoded from the connection word exactly as the stage kernels do
+      const int32_t w = inner ? dgk::conn_interior(c->mesh.EToE[i], c->mesh.EToF[i], c->mesh.orient[i]) : 0;
+      const int64_t e2 = w >> 5;
+      const int f2 = (w >> 3) & 3, o = w & 7;
+      for (int m = 0; m < Nfp; ++m) {
+        const size_t t = ((size_t(f) * 4 + f2) * 6 + o) * Nfp + m, out = i * Nfp + m;
+        if (vol_node) vol_node[out] = inner ? e2 * Np + tbl[t] : -1;
+        if (face_node) face_node[out] = inner ? int32_t(tbl[half + t]) : -1;
+      }
+    }
   return DG_OK;
 }
 

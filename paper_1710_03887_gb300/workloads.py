@@ -171,6 +171,22 @@ def random_order(K, seed=0):
     return np.random.default_rng(seed).permutation(K)
 
 
+def shuffle_vertices(xyz, EToV, seed=0):
+    """The same mesh with each element's vertex list in a seeded random
+    order, kept positively oriented (an odd permutation has its first two
+    entries swapped back). Mesh generators list the vertices of shared faces
+    in unrelated orders; the lattice generators here do not, so a shared
+    face meets only some of the six vertex correspondences between its two
+    sides. After this shuffle every correspondence occurs."""
+    rng = np.random.default_rng(seed)
+    E = np.array([row[rng.permutation(4)] for row in np.asarray(EToV)], dtype=np.int32)
+    v = xyz[E]
+    d = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0])
+    E[d < 0] = E[d < 0][:, [1, 0, 2, 3]]
+    _fix_orientation(xyz, E)
+    return E
+
+
 def element_centroids(xyz, EToV):
     return xyz[EToV].mean(axis=1)
 

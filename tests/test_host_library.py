@@ -76,6 +76,48 @@ def test_geometry_and_connectivity_match_oracle(jitter):
     np.testing.assert_allclose(S.node_coords(), G.x, atol=1e-15)
 
 
+def _pairing_meshes():
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=4)
+    yield "lattice", xyz, EToV, None
+    yield "shuffled", xyz, W.shuffle_vertices(xyz, EToV, seed=1), None
+    bx, bE = W.ball(4, 1.0, jitter=0.1, seed=2)
+    yield "ball shuffled", bx, W.shuffle_vertices(bx, bE, seed=3), None
+    yield "periodic shuffled", xyz, W.shuffle_vertices(xyz, EToV, seed=5), (2.0, 2.0, 2.0)
+
+
+@pytest.mark.parametrize("p", [1, 3, 4])
+def test_face_pairing_matches_the_oracle_for_every_orientation(p):
+    """Each face node's partner as the stage kernels decode it (connection
+    word + reference face-node tables) is the node the oracle pairs it with
+    by coordinates; with shuffled vertex lists all six vertex
+    correspondences between the sides of a face occur."""
+    from ._cases import orientation_codes
+    ref = ReferenceElement(p)
+    for name, xyz, EToV, period in _pairing_meshes():
+        vclass = W.periodic_vertex_classes(3) if period else None
+        S = B.Solver(p)
+        S.upload_mesh(xyz, EToV, vert_class=vclass)
+        vol, fac = S.face_pairs()
+        G = Geometry(ref, xyz, EToV, period=period)
+        inner = ~G.boundary
+        np.testing.assert_array_equal(vol[G.boundary], -1, err_msg=name)
+        np.testing.assert_array_equal(vol[inner], G.vmapP[inner], err_msg=name)
+        # the face-node position names the same node
+        e2, f2 = G.EToE[inner], G.EToF[inner]
+        np.testing.assert_array_equal(ref.Fmask[f2[:, None], fac[inner]], vol[inner] % ref.Np,
+                                      err_msg=name)
+        # the orientation codes of the tests' convention (uploaded with the
+        # oracle's factors) give the same pairing as the library's own
+        ids = EToV if period is None else vclass[EToV]              # vertices across the seam
+        EToE = np.where(G.boundary, -1, G.EToE)
+        codes = orientation_codes(ids, EToE, G.EToF)
+        S2 = B.Solver(p)
+        S2.upload_geometry(G.drdx, G.J, G.nrm, G.Fscale, EToE, G.EToF, codes)
+        np.testing.assert_array_equal(S2.face_pairs()[0], vol, err_msg=name)
+        if name != "lattice":
+            assert set(codes[inner].tolist()) == set(range(6)), name
+
+
 def test_stable_dt_matches_oracle():
     from oracle.euler_dg import Gas, Solver
     xyz, EToV = W.kuhn_cube(3, jitter=0.1)

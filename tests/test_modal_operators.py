@@ -62,9 +62,14 @@ def _kernel_rhs(ops, geom, EToV, q, bc_id, modes, t=0.0, inflow=(0.05, 565.0)):
     return rhs, (N + 10) * 2.0 ** -53 * mag
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_library_operators_reproduce_the_modal_oracle(p):
+@pytest.mark.parametrize("p,shuffled", [(1, False), (2, False), (3, False), (4, False),
+                                        (2, True), (3, True)])
+def test_library_operators_reproduce_the_modal_oracle(p, shuffled):
+    """Lattice vertex lists, and shuffled ones where every orientation code
+    (every variant 1 + o of the face operators) occurs."""
     xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=10 + p)
+    if shuffled:
+        EToV = W.shuffle_vertices(xyz, EToV, seed=20 + p)
     geom = Geometry(ReferenceElement(p), xyz, EToV)
     tags = direction_tags(xyz, EToV, geom)
     bc_id = np.where(tags < 0, 0, tags)

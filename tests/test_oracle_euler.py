@@ -40,6 +40,17 @@ def test_eq3_scaled_free_stream():
     assert pressure(gas.freestream(), gas.gamma) == pytest.approx(vals["p0"], rel=1e-15)
 
 
+def _flux_jacobian(q, n, g):
+    """dF_n/dq by central differences of the oracle's normal flux."""
+    J = np.zeros((5, 5))
+    for j in range(5):
+        h = 1e-6 * max(abs(q[j]), 1.0)
+        e = np.zeros(5)
+        e[j] = h
+        J[:, j] = (normal_flux(q + e, n, g) - normal_flux(q - e, n, g)) / (2 * h)
+    return J
+
+
 def test_flux_jacobian_eigenvalues():
     """dF_n/dq has eigenvalues u.n - c, u.n (x3), u.n + c (hyperbolicity of Eq. 1)."""
     rng = np.random.default_rng(0)
@@ -50,13 +61,7 @@ def test_flux_jacobian_eigenvalues():
         n = rng.normal(size=3)
         n /= np.linalg.norm(n)
         q = state(rho, u, p, g)
-        J = np.zeros((5, 5))
-        for j in range(5):
-            h = 1e-6 * max(abs(q[j]), 1.0)
-            e = np.zeros(5)
-            e[j] = h
-            J[:, j] = (normal_flux(q + e, n, g) - normal_flux(q - e, n, g)) / (2 * h)
-        ev = np.sort(np.linalg.eigvals(J).real)
+        ev = np.sort(np.linalg.eigvals(_flux_jacobian(q, n, g)).real)
         un, c = u @ n, np.sqrt(g * p / rho)
         np.testing.assert_allclose(ev, [un - c, un, un, un, un + c], atol=1e-6)
 
@@ -81,6 +86,26 @@ def test_llf_consistency_and_antisymmetry():
     np.testing.assert_array_equal(llf_flux(a, b, n, g), -llf_flux(b, a, -n, g))
 
 
+def test_llf_dissipation_is_the_larger_spectral_radius():
+    """The local Lax-Friedrichs flux (section 1.1) adds -lambda/2 (q+ - q-) to
+    the mean of the two normal fluxes, lambda the largest wave speed of the
+    two states: the larger spectral radius of dF_n/dq, taken here from the
+    eigenvalues of a difference Jacobian, never from the flux code's own
+    |u.n| + c. The same lambda must come out of all five components."""
+    rng = np.random.default_rng(7)
+    g = 1.4
+    for _ in range(6):
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        a = state(rng.uniform(0.6, 1.6), rng.normal(size=3) * 0.4, rng.uniform(0.5, 2.0), g)
+        b = state(rng.uniform(0.6, 1.6), rng.normal(size=3) * 0.4, rng.uniform(0.5, 2.0), g)
+        radius = [np.abs(np.linalg.eigvals(_flux_jacobian(q, n, g))).max() for q in (a, b)]
+        assert abs(radius[0] - radius[1]) > 0.05 * max(radius)        # the choice matters
+        mean = 0.5 * (normal_flux(a, n, g) + normal_flux(b, n, g))
+        lam = -2.0 * (llf_flux(a, b, n, g) - mean) / (b - a)
+        np.testing.assert_allclose(lam, max(radius), rtol=1e-6)
+
+
 def test_characteristic_ghost_free_stream_and_outgoing_wave():
     gas = Gas(1.4, 1.225, 101325.0)
     g = gas.gamma
@@ -103,6 +128,24 @@ def test_characteristic_ghost_free_stream_and_outgoing_wave():
     assert ug @ n < 0
     np.testing.assert_allclose(ug - (ug @ n) * n, 0.0, atol=1e-10)
     assert pressure(qg, g) / qg[0] ** g == pytest.approx(gas.p0 / gas.rho0 ** g, rel=1e-12)
+
+
+def test_characteristic_ghost_passes_an_outgoing_shear_wave():
+    """Where the free stream leaves the domain (u0.n > 0) a change of the
+    tangential velocity is carried out with the flow and nothing comes back
+    from outside, so the ghost must equal the interior state (no
+    reflection). Where the free stream enters, the ghost's tangential
+    velocity is the free stream's, whatever the interior holds."""
+    gas = Gas(1.4, 1.225, 101325.0, u0=(40.0, 10.0, -5.0))
+    g = gas.gamma
+    n = np.array([0.6, 0.8, 0.0])
+    tang = np.array([-0.8, 0.6, 0.0])
+    assert gas.u0 @ n > 0
+    qi = state(gas.rho0, gas.u0 + 15.0 * tang + np.array([0.0, 0.0, 7.0]), gas.p0, g)
+    np.testing.assert_allclose(ghost_characteristic(qi, n, gas), qi, rtol=1e-12)
+    qg = ghost_characteristic(qi, -n, gas)
+    ug = qg[1:4] / qg[0]
+    np.testing.assert_allclose(ug - (ug @ n) * n, gas.u0 - (gas.u0 @ n) * n, atol=1e-10)
 
 
 def test_slip_wall_flux_has_no_mass_or_energy_flux():
@@ -362,6 +405,31 @@ def test_strong_form_equals_weak_form_quadrature():
         np.testing.assert_allclose(weak.T, strong[k], atol=1e-11 * np.abs(strong).max())
 
 
+def test_rhs_does_not_depend_on_the_vertex_order():
+    """Listing an element's vertices in another order changes nothing but
+    the numbering of its nodes (the node set is symmetric under vertex
+    permutations): the right-hand side at every physical node must be the
+    same, which holds only if both sides of every face meet at the same
+    points for all six vertex correspondences."""
+    gas = Gas(1.4, 1.4, 1.0)
+    p = 3
+    ref = ReferenceElement(p)
+    xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=8)
+    E2 = W.shuffle_vertices(xyz, EToV, seed=9)
+    rhs = []
+    for E in (EToV, E2):
+        geom = Geometry(ref, xyz, E)
+        q = W.random_smooth_state(geom.x, 1.4, 1.4, 1.0, 0.1, seed=3)
+        rhs.append((geom.x, Solver(geom, gas).rhs(q)))
+    (x1, r1), (x2, r2) = rhs
+    d = np.linalg.norm(x1[:, :, None, :] - x2[:, None, :, :], axis=-1)     # [K, Np, Np]
+    match = np.argmin(d, axis=2)
+    assert np.all(np.take_along_axis(d, match[:, :, None], axis=2) < 1e-12)
+    r2m = np.take_along_axis(r2, match[:, None, :], axis=2)
+    scale = np.abs(r1).max(axis=(0, 2))
+    assert np.all(np.abs(r1 - r2m).max(axis=(0, 2)) <= 1e-11 * scale)
+
+
 def test_probes_interpolate_linear_fields():
     ref = ReferenceElement(1)
     xyz, EToV = W.kuhn_cube(2, jitter=0.1)
@@ -406,7 +474,9 @@ def test_inflow_ghost_is_the_free_stream_outside_the_pulse():
     n = np.array([[-1.0, 0.0, 0.0], [0.0, 0.6, -0.8]])
     qm = np.tile(gas.freestream(), (2, 1))
     alpha = 565.0
-    for t in (0.0, 2 * np.pi / alpha, 1.0, -1e-3):
+    # one unipolar pulse (section 2.4): nothing before it, at its ends, in the
+    # half period after it (where a second pulse would peak) or much later
+    for t in (0.0, 2 * np.pi / alpha, 3 * np.pi / alpha, 1.0, -1e-3):
         np.testing.assert_array_equal(ghost_inflow(qm, n, gas, t, 0.05, alpha), qm)
     # the pulse's peak is p0 (1 + 2 A) at half its length
     assert inflow_pressure(np.pi / alpha, gas, 0.05, alpha) == pytest.approx(1.1)

@@ -66,13 +66,16 @@ def test_discrete_conservation_periodic_and_ledger():
     gas = Gas(1.4, 1.4, 1.0)
     ref = ReferenceElement(2)
     xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=5)
-    geom = Geometry(ref, xyz, EToV, period=(2.0, 2.0, 2.0))
-    S, N = MD.ModalSolver(geom, gas), Solver(geom, gas)
-    q = W.random_smooth_state(geom.x, 1.4, 1.4, 1.0, 0.1, seed=2)
-    t0 = N.totals(q)
-    q2, _, led = S.run(q, 0.5 * N.stable_dt(q), 20)
-    np.testing.assert_allclose(N.totals(q2), t0, rtol=0, atol=1e-13 * np.abs(t0).max())
-    assert np.all(led == 0.0)
+    # periodic box, with the lattice's vertex lists and shuffled ones (both
+    # sides of a face must integrate over one point set in every orientation)
+    for E in (EToV, W.shuffle_vertices(xyz, EToV, seed=6)):
+        geom = Geometry(ref, xyz, E, period=(2.0, 2.0, 2.0))
+        S, N = MD.ModalSolver(geom, gas), Solver(geom, gas)
+        q = W.random_smooth_state(geom.x, 1.4, 1.4, 1.0, 0.1, seed=2)
+        t0 = N.totals(q)
+        q2, _, led = S.run(q, 0.5 * N.stable_dt(q), 20)
+        np.testing.assert_allclose(N.totals(q2), t0, rtol=0, atol=1e-13 * np.abs(t0).max())
+        assert np.all(led == 0.0)
     geom = Geometry(ref, xyz, EToV)
     S, N = MD.ModalSolver(geom, gas), Solver(geom, gas)
     q = W.gaussian_pulse_state(geom.x, 1.4, 1.4, 1.0, 0.2, 0.6)
@@ -98,15 +101,19 @@ def test_equals_the_nodal_strong_form_where_both_are_exact(p):
     nodes, is continuous across faces (zero LLF jumps) and its Euler flux is
     linear in the state, so the flux interpolant is exact and both Gauss
     rules integrate exactly: the weak form of Eq. 10 then equals the nodal
-    strong form term by term, on a jittered periodic mesh."""
+    strong form term by term, on a jittered periodic mesh, with the lattice's
+    vertex lists and with shuffled ones (every correspondence between the
+    two sides' face vertices, so the two sides' Gauss points must be the
+    same physical points whatever the rule's orientation)."""
     gas = Gas(1.4, 1.0, 1.0)
     xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=p)
-    geom = Geometry(ReferenceElement(p), xyz, EToV, period=(2.0, 2.0, 2.0))
-    q = _density_wave(geom.x, gas, 0.0, np.array([0.5, 0.3, 0.2]))
-    rm = MD.ModalSolver(geom, gas).rhs_nodal(q)
-    rn = Solver(geom, gas).rhs(q)
-    scale = np.abs(rn).max(axis=(0, 2))
-    assert np.all(np.abs(rm - rn).max(axis=(0, 2)) <= 1e-11 * scale)
+    for E in (EToV, W.shuffle_vertices(xyz, EToV, seed=p)):
+        geom = Geometry(ReferenceElement(p), xyz, E, period=(2.0, 2.0, 2.0))
+        q = _density_wave(geom.x, gas, 0.0, np.array([0.5, 0.3, 0.2]))
+        rm = MD.ModalSolver(geom, gas).rhs_nodal(q)
+        rn = Solver(geom, gas).rhs(q)
+        scale = np.abs(rn).max(axis=(0, 2))
+        assert np.all(np.abs(rm - rn).max(axis=(0, 2)) <= 1e-11 * scale)
 
 
 def test_second_order_convergence_at_p1():
