@@ -443,6 +443,16 @@ def test_probes_interpolate_linear_fields():
     np.testing.assert_allclose(P.sample(q), np.outer(lin(pts), np.arange(1, 6)), rtol=1e-13)
     with pytest.raises(ValueError):
         Probes(geom, [[2.0, 0.0, 0.0]])
+    # a mesh vertex lies in every element that has it as a vertex (found here
+    # from the element lists, not from coordinates); the probe belongs to the
+    # lowest-numbered of them
+    vid = int(EToV[5, 2])
+    owners = np.nonzero((EToV == vid).any(axis=1))[0]
+    assert len(owners) > 1
+    P = Probes(geom, [xyz[vid]])
+    assert P.elem[0] == owners.min()
+    per_element = np.broadcast_to(np.arange(geom.K, dtype=float)[:, None, None], q.shape)
+    np.testing.assert_allclose(P.sample(per_element)[0], owners.min(), rtol=1e-13)
 
 
 def test_rhs_parts_recombine_to_the_rhs():

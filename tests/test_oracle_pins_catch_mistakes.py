@@ -369,6 +369,66 @@ def _features_wout_sign(mp):
     _replace(mp, orig, bad)
 
 
+def _probe_tie_last(mp):
+    orig = ED.Probes.__init__
+
+    def init(self, geom, pts, tol=1e-12):
+        orig(self, geom, pts, tol)
+        pts = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+        v = geom.verts
+        T = np.stack([v[:, 1] - v[:, 0], v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]], axis=2)
+        for i, x in enumerate(pts):
+            lam = np.linalg.solve(T, (x - v[:, 0])[:, :, None])[:, :, 0]
+            hit = np.nonzero((lam.min(axis=1) >= -tol) & (1.0 - lam.sum(axis=1) >= -tol))[0]
+            e = hit[-1]                               # the last element, not the first
+            r, s, t = -1 + 2 * lam[e]
+            self.elem[i] = e
+            self.rows[i] = geom.ref.interp_row(r, s, t)[0]
+    mp.setattr(ED.Probes, "__init__", init)
+
+
+def _invariants_swapped(mp):
+    orig = ED.acoustic_invariants
+
+    def bad(qp, n, gas):
+        wout, win = orig(qp, n, gas)
+        return win, wout
+    _replace(mp, orig, bad)
+
+
+def _memory(mp, which):
+    def bad(psi, wout, r, gas):
+        if which == "sign":
+            return -(gas.c0 / (2.0 * r)) * (psi - wout)
+        return -(gas.c0 / r) * (psi + wout)
+    _replace(mp, ED.memory_rate, bad)
+
+
+def _learned_ghost(mp, which):
+    orig = ED.ghost_learned
+
+    def bad(qm, n, x, psi, gas, w, radius):
+        q0 = gas.freestream()
+        qc = ED.ghost_characteristic(qm, n, gas)
+        feats, s = ML.features(qm - q0, n, x, psi, gas, radius)
+        y, _ = ML.forward(w, feats.reshape(-1, ML.N_IN))
+        y = y.reshape(qm.shape)
+        _, wi_c = ED.acoustic_invariants(qc - q0, n, gas)
+        pref = gas.rho0 * gas.c0 ** 2
+        g = wi_c + pref * s * y[..., 0]
+        if which != "unbounded":
+            lim = np.maximum(np.abs(wi_c), pref * s)
+            g = np.clip(g, -lim, lim)
+        D = g - wi_c
+        c0 = gas.c0
+        q = qc.copy()
+        q[..., 0] += D / (2 * c0 * c0)
+        q[..., 1:4] += (1.0 if which == "momentum_sign" else -1.0) * (D / (2 * c0))[..., None] * n
+        q[..., 4] += D / (2 * (gas.gamma - 1.0))
+        return q
+    _replace(mp, orig, bad)
+
+
 P = functools.partial
 MISTAKES = {
     "Eq. 1 fluxes as printed": (_flux_as_printed, [E.test_flux_jacobian_eigenvalues]),
@@ -432,6 +492,19 @@ MISTAKES = {
                                         [E.test_lsrk_coefficients_and_order_conditions]),
     "Runge-Kutta update order": (_lsrk_update_order, [E.test_discrete_conservation_periodic_and_ledger]),
     "probe coordinates swapped": (_probe_coordinates_swapped, [E.test_probes_interpolate_linear_fields]),
+    "probe on a shared point takes the last element": (_probe_tie_last,
+                                                       [E.test_probes_interpolate_linear_fields]),
+    "acoustic invariants swapped": (_invariants_swapped, [L.test_learned_target_is_the_incoming_invariant_gap]),
+    "memory driven by -w_out": (P(_memory, which="sign"),
+                                [L.test_memory_reproduces_the_spherical_incoming_invariant]),
+    "memory rate c0/r": (P(_memory, which="rate"),
+                         [L.test_memory_reproduces_the_spherical_incoming_invariant]),
+    "learned ghost momentum increment sign": (
+        P(_learned_ghost, which="momentum_sign"),
+        [L.test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound]),
+    "learned ghost unbounded": (
+        P(_learned_ghost, which="unbounded"),
+        [L.test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound]),
     "modal volume rule one degree short": (P(_modal_rule_low, which="volume"),
                                            [P(M.test_rules_integrate_monomials_exactly, 4)]),
     "modal face rule one degree short": (P(_modal_rule_low, which="face"),
