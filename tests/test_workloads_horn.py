@@ -138,3 +138,29 @@ def test_rest_state_is_preserved_with_every_boundary_of_the_workload(kw):
     r = orc.rhs(q, 0.25 * 2 * np.pi / orc.inflow[1])
     moved = np.abs(r).max(axis=(1, 2)) > 1e-9 * scale
     assert moved.any() and np.all(np.any(tag[moved] == W.HORN_MOUTHPIECE, axis=1))
+
+
+def test_sensors_are_the_papers_positions():
+    """The workload's sensors are the four of the paper's horn study (section
+    3, Table 2; tests/golden/sensors_table2.txt) with the flare-room junction
+    moved from x = 1.48 m to the workload's bell plane, and they keep the
+    distances to the outer boundary that Table 2 lists (sensor 1: 1 cm below
+    the top wall, sensor 2: 2 cm and sensor 3: 1 cm before the far wall),
+    here measured on the mesh itself; each lies inside the mesh."""
+    from pathlib import Path
+    from oracle.euler_dg import Probes
+    rows, junction = [], None
+    for line in (Path(__file__).parent / "golden" / "sensors_table2.txt").read_text().splitlines():
+        if line.startswith("# junction_x"):
+            junction = float(line.split()[2])
+        elif line.strip() and not line.startswith("#"):
+            rows.append([float(v) for v in line.split()[1:]])
+    paper = np.array(rows)
+    xyz, EToV, _, info = W.horn_in_room(m1=1, growth=1.8)
+    s = info["sensors"]
+    np.testing.assert_allclose(s + [junction - info["bell_x"], 0.0, 0.0], paper, rtol=0, atol=1e-12)
+    top, far = xyz[:, 1].max(), xyz[:, 0].max()
+    assert top - s[0, 1] == pytest.approx(0.01, abs=1e-12)
+    assert far - s[1, 0] == pytest.approx(0.02, abs=1e-12)
+    assert far - s[2, 0] == pytest.approx(0.01, abs=1e-12)
+    Probes(Geometry(ReferenceElement(1), xyz, EToV), s)
