@@ -130,6 +130,28 @@ def _ptr(a):
     return a.ctypes.data
 
 
+def _require(x, shape, dtype, name, device=False):
+    """Refuse a buffer the library would read or write past, or misread:
+    another shape (None matches any extent), element type or layout, or a
+    host buffer where the library expects device memory (``device=True``)
+    and the other way round. The C ABI sees only a pointer, so this is the
+    last place a size can be checked."""
+    if x is None:
+        return
+    got = tuple(x.shape)
+    if len(got) != len(shape) or any(e is not None and g != e for g, e in zip(got, shape)):
+        raise ValueError(f"{name}: expected shape {shape}, got {got}")
+    if hasattr(x, "data_ptr"):                                  # torch tensor
+        import torch
+        ok = x.dtype == getattr(torch, np.dtype(dtype).name) and x.is_contiguous() \
+            and bool(x.is_cuda) == device
+    else:
+        ok = x.dtype == dtype and x.flags.c_contiguous and not device
+    if not ok:
+        where = "device (CUDA)" if device else "host"
+        raise ValueError(f"{name}: expected a C-contiguous {np.dtype(dtype).name} {where} buffer")
+
+
 def reference_mass(order):
     """Mass matrix of the library's reference element (host only)."""
     lib = load()
@@ -227,6 +249,10 @@ class Solver:
         EToV = np.ascontiguousarray(EToV, dtype=np.int32)
         ft = None if face_tag is None else np.ascontiguousarray(face_tag, dtype=np.int8)
         vc = None if vert_class is None else np.ascontiguousarray(vert_class, dtype=np.int64)
+        _require(xyz, (None, 3), np.float64, "xyz")
+        _require(EToV, (None, 4), np.int32, "EToV")
+        _require(ft, (EToV.shape[0], 4), np.int8, "face_tag")
+        _require(vc, (xyz.shape[0],), np.int64, "vert_class")
         self._check(self.lib.dg_upload_mesh(self.h, xyz.shape[0], _ptr(xyz), EToV.shape[0],
                                             _ptr(EToV), _ptr(ft), _ptr(vc)))
         self.K = EToV.shape[0]
@@ -262,30 +288,38 @@ class Solver:
 
     def stable_dt(self, q, cfl=0.5):
         q = np.ascontiguousarray(q, dtype=np.float64)
+        self._check_state_buffer(q, "stable_dt")
         dt = C.c_double()
         self._check(self.lib.dg_stable_dt(self.h, _ptr(q), cfl, C.byref(dt)))
         return dt.value
 
+    def _check_state_buffer(self, x, name):
+        """K * 5 * Np float64 values, on the host or (torch) on the GPU."""
+        _require(x, (self.K, 5, self.Np), np.float64, name,
+                 device=bool(getattr(x, "is_cuda", False)))
+
     def set_state(self, q, t=0.0):
-        """q: numpy [K,5,Np] (host) or a CUDA torch tensor of that shape (device)."""
-        if hasattr(q, "is_cuda") and q.is_cuda:
-            assert q.is_contiguous() and q.dtype.itemsize == 8
-            self._check(self.lib.dg_set_state_device(self.h, q.data_ptr(), t))
+        """q: numpy [K,5,Np] (host) or a torch tensor of that shape (CPU or CUDA), float64."""
+        if hasattr(q, "data_ptr"):
+            self._check_state_buffer(q, "set_state")
+            fn = self.lib.dg_set_state_device if q.is_cuda else self.lib.dg_set_state
+            self._check(fn(self.h, q.data_ptr(), t))
         else:
-            if hasattr(q, "numpy"):
-                assert q.is_contiguous()
-                self._check(self.lib.dg_set_state(self.h, q.data_ptr(), t))
-            else:
-                qa = np.ascontiguousarray(q, dtype=np.float64)
-                self._check(self.lib.dg_set_state(self.h, _ptr(qa), t))
+            qa = np.ascontiguousarray(q, dtype=np.float64)
+            self._check_state_buffer(qa, "set_state")
+            self._check(self.lib.dg_set_state(self.h, _ptr(qa), t))
 
     def get_state(self, out=None):
-        """Copy the state into ``out`` (numpy / CPU or CUDA tensor) or a new array; returns (q, t)."""
+        """Copy the state into ``out`` (numpy, or a CPU or CUDA torch tensor,
+        float64 [K,5,Np]) or a new array; returns (q, t)."""
         t = C.c_double()
         if out is None:
             out = np.zeros((self.K, 5, self.Np))
+        self._check_state_buffer(out, "get_state")
         if hasattr(out, "is_cuda") and out.is_cuda:
             self._check(self.lib.dg_get_state_device(self.h, out.data_ptr(), C.byref(t)))
+        elif hasattr(out, "data_ptr"):
+            self._check(self.lib.dg_get_state(self.h, out.data_ptr(), C.byref(t)))
         else:
             self._check(self.lib.dg_get_state(self.h, _ptr(out), C.byref(t)))
         return out, t.value
@@ -300,6 +334,7 @@ class Solver:
 
     def set_probes(self, xyz, capacity=1024):
         xyz = np.ascontiguousarray(np.atleast_2d(xyz), dtype=np.float64)
+        _require(xyz, (None, 3), np.float64, "probe positions")
         self._check(self.lib.dg_set_probes(self.h, xyz.shape[0], _ptr(xyz), capacity))
         self.nprobe = xyz.shape[0]
 
@@ -309,6 +344,9 @@ class Solver:
             cap = min(max_steps, 1 << 16)
             out = np.zeros((cap, max(n, 1), 5))
             max_steps = cap
+        else:
+            _require(out, (None, n, 5), np.float64, "read_probes out")
+            max_steps = min(max_steps, out.shape[0])          # never more rows than out holds
         got = C.c_int()
         self._check(self.lib.dg_read_probes(self.h, max_steps, _ptr(out), C.byref(got)))
         return out[: got.value, :n]
@@ -345,23 +383,39 @@ class Solver:
         e2f = np.ascontiguousarray(EToF, dtype=np.int8)
         ori = np.ascontiguousarray(orient, dtype=np.int8)
         b = None if bc is None else np.ascontiguousarray(bc, dtype=np.int8)
+        for x, shape, name in zip(a, ((K, 3, 3), (K,), (K, 4, 3), (K, 4)), ("drdx", "J", "nrm", "Fscale")):
+            _require(x, shape, np.float64, name)
+        _require(e2e, (K, 4), np.int32, "EToE")
+        for x, name in ((e2f, "EToF"), (ori, "orient"), (b, "bc")):
+            _require(x, (K, 4), np.int8, name)
         self._check(self.lib.dg_upload_geometry(self.h, K, *(_ptr(x) for x in a), _ptr(e2e), _ptr(e2f),
                                                 _ptr(ori), None if b is None else _ptr(b)))
         self.K = K
 
     def set_trace_faces(self, elem, face):
-        elem = np.ascontiguousarray(elem, dtype=np.int32)
-        face = np.ascontiguousarray(face, dtype=np.int8)
+        elem = np.ascontiguousarray(elem, dtype=np.int32).ravel()
+        face = np.ascontiguousarray(face, dtype=np.int8).ravel()
+        _require(face, elem.shape, np.int8, "trace face numbers")
         self._check(self.lib.dg_set_trace_faces(self.h, elem.size, _ptr(elem), _ptr(face)))
         self.ntrace = elem.size
 
     def sample_traces(self, X, Y, amp=None):
         """Fill device tensors X [ntrace*Nfp, 12], Y [ntrace*Nfp, 5] and, if
         given, amp [ntrace*Nfp] (float32)."""
+        n = getattr(self, "ntrace", 0) * self.Nfp
+        _require(X, (n, 12), np.float32, "X", device=True)
+        _require(Y, (n, 5), np.float32, "Y", device=True)
+        _require(amp, (n,), np.float32, "amp", device=True)
         self._check(self.lib.dg_sample_traces(self.h, X.data_ptr(), Y.data_ptr(),
                                               None if amp is None else amp.data_ptr()))
 
+    @staticmethod
+    def _samples(X, Y):
+        _require(X, (None, 12), np.float32, "X", device=True)
+        _require(Y, (X.shape[0], 5), np.float32, "Y", device=True)
+
     def mlp_loss_grad(self, X, Y):
+        self._samples(X, Y)
         loss = C.c_double()
         grad = np.zeros(DG_MLP_NPARAMS, dtype=np.float32)
         self._check(self.lib.dg_mlp_loss_grad(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0],
@@ -369,12 +423,15 @@ class Solver:
         return loss.value, grad
 
     def mlp_train(self, X, Y, iters, lr):
+        self._samples(X, Y)
         hist = np.zeros(max(iters, 1))
         self._check(self.lib.dg_mlp_train(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], int(iters),
                                           float(lr), _ptr(hist)))
         return hist[:iters]
 
     def mlp_forward(self, X, out):
+        _require(X, (None, 12), np.float32, "X", device=True)
+        _require(out, (X.shape[0], 5), np.float32, "out", device=True)
         self._check(self.lib.dg_mlp_forward(self.h, X.data_ptr(), X.shape[0], out.data_ptr()))
 
     def set_kernel_timing(self, enable=True):

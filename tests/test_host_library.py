@@ -118,6 +118,43 @@ def test_face_pairing_matches_the_oracle_for_every_orientation(p):
             assert set(codes[inner].tolist()) == set(range(6)), name
 
 
+def test_state_buffers_of_another_shape_or_type_are_refused():
+    """The library reads and writes K * 5 * Np float64 values through the
+    pointers it is given; the binding refuses any other buffer before the
+    call (nothing reaches the library here, so no GPU is needed)."""
+    import torch
+    xyz, EToV = W.kuhn_cube(1)
+    S = B.Solver(1)
+    S.upload_mesh(xyz, EToV)
+    K, Np = S.K, S.Np
+    for bad in (np.zeros((K, Np, 5)), np.zeros((K - 1, 5, Np)), torch.zeros((K, 5, Np), dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            S.set_state(bad)
+    for bad in (np.zeros((K, 5, Np), dtype=np.float32), np.zeros((Np, 5, K)).T, np.zeros((K + 1, 5, Np)),
+                torch.zeros((K, 5, Np), dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            S.get_state(bad)
+    with pytest.raises(ValueError):
+        S.stable_dt(np.ones((K, 5, Np + 1)))
+    # every other array argument: shape, element type, host or device
+    bad_calls = [
+        lambda: B.Solver(1).upload_mesh(xyz[:, :2], EToV),
+        lambda: B.Solver(1).upload_mesh(xyz, EToV[:, :3]),
+        lambda: B.Solver(1).upload_mesh(xyz, EToV, face_tag=np.zeros((K, 3))),
+        lambda: B.Solver(1).upload_mesh(xyz, EToV, vert_class=np.zeros(len(xyz) - 1)),
+        lambda: S.set_probes(np.zeros((2, 2))),
+        lambda: S.read_probes(4, out=np.zeros((4, 3, 5))),
+        lambda: S.upload_geometry(np.zeros((K, 9)), np.ones(K), np.zeros((K, 4, 3)), np.ones((K, 4)),
+                                  np.zeros((K, 4)), np.zeros((K, 4)), np.zeros((K, 4))),
+        lambda: S.set_trace_faces(np.arange(3), np.zeros(2)),
+        lambda: S.mlp_loss_grad(torch.zeros((8, 12)), torch.zeros((8, 5))),          # host tensors
+        lambda: S.mlp_forward(torch.zeros((8, 12)), torch.zeros((8, 5), dtype=torch.float64)),
+    ]
+    for call in bad_calls:
+        with pytest.raises(ValueError):
+            call()
+
+
 def test_stable_dt_matches_oracle():
     from oracle.euler_dg import Gas, Solver
     xyz, EToV = W.kuhn_cube(3, jitter=0.1)
