@@ -118,6 +118,20 @@ def test_face_pairing_matches_the_oracle_for_every_orientation(p):
             assert set(codes[inner].tolist()) == set(range(6)), name
 
 
+def test_one_and_two_element_meshes():
+    """The degenerate meshes: one tetrahedron (four boundary faces) and two
+    sharing a face, uploaded and paired as the oracle pairs them."""
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 1.0, 1.0]])
+    for EToV in (np.array([[0, 1, 2, 3]]), np.array([[0, 1, 2, 3], [2, 3, 1, 4]])):
+        for p in (1, 4):
+            S = B.Solver(p)
+            S.upload_mesh(xyz, EToV)
+            G = Geometry(ReferenceElement(p), xyz, EToV)
+            vol, _ = S.face_pairs()
+            np.testing.assert_array_equal(S.geometry()["EToE"] < 0, G.boundary)
+            np.testing.assert_array_equal(np.where(G.boundary[:, :, None], -1, G.vmapP), vol)
+
+
 def test_state_buffers_of_another_shape_or_type_are_refused():
     """The library reads and writes K * 5 * Np float64 values through the
     pointers it is given; the binding refuses any other buffer before the
