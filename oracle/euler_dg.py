@@ -48,14 +48,19 @@ What is computed, with the passage it follows:
   time by the same stages, so that total(t) - total(0) + ledger(t) = 0.
 
 Parity status: pinned (tests/test_oracle_euler.py: flux consistency and
-antisymmetry, free-stream preservation, discrete conservation, p+1
+antisymmetry, the LLF coefficient as the larger spectral radius of the two
+flux Jacobians, free-stream preservation, discrete conservation, p+1
 convergence against exact solutions, axis-permutation and inversion
-symmetry, LSRK order conditions, the characteristic ghost on 1D states, the
-inflow ghost's free stream outside the pulse and its first-order plane-wave
-flux, the contraction inputs recombining to the right-hand side;
-tests/test_oracle_mlp.py: the learned ghost's reduction to the
+symmetry, independence of the element vertex order, LSRK order conditions,
+the characteristic ghost on 1D states and on an outgoing shear wave, a
+plane simple wave leaving through it, the inflow ghost's free stream
+outside its single pulse and its first-order plane-wave flux, the
+contraction inputs recombining to the right-hand side, the probes' tie
+rule; tests/test_oracle_mlp.py: the learned ghost's reduction to the
 characteristic one and its bound, the memory against the closed form of an
-outgoing spherical wave and its decay on the free stream).
+outgoing spherical wave and its decay on the free stream). Planted mistakes
+in every part of it make one of these fail
+(tests/test_oracle_pins_catch_mistakes.py).
 """
 from __future__ import annotations
 

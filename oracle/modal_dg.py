@@ -40,10 +40,12 @@ Lax-Friedrichs flux. Written out here directly and slowly:
 
 Parity status: pinned (tests/test_oracle_modal.py): exactness of both rules
 on monomials, orthonormality of the basis, free-stream preservation,
-discrete conservation (periodic and with the ledger), reduction to the
+discrete conservation (periodic and with the ledger, also with shuffled
+vertex lists so that every face orientation occurs), reduction to the
 nodal strong form where both are exact (continuous fields with a flux that
 is polynomial in the state), second-order convergence at p = 1, and Heun's
-amplification factor on a linear problem.
+amplification factor on a linear problem; planted mistakes fail them
+(tests/test_oracle_pins_catch_mistakes.py).
 """
 from __future__ import annotations
 
