@@ -34,3 +34,17 @@ def test_morton_order_of_a_permuted_mesh_restores_locality():
     c = W.element_centroids(xyz, shuffled)
     m = W.morton_order(xyz, shuffled)
     assert _mean_step(c, m) < 0.25 * _mean_step(c, np.arange(len(EToV)))
+
+
+def test_shuffled_vertex_lists_keep_the_elements():
+    """Each element keeps its four vertices, positively oriented, in a
+    seeded order that differs from the lattice's for most elements."""
+    xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=3)
+    E = W.shuffle_vertices(xyz, EToV, seed=7)
+    assert E.shape == EToV.shape and E.dtype == np.int32
+    assert np.array_equal(np.sort(E, axis=1), np.sort(EToV, axis=1))
+    v = xyz[E]
+    vol = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0])
+    assert np.all(vol > 0)
+    assert np.mean(np.any(E != EToV, axis=1)) > 0.8
+    assert np.array_equal(W.shuffle_vertices(xyz, EToV, seed=7), E)      # seeded
