@@ -130,6 +130,46 @@ def test_characteristic_ghost_free_stream_and_outgoing_wave():
     assert pressure(qg, g) / qg[0] ** g == pytest.approx(gas.p0 / gas.rho0 ** g, rel=1e-12)
 
 
+def test_characteristic_ghost_carries_the_right_invariants():
+    """On random subsonic states and normals, read back from the ghost state
+    itself: its outgoing Riemann invariant u.n + 2c/(gamma-1) is the
+    interior's, its incoming one u.n - 2c/(gamma-1) the free stream's, and
+    its entropy p/rho^gamma and tangential velocity come from inside where
+    the ghost's normal velocity leaves the domain, from the free stream
+    where it enters."""
+    rng = np.random.default_rng(11)
+    gas = Gas(1.4, 1.225, 101325.0, u0=(20.0, -10.0, 5.0))
+    g = gas.gamma
+    N = 200
+    n = rng.normal(size=(N, 3))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    rho = gas.rho0 * rng.uniform(0.8, 1.25, N)
+    p = gas.p0 * rng.uniform(0.8, 1.25, N)
+    u = rng.normal(size=(N, 3)) * 0.2 * gas.c0
+    qi = np.stack([state(rho[i], u[i], p[i], g) for i in range(N)])
+    qb = ghost_characteristic(qi, n, gas)
+
+    def parts(q):
+        r = q[:, 0]
+        v = q[:, 1:4] / r[:, None]
+        pr = pressure(q, g)
+        c = np.sqrt(g * pr / r)
+        vn = np.sum(v * n, axis=1)
+        return vn, c, pr / r ** g, v - vn[:, None] * n
+
+    un_i, c_i, s_i, t_i = parts(qi)
+    un_b, c_b, s_b, t_b = parts(qb)
+    un_f = gas.u0 @ n.T
+    np.testing.assert_allclose(un_b + 2 * c_b / (g - 1), un_i + 2 * c_i / (g - 1), rtol=1e-12)
+    np.testing.assert_allclose(un_b - 2 * c_b / (g - 1), un_f - 2 * gas.c0 / (g - 1), rtol=1e-12)
+    out = un_b >= 0
+    assert 20 < out.sum() < N - 20                                # both branches occur
+    s_f = gas.p0 / gas.rho0 ** g
+    np.testing.assert_allclose(s_b, np.where(out, s_i, s_f), rtol=1e-12)
+    t_f = gas.u0[None, :] - un_f[:, None] * n
+    np.testing.assert_allclose(t_b, np.where(out[:, None], t_i, t_f), atol=1e-9 * gas.c0)
+
+
 def test_characteristic_ghost_passes_an_outgoing_shear_wave():
     """Where the free stream leaves the domain (u0.n > 0) a change of the
     tangential velocity is carried out with the flow and nothing comes back
