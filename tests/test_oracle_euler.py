@@ -247,6 +247,21 @@ def test_slip_wall_flux_has_no_mass_or_energy_flux():
     # the momentum flux is normal to the wall
     m = f[1:4]
     np.testing.assert_allclose(m - (m @ n) * n, 0.0, atol=1e-14)
+    # random states and walls: the mirror image keeps density, pressure and
+    # the tangential velocity, reverses the normal velocity, and no mass or
+    # energy crosses the wall
+    rng = np.random.default_rng(5)
+    nn = rng.normal(size=(50, 3))
+    nn /= np.linalg.norm(nn, axis=1)[:, None]
+    qs = np.stack([state(rng.uniform(0.5, 2), rng.normal(size=3) * 0.3, rng.uniform(0.5, 2)) for _ in range(50)])
+    qg = ghost_slip_wall(qs, nn, gas)
+    ui, ug = qs[:, 1:4] / qs[:, :1], qg[:, 1:4] / qg[:, :1]
+    np.testing.assert_array_equal(qg[:, 0], qs[:, 0])
+    np.testing.assert_allclose(pressure(qg, 1.4), pressure(qs, 1.4), rtol=1e-13)
+    np.testing.assert_allclose(np.sum(ug * nn, axis=1), -np.sum(ui * nn, axis=1), atol=1e-14)
+    np.testing.assert_allclose(np.cross(ug, nn), np.cross(ui, nn), atol=1e-14)
+    fw = llf_flux(qs, qg, nn, 1.4)
+    assert np.abs(fw[:, [0, 4]]).max() < 1e-14
 
 
 @pytest.mark.parametrize("mode", [CHARACTERISTIC, FREESTREAM])
