@@ -603,6 +603,31 @@ def test_inflow_ghost_is_the_free_stream_outside_the_pulse():
     assert np.abs(S.rhs(q, t=2 * np.pi / alpha)).max() < 1e-12
 
 
+def test_inflow_pulse_is_the_papers():
+    """The mouthpiece pulse against the values section 2.4 prints
+    (tests/golden/inflow_pulse_section24.txt): the oracle's default (A,
+    alpha) are the printed ones; its peak, p0 (1 + 2A), is the paper's
+    "about 10,000 Pa" above atmospheric pressure (within 2 %); it starts and
+    ends at p0 and is one unipolar bump; and the adiabatic relation with
+    C = gamma gives the scaled free stream's density (Eq. 3) at p = 1."""
+    from oracle.euler_dg import inflow_pressure
+    vals = {}
+    for line in (GOLDEN / "inflow_pulse_section24.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    A, alpha = vals["amplitude"], vals["alpha"]
+    geom = Geometry(ReferenceElement(1), *W.kuhn_cube(1))
+    assert Solver(geom, Gas(1.4, 1.4, 1.0)).inflow == (A, alpha)
+    si = Gas(1.4, 1.225, 101325.0)
+    t = np.linspace(0.0, 2 * np.pi / alpha, 2001)
+    excess = inflow_pressure(t, si, A, alpha) - si.p0
+    assert excess.max() == pytest.approx(vals["peak_excess_pa_approx"], rel=0.02)
+    assert excess[0] == 0.0 and abs(excess[-1]) < 1e-9 * si.p0
+    assert np.all(excess >= 0.0) and np.argmax(excess) == 1000            # one bump, peak mid-pulse
+    assert vals["C"] * 1.0 ** (1 / 1.4) == Gas(1.4, 1.4, 1.0).rho0
+
+
 def test_inflow_ghost_injects_the_planar_wave():
     """With the interior at rest, the local Lax-Friedrichs flux through an
     inflow face equals the flux of the plane acoustic wave entering through it
