@@ -534,6 +534,22 @@ def test_rhs_does_not_depend_on_the_vertex_order():
     assert np.all(np.abs(r1 - r2m).max(axis=(0, 2)) <= 1e-11 * scale)
 
 
+def test_stable_dt_closed_form_on_the_lattice():
+    """The time step's definition (CFL min r_in / ((p+1)^2 max(|u| + c)))
+    in closed form on the unjittered Kuhn lattice at rest: every Kuhn
+    tetrahedron of a cube of edge h has volume h^3/6 and faces of area
+    h^2/2 (two) and h^2 sqrt(2)/2 (two), so r_in = 3V / sum A =
+    h / (2 (1 + sqrt 2))."""
+    gas = Gas(1.4, 1.225, 101325.0)
+    for n, p in ((2, 1), (3, 3)):
+        xyz, EToV = W.kuhn_cube(n)
+        geom = Geometry(ReferenceElement(p), xyz, EToV)
+        q = W.uniform_state(geom.K, geom.ref.Np, gas.rho0, (0, 0, 0), gas.p0, gas.gamma)
+        h = 2.0 / n
+        expected = 0.5 * h / (2.0 * (1.0 + np.sqrt(2.0))) / ((p + 1) ** 2 * gas.c0)
+        assert Solver(geom, gas).stable_dt(q, 0.5) == pytest.approx(expected, rel=1e-12)
+
+
 def test_probes_interpolate_linear_fields():
     ref = ReferenceElement(1)
     xyz, EToV = W.kuhn_cube(2, jitter=0.1)

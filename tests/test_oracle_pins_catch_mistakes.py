@@ -429,6 +429,17 @@ def _learned_ghost(mp, which):
     _replace(mp, orig, bad)
 
 
+def _stable_dt_linear_in_order(mp):
+    def bad(self, q, cfl=0.5):
+        qn = np.transpose(q, (0, 2, 1))
+        rho = qn[..., 0]
+        u = qn[..., 1:4] / rho[..., None]
+        c = np.sqrt(self.gas.gamma * ED.pressure(qn, self.gas.gamma) / rho)
+        smax = np.max(np.linalg.norm(u, axis=-1) + c)
+        return cfl * np.min(GE.inscribed_radius(self.g)) / ((self.ref.p + 1) * smax)
+    mp.setattr(ED.Solver, "stable_dt", bad)
+
+
 P = functools.partial
 MISTAKES = {
     "Eq. 1 fluxes as printed": (_flux_as_printed, [E.test_flux_jacobian_eigenvalues]),
@@ -492,6 +503,8 @@ MISTAKES = {
                                         [E.test_lsrk_coefficients_and_order_conditions]),
     "Runge-Kutta update order": (_lsrk_update_order, [E.test_discrete_conservation_periodic_and_ledger]),
     "probe coordinates swapped": (_probe_coordinates_swapped, [E.test_probes_interpolate_linear_fields]),
+    "time step with (p+1) for (p+1)^2": (_stable_dt_linear_in_order,
+                                         [E.test_stable_dt_closed_form_on_the_lattice]),
     "probe on a shared point takes the last element": (_probe_tie_last,
                                                        [E.test_probes_interpolate_linear_fields]),
     "acoustic invariants swapped": (_invariants_swapped, [L.test_learned_target_is_the_incoming_invariant_gap]),
