@@ -262,23 +262,73 @@ def aggregate_value(world, dof_per_rank, steps, seconds):
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    workload: every number is what was measured on that sample (nothing is
+    scaled to the full mesh)."""
     if rank != 0:
         return
     xyz, EToV = build_workload()
-    value, sample, _ = cpu_sample_run(args.steps, args.warmup, xyz, EToV)
+    value, sample, K = cpu_sample_run(args.steps, args.warmup, xyz, EToV)
     Np = (WORKLOAD["order"] + 1) * (WORKLOAD["order"] + 2) * (WORKLOAD["order"] + 3) // 6
-    dof_full = 5 * Np * len(EToV)
+    dof_sample = 5 * Np * K
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dof_full / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dof_sample / value,
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "sample": sample,
-                   "ms_per_step": "the sample's rate applied to the whole workload (extrapolated)"},
+        "config": {"workload": "sample of: " + WORKLOAD_NAME, "sample": sample, "elements": K,
+                   "dof": dof_sample,
+                   "ms_per_step": "measured on the sample (the oracle's time per step of its elements)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def timed_repeats(args, S, q0_dev, dt, dev, stream, dist, sample_clocks, repeats):
+    """``repeats`` timed regions of ``args.steps`` steps, each from the same
+    initial state, with CUDA events on the solver's stream (synchronised and,
+    under torchrun, barriered on both sides; max over ranks). Per-launch
+    stage timing is on for all of them and the clock sampler runs across
+    all of them. Returns (ms per region list, summed stage-kernel ms, stage
+    launches, sampler)."""
+    import torch
+    S.set_kernel_timing(True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")) if sample_clocks else -1)
+    reps = []
+    with clk:
+        for _ in range(repeats):
+            S.set_state(q0_dev)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            start.record(stream)
+            S.step(args.steps, dt)
+            stop.record(stream)
+            torch.cuda.synchronize(dev)
+            if dist:
+                dist.barrier()
+            reps.append(reduce_max(start.elapsed_time(stop), dist, dev))
+    kms, klaunch = S.read_kernel_timing()
+    S.set_kernel_timing(False)
+    S.read_probes()
+    return reps, kms, klaunch, clk
+
+
+def repeat_stats(reps, steps, sm_mhz=None):
+    """Median, spread and per-step times of the repeated timed regions."""
+    med = statistics.median(reps)
+    out = {"n": len(reps), "ms_per_step": [r / steps for r in reps],
+           "median_ms_per_step": med / steps, "min_ms_per_step": min(reps) / steps,
+           "max_ms_per_step": max(reps) / steps,
+           "spread_rel": (max(reps) - min(reps)) / med}
+    if sm_mhz:
+        # clock-normalised time: a run at a lower clock shows a larger
+        # product only if it was slowed by more than the clock
+        out["median_ms_per_step_x_sm_mhz"] = med / steps * sm_mhz
+    return out
 
 
 def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_clocks, mlp=None):
@@ -308,45 +358,32 @@ def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_cl
     S.step(args.warmup, dt)
     torch.cuda.synchronize(dev)
     S.read_probes()
-    S.set_state(q0_dev)
-    torch.cuda.synchronize(dev)
-    S.set_kernel_timing(True)
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")) if sample_clocks else -1)
-    with clk:
-        start.record(stream)
-        S.step(args.steps, dt)
-        stop.record(stream)
-        torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    ms = reduce_max(start.elapsed_time(stop), dist, dev)
-    kms, klaunch = S.read_kernel_timing()
-    S.set_kernel_timing(False)
+    reps, kms, klaunch, clk = timed_repeats(args, S, q0_dev, dt, dev, stream, dist,
+                                            sample_clocks, args.repeats)
+    ms = statistics.median(reps)
     S.sync()
     q_end = torch.empty_like(q0_dev)
     S.get_state(q_end)
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers (median of three runs)
     q0_host = torch.from_numpy(q0).pin_memory()
     q_out = torch.empty_like(q0_host).pin_memory()
     nprobe = probes.shape[0]
     psamples = np.zeros((args.steps, nprobe, 5))
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    S.set_state(q0_host)
-    S.step(args.steps, dt)
-    S.read_probes(args.steps, out=psamples)
-    S.get_state(q_out)
-    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e_runs = []
+    for _ in range(3):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        S.set_state(q0_host)
+        S.step(args.steps, dt)
+        S.read_probes(args.steps, out=psamples)
+        S.get_state(q_out)
+        e2e_runs.append(reduce_max(time.perf_counter() - t0, dist, dev))
+    e2e_s = statistics.median(e2e_runs)
     S.close()
-    return dict(precision=precision, ms=ms, kms=kms, klaunch=klaunch, dof=dof, K=len(EToV),
-                dt=dt, q0=q0, q_end=q_end.cpu().numpy(), e2e_s=e2e_s, nprobe=nprobe,
+    return dict(precision=precision, ms=ms, reps=reps, kms=kms, klaunch=klaunch, dof=dof,
+                K=len(EToV), dt=dt, q0=q0, q_end=q_end.cpu().numpy(), e2e_s=e2e_s, nprobe=nprobe,
                 clocks=clk.summary() if sample_clocks else None,
                 value=aggregate_value(world, dof, args.steps, ms * 1e-3),
                 e2e=aggregate_value(world, dof, args.steps, e2e_s))
@@ -705,6 +742,121 @@ def production_section(args, dev, stream):
             "setup_seconds": setup}
 
 
+# six probes near the axes at r = 0.5: images of one point inside an element
+# under reflections and axis swaps of the lattice, so a centred pulse gives
+# them equal values (exactly on an unjittered lattice ball)
+_A, _B, _C = 0.5, 0.013, 0.007
+AXIS_PROBES = np.array([[_A, _B, _C], [-_A, _B, _C], [_B, _A, _C], [_B, -_A, _C], [_C, _B, _A],
+                        [_C, _B, -_A]], dtype=np.float64)
+
+
+def acoustic_energy(q_rel, J, M, gamma, rho0, p0):
+    """Acoustic energy  sum_e J_e (p'^T M p' / (2 rho0 c0^2) + m'^T M m' / (2 rho0))  of a
+    perturbation given as (rho', m', p') on the nodes: q_rel[K, 5, Np] holds
+    rho', m_x, m_y, m_z and p' (pressure perturbation, not energy)."""
+    c2 = gamma * p0 / rho0
+    pm = np.einsum("ki,ij,kj->k", q_rel[:, 4], M, q_rel[:, 4]) / (2.0 * rho0 * c2)
+    mm = sum(np.einsum("ki,ij,kj->k", q_rel[:, v], M, q_rel[:, v]) for v in (1, 2, 3)) / (2.0 * rho0)
+    return float(np.sum(J * (pm + mm)))
+
+
+def pressure(q, gamma):
+    """p = (gamma - 1)(E - |m|^2 / (2 rho)) of conserved states q[..., 5, ...] (axis -2)."""
+    rho, E = q[..., 0, :], q[..., 4, :]
+    m2 = q[..., 1, :] ** 2 + q[..., 2, :] ** 2 + q[..., 3, :] ** 2
+    return (gamma - 1.0) * (E - 0.5 * m2 / rho)
+
+
+def precision_comparison(run32, run64, amplitude, M, gamma, rho0, p0):
+    """The float32 perturbation form against plain float64 DG after the same
+    steps from the same pulse. Each run: q0, q (end states [K, 5, Np]),
+    probes [steps, 6, 5] (the axis probes), tot0, tot, led (conserved totals
+    at start and end, boundary ledger), J. Returns the comparison's figures,
+    every one relative to a stated scale."""
+    q0, q32, q64 = run64["q0"], run32["q"], run64["q"]
+    K, _, Np = q0.shape
+    base = np.zeros((1, 5, 1))
+    base[0, 0, 0] = rho0
+    base[0, 4, 0] = p0 / (gamma - 1.0)
+    num = np.abs(q32 - q64).max(axis=(0, 2))
+    den = np.abs(q64 - base).max(axis=(0, 2))
+    p32, p64 = pressure(q32, gamma), pressure(q64, gamma)
+    apulse = amplitude * p0
+    diff = np.empty_like(q64)
+    diff[:, 0:4] = q32[:, 0:4] - q64[:, 0:4]
+    diff[:, 4] = p32 - p64
+    init = np.zeros_like(q0)
+    init[:, 0:4] = q0[:, 0:4] - base[:, 0:4]
+    init[:, 4] = pressure(q0, gamma) - p0
+    e_init = acoustic_energy(init, run64["J"], M, gamma, rho0, p0)
+    e_diff = acoustic_energy(diff, run64["J"], M, gamma, rho0, p0)
+    pr32 = pressure(np.swapaxes(run32["probes"], 1, 2), gamma)       # [steps, 6]
+    pr64 = pressure(np.swapaxes(run64["probes"], 1, 2), gamma)
+    out = {
+        "max_err_per_var_rel_to_perturbation": (num / np.where(den > 0, den, 1.0)).tolist(),
+        "pressure_max_diff_rel_to_pulse_amplitude": float(np.abs(p32 - p64).max() / apulse),
+        "energy_of_difference_rel_to_initial_acoustic_energy": e_diff / e_init,
+        "axis_probes_f32_minus_fp64_max_rel_to_pulse_amplitude": float(np.abs(pr32 - pr64).max() / apulse),
+        "axis_probes_spread_rel_to_pulse_amplitude": {
+            "f32": float((pr32.max(axis=1) - pr32.min(axis=1)).max() / apulse),
+            "fp64": float((pr64.max(axis=1) - pr64.min(axis=1)).max() / apulse)},
+        "axis_probes_peak_rel_to_pulse_amplitude": float(np.abs(pr64 - p0).max() / apulse),
+    }
+    for name, r in (("f32", run32), ("fp64", run64)):
+        bal = r["tot"] - r["tot0"] + r["led"]
+        out["balance_rel_" + name] = (np.abs(bal) / np.abs(r["tot0"]).clip(min=1e-300)).tolist()
+    scale = np.abs(run64["tot0"]).clip(min=1e-300)
+    out["ledger_f32_minus_fp64_rel_to_totals"] = (np.abs(run32["led"] - run64["led"]) / scale).tolist()
+    return out
+
+
+def precision_run(order, xyz, EToV, precision, steps, amplitude, width, cfl, dev, stream):
+    """One run of the C2 comparison: the pulse at the centre, the six axis
+    probes sampled every step. Returns the dict precision_comparison reads."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=precision)
+    S.set_stream(stream.cuda_stream)
+    S.upload_mesh(xyz, EToV)
+    q0 = W.gaussian_pulse_state(S.node_coords(), W.GAMMA, W.RHO0_SI, W.P0_SI, amplitude, width)
+    dt = S.stable_dt(q0, cfl)
+    S.set_probes(AXIS_PROBES, capacity=max(steps, 1))
+    S.set_state(torch.from_numpy(q0).to(dev))
+    tot0 = S.totals()
+    t0 = time.perf_counter()
+    S.step(steps, dt)
+    S.sync()
+    secs = time.perf_counter() - t0
+    q, _ = S.get_state()
+    out = dict(q0=q0, q=q, probes=S.read_probes(steps), tot0=tot0, tot=S.totals(),
+               led=S.boundary_flux(), J=S.geometry()["J"], dt=dt, seconds=secs)
+    S.close()
+    return out
+
+
+def c2_section(args, xyz, EToV, dev, stream):
+    """Configuration C2 at its full length: plain float64 DG and the float32
+    perturbation form, from the same 10 % p0 pulse at the centre of the bench
+    ball, for --c2-steps steps; element-wise, probe, energy and balance
+    comparison (precision_comparison)."""
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    w = WORKLOAD
+    r64 = precision_run(w["order"], xyz, EToV, B.DG_PREC_FP64, args.c2_steps, w["amplitude"],
+                        w["width"], w["cfl"], dev, stream)
+    r32 = precision_run(w["order"], xyz, EToV, B.DG_PREC_F32, args.c2_steps, w["amplitude"],
+                        w["width"], w["cfl"], dev, stream)
+    out = precision_comparison(r32, r64, w["amplitude"], B.reference_mass(w["order"]), W.GAMMA,
+                               W.RHO0_SI, W.P0_SI)
+    c0 = float(np.sqrt(W.GAMMA * W.P0_SI / W.RHO0_SI))
+    out.update({"steps": args.c2_steps, "dt": r64["dt"],
+                "distance_travelled_c0_t": c0 * r64["dt"] * args.c2_steps,
+                "seconds": {"fp64": r64["seconds"], "f32": r32["seconds"]},
+                "workload": WORKLOAD_NAME + "; axis probes at r = 0.5"})
+    return out
+
+
 def run_gpu(args, rank, world):
     import torch
 
@@ -740,10 +892,12 @@ def run_gpu(args, rank, world):
         "gpu_launches": args.steps * (3 if head["precision"] == "modal" else 6),
         "roofline": roofline_for(head, w["order"]),
         "clocks": head["clocks"],
+        "repeats": repeat_stats(head["reps"], args.steps, (head["clocks"] or {}).get("sm_mhz")),
     }
     forms_out = {}
     for f, m in res.items():
         forms_out[f] = {"value": m["value"], "ms_per_step": m["ms"] / args.steps, "e2e": m["e2e"],
+                        "repeats": repeat_stats(m["reps"], args.steps),
                         "roofline": roofline_for(m, w["order"])}
     from paper_1710_03887_gb300 import workloads as W
     for f in ("f32", "f32_tc"):
@@ -770,6 +924,8 @@ def run_gpu(args, rank, world):
             "max_diff_per_var_rel_to_perturbation": (num / den).tolist(), "after_steps": args.steps,
             "speedup_per_step": a["value"] / b["value"]}
     line["forms"] = forms_out
+    if args.c2_steps > 0:
+        line["f32_vs_fp64_%d" % args.c2_steps] = c2_section(args, xyz, EToV, dev, stream)
     if args.learned_n > 0:
         # rank 0 only, after the replicas' timed regions: no barrier inside
         lb = learned_bc_section(args, xyz, EToV, dev, stream, None, 1)
@@ -796,6 +952,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of --steps steps per form (median reported, spread beside it)")
+    ap.add_argument("--c2-steps", type=int, default=2000,
+                    help="steps of the float32-against-float64 run on the bench workload (0: skip it)")
     ap.add_argument("--cpu-steps", type=int, default=50,
                     help="oracle steps on the CPU sample (about 10-20 s of one core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -822,6 +982,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.repeats < 1:
+        ap.error("--repeats must be >= 1")
     WORKLOAD["n"] = args.mesh_n
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -346,7 +346,10 @@ int dg_mlp_forward(dg_ctx* ctx, const float* X, int64_t N, float* out);
  * (160 KiB), which every GPU that loads the library keeps until the process
  * exits. The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture. All calls share the array and it keeps the last
+ * before any stream capture. The address is kept per device and context: the
+ * first call after a cudaDeviceReset looks it up again and is a first call in
+ * that sense. Errors are those of this call's own launches (an earlier
+ * asynchronous error on the thread is left for the caller to read). All calls share the array and it keeps the last
  * call's contents (nothing in it needs to start at zero); calls on the same
  * device that can overlap on the GPU (for instance on different streams)
  * race on the array and must be serialised by the caller. Returns DG_ERR_ARG for a null pointer, K <= 0,

@@ -409,8 +409,10 @@ stage_tc_kernel(const StageArgsF32 A) {
   }
   cp_async_wait_all();
   // a wait that gave up may leave MMAs in flight: give them a bounded chance
-  // to finish before the tensor memory is released
-  if (*sAbort && tid == 0) tc::mbar_wait(mbar, phase, kWaitTries);
+  // to finish before the tensor memory is released. `phase` was flipped after
+  // the wait that gave up, so that wait's parity is phase ^ 1 (waiting on
+  // `phase` itself would ask about the phase before it, complete long ago).
+  if (*sAbort && tid == 0) tc::mbar_wait(mbar, phase ^ 1u, kWaitTries);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {

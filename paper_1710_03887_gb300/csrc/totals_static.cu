@@ -60,10 +60,52 @@ __global__ void static_totals_final(const double* __restrict__ partial, int nblo
   }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and
+// context. The runtime gives host code only a stand-in for g_totals_scratch;
+// the address comes from cudaGetSymbolAddress with the device current. A
+// cudaDeviceReset destroys the primary context and the module with it, so the
+// address is keyed on the context's process-unique id (cuCtxGetId, reached
+// through the runtime's driver entry points) and looked up again when that id
+// changes.
 constexpr int kMaxDevices = 64;
+struct ScratchSlot {
+  void* addr = nullptr;
+  unsigned long long ctx_id = 0;
+};
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+ScratchSlot g_slot[kMaxDevices];
+
+typedef int (*PfnCtxGetCurrent)(void** ctx);
+typedef int (*PfnCtxGetId)(void* ctx, unsigned long long* id);
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+bool g_entry_points_tried = false;
+
+// id of the current context, 0 when it cannot be told (no context yet, or a
+// driver without the entry points)
+unsigned long long current_ctx_id() {
+  if (!g_entry_points_tried) {
+    g_entry_points_tried = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+      g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f2);
+    }
+  }
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+  if (g_ctx_get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 }  // namespace
 
@@ -78,19 +120,32 @@ extern "C" int dg_weighted_totals_static(const double* q, const double* J, const
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-      // host code sees only a stand-in for g_totals_scratch; the device
-      // address comes from the runtime, with this device current
+    ScratchSlot& slot = g_slot[dev];
+    const unsigned long long id = slot.addr ? current_ctx_id() : 0;
+    if (!slot.addr || id != slot.ctx_id) {
+      // set-up for this device and context: the lookup also creates the
+      // primary context if none is current yet
       void* addr = nullptr;
       if (cudaGetSymbolAddress(&addr, g_totals_scratch) != cudaSuccess || !addr) return DG_ERR_CUDA;
-      g_scratch_addr[dev] = addr;
+      slot.addr = addr;
+      slot.ctx_id = current_ctx_id();
     }
-    scratch = g_scratch_addr[dev];
+    scratch = slot.addr;
   }
   const int nblocks = int((K + kElemsPerBlock - 1) / kElemsPerBlock);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* partial = static_cast<double*>(scratch);
-  static_totals_partial<<<nblocks, kThreads, 0, s>>>(q, J, w, K, Np, partial);
-  static_totals_final<<<1, 32, 0, s>>>(partial, nblocks, out);
-  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+  // cudaLaunchKernel returns the error of this launch itself, so an earlier
+  // asynchronous error of the caller's is neither reported as ours nor
+  // cleared from the thread's error state
+  void* a1[] = {(void*)&q, (void*)&J, (void*)&w, (void*)&K, (void*)&Np, (void*)&partial};
+  if (cudaLaunchKernel((const void*)static_totals_partial, dim3(nblocks), dim3(kThreads), a1, 0,
+                       s) != cudaSuccess)
+    return DG_ERR_CUDA;
+  const double* cpartial = partial;
+  void* a2[] = {(void*)&cpartial, (void*)&nblocks, (void*)&out};
+  if (cudaLaunchKernel((const void*)static_totals_final, dim3(1), dim3(32), a2, 0, s) !=
+      cudaSuccess)
+    return DG_ERR_CUDA;
+  return DG_OK;
 }

@@ -53,9 +53,15 @@ def test_c1_pulse_100_steps(cuda_device):
     assert tg == pytest.approx(to, rel=1e-15)
     err = state_err(qg, qo, case.gas)
     assert np.all(err < TOL), err
-    # the perturbation itself (q - q0) also agrees
+    # the perturbation itself (q - q0) also agrees. Density and energy carry
+    # the base state (rho0, E0), whose float64 rounding is ~300x the 0.5 %
+    # pulse's own scale: 1e-8. Momentum has no base part (u0 = 0), so it is
+    # held to its own scale, max |m|: the rounding floor there is that of
+    # the momentum flux rho u^2 + p, eps p0 per evaluation against the
+    # acoustic momentum flux A p0, i.e. ~1e-11 after 100 steps; bound 1e-10.
     dq = np.abs(qg - qo).max(axis=(0, 2)) / np.abs(qo - q0).max(axis=(0, 2))
     assert np.all(dq[[0, 4]] < 1e-8), dq
+    assert np.all(dq[1:4] < 1e-10), dq
     samples = S.read_probes()
     assert samples.shape == (100, 3, 5)
     scale = np.abs(samples_o).max(axis=(0, 1))
