@@ -298,8 +298,9 @@ def timed_repeats(args, S, q0_dev, dt, dev, stream, dist, sample_clocks, repeats
     stop = torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")) if sample_clocks else -1)
     reps = []
+    target = repeats if repeats > 0 else 5
     with clk:
-        for _ in range(repeats):
+        while len(reps) < target:
             S.set_state(q0_dev)
             if dist:
                 dist.barrier()
@@ -311,6 +312,10 @@ def timed_repeats(args, S, q0_dev, dt, dev, stream, dist, sample_clocks, repeats
             if dist:
                 dist.barrier()
             reps.append(reduce_max(start.elapsed_time(stop), dist, dev))
+            if repeats <= 0 and len(reps) == 1:
+                # automatic count: at least 5 regions, and enough of them for
+                # the regions to span ~0.5 s (ten clock samples at 50 ms)
+                target = int(min(200, max(5, np.ceil(500.0 / max(reps[0], 1e-3)))))
     kms, klaunch = S.read_kernel_timing()
     S.set_kernel_timing(False)
     S.read_probes()
@@ -504,11 +509,13 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
                    f"{every} steps at r=1 (fraction {args.learned_fraction:g} of the trace nodes); "
                    "measured with centred pulses of width 0.3 and one "
                    "off-centre pulse of width 0.25; 'spherical' is the memory closure w_in = psi "
-                   "without training"),
+                   "(the untrained network: its output layer starts at zero and its output "
+                   "corrects psi)"),
         "samples": int(X.shape[0]), "iters": iters, "loss_first": float(hist[0]),
         "loss_last": float(hist[-1]),
         "reflected_energy_rel": table,
         "gain_vs_characteristic": {k: v["characteristic"] / v["learned"] for k, v in table.items()},
+        "gain_vs_spherical": {k: v["spherical"] / v["learned"] for k, v in table.items()},
         "vs_plain_fp64": fp64_check,
         "seconds": {"record": t_rec, "train": t_train, "evaluate": t_eval},
         "bench_workload_learned_bc": {"value": m["value"], "unit": UNIT,
@@ -802,10 +809,14 @@ def precision_comparison(run32, run64, amplitude, M, gamma, rho0, p0):
             "fp64": float((pr64.max(axis=1) - pr64.min(axis=1)).max() / apulse)},
         "axis_probes_peak_rel_to_pulse_amplitude": float(np.abs(pr64 - p0).max() / apulse),
     }
+    # scale of each total: its own size, and for the momentum components
+    # (zero at rest) the total mass times c0
+    scale = np.abs(run64["tot0"]).astype(np.float64)
+    scale[1:4] = np.maximum(scale[1:4], abs(run64["tot0"][0]) * np.sqrt(gamma * p0 / rho0))
+    scale = scale.clip(min=1e-300)
     for name, r in (("f32", run32), ("fp64", run64)):
         bal = r["tot"] - r["tot0"] + r["led"]
-        out["balance_rel_" + name] = (np.abs(bal) / np.abs(r["tot0"]).clip(min=1e-300)).tolist()
-    scale = np.abs(run64["tot0"]).clip(min=1e-300)
+        out["balance_rel_" + name] = (np.abs(bal) / scale).tolist()
     out["ledger_f32_minus_fp64_rel_to_totals"] = (np.abs(run32["led"] - run64["led"]) / scale).tolist()
     return out
 
@@ -952,8 +963,9 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--repeats", type=int, default=5,
-                    help="timed regions of --steps steps per form (median reported, spread beside it)")
+    ap.add_argument("--repeats", type=int, default=0,
+                    help="timed regions of --steps steps per form (median reported, spread beside "
+                         "it); 0 = at least 5 and enough to span ~0.5 s")
     ap.add_argument("--c2-steps", type=int, default=2000,
                     help="steps of the float32-against-float64 run on the bench workload (0: skip it)")
     ap.add_argument("--cpu-steps", type=int, default=50,
@@ -982,8 +994,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.repeats < 1:
-        ap.error("--repeats must be >= 1")
+    if args.repeats < 0:
+        ap.error("--repeats must be >= 0")
     WORKLOAD["n"] = args.mesh_n
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

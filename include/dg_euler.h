@@ -276,25 +276,53 @@ int dg_set_kernel_timing(dg_ctx* ctx, int enable);
 int dg_read_kernel_timing(dg_ctx* ctx, double* total_ms, int64_t* launches);
 
 /* ------------------------------------------------------------------------
- * Learned boundary closure. The paper's pass-through condition (section 2.2)
- * and the characteristic ghost both assume what lies outside the truncation
- * surface; this closure learns it from the method's own solution in a larger
- * domain. A network 12 -> 64 -> 64 -> 5 (tanh, float32) acts as a learned
- * impedance: from what leaves the domain at an outer-face node it predicts
- * the acoustic wave that enters. With perturbation trace q' = q- - q0,
- * outgoing invariant w_out = p' + rho0 c0 u.n and outgoing amplitude
- * s = |w_out| / (rho0 c0^2) + 1e-12, the features are
- *   (w_out/(rho0 c0^2 s), (rho' - p'/c0^2)/(rho0 s), u_t/(c0 s) (3), n (3),
- *    x/R (3), 10 w_out/(2 p0))
- * and output 0 is the incoming invariant w_in = p' - rho0 c0 u.n of the
- * ghost relative to that of the characteristic ghost, in units of
- * rho0 c0^2 s (outputs 1..4 unused). The ghost is the characteristic one
- * with only w_in moved, by D = clamp(w_in,c + rho0 c0^2 s y0, -L, L) - w_in,c
- * with L = max(|w_in,c|, 0.5 |w_out|): rho += D/(2c0^2), m -= D n/(2c0),
- * E += D/(2(gamma-1)). The bound keeps the energy the ghost feeds back below
- * what leaves, so the closure cannot drive the solution unstable.
+ * Learned boundary closure (boundary mode DG_BC_LEARNED, float32 forms). The
+ * paper's pass-through condition (section 2.2) and the characteristic ghost
+ * both assume what lies outside the truncation surface; section 1 names the
+ * asymptotic far-field conditions as the other route. This closure starts
+ * from the lowest-order such condition for an outgoing spherical wave and
+ * learns the rest from the method's own solution in a larger domain.
+ *
+ * At every node of an outer face with this mode, with perturbation trace
+ * q' = q- - q0 (rho', m', E'), rho = rho0 + rho', u = m'/rho,
+ * p' = (gamma - 1)(E' - |m'|^2 / (2 rho)), outward unit normal n, node
+ * position x, scale R (dg_set_bc_mlp), c0^2 = gamma p0 / rho0, Z = rho0 c0:
+ *   w_out = p' + Z u.n          outgoing acoustic invariant of the trace
+ *   psi   memory of the node: d psi/dt = -(c0 / (2 r)) (psi + w_out),
+ *         r = max(|x|, 1e-3 R), advanced by the same Runge-Kutta stages as
+ *         the state, zero after dg_set_state. For an outgoing spherical wave
+ *         of linear acoustics centred at the origin, psi is exactly the
+ *         incoming invariant.
+ *   s     = (|w_out| + |psi|) / (rho0 c0^2) + 1e-12   (amplitude)
+ *   features f[12] = ( w_out / (rho0 c0^2 s),
+ *                      (rho' - p'/c0^2) / (rho0 s),
+ *                      u_t / (c0 s)  (3; u_t = u - (u.n) n),
+ *                      n  (3),
+ *                      x / R  (3),
+ *                      psi / (rho0 c0^2 s) )
+ * A network 12 -> 64 -> 64 -> 5 (tanh hidden layers, linear output, float32)
+ * maps f to y; only y[0] is used (outputs 1..4 are trained towards zero).
+ * The ghost's incoming invariant is
+ *   g = clamp(psi + rho0 c0^2 s y[0], -L, L),  L = max(|w_in,c|, rho0 c0^2 s),
+ * with w_in,c = p'_c - Z u_c.n the incoming invariant of the characteristic
+ * ghost of the same trace. The ghost is that characteristic ghost moved along
+ * the incoming acoustic wave by D = g - w_in,c:
+ *   rho += D / (2 c0^2),  m -= D n / (2 c0),  E += D / (2 (gamma - 1)).
+ * The characteristic ghost is kept where the result is not finite or has
+ * rho <= 0 or p <= 0, and on every node while no parameters are set. An
+ * all-zero output layer (y = 0) gives g = psi, the spherical-wave condition;
+ * since |psi| <= rho0 c0^2 s <= L the bound never cuts that value. The bound
+ * limits |g| only; it is not an energy or stability guarantee.
+ *
+ * Worked example (rho0 = 1, gamma = 1.4, p0 = 1/1.4, so c0 = 1): the trace
+ *   q' = (0.01, 0.02, -0.03, 0.04, 0.05), n = (0, 0, 1), x = (0.3, -0.4, 1.2),
+ *   R = 2, psi = -0.02
+ * has w_out = 0.0590297030, s = 0.0790297030 (+1e-12) and features
+ * EXAMPLE_FEATURES: 0.7469305938 -0.1192683538 0.2505637685 -0.3758456527 0 0 0 1 0.15 -0.2 0.6 -0.2530694062
+ *
  * Parameters (DG_MLP_NPARAMS floats, row-major, input index first):
- *   W1[12][64], b1[64], W2[64][64], b2[64], W3[64][5], b3[5].
+ *   W1[12][64], b1[64], W2[64][64], b2[64], W3[64][5], b3[5];
+ *   y = tanh(tanh(f W1 + b1) W2 + b2) W3 + b3.
  * Training minimises (1/N) sum |network(features) - target|^2 over samples
  * recorded with dg_sample_traces, full batch, Adam (beta 0.9 / 0.999,
  * eps 1e-8), on the GPU. All float32. */
@@ -313,8 +341,9 @@ int dg_get_bc_mlp(dg_ctx* ctx, float* w);
 int dg_set_trace_faces(dg_ctx* ctx, int64_t n, const int32_t* elem, const int8_t* face);
 /* Training pairs from the current state at every node of the trace faces:
  * X[n*Nfp][12] the features above of the inner trace and its memory,
- * Y[n*Nfp][5] the target output: Y0 = (w_in(outer trace) - w_in(characteristic
- * ghost of the inner trace)) / (rho0 c0^2 s), Y1..4 = 0; amp[n*Nfp] (nullable)
+ * Y[n*Nfp][5] the target output: Y0 = (w_in(outer trace) - psi) /
+ * (rho0 c0^2 s), what the outer trace's incoming invariant adds to the
+ * memory's spherical-wave value, Y1..4 = 0; amp[n*Nfp] (nullable)
  * the amplitude rho0 c0^2 s = |w_out| + |psi| in pressure units, for choosing
  * the samples a wave has reached. The memories of the trace nodes restart at
  * zero with dg_set_state and advance with every dg_step.

@@ -35,9 +35,9 @@ What is computed, with the passage it follows:
                     normal component, u+ = u- - 2 (u-.n) n, which is what the
                     text around Eq. 4 states.
     LEARNED         not in the paper: the characteristic ghost with its
-                    incoming acoustic invariant moved by a network's
-                    prediction, within a bound (``ghost_learned``); the
-                    network is oracle/mlp.py.
+                    incoming acoustic invariant set to the spherical-wave
+                    memory psi plus a network's correction, within a bound
+                    (``ghost_learned``); the network is oracle/mlp.py.
 * Time integration of the ODE system dc/dt = f(c) (Eq. 12) by the five-stage
   2N-storage fourth-order Runge-Kutta scheme of Carpenter and Kennedy (1994)
   instead of the paper's RK2 (section 1.1), stage by stage:
@@ -250,28 +250,28 @@ def memory_rate(psi, wout, r, gas):
 
 def learned_target(qm, qo, n, psi, gas):
     """Training target of the closure at a face node with inner trace qm, outer
-    trace qo (total states) and memory psi: the correction of the incoming
-    acoustic invariant over the characteristic ghost's, in units of
-    rho0 c0^2 s."""
+    trace qo (total states) and memory psi: what the outer trace's incoming
+    acoustic invariant adds to the memory's spherical-wave value psi, in units
+    of rho0 c0^2 s."""
     from . import mlp
     q0 = gas.freestream()
-    qc = ghost_characteristic(qm, n, gas)
     _, s = mlp.features(qm - q0, n, np.zeros_like(n), psi, gas, 1.0)
     _, wi_o = acoustic_invariants(qo - q0, n, gas)
-    _, wi_c = acoustic_invariants(qc - q0, n, gas)
     y = np.zeros(qm.shape)
-    y[..., 0] = (wi_o - wi_c) / (gas.rho0 * gas.c0 ** 2 * s)
+    y[..., 0] = (wi_o - psi) / (gas.rho0 * gas.c0 ** 2 * s)
     return y
 
 
 def ghost_learned(qm, n, x, psi, gas, w, radius):
     """Learned closure. At rest the local Lax-Friedrichs flux takes the
     outgoing acoustic invariant w_out from inside and only the incoming one,
-    g, from the ghost. The network's output 0 corrects the characteristic
-    ghost's incoming invariant (in units of rho0 c0^2 s, s from the features
-    with the node's memory psi); the result is bounded by |g| <= L with
-    L = max(|w_in(characteristic)|, |w_out(inside)| + |psi|), which holds the
-    exact spherical-wave value psi; the characteristic ghost is moved to that
+    g, from the ghost. The lowest-order far-field condition of section 1 for
+    an outgoing spherical wave sets g to the node's memory psi
+    (``memory_rate``); the network's output 0 corrects that value (in units of
+    rho0 c0^2 s, s from the features with psi), so a network whose output
+    layer is zero is the spherical-wave condition itself. The result is
+    bounded by |g| <= L with L = max(|w_in(characteristic)|, |w_out(inside)| +
+    |psi|), which holds psi; the characteristic ghost is moved to that
     invariant at fixed outgoing invariant (isentropic increments D/2c0^2,
     -D n/2c0, D/2(gamma-1), D = g - w_in(characteristic)). The
     characteristic ghost is kept where the result is not finite or has
@@ -285,7 +285,7 @@ def ghost_learned(qm, n, x, psi, gas, w, radius):
     _, wi_c = acoustic_invariants(qc - q0, n, gas)
     pref = gas.rho0 * gas.c0 ** 2
     lim = np.maximum(np.abs(wi_c), pref * s)
-    D = np.clip(wi_c + pref * s * y[..., 0], -lim, lim) - wi_c
+    D = np.clip(psi + pref * s * y[..., 0], -lim, lim) - wi_c
     c0 = gas.c0
     q = qc.copy()
     q[..., 0] += D / (2 * c0 * c0)

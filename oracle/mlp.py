@@ -18,9 +18,9 @@ there: the outgoing acoustic invariant w_out = p' + rho0 c0 u.n, the entropy
 mode, the tangential velocity and the node's memory psi of past outgoing
 waves (``oracle.euler_dg.memory_rate``), each divided by the amplitude
 s = (|w_out| + |psi|) / (rho0 c0^2) + 1e-12 (see ``features``). Output 0 is
-the incoming invariant the closure sets, relative to the characteristic
-ghost's, in units of rho0 c0^2 s; the closure itself (bounded, invariant by
-invariant) is ``oracle.euler_dg.ghost_learned``.
+the incoming invariant the closure sets, relative to the memory psi (the
+spherical-wave value), in units of rho0 c0^2 s; the closure itself (bounded,
+invariant by invariant) is ``oracle.euler_dg.ghost_learned``.
 
 Parity status: pinned (tests/test_oracle_mlp.py: central finite differences
 of the loss, closed forms at zero weights, Adam's first step, the feature

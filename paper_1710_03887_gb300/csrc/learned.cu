@@ -4,9 +4,9 @@
 //
 // Training data are traces the method records itself: at every node of a
 // chosen set of interior faces (the truncation sphere inside a larger
-// domain) the features of the inner trace and, as target, the correction
-// that turns the characteristic ghost of that trace into the outer trace
-// (see mlp.cuh for the feature and target definitions).
+// domain) the features of the inner trace and, as target, the part of the
+// outer trace's incoming acoustic invariant that the spherical-wave memory
+// psi misses (see mlp.cuh for the feature and target definitions).
 //
 // Loss: L = (1/N) sum_samples sum_outputs (y_pred - y)^2. Gradients come from
 // hand-written backward passes over 64-sample chunks; every block owns a
@@ -47,7 +47,7 @@ __global__ void sample_traces_kernel(const float* __restrict__ q, int Np, int Nf
   const int f2 = (c >> 3) & 3, o = c & 7;
   const int nm = fmask[f * Nfp + m];
   const int np = tbl[((f * 4 + f2) * 6 + o) * Nfp + m];
-  float qm[5], qo[5], qc[5];
+  float qm[5], qo[5];
   for (int v = 0; v < 5; ++v) {
     qm[v] = q[(e * 5 + v) * Np + nm];
     qo[v] = q[(e2 * 5 + v) * Np + np];
@@ -55,16 +55,15 @@ __global__ void sample_traces_kernel(const float* __restrict__ q, int Np, int Nf
   const float* g = geo + e * kGeoStride + kGeoNrm + 3 * f;
   const float nv[3] = {g[0], g[1], g[2]};
   const float xv[3] = {txyz[i * 3], txyz[i * 3 + 1], txyz[i * 3 + 2]};
-  ghost_state_f(1, qm, nv, bg, qc);
   float feat[mlp::kIn];
   const float s = mlp::features(qm, nv, xv, tr_psi[i], S, feat);
-  float wo_o, wi_o, wo_c, wi_c;
+  float wo_o, wi_o;
   acoustic_invariants(qo, nv, bg, wo_o, wi_o);
-  acoustic_invariants(qc, nv, bg, wo_c, wi_c);
   for (int k = 0; k < mlp::kIn; ++k) X[i * mlp::kIn + k] = feat[k];
-  // target: incoming-invariant correction in units of rho0 c0^2 s; the other
-  // outputs are not used by the closure and are trained towards zero
-  Y[i * 5] = (wi_o - wi_c) / (bg.rho0 * bg.c0 * bg.c0 * s);
+  // target: what the outer trace's incoming invariant adds to the memory's
+  // spherical-wave value psi, in units of rho0 c0^2 s; the other outputs are
+  // not used by the closure and are trained towards zero
+  Y[i * 5] = (wi_o - tr_psi[i]) / (bg.rho0 * bg.c0 * bg.c0 * s);
   for (int v = 1; v < 5; ++v) Y[i * 5 + v] = 0.0f;
   if (amp) amp[i] = bg.rho0 * bg.c0 * bg.c0 * s;
 }
@@ -126,10 +125,11 @@ closure_kernel(ClosureArgs A, BaseGhost bg) {
     const float s = mlp::features(qm, nv, xv, psi, A.S, feat);
     mlp::forward_smem<1>(sw, feat, y);              // output 0 only
     const float pref = bg.rho0 * bg.c0 * bg.c0;
-    // bounded by the characteristic ghost's own |w_in| or |w_out| + |psi|
-    // (= rho0 c0^2 s), which holds the spherical-wave value psi
+    // the spherical-wave value psi plus the network's correction, bounded by
+    // the characteristic ghost's own |w_in| or |w_out| + |psi| (= rho0 c0^2 s),
+    // which holds psi
     const float lim = fmaxf(fabsf(wi_c), pref * s);
-    const float gin = fminf(fmaxf(wi_c + pref * s * y[0], -lim), lim);
+    const float gin = fminf(fmaxf(psi + pref * s * y[0], -lim), lim);
     D = gin - wi_c;
   }
   A.D[i] = D;

@@ -13,7 +13,8 @@
 //   feat = (w_out / (rho0 c0^2 s),  (rho' - p'/c0^2) / (rho0 s),
 //           u_t / (c0 s) (3),  n (3),  x / R (3),  psi / (rho0 c0^2 s))  (12 values)
 // Output 0 is the incoming invariant the condition sets, relative to the
-// characteristic ghost's, in units of rho0 c0^2 s; outputs 1..4 are unused.
+// memory psi (the spherical-wave value), in units of rho0 c0^2 s; outputs
+// 1..4 are unused. A zero output layer gives the spherical-wave condition.
 // The normalised perturbation z = (rho'/rho0, m'/(rho0 c0), E'/(rho0 c0^2))
 // is kept for the trace diagnostics.
 // Parameter packing (row-major, input index first):

@@ -8,8 +8,8 @@ orchestrates calls and keeps tensors):
    inner part of the large one, element for element.
 2. ``record``: seeded reference runs on the large ball; at the interior faces
    on r = 1 the library integrates the memory of the inner trace and samples
-   (features of the inner trace and memory, target correction of the
-   characteristic ghost's incoming invariant towards the outer trace's)
+   (features of the inner trace and memory; target: what the outer trace's
+   incoming invariant adds to the memory's spherical-wave value)
    (dg_sample_traces).
 3. ``train``: full-batch Adam on the GPU with the library's own forward and
    backward kernels (dg_mlp_train).
@@ -134,7 +134,9 @@ def record(order, nested, runs, every, device, width_scale=1.0, precision=None, 
 
 
 def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
-    """Adam on the GPU from seeded Glorot weights; returns (weights, losses)."""
+    """Adam on the GPU from seeded Glorot hidden layers and a zero output
+    layer (so training starts from the spherical-wave condition); returns
+    (weights, losses)."""
     rng = np.random.default_rng(seed)
     w0 = []
     dims = [(12, 64), (64, 64), (64, 5)]
@@ -143,7 +145,7 @@ def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
         w0.append(rng.uniform(-lim, lim, size=(a, b)).ravel())
         w0.append(np.zeros(b))
     w0 = np.concatenate(w0).astype(np.float32)
-    w0[-5 - 64 * 5:-5] *= 0.01              # start close to the characteristic ghost
+    w0[-5 - 64 * 5:] = 0.0                    # W3, b3: output 0 starts at zero
     S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
     S.set_bc_mlp(w0, radius)
     hist = S.mlp_train(X, Y, iters, lr)
@@ -152,18 +154,13 @@ def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
     return w, hist
 
 
-def spherical_weights(eps=1e-2):
-    """Parameters that make the network the exact spherical-wave closure
-    w_in = psi: one tanh path from feature 11 (psi / rho0 c0^2 s) to output 0,
-    y0 = tanh(eps tanh(eps f11)) / eps^2 = f11 (1 + O(eps^2)). With the
-    characteristic ghost's own w_in of second order at rest, the closure then
-    sets the incoming invariant to the memory, exactly right for an outgoing
-    spherical wave centred at the origin."""
-    w = np.zeros(B.DG_MLP_NPARAMS, dtype=np.float32)
-    w[11 * 64 + 0] = eps                  # W1[11][0]
-    w[12 * 64 + 64 + 0] = eps             # W2[0][0]
-    w[12 * 64 + 64 + 64 * 64 + 64 + 0] = 1.0 / (eps * eps)   # W3[0][0]
-    return w
+def spherical_weights():
+    """Parameters of the spherical-wave condition w_in = psi: the network's
+    output is a correction to the memory psi, so an all-zero parameter set
+    (output 0 identically zero) sets the incoming invariant to the memory,
+    exactly right for an outgoing spherical wave of linear acoustics centred
+    at the origin."""
+    return np.zeros(B.DG_MLP_NPARAMS, dtype=np.float32)
 
 
 def acoustic_energy_weights(order):

@@ -141,4 +141,6 @@ def test_precision_comparison_figures(bench):
         (gamma - 1.0) * 7.0 / (0.1 * p0))
     assert out["axis_probes_spread_rel_to_pulse_amplitude"]["fp64"] == 0.0
     assert out["balance_rel_f32"][0] == pytest.approx(2e-3 / 5.0)
+    c0 = np.sqrt(gamma * p0 / rho0)
+    assert out["balance_rel_f32"][2] == pytest.approx(2e-3 / (5.0 * c0))   # momentum: mass x c0
     assert out["ledger_f32_minus_fp64_rel_to_totals"][4] == pytest.approx(2e-3 / 1e6)

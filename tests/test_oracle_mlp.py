@@ -72,12 +72,32 @@ def _trace_states(gas, rng, k=7, amp=1e-3):
     return qm, n, rng.normal(size=(k, 3)), psi
 
 
-def test_learned_ghost_reduces_to_characteristic_without_correction():
+def test_learned_ghost_with_zero_output_is_the_spherical_condition():
+    """A network whose output is zero leaves the characteristic ghost's
+    outgoing invariant alone and sets its incoming invariant to the memory
+    psi (linearised invariants: to second order in the amplitude); with
+    psi = 0 as well it is the characteristic ghost moved to w_in = 0."""
+    from oracle.euler_dg import acoustic_invariants
     gas = Gas(1.4, 1.225, 101325.0)
     qm, n, x, psi = _trace_states(gas, np.random.default_rng(5))
+    q0 = gas.freestream()
     gc = ghost_characteristic(qm, n, gas)
     w = np.zeros(mlp.N_PARAMS)
-    np.testing.assert_allclose(ghost_learned(qm, n, x, psi, gas, w, 1.0), gc, rtol=1e-15)
+    gl = ghost_learned(qm, n, x, psi, gas, w, 1.0)
+    wo_c, wi_c = acoustic_invariants(gc - q0, n, gas)
+    wo_l, wi_l = acoustic_invariants(gl - q0, n, gas)
+    wo_m, _ = acoustic_invariants(qm - q0, n, gas)
+    amp = np.abs(wo_m) + np.abs(psi)
+    tol = 1e-2 * (amp + np.abs(psi - wi_c))
+    assert np.all(np.abs(wi_l - psi) <= tol)
+    assert np.all(np.abs(wo_l - wo_c) <= tol)
+    # exactly: the increment is D = psi - w_in,c along the incoming wave
+    D = psi - wi_c
+    want = gc.copy()
+    want[:, 0] += D / (2 * gas.c0 ** 2)
+    want[:, 1:4] -= (D / (2 * gas.c0))[:, None] * n
+    want[:, 4] += D / (2 * (gas.gamma - 1.0))
+    np.testing.assert_allclose(gl, want, rtol=1e-15, atol=0)
 
 
 def test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound():
@@ -100,7 +120,7 @@ def test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound():
         gl = ghost_learned(qm, n, x, psi, gas, w, 1.0)
         wo_l, wi_l = acoustic_invariants(gl - q0, n, gas)
         lim = np.maximum(np.abs(wi_c), pref * s)
-        want = np.clip(wi_c + pref * s * b0, -lim, lim)
+        want = np.clip(psi + pref * s * b0, -lim, lim)
         # outgoing invariant unchanged, incoming one moved to the bounded target
         # (linearised invariants: second-order terms ~ amplitude x change)
         tol = 1e-2 * (amp + np.abs(want - wi_c))
@@ -111,6 +131,9 @@ def test_learned_ghost_moves_only_the_incoming_invariant_within_the_bound():
 
 
 def test_learned_target_is_the_incoming_invariant_gap():
+    """The target is what the outer trace's incoming invariant adds to the
+    memory psi, in units of rho0 c0^2 s; it vanishes where the outer trace
+    carries exactly psi."""
     from oracle.euler_dg import acoustic_invariants, learned_target
     gas = Gas(1.4, 1.225, 101325.0)
     rng = np.random.default_rng(8)
@@ -119,14 +142,20 @@ def test_learned_target_is_the_incoming_invariant_gap():
     q0 = gas.freestream()
     y = learned_target(qm, qo, n, psi, gas)
     _, wi_o = acoustic_invariants(qo - q0, n, gas)
-    _, wi_c = acoustic_invariants(ghost_characteristic(qm, n, gas) - q0, n, gas)
     wo_m, _ = acoustic_invariants(qm - q0, n, gas)
     s = (np.abs(wo_m) + np.abs(psi)) / (gas.rho0 * gas.c0 ** 2) + 1e-12
-    np.testing.assert_allclose(y[:, 0] * gas.rho0 * gas.c0 ** 2 * s, wi_o - wi_c, rtol=1e-12)
+    np.testing.assert_allclose(y[:, 0] * gas.rho0 * gas.c0 ** 2 * s, wi_o - psi, rtol=1e-12)
     assert np.all(y[:, 1:] == 0)
-    # with the outer trace equal to the characteristic ghost there is nothing to learn
-    assert np.allclose(learned_target(qm, ghost_characteristic(qm, n, gas), n, psi, gas), 0,
-                       atol=1e-12)
+    # an outer trace whose incoming invariant is psi: nothing to learn. Move
+    # qo along the incoming wave (isentropic increments) until w_in = psi.
+    qo2 = qo.copy()
+    for _ in range(30):                         # the invariants are nonlinear: iterate
+        _, wi = acoustic_invariants(qo2 - q0, n, gas)
+        D = psi - wi
+        qo2[:, 0] += D / (2 * gas.c0 ** 2)
+        qo2[:, 1:4] -= (D / (2 * gas.c0))[:, None] * n
+        qo2[:, 4] += D / (2 * (gas.gamma - 1.0))
+    assert np.allclose(learned_target(qm, qo2, n, psi, gas)[:, 0], 0, atol=1e-9)
 
 
 def test_features_definition():
@@ -194,9 +223,11 @@ def test_memory_reproduces_the_spherical_incoming_invariant():
 
 
 def test_solver_memory_decays_on_the_free_stream():
-    """On the free stream w_out = 0, so every memory decays as
-    psi0 exp(-c0 t / 2r), learned faces and trace faces alike, while the state
-    (zero network: the characteristic ghost) stays the free stream."""
+    """On the free stream w_out = 0, so a memory decays as
+    psi0 exp(-c0 t / 2r). Trace faces (whose memory feeds nothing back) start
+    from random memories and decay so; learned faces start from zero, so the
+    zero network (the spherical condition, w_in = psi = 0) keeps the free
+    stream and their memories stay zero."""
     from oracle.euler_dg import LEARNED, Solver
     from oracle.geometry import Geometry
     from oracle.reference_element import ReferenceElement
@@ -214,6 +245,7 @@ def test_solver_memory_decays_on_the_free_stream():
     assert nl == int(geom.boundary.sum()) and len(S.mem_elem) == nl + 5
     rng = np.random.default_rng(3)
     psi0 = rng.normal(size=S.psi.shape) * 100.0
+    psi0[:nl] = 0.0
     S.psi = psi0.copy()
     q = W.uniform_state(geom.K, geom.ref.Np, gas.rho0, (0, 0, 0), gas.p0, gas.gamma)
     q0 = q.copy()
@@ -224,15 +256,43 @@ def test_solver_memory_decays_on_the_free_stream():
     np.testing.assert_allclose(q, q0, rtol=1e-14, atol=1e-9)
     r = np.linalg.norm(S.mem_x, axis=-1)
     np.testing.assert_allclose(S.psi, psi0 * np.exp(-gas.c0 * t / (2 * r)), rtol=1e-9)
+    assert np.all(S.psi[:nl] == 0.0) and np.all(np.abs(S.psi[nl:]) > 0)
 
 
-def test_spherical_weights_realise_the_memory_feature():
-    """The parameter set of the exact spherical closure: output 0 equals
-    feature 11 (psi / rho0 c0^2 s) to second order in the small signal, and
-    nothing else reaches the outputs."""
+def test_spherical_weights_realise_the_memory_condition():
+    """The spherical-wave parameter set is the all-zero network: every output
+    is zero, so the closure's incoming invariant is the memory psi."""
     from paper_1710_03887_gb300 import learned_bc as L
     w = L.spherical_weights().astype(np.float64)
     X = np.random.default_rng(4).uniform(-1, 1, size=(500, mlp.N_IN))
     y, _ = mlp.forward(w, X)
-    np.testing.assert_allclose(y[:, 0], X[:, 11], atol=1e-4)
-    assert np.all(y[:, 1:] == 0)
+    assert np.all(y == 0)
+
+
+def test_header_worked_example_matches_features():
+    """The boundary header documents the closure's features with a worked
+    example (EXAMPLE_FEATURES); the oracle's feature definition gives those
+    numbers for that trace, so the header's contract is the one computed."""
+    import re
+    from pathlib import Path
+    text = (Path(__file__).resolve().parent.parent / "include" / "dg_euler.h").read_text()
+    m = re.search(r"EXAMPLE_FEATURES:([-0-9.\s]+)", text)
+    want = np.array([float(v) for v in m.group(1).split()])
+    assert want.size == mlp.N_IN
+    gas = Gas(1.4, 1.0, 1.0 / 1.4)              # rho0 = 1, c0 = 1
+    q = np.array([[0.01, 0.02, -0.03, 0.04, 0.05]])
+    n = np.array([[0.0, 0.0, 1.0]])
+    x = np.array([[0.3, -0.4, 1.2]])
+    f, s = mlp.features(q, n, x, np.array([-0.02]), gas, 2.0)
+    np.testing.assert_allclose(f[0], want, rtol=0, atol=1e-10)
+    m = re.search(r"s = ([0-9.]+) \(\+1e-12\)", text)
+    assert s[0] == pytest.approx(float(m.group(1)) + 1e-12, abs=1e-10)
+    # the same vector by hand from the header's definitions
+    rho = 1.01
+    u = q[0, 1:4] / rho
+    pp = 0.4 * (0.05 - 0.5 * np.sum(q[0, 1:4] ** 2) / rho)
+    wout = pp + u[2]
+    amp = abs(wout) + 0.02 + 1e-12
+    hand = np.concatenate([[wout / amp, (0.01 - pp) / amp], [u[0] / amp, u[1] / amp, 0.0],
+                           [0, 0, 1], [0.15, -0.2, 0.6], [-0.02 / amp]])
+    np.testing.assert_allclose(want, hand, rtol=0, atol=1e-10)

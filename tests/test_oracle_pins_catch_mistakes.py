@@ -415,7 +415,7 @@ def _learned_ghost(mp, which):
         y = y.reshape(qm.shape)
         _, wi_c = ED.acoustic_invariants(qc - q0, n, gas)
         pref = gas.rho0 * gas.c0 ** 2
-        g = wi_c + pref * s * y[..., 0]
+        g = psi + pref * s * y[..., 0]
         if which != "unbounded":
             lim = np.maximum(np.abs(wi_c), pref * s)
             g = np.clip(g, -lim, lim)
