@@ -601,6 +601,80 @@ def horn_section(args, dev, stream):
     return out
 
 
+# the outer domains of section 1.2 (Table 1) at ~1.5 M elements: type B with
+# the default lattice, type A (the room reaches 1.02 behind the mouthpiece)
+# with a coarser one
+HORN_DOMAINS = {
+    "B-half-cube": dict(shape="box"),
+    "B-half-sphere": dict(shape="sphere"),
+    "B-half-cone": dict(shape="cone"),
+    "A-cube": dict(shape="box", behind=1.02, m1=3, growth=1.3, aspect=4.0),
+    "A-sphere": dict(shape="sphere", behind=1.02, m1=3, growth=1.3, aspect=4.0),
+    "A-cone": dict(shape="cone", behind=1.02, m1=3, growth=1.3, aspect=4.0),
+    "A-scone": dict(shape="scone", behind=1.02, m1=3, growth=1.3, aspect=4.0),
+}
+
+
+def domains_section(args, dev, stream):
+    """The float32 form on full-size outer domains of Table 1 (slip-walled
+    horn, the inflow pulse of 10 % p0 at the mouthpiece, characteristic
+    condition on the outer surface), timed like the bench workload, with the
+    Table 2 sensor analogues recorded every step."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    out = {"steps": args.horn_steps, "precision": "f32"}
+    for name in [n for n in args.domains.split(",") if n]:
+        kw = HORN_DOMAINS[name]
+        t0 = time.perf_counter()
+        xyz, EToV, tag, info = W.horn_in_room(**kw)
+        t_mesh = time.perf_counter() - t0
+        S = B.Solver(3, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
+        S.set_stream(stream.cuda_stream)
+        S.upload_mesh(xyz, EToV, face_tag=tag)
+        S.set_bc(W.HORN_OUTER, B.DG_BC_CHARACTERISTIC)
+        S.set_bc(W.HORN_WALL, B.DG_BC_SLIP_WALL)
+        S.set_bc(W.HORN_MOUTHPIECE, B.DG_BC_INFLOW_PULSE)
+        S.set_inflow(0.05, 565.0)
+        q0 = torch.empty((S.K, 5, S.Np), dtype=torch.float64, device=dev)
+        q0[:] = torch.from_numpy(W.uniform_state(1, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI,
+                                                 W.GAMMA)).to(dev)
+        dt = rest_cfl_dt(xyz, EToV, 3, W.P0_SI, W.RHO0_SI)
+        S.set_probes(info["sensors"], capacity=max(args.horn_steps, 1))
+        S.set_state(q0)
+        S.step(args.warmup, dt)
+        S.read_probes()
+        S.set_state(q0)
+        torch.cuda.synchronize(dev)
+        S.set_kernel_timing(True)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        S.step(args.horn_steps, dt)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = start.elapsed_time(stop)
+        kms, kl = S.read_kernel_timing()
+        S.set_kernel_timing(False)
+        series = S.read_probes(args.horn_steps)
+        led = S.boundary_flux()
+        S.sync()
+        dof = 5 * S.Np * S.K
+        avg = kms / max(kl, 1)
+        out[name] = {
+            "elements": int(S.K), "horn_elements": info["n_horn"], "mesh_seconds": t_mesh,
+            "lattice": {k: v for k, v in kw.items() if k != "shape"},
+            "value": dof * args.horn_steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / args.horn_steps, "dt": dt, "avg_stage_launch_ms": avg,
+            "stage_tflops": stage_flops_per_element(3) * S.K / (avg * 1e-3) / 1e12,
+            "mass_in_through_mouthpiece": float(-led[0]),
+            "sensor_max_abs_dp_rel_p0": float(np.abs(series[..., 4] - series[:1, :, 4]).max()
+                                              * (W.GAMMA - 1.0) / W.P0_SI)}
+        S.close()
+        del q0
+    return out
+
+
 def locality_section(args, xyz, EToV, dev, stream):
     """The float32 form on the bench mesh with its elements in three orders:
     as built (lattice order), sorted along a Morton curve, and randomly
@@ -945,6 +1019,8 @@ def run_gpu(args, rank, world):
         line["learned_bc"] = lb
     if args.horn_steps > 0:
         line["horn"] = horn_section(args, dev, stream)
+        if args.domains:
+            line["domains"] = domains_section(args, dev, stream)
     if args.locality_steps > 0:
         line["locality"] = locality_section(args, xyz, EToV, dev, stream)
     if args.paper_steps > 0:
@@ -986,6 +1062,9 @@ def main():
                     help="steps timed per element order in the locality section (0: skip it)")
     ap.add_argument("--horn-steps", type=int, default=20,
                     help="steps timed on the horn-in-room workload (0: skip it)")
+    ap.add_argument("--domains", default="B-half-sphere,A-sphere",
+                    help="comma-separated outer domains of Table 1 timed at full size after the "
+                         "horn section (names of bench.HORN_DOMAINS; empty: none)")
     ap.add_argument("--learned-every", type=int, default=10, help="steps between trace samples")
     ap.add_argument("--learned-fraction", type=float, default=1.0,
                     help="fraction of trace nodes kept per sample (seeded)")

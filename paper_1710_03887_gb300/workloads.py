@@ -282,6 +282,105 @@ def _graded(h0, length, growth):
     return np.concatenate([[0.0, h0], h0 + rest * ((length - h0) / rest[-1])])
 
 
+# the outer shapes of section 1.2 (Table 1) around the horn
+HORN_SHAPES = ("box", "cylinder", "sphere", "cone", "scone")
+_COS45 = np.sqrt(0.5)
+
+
+def _outer_shape(shape, enclose, L, Rl, H, behind, rad1_0, sensor_dx=0.01):
+    """Outer surface of a horn domain (section 1.2, Table 1). Returns a dict:
+
+    x_lo, x_hi  the first and last lattice plane (the flat ends before any map)
+    side(x)     outer radius of the lattice's last ring on each plane; a box
+                or cylinder of that radius is meshed first
+    radius      for the cylinder-based shapes, that constant radius
+    cap_hi      None, or rho -> x of a curved right end (planes bent onto it)
+    map         None, or (norm, xc, R, q): a radial map in the (x - xc, rho)
+                half-plane, p -> p (1 - beta (1 - |p|_inf / |p|_n)),
+                beta = (|p|_inf / R)^q, that takes the cylinder's side and
+                flat ends onto a sphere (n = 2) or a 45-degree cone (n = 1)
+                of radius R about (xc, 0, 0), and leaves points near the
+                centre (and the plane x = xc) in place.
+
+    Type B domains (``enclose`` False) start at the bell plane x = L; type A
+    domains reach ``behind`` past the mouthpiece plane x = 0 on the axis.
+
+    box, cylinder   flat ends at x = -behind (A) or L (B) and L + Rl; side H
+                    (the box's square cross-section is blended in the caller)
+    sphere     A: the ball through x = -behind and x = L + Rl on the axis
+                  (centre (L + Rl - behind) / 2, radius (L + Rl + behind) / 2)
+               B: the half-ball in front of the bell plane, centred on the
+                  bell's centre, radius Rl (the rotated hemisphere)
+    cone       A: apex on the axis at x = -behind, flat base at x = L + Rl,
+                  side through radius H at x = L + sensor_dx (just above
+                  sensor 1 of Table 2); the apex is cut off by a flat face
+                  where the radius is halfway between the horn's outer
+                  radius and the cone's radius at the mouthpiece plane
+               B: base disc of radius Rl in the bell plane, apex on the axis
+                  at x = L + Rl (a 45-degree side, facing the bell)
+    scone      A: the spherical cone (sector): the A cone's apex, side and
+                  cut, closed by the sphere about the apex through x = L + Rl
+                  (it meets the side at a right angle)"""
+    def const(R):
+        return lambda x: np.full_like(np.asarray(x, dtype=np.float64), R)
+    if shape in ("box", "cylinder"):
+        return dict(x_lo=-behind if enclose else L, x_hi=L + Rl, side=const(H), radius=H,
+                    cap_hi=None, map=None)
+    if shape == "sphere":
+        if enclose:
+            xc, R = 0.5 * (L + Rl - behind), 0.5 * (L + Rl + behind)
+            return dict(x_lo=xc - R, x_hi=xc + R, side=const(R), radius=R, cap_hi=None,
+                        map=("l2", xc, R, 2.0))
+        return dict(x_lo=L, x_hi=L + Rl, side=const(Rl), radius=Rl, cap_hi=None,
+                    map=("l2", L, Rl, 2.0))
+    if shape == "cone" and not enclose:
+        return dict(x_lo=L, x_hi=L + Rl, side=const(Rl), radius=Rl, cap_hi=None,
+                    map=("l1", L, Rl, 0.5))
+    if shape in ("cone", "scone"):
+        if not enclose:
+            raise ValueError("the spherical cone is a type A domain (behind > 0)")
+        xa = -behind
+        k = H / (L + sensor_dx - xa)
+
+        def side(x):
+            return k * (np.asarray(x, dtype=np.float64) - xa)
+        x_lo = xa + (rad1_0 + 0.5 * (float(side(0.0)) - rad1_0)) / k
+        if shape == "cone":
+            return dict(x_lo=x_lo, x_hi=L + Rl, side=side, radius=None, cap_hi=None, map=None)
+        Rs = L + Rl - xa
+
+        def cap_hi(rho):
+            return xa + np.sqrt(np.maximum(Rs * Rs - rho * rho, 0.0))
+        return dict(x_lo=x_lo, x_hi=xa + Rs / np.sqrt(1.0 + k * k), side=side, radius=None,
+                    cap_hi=cap_hi, map=None)
+    raise ValueError(f"shape must be one of {HORN_SHAPES}")
+
+
+def _ring_offsets(width, n, first):
+    """Offsets of rings 0..n from the inner radius across a gap of ``width``
+    (per plane): geometric with first spacing ``first`` where the gap holds
+    n such spacings, else uniform. Returns [planes, n + 1]."""
+    width = np.asarray(width, dtype=np.float64)
+    j = np.arange(n + 1, dtype=np.float64)
+    out = np.empty(width.shape + (n + 1,))
+    geo = width > n * first * (1.0 + 1e-12)
+    out[~geo] = width[~geo, None] * j / n
+    if np.any(geo):
+        wg = width[geo]
+        lo, hi = np.ones_like(wg) * (1.0 + 1e-12), np.full_like(wg, 4.0)
+        while np.any(first * (hi ** n - 1.0) / (hi - 1.0) < wg):
+            hi = np.where(first * (hi ** n - 1.0) / (hi - 1.0) < wg, 2.0 * hi, hi)
+        for _ in range(200):                     # bisection for the growth factor
+            mid = 0.5 * (lo + hi)
+            big = first * (mid ** n - 1.0) / (mid - 1.0) > wg
+            hi = np.where(big, mid, hi)
+            lo = np.where(big, lo, mid)
+        g = 0.5 * (lo + hi)
+        out[geo] = first * (g[:, None] ** j - 1.0) / (g[:, None] - 1.0)
+        out[geo] *= (wg / out[geo][:, -1])[:, None]
+    return out
+
+
 def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12,
                  horn_length=1.0, wall=0.002, aspect=1.0, behind=0.0, profile=horn_radius):
     """A flared horn and the room around it, meshed without a mesh generator.
@@ -316,29 +415,48 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
     Returns ``(xyz, EToV, face_tag, info)``; ``info`` has the bell plane,
     element counts, and the sensor analogues of Table 2.
     """
-    if shape not in ("box", "cylinder"):
-        raise ValueError("shape must be 'box' or 'cylinder'")
+    if shape not in HORN_SHAPES:
+        raise ValueError(f"shape must be one of {HORN_SHAPES}")
     m1 = int(m1)
     if m1 < 1:
         raise ValueError("m1 must be >= 1")
     enclose = behind > 0.0
+    rad1_0 = float(profile(np.asarray(0.0))) + wall
+    spec = _outer_shape(shape, enclose, horn_length, room_length, room_half, behind, rad1_0)
+    x_lo, x_hi, side, cap_hi = spec["x_lo"], spec["x_hi"], spec["side"], spec["cap_hi"]
+    r_cyl = room_half if spec["radius"] is None else spec["radius"]
+    if enclose and x_lo >= -2.0 * wall:
+        raise ValueError("the domain must reach further behind the mouthpiece")
     # planes along the axis: behind the mouthpiece, along the horn, in front
     xh = [0.0]
     while xh[-1] < horn_length:
         xh.append(xh[-1] + aspect * float(profile(xh[-1])) / m1)
     xh = np.asarray(xh) * (horn_length / xh[-1])
-    back = -_graded(wall, behind, growth)[:0:-1] if enclose else np.zeros(0)
+    back = -_graded(wall, -x_lo, growth)[:0:-1] if enclose else np.zeros(0)
     i0 = len(back)                       # plane of the mouthpiece
     i1 = i0 + len(xh) - 1                # plane of the bell
-    xs = np.concatenate([back, xh, horn_length + _graded(wall, room_length, growth)[1:]])
+    xs = np.concatenate([back, xh, horn_length + _graded(wall, x_hi - horn_length, growth)[1:]])
     NX = len(xs) - 1
     r_max = float(profile(np.asarray(horn_length)))
-    if room_half <= r_max + 2 * wall:
+    if r_cyl <= r_max + 2 * wall:
         raise ValueError("the room must be wider than the bell and its rim")
     # ring fractions beyond the wall (from the bell's cross-section)
-    rho = (r_max + wall) + _graded(wall, room_half - r_max - wall, growth)
+    rho = (r_max + wall) + _graded(wall, r_cyl - r_max - wall, growth)
     psi = (rho - rho[0]) / (rho[-1] - rho[0])          # 0 at ring 1 .. 1 at the side wall
-    m = m1 + len(rho)
+    round_ = spec["radius"] is None                     # a side radius that changes along x
+    if round_:
+        # rings of a surface of revolution whose radius changes along the
+        # axis: per plane, first spacing one wall thickness and geometric
+        # growth out to the side (uniform where the gap is narrow)
+        rad1_x = profile(np.clip(xs, 0.0, horn_length)) + wall
+        gap = side(xs) - rad1_x
+        if np.any(gap <= wall):
+            raise ValueError("the outer surface comes too close to the horn")
+        nr = len(_graded(wall, float(gap.max()), growth)) - 1
+        ring_off = _ring_offsets(gap, nr, wall)            # [planes, nr + 1]
+        m = m1 + 1 + nr
+    else:
+        m = m1 + len(rho)
     beta = 1.0 if shape == "box" else 0.0
 
     # vertex positions on the full logical lattice
@@ -357,14 +475,51 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
     gfac = 1.0 - linf * (1.0 - np.where(L2 > 0, S / safe, 1.0))
     yz[inner] = (R[:, None] * v * gfac[:, None])[inner]
     outer = ~inner
-    kr = np.clip(S - m1 - 1, 0, len(psi) - 1)          # ring index beyond the wall
     rad1 = R + wall
-    radk = rad1 + (room_half - rad1) * psi[kr]
-    bk = beta * psi[kr]
     dir_c = np.stack([I, J], axis=1) / safe[:, None]
-    dir_s = np.stack([I, J], axis=1) / np.where(S > 0, S, 1)[:, None]
-    yz_o = radk[:, None] * ((1.0 - bk)[:, None] * dir_c + bk[:, None] * dir_s)
+    if round_:
+        kr = np.clip(S - m1 - 1, 0, nr)                 # ring index beyond the wall
+        radk = rad1 + ring_off[IX, kr]
+        yz_o = radk[:, None] * dir_c
+    else:
+        kr = np.clip(S - m1 - 1, 0, len(psi) - 1)
+        radk = rad1 + (r_cyl - rad1) * psi[kr]
+        bk = beta * psi[kr]
+        dir_s = np.stack([I, J], axis=1) / np.where(S > 0, S, 1)[:, None]
+        yz_o = radk[:, None] * ((1.0 - bk)[:, None] * dir_c + bk[:, None] * dir_s)
     yz[outer] = yz_o[outer]
+    # a curved right end: the flat end plane is bent onto the end surface,
+    # the bend fading out towards the bell plane (weight 0 there) so the
+    # planes stay ordered along every lattice line; a point at radius rho of
+    # a plane whose side radius is side(x) takes the bend of radius
+    # rho s_hi / side(x) of the end plane, so the side itself does not move
+    rr = np.hypot(yz[:, 0], yz[:, 1])
+    if cap_hi is not None:
+        s_hi = float(side(np.asarray(x_hi)))
+        rhat = np.minimum(rr * s_hi / np.maximum(side(x), 1e-300), s_hi)
+        b = cap_hi(rhat) - x_hi
+        wgt = np.clip((x - horn_length) / (x_hi - horn_length), 0.0, 1.0) ** 2
+        x = x + wgt * b
+        rr = np.hypot(yz[:, 0], yz[:, 1])
+    if spec["map"] is not None:
+        # the cylinder onto the sphere or cone. In the (a, rho) half-plane
+        # the map p -> p g, g = 1 - beta (1 - f), f = |p|_inf / |p|_n of
+        # degree 0 and beta of degree q, has Jacobian g (1 - (1 + q) beta (1 - f)),
+        # positive for q < 1 / (1 - 1/sqrt 2) - 1 (n = 2) or q < 1 (n = 1).
+        # The horn (interior, wall, cap: rings up to the wall's outer one
+        # between the cap's back and the bell) is held in place; its image
+        # would move by at most |p|^3 / R^2 there.
+        norm, xc, Rm, q = spec["map"]
+        a = x - xc
+        pinf = np.maximum(np.abs(a), rr)
+        pn = np.hypot(a, rr) if norm == "l2" else np.abs(a) + rr
+        f = np.where(pn > 0, pinf / np.where(pn > 0, pn, 1.0), 1.0)
+        g = 1.0 - (pinf / Rm) ** q * (1.0 - f)
+        if enclose:
+            held = (S <= m1 + 1) & (x >= -wall - 1e-15) & (x <= horn_length + 1e-15)
+            g = np.where(held, 1.0, g)
+        x = xc + a * g
+        yz = yz * g[:, None]
     xyz_all = np.column_stack([x, yz])
 
     # cells
@@ -435,10 +590,15 @@ def horn_in_room(m1=3, room_length=1.02, room_half=1.0, shape="box", growth=1.12
     _fix_orientation(xyz, EToV)
     horn_cells = (cx >= i0) & (cx < i1) & (np.maximum(np.maximum(np.abs(ci), np.abs(ci + 1)),
                                                         np.maximum(np.abs(cj), np.abs(cj + 1))) <= m1)
+    names = {("box", True): "A-cube", ("box", False): "B-half-cube", ("sphere", True): "A-sphere",
+             ("sphere", False): "B-half-sphere", ("cone", True): "A-cone", ("cone", False): "B-half-cone",
+             ("scone", True): "A-scone", ("cylinder", True): "A-cylinder",
+             ("cylinder", False): "B-half-cylinder"}
     info = {
         "bell_x": horn_length,
         "bell_radius": r_max,
         "type": "A" if enclose else "B",
+        "name": names[(shape, enclose)],
         "n_horn": int(6 * np.count_nonzero(horn_cells)),
         "n_room": int(EToV.shape[0] - 6 * np.count_nonzero(horn_cells)),
         "horn_elements": np.repeat(horn_cells, 6),
