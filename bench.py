@@ -394,6 +394,52 @@ def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_cl
                 e2e=aggregate_value(world, dof, args.steps, e2e_s))
 
 
+def measure_partitioned(args, xyz, EToV, dev, stream, dist, world, rank):
+    """The bench workload split across the ranks (Morton slabs; the face
+    traces of cut faces exchanged before every stage over NCCL), timed like
+    measure_form: ``repeats`` regions of ``steps`` steps, max over ranks.
+    value = DOF of the whole mesh x steps / time (strong scaling)."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import partition as PT
+    from paper_1710_03887_gb300 import workloads as W
+    w = WORKLOAD
+    prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC, "fp64": B.DG_PREC_FP64}[args.precision]
+    part = PT.partition_elements(xyz, EToV, world)
+    L = PT.local_mesh(xyz, EToV, part, rank)
+    PS = PT.PartitionedSolver(w["order"], L, W.GAMMA, W.RHO0_SI, W.P0_SI, prec, dev)
+    S = PS.S
+    q0 = W.gaussian_pulse_state(S.node_coords(), W.GAMMA, W.RHO0_SI, W.P0_SI, w["amplitude"],
+                                w["width"])
+    dt = reduce_max(-S.stable_dt(q0, w["cfl"]), dist, dev) * -1.0      # the smallest over ranks
+    q0_dev = torch.from_numpy(q0).to(dev)
+    PS.set_state(q0_dev)
+    PS.step(args.warmup, dt)
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    reps = []
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with clk:
+        for _ in range(max(args.repeats, 5)):
+            PS.set_state(q0_dev)
+            dist.barrier()
+            torch.cuda.synchronize(dev)
+            start.record(stream)
+            PS.step(args.steps, dt)
+            stop.record(stream)
+            torch.cuda.synchronize(dev)
+            dist.barrier()
+            reps.append(reduce_max(start.elapsed_time(stop), dist, dev))
+    ms = statistics.median(reps)
+    dof_total = 5 * S.Np * len(EToV)
+    out = dict(ms=ms, reps=reps, value=dof_total * args.steps / (ms * 1e-3), dof=dof_total,
+               K=len(EToV), K_own=L.K_own, cut_faces=int(L.send_elem.size), dt=dt,
+               clocks=clk.summary(), peers=L.peers)
+    S.close()
+    return out
+
+
 def roofline_for(m, order):
     """Roofline object of the stage kernel of one measured form."""
     K = m["K"]
@@ -954,6 +1000,25 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     w = WORKLOAD
     xyz, EToV = build_workload()
+    if args.partition and world > 1:
+        m = measure_partitioned(args, xyz, EToV, dev, stream, dist, world, rank)
+        if rank == 0:
+            line = {
+                "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"] / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, "elements": m["K"], "order": w["order"],
+                           "dof": m["dof"], "dt": m["dt"], "precision": args.precision,
+                           "parallelism": f"element partition x{world} (Morton slabs; halo "
+                                          "exchange of cut-face traces before every stage, NCCL)",
+                           "rank0_elements": m["K_own"], "rank0_cut_faces": m["cut_faces"]},
+                "repeats": repeat_stats(m["reps"], args.steps),
+                "gpu_launches": args.steps * 5 * (3 if m["peers"] else 1),
+                "clocks": m["clocks"],
+            }
+            print(json.dumps(line), flush=True)
+        return
     forms = [args.precision] + [f for f in ("f32_tc", "f32", "fp64", "modal")
                                 if f != args.precision and not args.one_form]
     res = {f: measure_form(args, f, xyz, EToV, dev, stream, dist, world, sample_clocks=(f == args.precision))
@@ -1050,6 +1115,9 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64", "modal"],
                     help="arithmetic form of the headline number (the other is measured beside it)")
     ap.add_argument("--one-form", action="store_true", help="measure only --precision")
+    ap.add_argument("--partition", action="store_true",
+                    help="under torchrun: split the one mesh across the ranks (halo exchange per "
+                         "stage, strong scaling) instead of running independent replicas")
     ap.add_argument("--learned-n", type=int, default=16,
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")

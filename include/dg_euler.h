@@ -361,6 +361,50 @@ int dg_mlp_train(dg_ctx* ctx, const float* X, const float* Y, int64_t N, int ite
 /* Network outputs out[N][5] (device) for features X[N][12] (device). */
 int dg_mlp_forward(dg_ctx* ctx, const float* X, int64_t N, float* out);
 
+/* ------------------------------------------------------------------------
+ * Partitioned meshes (one rank per GPU). The element partition of Omega
+ * (Appendix A, Eq. 9) lets each rank own a set of elements; a face between
+ * elements of two ranks (a cut face) needs, once per Runge-Kutta stage, the
+ * neighbour's trace on that face (the surface term of Eq. 10). A rank's mesh
+ * holds its own elements first, then copies of the neighbour elements
+ * across its cut faces (halo elements); faces of a halo element that lead
+ * nowhere on this rank carry any boundary id (they are never evaluated).
+ *
+ * dg_set_owned: elements [0, K_own) are this rank's, [K_own, K) halo copies.
+ *   Halo elements are never advanced; totals, the boundary ledger and
+ *   sensors count own elements only (a sensor must lie in an own element).
+ *   Call after the mesh upload and before dg_set_state (it discards device
+ *   buffers). DG_ERR_UNSUPPORTED for DG_PREC_MODAL: the paper's
+ *   discretisation picks each face's quadrature points by element number,
+ *   which a partition renumbers.
+ * dg_set_halo: the exchange lists (host arrays, copied): send entry i is
+ *   face send_face[i] of own element send_elem[i] (a cut face); receive entry
+ *   i is face recv_face[i] of halo element recv_elem[i] (its face to an own
+ *   element). DG_ERR_ARG for an entry that is not such a face. Call after
+ *   dg_set_owned.
+ * dg_halo_pack: buf[n_send][5][Nfp] <- the current state at the nodes of the
+ *   send faces (face node order of the reference element), in the state's
+ *   own representation: double total state for DG_PREC_FP64, float
+ *   perturbation q - q0 for the float32 forms. Device buffer, caller-owned,
+ *   enqueued on the stream.
+ * dg_halo_unpack: the current state at the nodes of the receive faces <-
+ *   buf[n_recv][5][Nfp] (same layout and type). A receive entry's buffer row
+ *   is the send row of the same face on the rank that owns the element.
+ * dg_step_stages: advance n Runge-Kutta stages (continuing a step in
+ *   progress); the time advances and the sensors sample after the last stage
+ *   of a step. A partitioned run exchanges halos before every stage:
+ *   pack, send / receive, unpack, dg_step_stages(1). dg_step refuses
+ *   (DG_ERR_ORDER) while a step is in progress; dg_set_state ends it.
+ * dg_stage_index: the next stage (0..stages_per_step - 1) and the stages per
+ *   step (5 for the Runge-Kutta forms, 2 for the paper's Heun scheme). */
+int dg_set_owned(dg_ctx* ctx, int64_t K_own);
+int dg_set_halo(dg_ctx* ctx, int64_t n_send, const int32_t* send_elem, const int8_t* send_face,
+                int64_t n_recv, const int32_t* recv_elem, const int8_t* recv_face);
+int dg_halo_pack(dg_ctx* ctx, void* buf);
+int dg_halo_unpack(dg_ctx* ctx, const void* buf);
+int dg_step_stages(dg_ctx* ctx, int n, double dt);
+int dg_stage_index(dg_ctx* ctx, int* k, int* stages_per_step);
+
 /* Conserved totals that allocate nothing (no counterpart in the paper: this
  * is a service for callers that cannot call cudaMalloc where they need the
  * totals, e.g. code whose device memory is entirely owned by another

@@ -83,6 +83,12 @@ _SIGS = {
     "dg_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_int64, _D, _P]),
     "dg_mlp_train": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, C.c_double, _P]),
     "dg_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P]),
+    "dg_set_owned": (C.c_int, [_P, C.c_int64]),
+    "dg_set_halo": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int64, _P, _P]),
+    "dg_halo_pack": (C.c_int, [_P, _P]),
+    "dg_halo_unpack": (C.c_int, [_P, _P]),
+    "dg_step_stages": (C.c_int, [_P, C.c_int, C.c_double]),
+    "dg_stage_index": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
 }
 
 _lib = None
@@ -222,6 +228,7 @@ class Solver:
             raise DGError(rc, "dg_create failed (order or parameters)")
         self.h = h
         self.order = order
+        self.precision = precision
         self.K = 0
         self.Np = (order + 1) * (order + 2) * (order + 3) // 6
         self.Nfp = (order + 1) * (order + 2) // 2
@@ -433,6 +440,47 @@ class Solver:
         _require(X, (None, 12), np.float32, "X", device=True)
         _require(out, (X.shape[0], 5), np.float32, "out", device=True)
         self._check(self.lib.dg_mlp_forward(self.h, X.data_ptr(), X.shape[0], out.data_ptr()))
+
+    # ---- partitioned meshes (own elements first, then halo copies)
+    def set_owned(self, K_own):
+        self._check(self.lib.dg_set_owned(self.h, int(K_own)))
+        self.K_own = int(K_own)
+
+    def set_halo(self, send_elem, send_face, recv_elem, recv_face):
+        se = np.ascontiguousarray(send_elem, dtype=np.int32).ravel()
+        sf = np.ascontiguousarray(send_face, dtype=np.int8).ravel()
+        re_ = np.ascontiguousarray(recv_elem, dtype=np.int32).ravel()
+        rf = np.ascontiguousarray(recv_face, dtype=np.int8).ravel()
+        _require(sf, se.shape, np.int8, "send faces")
+        _require(rf, re_.shape, np.int8, "receive faces")
+        self._check(self.lib.dg_set_halo(self.h, se.size, _ptr(se), _ptr(sf), re_.size, _ptr(re_),
+                                         _ptr(rf)))
+        self.n_send, self.n_recv = se.size, re_.size
+
+    def halo_dtype(self):
+        """Element type of halo buffers: the state's own representation."""
+        return np.float32 if self.precision in (DG_PREC_F32, DG_PREC_F32_TC) else np.float64
+
+    def halo_pack(self, buf):
+        """buf: CUDA tensor [n_send, 5, Nfp] of halo_dtype()."""
+        _require(buf, (getattr(self, "n_send", 0), 5, self.Nfp), self.halo_dtype(), "send buffer",
+                 device=True)
+        self._check(self.lib.dg_halo_pack(self.h, buf.data_ptr()))
+
+    def halo_unpack(self, buf):
+        """buf: CUDA tensor [n_recv, 5, Nfp] of halo_dtype()."""
+        _require(buf, (getattr(self, "n_recv", 0), 5, self.Nfp), self.halo_dtype(),
+                 "receive buffer", device=True)
+        self._check(self.lib.dg_halo_unpack(self.h, buf.data_ptr()))
+
+    def step_stages(self, n, dt):
+        self._check(self.lib.dg_step_stages(self.h, int(n), float(dt)))
+
+    def stage_index(self):
+        """(next stage, stages per step)."""
+        k, n = C.c_int(), C.c_int()
+        self._check(self.lib.dg_stage_index(self.h, C.byref(k), C.byref(n)))
+        return k.value, n.value
 
     def set_kernel_timing(self, enable=True):
         self._check(self.lib.dg_set_kernel_timing(self.h, int(enable)))

@@ -131,6 +131,13 @@ struct dg_ctx {
   float* txyz = nullptr;
   float* tr_psi = nullptr;         // memory of the trace face nodes [n][Nfp]
   float* tr_res = nullptr;
+  // partitioned mesh: elements [K_own, K) are halo copies of a neighbour
+  // rank's elements (not advanced; read through their cut-face nodes)
+  int64_t K_own = -1;
+  int64_t n_send = 0, n_recv = 0;
+  int32_t* halo_send = nullptr;    // e * 4 + f of own cut faces, send order
+  int32_t* halo_recv = nullptr;    // e * 4 + f of halo faces, receive order
+  int stage_k = 0;                 // next Runge-Kutta stage of the step in progress
   // stage-kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;   // created lazily, reused
@@ -158,6 +165,8 @@ struct dg_ctx {
     dfree(q32[0]); dfree(q32[1]); dfree(res32); dfree(scratch32); dfree(geo32); dfree(ops32);
     dfree(bxyz); dfree(bface); dfree(bpsi); dfree(bpsi_res); dfree(bD); dfree(face_list);
     dfree(tr_elem); dfree(tr_face); dfree(txyz); dfree(tr_psi); dfree(tr_res);
+    dfree(halo_send); dfree(halo_recv);
+    n_send = n_recv = 0;
     ntrace = 0;
     nbf = 0;
     dev_ready = false;
@@ -165,6 +174,7 @@ struct dg_ctx {
     nprobe = 0;
   }
   size_t state_elems() const { return size_t(mesh.K) * 5 * ref.Np; }
+  int64_t owned() const { return K_own < 0 ? mesh.K : K_own; }
   bool f32() const { return prec == DG_PREC_F32 || prec == DG_PREC_F32_TC; }
 };
 
@@ -214,7 +224,8 @@ int ensure_device(dg_ctx* c) {
   const int ET = tcf ? dgk::stage_tc_tile_elems(p)
                      : (f32 ? dgk::stage_f32_tile_elems(p)
                             : (modal ? dgk::stage_modal_tile_elems(p) : dgk::stage_tile_elems(p)));
-  c->ntiles = int((K + ET - 1) / ET);
+  const int64_t Kown = c->owned();
+  c->ntiles = int((Kown + ET - 1) / ET);
   c->grid = std::min(c->ntiles, c->sms * bps);
   const size_t nq = c->state_elems();
   if (f32) {
@@ -296,7 +307,7 @@ int ensure_device(dg_ctx* c) {
     std::vector<uint8_t> fl(size_t(c->ntiles) * row, 0);
     std::vector<uint8_t> grp[3];
     for (int t = 0; t < c->ntiles; ++t) {
-      const int64_t e0 = int64_t(t) * ET, e1 = std::min<int64_t>(K, e0 + ET);
+      const int64_t e0 = int64_t(t) * ET, e1 = std::min<int64_t>(Kown, e0 + ET);
       for (auto& g : grp) g.clear();
       for (int64_t e = e0; e < e1; ++e)
         for (int f = 0; f < 4; ++f) {
@@ -398,7 +409,7 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
   A.face_list = c->face_list;
   A.led = ledger_args(c, update, a, b, dt);
   A.status = c->status;
-  A.K = c->mesh.K;
+  A.K = c->owned();
   A.ntiles = c->ntiles;
   for (int i = 0; i < 8; ++i) A.bc_mode[i] = c->bc_mode[i];
   A.a = a;
@@ -492,7 +503,7 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
     A.fmask = c->fmask;
     A.led = ledger_args(c, !to_scratch, a, b, dt);
     A.status = c->status;
-    A.K = c->mesh.K;
+    A.K = c->owned();
     A.ntiles = c->ntiles;
     for (int i = 0; i < 8; ++i) A.bc_mode[i] = c->bc_mode[i];
     A.a = float(a);
@@ -561,6 +572,7 @@ int record_event(dg_ctx* c) {
 
 int reset_run(dg_ctx* c, double t) {
   c->t = t;
+  c->stage_k = 0;
   c->have_state = true;
   c->precorded = 0;
   DG_CUDA(cudaMemsetAsync(c->ledger, 0, 10 * 8, c->stream));
@@ -655,6 +667,7 @@ int dg_upload_mesh(dg_ctx* c, int64_t nvert, const double* xyz, int64_t K, const
   if (K > (int64_t(1) << 26)) return c->fail(DG_ERR_ARG, "too many elements (max 2^26)");
   c->free_device();
   c->have_mesh = false;
+  c->K_own = -1;
   std::string err;
   if (!dg::build_mesh(c->ref, nvert, xyz, K, EToV, face_tag, vert_class, c->mesh, err))
     return c->fail(DG_ERR_MESH, err);
@@ -671,6 +684,7 @@ int dg_upload_geometry(dg_ctx* c, int64_t K, const double* drdx, const double* J
   if (K > (int64_t(1) << 26)) return c->fail(DG_ERR_ARG, "too many elements (max 2^26)");
   c->free_device();
   c->have_mesh = false;
+  c->K_own = -1;
   dg::Mesh m;
   m.K = K;
   m.drdx.assign(drdx, drdx + size_t(K) * 9);
@@ -927,30 +941,25 @@ int dg_get_state_device(dg_ctx* c, double* dq, double* t) {
   return DG_OK;
 }
 
-int dg_step(dg_ctx* c, int n, double dt) {
-  if (!c) return DG_ERR_ARG;
-  if (n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return c->fail(DG_ERR_ARG, "need n >= 0 and dt > 0");
-  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
-  // a named range per call for timeline tools (no cost without one attached)
-  struct Range {
-    Range() { nvtxRangePushA("dg_step"); }
-    ~Range() { nvtxRangePop(); }
-  } range;
+// Advance n Runge-Kutta stages from the stage counter on; after the last
+// stage of a step the time advances and the sensors are sampled.
+static int advance_stages(dg_ctx* c, int64_t n, double dt) {
   const bool heun = c->prec == DG_PREC_MODAL;
   const int nstage = heun ? 2 : 5;
   const double* RA = heun ? kHeunA : kRkA;
   const double* RB = heun ? kHeunB : kRkB;
   const double* RC = heun ? kHeunC : kRkC;
-  for (int s = 0; s < n; ++s) {
-    for (int k = 0; k < nstage; ++k) {
-      int rc = record_event(c);
-      if (rc) return rc;
-      rc = run_stage(c, false, RA[k], RB[k], dt, c->t + RC[k] * dt);
-      if (rc) return rc;
-      rc = record_event(c);
-      if (rc) return rc;
-      c->cur = 1 - c->cur;
-    }
+  for (int64_t s = 0; s < n; ++s) {
+    const int k = c->stage_k;
+    int rc = record_event(c);
+    if (rc) return rc;
+    rc = run_stage(c, false, RA[k], RB[k], dt, c->t + RC[k] * dt);
+    if (rc) return rc;
+    rc = record_event(c);
+    if (rc) return rc;
+    c->cur = 1 - c->cur;
+    c->stage_k = (k + 1) % nstage;
+    if (c->stage_k != 0) continue;
     c->t += dt;
     if (c->nprobe > 0) {
       const int slotp = int(c->precorded % c->pcap);
@@ -964,6 +973,120 @@ int dg_step(dg_ctx* c, int n, double dt) {
       ++c->precorded;
     }
   }
+  return DG_OK;
+}
+
+int dg_step(dg_ctx* c, int n, double dt) {
+  if (!c) return DG_ERR_ARG;
+  if (n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return c->fail(DG_ERR_ARG, "need n >= 0 and dt > 0");
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  if (c->stage_k != 0) return c->fail(DG_ERR_ORDER, "a step is in progress (dg_step_stages)");
+  // a named range per call for timeline tools (no cost without one attached)
+  struct Range {
+    Range() { nvtxRangePushA("dg_step"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
+  return advance_stages(c, int64_t(n) * (c->prec == DG_PREC_MODAL ? 2 : 5), dt);
+}
+
+int dg_step_stages(dg_ctx* c, int n, double dt) {
+  if (!c) return DG_ERR_ARG;
+  if (n < 0 || !(dt > 0.0) || !std::isfinite(dt)) return c->fail(DG_ERR_ARG, "need n >= 0 and dt > 0");
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  return advance_stages(c, n, dt);
+}
+
+int dg_stage_index(dg_ctx* c, int* k, int* stages_per_step) {
+  if (!c || !k || !stages_per_step) return DG_ERR_ARG;
+  *k = c->stage_k;
+  *stages_per_step = c->prec == DG_PREC_MODAL ? 2 : 5;
+  return DG_OK;
+}
+
+int dg_set_owned(dg_ctx* c, int64_t K_own) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->have_mesh) return c->fail(DG_ERR_ORDER, "no mesh uploaded");
+  if (K_own < 1 || K_own > c->mesh.K) return c->fail(DG_ERR_ARG, "need 1 <= K_own <= K");
+  if (c->prec == DG_PREC_MODAL)
+    return c->fail(DG_ERR_UNSUPPORTED,
+                   "the paper's discretisation ties its face rule to the element numbering; "
+                   "partitioned meshes run the nodal forms");
+  c->free_device();
+  c->K_own = K_own;
+  return DG_OK;
+}
+
+int dg_set_halo(dg_ctx* c, int64_t n_send, const int32_t* send_elem, const int8_t* send_face,
+                int64_t n_recv, const int32_t* recv_elem, const int8_t* recv_face) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->have_mesh) return c->fail(DG_ERR_ORDER, "no mesh uploaded");
+  if (n_send < 0 || n_recv < 0 || (n_send > 0 && (!send_elem || !send_face)) ||
+      (n_recv > 0 && (!recv_elem || !recv_face)))
+    return c->fail(DG_ERR_ARG, "bad halo list arguments");
+  const int64_t Kown = c->owned();
+  std::vector<int32_t> snd(static_cast<size_t>(n_send)), rcv(static_cast<size_t>(n_recv));
+  for (int64_t i = 0; i < n_send; ++i) {
+    const int32_t e = send_elem[i];
+    const int f = send_face[i];
+    if (e < 0 || e >= Kown || f < 0 || f > 3)
+      return c->fail(DG_ERR_ARG, "send entry " + std::to_string(i) + " is not a face of an own element");
+    if (c->mesh.EToE[size_t(e) * 4 + f] < Kown)
+      return c->fail(DG_ERR_ARG, "send entry " + std::to_string(i) + " is not a face to a halo element");
+    snd[size_t(i)] = e * 4 + f;
+  }
+  for (int64_t i = 0; i < n_recv; ++i) {
+    const int32_t e = recv_elem[i];
+    const int f = recv_face[i];
+    if (e < Kown || e >= c->mesh.K || f < 0 || f > 3)
+      return c->fail(DG_ERR_ARG, "receive entry " + std::to_string(i) + " is not a face of a halo element");
+    const int64_t nb = c->mesh.EToE[size_t(e) * 4 + f];
+    if (nb < 0 || nb >= Kown)
+      return c->fail(DG_ERR_ARG, "receive entry " + std::to_string(i) + " is not a face to an own element");
+    rcv[size_t(i)] = e * 4 + f;
+  }
+  dfree(c->halo_send);
+  dfree(c->halo_recv);
+  c->n_send = c->n_recv = 0;
+  if (n_send > 0) {
+    DG_CUDA(cudaMalloc(&c->halo_send, snd.size() * 4));
+    DG_CUDA(cudaMemcpy(c->halo_send, snd.data(), snd.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (n_recv > 0) {
+    DG_CUDA(cudaMalloc(&c->halo_recv, rcv.size() * 4));
+    DG_CUDA(cudaMemcpy(c->halo_recv, rcv.data(), rcv.size() * 4, cudaMemcpyHostToDevice));
+  }
+  c->n_send = n_send;
+  c->n_recv = n_recv;
+  return DG_OK;
+}
+
+int dg_halo_pack(dg_ctx* c, void* buf) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  if (c->n_send == 0) return DG_OK;
+  if (!buf) return DG_ERR_ARG;
+  if (c->f32())
+    DG_CUDA(dgk::launch_halo_pack<float>(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->halo_send,
+                                         c->fmask, c->n_send, static_cast<float*>(buf), c->stream));
+  else
+    DG_CUDA(dgk::launch_halo_pack<double>(c->q[c->cur], c->ref.Np, c->ref.Nfp, c->halo_send,
+                                          c->fmask, c->n_send, static_cast<double*>(buf), c->stream));
+  return DG_OK;
+}
+
+int dg_halo_unpack(dg_ctx* c, const void* buf) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->have_state) return c->fail(DG_ERR_ORDER, "no state set");
+  if (c->n_recv == 0) return DG_OK;
+  if (!buf) return DG_ERR_ARG;
+  if (c->f32())
+    DG_CUDA(dgk::launch_halo_unpack<float>(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->halo_recv,
+                                           c->fmask, c->n_recv, static_cast<const float*>(buf),
+                                           c->stream));
+  else
+    DG_CUDA(dgk::launch_halo_unpack<double>(c->q[c->cur], c->ref.Np, c->ref.Nfp, c->halo_recv,
+                                            c->fmask, c->n_recv, static_cast<const double*>(buf),
+                                            c->stream));
   return DG_OK;
 }
 
@@ -999,7 +1122,7 @@ int dg_set_probes(dg_ctx* c, int n, const double* xyz, int capacity) {
     const double* x = xyz + 3 * i;
     int64_t found = -1;
     double rst[3] = {0, 0, 0};
-    for (int64_t e = 0; e < c->mesh.K && found < 0; ++e) {
+    for (int64_t e = 0; e < c->owned() && found < 0; ++e) {
       const double* v = &c->mesh.verts[size_t(e) * 12];
       const double* m = &c->mesh.drdx[size_t(e) * 9];
       // (r,s,t) = -1 + drdx (x - v1) * ... : r_a + 1 = sum_b drdx[a][b] (x_b - v1_b)
@@ -1073,7 +1196,7 @@ int dg_conserved_totals(dg_ctx* c, double out[5]) {
     if (rc) return rc;
     src = c->scratch;
   }
-  DG_CUDA(dgk::launch_totals(src, c->geo, c->mass_w, c->mesh.K, c->ref.Np, c->totals_part,
+  DG_CUDA(dgk::launch_totals(src, c->geo, c->mass_w, c->owned(), c->ref.Np, c->totals_part,
                              kTotalsBlocks, c->totals_part + size_t(kTotalsBlocks) * 5, c->stream));
   int rc = check_status(c);
   if (rc) return rc;

@@ -207,6 +207,14 @@ cudaError_t launch_stage_modal(int p, const StageArgs& a, int grid, cudaStream_t
 
 cudaError_t launch_probe_sample(const double* q, int Np, int n, const int32_t* elem,
                                 const double* rows, double* out, cudaStream_t s);
+// halo exchange of a partitioned mesh (halo.cu): entries ef[i] = e * 4 + f,
+// buffers [n][5][Nfp] of the state's type
+template <typename T>
+cudaError_t launch_halo_pack(const T* q, int Np, int Nfp, const int32_t* ef, const int32_t* fmask,
+                             int64_t n, T* buf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_halo_unpack(T* q, int Np, int Nfp, const int32_t* ef, const int32_t* fmask,
+                               int64_t n, const T* buf, cudaStream_t s);
 cudaError_t launch_totals(const double* q, const double* geo, const double* mass_w, int64_t K,
                           int Np, double* partial, int nblocks, double* out, cudaStream_t s);
 

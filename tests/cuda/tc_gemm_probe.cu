@@ -191,8 +191,22 @@ __global__ void tc_wait_timeout_kernel(uint32_t max_tries, int* status) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = slot;
-  const bool ok = tc::mbar_wait(&mbar, 0, max_tries);
+  uint32_t phase = 0;
+  const bool ok = tc::mbar_wait(&mbar, phase, max_tries);
   if (!ok && tid == 0) atomicOr(status, 1);
+  phase ^= 1u;                        // the stage kernel flips the parity after every wait
+  if (tid == 0) {
+    // the stage kernel's cleanup wait after a wait that gave up asks about
+    // the parity that timed out (phase ^ 1): it must spin to its limit here,
+    // since nothing ever completes that phase; the parity `phase` itself
+    // names the phase before it, which counts as complete at once
+    uint32_t used = 0;
+    while (used < max_tries && !tc::mbar_try_wait(&mbar, phase ^ 1u)) ++used;
+    status[1] = int(used);
+    used = 0;
+    while (used < max_tries && !tc::mbar_try_wait(&mbar, phase)) ++used;
+    status[2] = int(used);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {

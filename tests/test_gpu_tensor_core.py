@@ -120,11 +120,16 @@ def test_bounded_completion_wait_gives_up_and_the_device_stays_usable(cuda_devic
     import torch
     probe.tc_wait_timeout_probe.restype = ctypes.c_int
     probe.tc_wait_timeout_probe.argtypes = [ctypes.c_uint, ctypes.c_void_p]
-    st = torch.zeros(1, dtype=torch.int32, device=cuda_device)
+    st = torch.zeros(3, dtype=torch.int32, device=cuda_device)
     t0 = time.perf_counter()
     assert probe.tc_wait_timeout_probe(1 << 12, st.data_ptr()) == 0
     assert time.perf_counter() - t0 < 10.0
-    assert int(st.item()) == 1
+    status, cleanup_tries, other_parity_tries = (int(v) for v in st.cpu())
+    assert status == 1
+    # the cleanup wait (on the parity that timed out) really waits, to its
+    # limit; the flipped parity would have returned at the first try
+    assert cleanup_tries == 1 << 12
+    assert other_parity_tries == 0
     test_tf32_mma_matches_host(cuda_device, probe, 16, 8)
 
 
