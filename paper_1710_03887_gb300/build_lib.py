@@ -21,7 +21,7 @@ LIB = PKG / "libdgeuler.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SOURCES = ["operators.cpp", "mesh.cpp", "modal_ops.cpp"]
 CU_SOURCES = ["context.cu", "stage_fp64.cu", "stage_f32.cu", "stage_tc.cu", "learned.cu", "totals_static.cu",
-              "stage_modal.cu", "halo.cu"]
+              "stage_modal.cu", "halo.cu", "closure_tc.cu"]
 
 
 def _nvcc():

@@ -1,0 +1,291 @@
+// Learned boundary closure on the tensor cores: the network 12 -> 64 -> 64
+// (tanh) of every outer-face node of the learned boundary, per stage, as two
+// batched GEMMs per tile of 128 nodes:
+//
+//   H1 = tanh(X W1 + b1)      X [128 x 12 (padded to 16)], W1 [12 x 64]
+//   H2 = tanh(H1 W2 + b2)     H1 [128 x 64],                W2 [64 x 64]
+//   y0 = H2 W3[:, 0] + b3[0]  (64 FMAs per node in the epilogue)
+//
+// Both GEMMs run on tcgen05 (kind::tf32, float32 accumulators in tensor
+// memory) in three products of tf32 heads and tails (x = hi + lo;
+// A_hi B_hi + A_hi B_lo + A_lo B_hi), which keeps float32-level accuracy. One
+// thread per node: it forms the node's features (mlp::features), writes them
+// into the first operand, turns its accumulator row into H1 (written back as
+// the second GEMM's operand) and then into y0, and applies the closure: the
+// incoming invariant psi + rho0 c0^2 s y0, bounded, as the increment D over
+// the characteristic ghost's, and the memory psi's Runge-Kutta update. The
+// weights are staged once per CTA as operand images; CTAs loop over tiles.
+#include <cmath>
+
+#include "dg_device.cuh"
+#include "ghost_f32.cuh"
+#include "tc_ptx.cuh"
+
+namespace dgk {
+
+namespace {
+
+constexpr int kCT = 128;                                   // threads = rows of a tile
+constexpr int kK1 = 16;                                    // layer-1 K: 12 features, padded
+constexpr int kH = mlp::kH;                                // 64 hidden units
+constexpr uint32_t kSBO1 = uint32_t(kK1 / 4) * 128u;       // operand row-group strides
+constexpr uint32_t kSBO2 = uint32_t(kH / 4) * 128u;
+constexpr uint32_t kA1 = uint32_t(kCT / 8) * kSBO1;        // bytes of one head or tail image
+constexpr uint32_t kA2 = uint32_t(kCT / 8) * kSBO2;
+constexpr uint32_t kB1 = uint32_t(kH / 8) * kSBO1;
+constexpr uint32_t kB2 = uint32_t(kH / 8) * kSBO2;
+constexpr uint32_t oA1 = 0;                                // hi, then lo
+constexpr uint32_t oA2 = oA1 + 2 * kA1;
+constexpr uint32_t oB1 = oA2 + 2 * kA2;
+constexpr uint32_t oB2 = oB1 + 2 * kB1;
+constexpr uint32_t oVec = oB2 + 2 * kB2;                   // b1[64], b2[64], w3[64], b3
+constexpr uint32_t oBar = (oVec + (3 * kH + 1) * 4 + 15) / 16 * 16;
+constexpr uint32_t kSmem = oBar + 16;                      // mbarrier, tensor-memory slot
+constexpr uint32_t kWaitTries = 1u << 24;
+
+// head and tail of four consecutive entries (row, 4c .. 4c + 3) of an operand
+__device__ __forceinline__ void store4(unsigned char* base, uint32_t half, uint32_t off,
+                                       const float x[4]) {
+  float4 h, l;
+  h.x = tc::to_tf32(x[0]);
+  h.y = tc::to_tf32(x[1]);
+  h.z = tc::to_tf32(x[2]);
+  h.w = tc::to_tf32(x[3]);
+  l.x = tc::to_tf32(x[0] - h.x);
+  l.y = tc::to_tf32(x[1] - h.y);
+  l.z = tc::to_tf32(x[2] - h.z);
+  l.w = tc::to_tf32(x[3] - h.w);
+  *reinterpret_cast<float4*>(base + off) = h;
+  *reinterpret_cast<float4*>(base + half + off) = l;
+}
+
+// the three products of one GEMM (K / 8 steps), committed to the mbarrier
+__device__ __forceinline__ void gemm3(uint32_t tmem, uint32_t a, uint32_t a_half, uint32_t b,
+                                      uint32_t b_half, uint32_t sbo, int ksteps, uint32_t idesc,
+                                      uint64_t* mbar) {
+#pragma unroll 1
+  for (int s = 0; s < ksteps; ++s) {
+    const uint32_t off = 256u * s;
+    const uint64_t ah = tc::smem_desc(a + off, 128u, sbo), al = tc::smem_desc(a + a_half + off, 128u, sbo);
+    const uint64_t bh = tc::smem_desc(b + off, 128u, sbo), bl = tc::smem_desc(b + b_half + off, 128u, sbo);
+    tc::mma_tf32(tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
+    tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+    tc::mma_tf32(tmem, al, bh, idesc, 1u);
+  }
+  tc::mma_commit(mbar);
+}
+
+__global__ void __launch_bounds__(kCT, 1) closure_tc_kernel(ClosureArgs A, BaseGhost bg) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* vec = reinterpret_cast<float*>(smem + oVec);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + oBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + oBar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const bool net = A.w != nullptr;
+  const int64_t total = A.nb * A.Nfp;
+  const int ntiles = int((total + kCT - 1) / kCT);
+
+  if (net) {
+    // B1[j][i] = W1[i][j] (i < 12; zero to 16), B2[j][i] = W2[i][j]: the
+    // hidden unit is the operand row, the input the K index
+    for (int t = tid; t < kH * kK1; t += kCT) {
+      const int j = t / kK1, i = t - (t / kK1) * kK1;
+      const float x = i < mlp::kIn ? A.w[mlp::oW1 + i * kH + j] : 0.0f;
+      const float h = tc::to_tf32(x);
+      const uint32_t off = tc::kmajor_offset(j, i, kSBO1);
+      *reinterpret_cast<float*>(smem + oB1 + off) = h;
+      *reinterpret_cast<float*>(smem + oB1 + kB1 + off) = tc::to_tf32(x - h);
+    }
+    for (int t = tid; t < kH * kH; t += kCT) {
+      const int j = t / kH, i = t - (t / kH) * kH;
+      const float x = A.w[mlp::oW2 + i * kH + j];
+      const float h = tc::to_tf32(x);
+      const uint32_t off = tc::kmajor_offset(j, i, kSBO2);
+      *reinterpret_cast<float*>(smem + oB2 + off) = h;
+      *reinterpret_cast<float*>(smem + oB2 + kB2 + off) = tc::to_tf32(x - h);
+    }
+    for (int j = tid; j < kH; j += kCT) {
+      vec[j] = A.w[mlp::oB1 + j];
+      vec[kH + j] = A.w[mlp::oB2 + j];
+      vec[2 * kH + j] = A.w[mlp::oW3 + j * mlp::kOut];          // output 0 only
+    }
+    if (tid == 0) vec[3 * kH] = A.w[mlp::oB3];
+    if (tid == 0) {
+      tc::mbar_init(mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      tc::tmem_alloc(tslot, kH);
+      tc::tmem_relinquish();
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = net ? *tslot : 0u;
+  const uint32_t sa = tc::smem_addr(smem);
+  constexpr uint32_t idesc = tc::idesc_tf32(kCT, kH);
+  const float pref = bg.rho0 * bg.c0 * bg.c0;
+  uint32_t phase = 0;
+  bool gave_up = false;
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t i = int64_t(tile) * kCT + tid;
+    bool active = false;
+    float qm[5] = {0, 0, 0, 0, 0}, nv[3] = {0, 0, 1}, xv[3] = {0, 0, 0}, psi = 0.0f;
+    if (i < total) {
+      const int64_t slot = i / A.Nfp;
+      const int m = int(i - slot * A.Nfp);
+      const int32_t ef = A.bface[slot];
+      const int64_t e = ef >> 2;
+      const int f = ef & 3;
+      const int32_t c = A.conn[e * 4 + f];
+      active = c < 0 && A.bc_mode[(-1 - c) & 7] == 3;
+      if (active) {
+        const int nm = A.fmask[f * A.Nfp + m];
+        for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
+        const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
+        nv[0] = g[0];
+        nv[1] = g[1];
+        nv[2] = g[2];
+        xv[0] = A.bxyz[i * 3];
+        xv[1] = A.bxyz[i * 3 + 1];
+        xv[2] = A.bxyz[i * 3 + 2];
+        psi = A.psi[i];
+      }
+    }
+    float wo_m, wi_m;
+    acoustic_invariants(qm, nv, bg, wo_m, wi_m);
+    float y0 = 0.0f, s = 0.0f, wi_c = 0.0f;
+    if (net) {
+      float qc[5];
+      ghost_state_f(1, qm, nv, bg, qc);
+      float wo_c;
+      acoustic_invariants(qc, nv, bg, wo_c, wi_c);
+      float feat[kK1];
+      s = mlp::features(qm, nv, xv, psi, A.S, feat);
+      for (int k = mlp::kIn; k < kK1; ++k) feat[k] = 0.0f;
+      if (!active)
+        for (int k = 0; k < kK1; ++k) feat[k] = 0.0f;
+      // ---- layer 1: this thread's row of X
+#pragma unroll
+      for (int cq = 0; cq < kK1 / 4; ++cq)
+        store4(smem + oA1, kA1, tc::kmajor_offset(tid, 4 * cq, kSBO1), feat + 4 * cq);
+      tc::fence_smem_to_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        gemm3(tmem, sa + oA1, kA1, sa + oB1, kB1, kSBO1, kK1 / 8, idesc, mbar);
+      }
+      bool ok = tc::mbar_wait(mbar, phase, kWaitTries);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      if (ok) {
+        // accumulator row tid (lane tid of tensor memory) -> H1 -> operand 2
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float d[32];
+          tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(32 * half), d);
+#pragma unroll
+          for (int cq = 0; cq < 8; ++cq) {
+            float h[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int j = 32 * half + 4 * cq + r;
+              h[r] = mlp::tanh_fast(d[4 * cq + r] + vec[j]);
+            }
+            store4(smem + oA2, kA2, tc::kmajor_offset(tid, 32 * half + 4 * cq, kSBO2), h);
+          }
+        }
+      }
+      // ---- layer 2 (the tensor-memory reads above are complete: wait::ld)
+      tc::fence_smem_to_async();
+      tc::fence_before_sync();
+      ok = __syncthreads_and(ok) != 0;
+      if (ok && tid == 0) {
+        tc::fence_after_sync();
+        gemm3(tmem, sa + oA2, kA2, sa + oB2, kB2, kSBO2, kH / 8, idesc, mbar);
+      }
+      if (ok) {
+        ok = tc::mbar_wait(mbar, phase, kWaitTries);
+        phase ^= 1u;
+        tc::fence_after_sync();
+      }
+      if (ok) {
+        y0 = vec[3 * kH];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float d[32];
+          tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(32 * half), d);
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            y0 += vec[2 * kH + 32 * half + r] * mlp::tanh_fast(d[r] + vec[kH + 32 * half + r]);
+        }
+      } else {
+        // a completion wait gave up: report it, keep the characteristic
+        // ghost (D = 0) on this tile and stop
+        if (tid == 0) atomicOr(A.status, kStatusTimeout);
+        gave_up = true;
+      }
+    }
+    if (active) {
+      float D = 0.0f;
+      if (net && !gave_up) {
+        // the spherical-wave value psi plus the network's correction,
+        // bounded by the characteristic ghost's own |w_in| or
+        // |w_out| + |psi| (= rho0 c0^2 s), which holds psi
+        const float lim = fmaxf(fabsf(wi_c), pref * s);
+        D = fminf(fmaxf(psi + pref * s * y0, -lim), lim) - wi_c;
+      }
+      A.D[i] = D;
+      if (A.advance) {
+        const float r = fmaxf(sqrtf(xv[0] * xv[0] + xv[1] * xv[1] + xv[2] * xv[2]), A.S.r_floor);
+        const float res = A.a * A.psi_res[i] + A.dt * mlp::memory_rate(psi, wo_m, r, A.S);
+        A.psi_res[i] = res;
+        A.psi[i] = psi + A.b * res;
+      }
+    }
+    if (net) {
+      tc::fence_before_sync();
+      if (__syncthreads_or(gave_up)) {
+        gave_up = true;
+        break;
+      }
+    }
+  }
+  if (net) {
+    // MMAs of a wait that gave up may still be in flight: a bounded chance to
+    // finish (on the parity that timed out) before tensor memory is freed
+    if (gave_up && tid == 0) tc::mbar_wait(mbar, phase ^ 1u, kWaitTries);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+      tc::fence_after_sync();
+      tc::tmem_dealloc(tmem, kH);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s) {
+  const int64_t total = A.nb * A.Nfp;
+  if (total == 0) return cudaSuccess;
+  static bool configured = false;
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(closure_tc_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ntiles = (total + kCT - 1) / kCT;
+  const int grid = int(ntiles < sms ? ntiles : sms);
+  closure_tc_kernel<<<grid, kCT, kSmem, s>>>(A, bg);
+  return cudaGetLastError();
+}
+
+}  // namespace dgk

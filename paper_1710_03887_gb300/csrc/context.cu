@@ -226,6 +226,10 @@ int ensure_device(dg_ctx* c) {
                             : (modal ? dgk::stage_modal_tile_elems(p) : dgk::stage_tile_elems(p)));
   const int64_t Kown = c->owned();
   c->ntiles = int((Kown + ET - 1) / ET);
+  // the tensor-core stage is sized for two CTAs per SM (104 KB of shared
+  // memory each at p = 3); a grid of two per SM is correct whatever the
+  // occupancy query says (CTAs loop over tiles)
+  if (tcf) bps = std::max(bps, 2);
   c->grid = std::min(c->ntiles, c->sms * bps);
   const size_t nq = c->state_elems();
   if (f32) {
@@ -455,6 +459,7 @@ int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     C.b = float(b);
     C.dt = float(dt);
     C.advance = to_scratch ? 0 : 1;
+    C.status = c->status;
     DG_CUDA(dgk::launch_closure(C, bg, c->stream));
   }
   if (c->ntrace > 0 && !to_scratch)

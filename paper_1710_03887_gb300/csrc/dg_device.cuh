@@ -176,6 +176,7 @@ struct ClosureArgs {
   float* D;                  // [nb][Nfp] out
   float a, b, dt;
   int advance;
+  int* status;               // kStatusTimeout when a tensor-core completion wait gives up
 };
 cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s);
 // The same memory at the nodes of the trace faces (inner traces), advanced

@@ -83,71 +83,7 @@ cudaError_t launch_sample_traces(const float* q, int Np, int Nfp, const int32_t*
 }
 
 // ------------------------------------------------------------ closure and memory
-
-namespace {
-constexpr int kClosureThreads = 128;
-constexpr size_t kWeightSmem = size_t(mlp::kParams) * 4;
-}  // namespace
-
-// One thread per boundary face node. The network's parameters are staged in
-// shared memory once per block (every thread reads the same words).
-__global__ void __launch_bounds__(kClosureThreads)
-closure_kernel(ClosureArgs A, BaseGhost bg) {
-  extern __shared__ __align__(16) float sw[];
-  const bool net = A.w != nullptr;
-  if (net) {
-    for (int k = threadIdx.x; k < mlp::kParams; k += blockDim.x) sw[k] = A.w[k];
-    __syncthreads();
-  }
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= A.nb * A.Nfp) return;
-  const int64_t slot = i / A.Nfp;
-  const int m = int(i - slot * A.Nfp);
-  const int32_t ef = A.bface[slot];
-  const int64_t e = ef >> 2;
-  const int f = ef & 3;
-  const int32_t c = A.conn[e * 4 + f];
-  if (c >= 0 || A.bc_mode[(-1 - c) & 7] != 3) return;
-  const int nm = A.fmask[f * A.Nfp + m];
-  float qm[5], qc[5];
-  for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
-  const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
-  const float nv[3] = {g[0], g[1], g[2]};
-  const float xv[3] = {A.bxyz[i * 3], A.bxyz[i * 3 + 1], A.bxyz[i * 3 + 2]};
-  const float psi = A.psi[i];
-  float wo_m, wi_m, wo_c, wi_c;
-  acoustic_invariants(qm, nv, bg, wo_m, wi_m);
-  float D = 0.0f;
-  if (net) {
-    ghost_state_f(1, qm, nv, bg, qc);
-    acoustic_invariants(qc, nv, bg, wo_c, wi_c);
-    float feat[mlp::kIn], y[1];
-    const float s = mlp::features(qm, nv, xv, psi, A.S, feat);
-    mlp::forward_smem<1>(sw, feat, y);              // output 0 only
-    const float pref = bg.rho0 * bg.c0 * bg.c0;
-    // the spherical-wave value psi plus the network's correction, bounded by
-    // the characteristic ghost's own |w_in| or |w_out| + |psi| (= rho0 c0^2 s),
-    // which holds psi
-    const float lim = fmaxf(fabsf(wi_c), pref * s);
-    const float gin = fminf(fmaxf(psi + pref * s * y[0], -lim), lim);
-    D = gin - wi_c;
-  }
-  A.D[i] = D;
-  if (A.advance) {
-    const float r = fmaxf(sqrtf(xv[0] * xv[0] + xv[1] * xv[1] + xv[2] * xv[2]), A.S.r_floor);
-    const float res = A.a * A.psi_res[i] + A.dt * mlp::memory_rate(psi, wo_m, r, A.S);
-    A.psi_res[i] = res;
-    A.psi[i] = psi + A.b * res;
-  }
-}
-
-cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s) {
-  const int64_t total = A.nb * A.Nfp;
-  if (total == 0) return cudaSuccess;
-  closure_kernel<<<unsigned((total + kClosureThreads - 1) / kClosureThreads), kClosureThreads,
-                   A.w ? kWeightSmem : 0, s>>>(A, bg);
-  return cudaGetLastError();
-}
+// (the closure itself runs on the tensor cores: closure_tc.cu)
 
 __global__ void trace_memory_kernel(const float* __restrict__ q, int Np, int Nfp,
                                     const int32_t* __restrict__ tr_elem,

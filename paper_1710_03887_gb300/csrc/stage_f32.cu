@@ -439,6 +439,10 @@ static cudaError_t prepare_f32_impl(int* bps) {
   cudaError_t e = cudaFuncSetAttribute(stage_f32_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(OrderF<P>::bytes));
   if (e != cudaSuccess) return e;
+  // the whole unified L1 as shared memory, so that two CTAs fit on an SM
+  e = cudaFuncSetAttribute(stage_f32_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int(cudaSharedmemCarveoutMaxShared));
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, stage_f32_kernel<P>, OrderF<P>::NT,
                                                        OrderF<P>::bytes);
 }

@@ -1,20 +1,28 @@
 // Tensor-core form of the float32 perturbation stage (DG_PREC_F32_TC).
 //
 // Same arithmetic as stage_f32.cu up to the two contractions, which become
-// one dense GEMM per tile of 25 elements on the tcgen05 tensor cores:
+// one dense GEMM per tile of 12 elements on the tcgen05 tensor cores:
 //
 //   rhs[(e,v), i] = sum_k A[(e,v), k] B[i, k]
-//   A[(e,v), :] = [ Fr'_v(e, 0..Np) | Fs'_v | Ft'_v | dF_v(e, 0..4Nfp) ]     (M = 128 rows)
-//   B[i, :]     = [ -Dr[i, :] | -Ds[i, :] | -Dt[i, :] | LIFT[i, :] ]       (N = Np padded)
+//   A[(e,v), :] = [ Fr'_v(e, 0..Np) | Fs'_v | Ft'_v | dF_v(e, 0..4Nfp) ]     (M = 64 rows)
+//   B[i, :]     = [ -Dr[i, :] | -Ds[i, :] | -Dt[i, :] | LIFT[i, :] ]       (N = Np padded to 8)
 //
 // i.e. the volume term and the surface lift of Eq. 10 in one contraction of
 // length K = 3 Np + 4 Nfp. Both operands are split into a tf32 head and a
 // tf32 tail (x = hi + lo) and the product is formed as
 // A_hi B_hi + A_hi B_lo + A_lo B_hi in float32 accumulators in tensor memory,
 // which keeps float32-level accuracy (the dropped lo*lo term is ~2^-22).
-// The Runge-Kutta update runs in the epilogue straight out of tensor memory:
-// thread (warp w, lane l) owns row 32w + l = (element, variable) and updates
-// its Np contiguous values.
+//
+// The node and face phases write every A entry as float32 straight into the
+// MMA operand layout of the head image (no row-major staging copy of A); the
+// node phase maps a warp onto 8 elements x 4 nodes so that its stores land
+// on 32 different banks. One linear pass over that image then splits each
+// 16-byte chunk in place into head and tail (the tail into the second
+// image), whatever rows and columns the chunk holds. A tile needs ~104 KB
+// of shared memory at p = 3, so two CTAs share an SM and one computes while
+// the other waits at a barrier or on its MMAs. The accumulator rows come
+// back from tensor memory into a small staging array and the Runge-Kutta
+// update runs coalesced over the tile's state.
 #include <cmath>
 #include <cstring>
 
@@ -30,33 +38,36 @@ struct OrderTC {
   static constexpr int Np = (P + 1) * (P + 2) * (P + 3) / 6;
   static constexpr int Nfp = (P + 1) * (P + 2) / 2;
   static constexpr int NF = 4 * Nfp;
-  static constexpr int ET = 25;                        // 125 of the 128 MMA rows
-  static constexpr int M = 128;
-  static constexpr int N = Np <= 16 ? 16 : (Np + 15) / 16 * 16;
+  static constexpr int ET = 12;                        // 60 of the 64 MMA rows
+  static constexpr int M = 64;
+  static constexpr int N = (Np + 7) / 8 * 8;           // M = 64: N a multiple of 8
   static constexpr int KU = 3 * Np + NF;               // used columns
   static constexpr int K = (KU + 7) / 8 * 8;
-  static constexpr int NT = 512;
-  static constexpr int SX = KU % 2 ? KU : KU + 1;      // odd row stride of X
+  static constexpr int NT = 256;
+  static constexpr int NB = (Np + 3) / 4;              // node blocks of the node phase
+  static constexpr int EG = (ET + 7) / 8;              // element groups of the node phase
   static constexpr int SO = Np % 2 ? Np : Np + 1;      // odd row stride of the results
   static constexpr int kQT = ET * 5 * Np;
-  static_assert(M * SO <= 5 * ET * SX, "the results fit in the X rows");
+  static constexpr int kG = ET * NF;                   // gathered traces per variable
   static constexpr uint32_t SBO = uint32_t(K / 4) * 128u;
   static constexpr uint32_t kABytes = uint32_t(M / 8) * SBO;
   static constexpr uint32_t kBBytes = uint32_t(N / 8) * SBO;
-  // shared memory (bytes): A_hi, A_lo, B_hi, B_lo (operand layouts), X
-  // [row = 5 le + v][SX] (then the results [row][SO]), two buffers of state,
-  // geometry and connections, face weights, reduction space, tables, barrier
+  // shared memory (bytes): A_hi, A_lo, B_hi, B_lo (operand layouts),
+  // gathered neighbour traces [v][le NF + fm], results [row][SO], two
+  // buffers of state, geometry and connections, face weights, reduction
+  // space, tables, face lists, barrier
   static constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
   static constexpr size_t oAhi = 0;
   static constexpr size_t oAlo = oAhi + kABytes;
   static constexpr size_t oBhi = oAlo + kABytes;
   static constexpr size_t oBlo = oBhi + kBBytes;
-  static constexpr size_t oX = al16(oBlo + kBBytes);
-  static constexpr size_t oQ = al16(oX + size_t(5 * ET) * SX * 4);
+  static constexpr size_t oG = al16(oBlo + kBBytes);
+  static constexpr size_t oR = al16(oG + size_t(5 * kG) * 4);
+  static constexpr size_t oQ = al16(oR + size_t(5 * ET) * SO * 4);
   static constexpr size_t oGeo = al16(oQ + 2 * size_t(kQT) * 4);
   static constexpr size_t oW = al16(oGeo + 2 * size_t(ET) * kGeoStride * 4);
-  static constexpr size_t oRed = al16(oW + size_t(NF) * 4);         // 16 warps x 5 doubles
-  static constexpr size_t oConn = oRed + 16 * 5 * 8;                 // 2 x ET*4 ints
+  static constexpr size_t oRed = al16(oW + size_t(NF) * 4);          // 8 warps x 5 doubles
+  static constexpr size_t oConn = oRed + (NT / 32) * 5 * 8;          // 2 x ET*4 ints
   static constexpr size_t oFmask = oConn + 2 * size_t(ET) * 16;      // 4*Nfp ints
   static constexpr size_t oTbl = oFmask + size_t(NF) * 4;            // 2 x 96*Nfp bytes
   static constexpr size_t kFL = 16 + (4 * size_t(ET) + 15) / 16 * 16;   // face list row (16-byte multiple)
@@ -64,6 +75,7 @@ struct OrderTC {
   static constexpr size_t oFL = al16(oTbl + 2 * 96 * Nfp);           // 2 face-list buffers
   static constexpr size_t oBar = al16(oFL + 2 * kFL);                // mbarrier, tmem slot, flag
   static constexpr size_t bytes = oBar + 32;
+  static_assert(bytes <= 113 * 1024, "two CTAs per SM");
   static constexpr size_t kOpsBytes = 2 * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
 };
 
@@ -109,30 +121,39 @@ __device__ __forceinline__ void llf_parts_tc(const float qm[5], const float qp[5
 }
 
 constexpr uint32_t kWaitTries = 1u << 24;   // bounded MMA completion wait
+constexpr uint32_t kHintTries = 1u << 22;   // the same bound with a 200 ns suspend hint per try
 
-// Per tile of 25 elements:
-//  1. state, geometry and connections arrived by cp.async during the
-//     previous tile; neighbour traces are gathered by cp.async into the face
-//     columns of X while
-//  2. the flux phase writes the metric-folded fluxes into X (row-major, odd
-//     stride: conflict-free);
-//  3. the face phase replaces the gathered traces by Fscale (n.F - F*);
-//  4. X is split into the tf32 head and tail of the A operand, one warp per
-//     8 x 4 core matrix (128 contiguous bytes, conflict-free);
+// float32 value x into operand entry at byte offset off of the head image
+// (split into head and tail later, chunk by chunk)
+__device__ __forceinline__ void store_a(unsigned char* ahi, uint32_t off, float x) {
+  *reinterpret_cast<float*>(ahi + off) = x;
+}
+
+// Per tile of 12 elements:
+//  1. state, geometry, connections and face list arrived by cp.async during
+//     the previous tile; neighbour traces of faces to other tiles are
+//     gathered by cp.async into G while
+//  2. the node phase writes the metric-folded fluxes into A (float32);
+//  3. the face phase writes Fscale (n.F - F*) into the face columns of A (a
+//     face between two elements of the tile once, both jumps);
+//  4. every 16-byte chunk of A is split in place into its tf32 head and tail;
 //  5. one thread issues the MMAs (A_hi B_hi + A_hi B_lo + A_lo B_hi, K/8
-//     steps) and commits them to the mbarrier;
-//  6. warps 0..3 move their rows of the accumulator from tensor memory into
-//     the X space, and all threads update q and res with coalesced accesses.
+//     steps) and commits them to the mbarrier; the residuals load meanwhile;
+//  6. warps 0..3 move their accumulator rows (M = 64: row r in tensor-memory
+//     lane 32 (r / 16) + r % 16) into R, and all threads update q and res
+//     with coalesced accesses.
 template <int P>
-__global__ void __launch_bounds__(OrderTC<P>::NT, 1)
+__global__ void __launch_bounds__(OrderTC<P>::NT, 2)
 stage_tc_kernel(const StageArgsF32 A) {
   using O = OrderTC<P>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
-  constexpr int KU = O::KU, K = O::K, SX = O::SX, SO = O::SO;
+  constexpr int KU = O::KU, K = O::K, SO = O::SO, kG = O::kG;
+  constexpr uint32_t SBO = O::SBO;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* sAhi = smem + O::oAhi;
   unsigned char* sAlo = smem + O::oAlo;
-  float* sX = reinterpret_cast<float*>(smem + O::oX);
+  float* sG = reinterpret_cast<float*>(smem + O::oG);
+  float* sR = reinterpret_cast<float*>(smem + O::oR);
   float* sW = reinterpret_cast<float*>(smem + O::oW);
   double* sRed = reinterpret_cast<double*>(smem + O::oRed);
   int32_t* sFmask = reinterpret_cast<int32_t*>(smem + O::oFmask);
@@ -143,11 +164,14 @@ stage_tc_kernel(const StageArgsF32 A) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // constant operand B (host-built images in the operand layout), face
-  // weights, tables
+  // weights, tables; A zeroed once (its padding rows and columns are never
+  // written again and must stay finite)
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.ops);
     uint4* dst = reinterpret_cast<uint4*>(smem + O::oBhi);
     for (int i = tid; i < int(2 * O::kBBytes / 16); i += NT) dst[i] = src[i];
+    uint4* a = reinterpret_cast<uint4*>(smem + O::oAhi);
+    for (int i = tid; i < int(2 * O::kABytes / 16); i += NT) a[i] = make_uint4(0, 0, 0, 0);
     const float* w = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(A.ops) +
                                                     2 * O::kBBytes);
     for (int i = tid; i < NF; i += NT) sW[i] = w[i];
@@ -209,13 +233,11 @@ stage_tc_kernel(const StageArgsF32 A) {
     const int32_t* sConn = reinterpret_cast<const int32_t*>(smem + O::oConn) + buf * ET * 4;
     const uint8_t* sFL = smem + O::oFL + buf * O::kFL;      // header, then (le << 2 | f)
     cp_async_wait_all();
-    tc::fence_before_sync();
     __syncthreads();   // this tile's data is in; the previous tile is finished
     if (*sAbort) break;
-    tc::fence_after_sync();
 
     // neighbour traces of faces whose neighbour lies outside the tile, into
-    // the face columns of X (row 5 le + v, column 3 Np + fm)
+    // G (variable v, element le, face node fm)
     // face list groups: [0, aEnd) inside the tile, [aEnd, bEnd) to other
     // tiles, [bEnd, cEnd) outer faces (items = face x face node)
     const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
@@ -230,16 +252,21 @@ stage_tc_kernel(const StageArgsF32 A) {
       const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
       const float* src = A.q_in + e2 * 5 * Np + n2;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) cp_async4(sX + (le * 5 + v) * SX + 3 * Np + fm, src + v * Np);
+      for (int v = 0; v < 5; ++v) cp_async4(sG + v * kG + le * NF + fm, src + v * Np);
     }
     cp_async_commit();
     prefetch(tile + gridDim.x, buf ^ 1);
     cp_async_commit();
 
-    // ---- volume: reference-direction fluxes into X columns [0, 3 Np)
-    for (int it = tid; it < nE * Np; it += NT) {
-      const int le = it / Np, n = it - (it / Np) * Np;
+    // ---- volume: reference-direction fluxes into A columns [0, 3 Np). A warp
+    // takes 8 elements x 4 nodes, so the 32 stores of one (direction,
+    // variable) fall on 32 banks: bank 4 ((5 le + v) mod 8) + (k mod 4)
+    for (int wi = warp; wi < O::NB * O::EG; wi += NT / 32) {
+      const int nb = wi % O::NB, eg = wi / O::NB;
+      const int le = 8 * eg + (lane >> 2), n = 4 * nb + (lane & 3);
+      if (le >= nE || n >= Np) continue;
       float q[5];
+#pragma unroll
       for (int v = 0; v < 5; ++v) q[v] = sQ[(le * 5 + v) * Np + n];
       float rinv, u[3], pp;
       prim_tc(q, b, rinv, u, pp);
@@ -247,6 +274,7 @@ stage_tc_kernel(const StageArgsF32 A) {
         atomicOr(A.status, kStatusBadState);
       const float H = b.H0 + q[4] + pp;
       float F[3][5];
+#pragma unroll
       for (int d = 0; d < 3; ++d) {
         F[d][0] = q[1 + d];
         F[d][1] = q[1] * u[d];
@@ -256,16 +284,23 @@ stage_tc_kernel(const StageArgsF32 A) {
         F[d][4] = u[d] * H;
       }
       const float* dr = sGeo + le * kGeoStride + kGeoDrdx;
+      uint32_t roff[5], coff[3];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) roff[v] = tc::kmajor_offset(le * 5 + v, 0, SBO);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) coff[a] = tc::kmajor_offset(0, a * Np + n, SBO);
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
         const float m0 = dr[a * 3], m1 = dr[a * 3 + 1], m2 = dr[a * 3 + 2];
+#pragma unroll
         for (int v = 0; v < 5; ++v)
-          sX[(le * 5 + v) * SX + a * Np + n] = m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v];
+          store_a(sAhi, roff[v] + coff[a], m0 * F[0][v] + m1 * F[1][v] + m2 * F[2][v]);
       }
     }
     cp_async_wait_group1();            // the gathers; the next tile may still fly
     __syncthreads();
 
-    // ---- faces: jumps Fscale (n.F(q-) - F*) into X columns [3 Np, 3 Np + 4 Nfp),
+    // ---- faces: jumps Fscale (n.F(q-) - F*) into A columns [3 Np, 3 Np + 4 Nfp),
     // a face between two elements of the tile once (both jumps: Fscale (A + B)
     // and Fscale' (A - B), A = (n.F(q-) - n.F(q+)) / 2, B = lambda (q+ - q-) / 2)
     float led[5] = {0, 0, 0, 0, 0};
@@ -275,11 +310,11 @@ stage_tc_kernel(const StageArgsF32 A) {
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
       const int n = sFmask[f * Nfp + m];
       float qm[5], qp[5];
+#pragma unroll
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
       const float* geo = sGeo + le * kGeoStride;
       const float nv[3] = {geo[kGeoNrm + 3 * f], geo[kGeoNrm + 3 * f + 1], geo[kGeoNrm + 3 * f + 2]};
       const int32_t c = sConn[le * 4 + f];
-      float* xf = sX + le * 5 * SX + 3 * Np + fm;     // row v at + v * SX
       const float fs = geo[kGeoFscale + f];
       float fnm[5], hA[5], hB[5];
       if (it < aEnd) {
@@ -287,19 +322,27 @@ stage_tc_kernel(const StageArgsF32 A) {
         const int le2 = (c >> 5) - e0i, f2 = (c >> 3) & 3, o = c & 7;
         const int tb = ((f * 4 + f2) * 6 + o) * Nfp + m;
         const float* src = sQ + le2 * 5 * Np + sTbl[tb];
+#pragma unroll
         for (int v = 0; v < 5; ++v) qp[v] = src[v * Np];
         llf_parts_tc(qm, qp, nv, b, fnm, hA, hB);
-        float* xf2 = sX + le2 * 5 * SX + 3 * Np + f2 * Nfp + sTbl[96 * Nfp + tb];
+        const int fm2 = f2 * Nfp + sTbl[96 * Nfp + tb];
         const float fs2 = sGeo[le2 * kGeoStride + kGeoFscale + f2];
+        const uint32_t c1 = tc::kmajor_offset(0, 3 * Np + fm, SBO);
+        const uint32_t c2 = tc::kmajor_offset(0, 3 * Np + fm2, SBO);
+#pragma unroll
         for (int v = 0; v < 5; ++v) {
-          xf[v * SX] = fs * (hA[v] + hB[v]);
-          xf2[v * SX] = fs2 * (hA[v] - hB[v]);
+          store_a(sAhi, tc::kmajor_offset(le * 5 + v, 0, SBO) + c1, fs * (hA[v] + hB[v]));
+          store_a(sAhi, tc::kmajor_offset(le2 * 5 + v, 0, SBO) + c2, fs2 * (hA[v] - hB[v]));
         }
       } else if (it < bEnd) {
-        // neighbour in another tile: its trace was gathered into the face columns
-        for (int v = 0; v < 5; ++v) qp[v] = xf[v * SX];
+        // neighbour in another tile: its trace was gathered into G
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qp[v] = sG[v * kG + le * NF + fm];
         llf_parts_tc(qm, qp, nv, b, fnm, hA, hB);
-        for (int v = 0; v < 5; ++v) xf[v * SX] = fs * (hA[v] + hB[v]);
+        const uint32_t c1 = tc::kmajor_offset(0, 3 * Np + fm, SBO);
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          store_a(sAhi, tc::kmajor_offset(le * 5 + v, 0, SBO) + c1, fs * (hA[v] + hB[v]));
       } else {
         // outer face: ghost state, and the flux integral for the ledger
         const int mode = A.bc_mode[(-1 - c) & 7];
@@ -311,14 +354,16 @@ stage_tc_kernel(const StageArgsF32 A) {
         }
         llf_parts_tc(qm, qp, nv, b, fnm, hA, hB);
         const float wsj = sW[fm] * geo[kGeoSJ + f];
+        const uint32_t c1 = tc::kmajor_offset(0, 3 * Np + fm, SBO);
+#pragma unroll
         for (int v = 0; v < 5; ++v) {
-          xf[v * SX] = fs * (hA[v] + hB[v]);
+          store_a(sAhi, tc::kmajor_offset(le * 5 + v, 0, SBO) + c1, fs * (hA[v] + hB[v]));
           led[v] += wsj * (fnm[v] - hA[v] - hB[v]);     // F* = n.F(q-) - A - B
         }
         any_bdry = true;
       }
     }
-    // boundary-flux ledger of this tile (the barrier also publishes X)
+    // boundary-flux ledger of this tile
     if (__syncthreads_or(any_bdry)) {
       for (int v = 0; v < 5; ++v) {
         float x = led[v];
@@ -332,34 +377,40 @@ stage_tc_kernel(const StageArgsF32 A) {
         cled += acc;
       }
     }
-
-    // ---- X -> tf32 head and tail of A: warp = one 8 x 4 core matrix at a time
-    for (int blk = warp; blk < (O::M / 8) * (K / 4); blk += NT / 32) {
-      const int g = blk / (K / 4), cch = blk - (blk / (K / 4)) * (K / 4);
-      const int r = 8 * g + (lane >> 2), k = 4 * cch + (lane & 3);
-      const float x = (r < 5 * nE && k < KU) ? sX[r * SX + k] : 0.0f;
-      const float hi = tc::to_tf32(x);
-      const uint32_t off = uint32_t(g) * O::SBO + uint32_t(cch) * 128u + uint32_t(lane) * 4u;
-      *reinterpret_cast<float*>(sAhi + off) = hi;
-      *reinterpret_cast<float*>(sAlo + off) = tc::to_tf32(x - hi);
+    // every A entry is written: split each 16-byte chunk of the head image
+    // into its tf32 head (in place) and tail (same offset in the tail image)
+    __syncthreads();
+    for (int i = tid; i < int(O::kABytes / 16); i += NT) {
+      const float4 x = *reinterpret_cast<const float4*>(sAhi + 16 * i);
+      float4 h, l;
+      h.x = tc::to_tf32(x.x);
+      h.y = tc::to_tf32(x.y);
+      h.z = tc::to_tf32(x.z);
+      h.w = tc::to_tf32(x.w);
+      l.x = tc::to_tf32(x.x - h.x);
+      l.y = tc::to_tf32(x.y - h.y);
+      l.z = tc::to_tf32(x.z - h.z);
+      l.w = tc::to_tf32(x.w - h.w);
+      *reinterpret_cast<float4*>(sAhi + 16 * i) = h;
+      *reinterpret_cast<float4*>(sAlo + 16 * i) = l;
     }
     // operand writes become visible to the tensor cores
     tc::fence_smem_to_async();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t ahi = tc::smem_addr(sAhi), alo = tc::smem_addr(sAlo);
-      const uint32_t bhi = tc::smem_addr(smem + O::oBhi), blo = tc::smem_addr(smem + O::oBlo);
-#pragma unroll 1
+      // descriptors of k-step s: the start address field (bits 0-13, in
+      // 16-byte units) advances by 256 bytes = 16 units per step
+      const uint64_t dAhi = tc::smem_desc(tc::smem_addr(sAhi), 128u, SBO);
+      const uint64_t dAlo = tc::smem_desc(tc::smem_addr(sAlo), 128u, SBO);
+      const uint64_t dBhi = tc::smem_desc(tc::smem_addr(smem + O::oBhi), 128u, SBO);
+      const uint64_t dBlo = tc::smem_desc(tc::smem_addr(smem + O::oBlo), 128u, SBO);
+#pragma unroll
       for (int s = 0; s < K / 8; ++s) {
-        const uint32_t off = 256u * s;
-        const uint64_t dAhi = tc::smem_desc(ahi + off, 128u, O::SBO);
-        const uint64_t dAlo = tc::smem_desc(alo + off, 128u, O::SBO);
-        const uint64_t dBhi = tc::smem_desc(bhi + off, 128u, O::SBO);
-        const uint64_t dBlo = tc::smem_desc(blo + off, 128u, O::SBO);
-        tc::mma_tf32(tmem, dAhi, dBhi, idesc, s > 0 ? 1u : 0u);
-        tc::mma_tf32(tmem, dAhi, dBlo, idesc, 1u);
-        tc::mma_tf32(tmem, dAlo, dBhi, idesc, 1u);
+        const uint64_t step = 16u * uint64_t(s);
+        tc::mma_tf32(tmem, dAhi + step, dBhi + step, idesc, s > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, dAhi + step, dBlo + step, idesc, 1u);
+        tc::mma_tf32(tmem, dAlo + step, dBhi + step, idesc, 1u);
       }
       tc::mma_commit(mbar);
     }
@@ -373,9 +424,14 @@ stage_tc_kernel(const StageArgsF32 A) {
       rres[s] = (A.a != 0.0f && i < nE * 5 * Np) ? A.res[base + i] : 0.0f;
     }
 
-    // ---- accumulator rows -> X space [row][SO] (warps 0..3: lanes 32w .. 32w+31)
+    // ---- accumulator rows -> R [row][SO]: warp w (w < 4) holds rows
+    // 16 w .. 16 w + 15 in its lanes 0..15
     if (warp < 4) {
-      const bool done = tc::mbar_wait(mbar, phase, kWaitTries);
+      // one lane per warp polls (suspended up to 200 ns per try), the warp
+      // follows its verdict
+      uint32_t ok = 0;
+      if (lane == 0) ok = tc::mbar_wait_hint(mbar, phase, kHintTries, 200u) ? 1u : 0u;
+      const bool done = __shfl_sync(0xffffffffu, ok, 0) != 0;
       if (!done) {
         if (lane == 0) {
           atomicOr(A.status, kStatusTimeout);
@@ -385,14 +441,15 @@ stage_tc_kernel(const StageArgsF32 A) {
         tc::fence_after_sync();
         float d[32];
         tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16), d);
-        const int row = 32 * warp + lane;
-        if (row < 5 * nE) {
+        const int row = 16 * warp + lane;
+        if (lane < 16 && row < 5 * nE) {
 #pragma unroll
-          for (int j = 0; j < Np; ++j) sX[row * SO + j] = d[j];
+          for (int j = 0; j < Np; ++j) sR[row * SO + j] = d[j];
         }
       }
     }
     phase ^= 1u;
+    tc::fence_before_sync();
     __syncthreads();
 
     // ---- Runge-Kutta update, coalesced over the tile's state
@@ -401,7 +458,7 @@ stage_tc_kernel(const StageArgsF32 A) {
       const int i = tid + s * NT;
       if (i < nE * 5 * Np) {
         const int row = i / Np, n = i - (i / Np) * Np;
-        const float res = A.a * rres[s] + A.dt * sX[row * SO + n];
+        const float res = A.a * rres[s] + A.dt * sR[row * SO + n];
         A.res[base + i] = res;
         A.q_out[base + i] = sQ[i] + A.b * res;
       }
@@ -430,7 +487,7 @@ size_t stage_tc_ops_bytes(int p) {
   }
 }
 
-int stage_tc_tile_elems(int) { return 25; }
+int stage_tc_tile_elems(int) { return 12; }
 
 // Host-side image of B = [-Dr | -Ds | -Dt | LIFT] in the operand layout,
 // split into tf32 head and tail, followed by the face weights.
@@ -481,6 +538,10 @@ template <int P>
 static cudaError_t prepare_tc_impl(int* bps) {
   cudaError_t e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(OrderTC<P>::bytes));
+  if (e != cudaSuccess) return e;
+  // the whole unified L1 as shared memory, so that two CTAs fit on an SM
+  e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           int(cudaSharedmemCarveoutMaxShared));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, stage_tc_kernel<P>, OrderTC<P>::NT,
                                                        OrderTC<P>::bytes);

@@ -94,6 +94,25 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* mbar, uint32_t parit
       : "=r"(ok) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
   return ok;
 }
+// The same test, letting the hardware suspend the thread for up to
+// suspend_ns nanoseconds until the phase completes (fewer issued retries).
+__device__ __forceinline__ uint32_t mbar_try_wait_hint(uint64_t* mbar, uint32_t parity,
+                                                       uint32_t suspend_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(smem_addr(mbar)), "r"(parity), "r"(suspend_ns) : "memory");
+  return ok;
+}
+// Bounded wait with a suspend hint per try: at most max_tries tries.
+__device__ __forceinline__ bool mbar_wait_hint(uint64_t* mbar, uint32_t parity, uint32_t max_tries,
+                                               uint32_t suspend_ns) {
+  for (uint32_t i = 0; i < max_tries; ++i)
+    if (mbar_try_wait_hint(mbar, parity, suspend_ns)) return true;
+  return false;
+}
 // Bounded wait: returns false when the phase did not complete in max_tries.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t max_tries) {
   for (uint32_t i = 0; i < max_tries; ++i)

@@ -42,12 +42,16 @@ def _mesh():
 
 
 def _close(stitched, q_ref, q0, prec):
-    """Per variable: float64 to 1e-14 of max |q|, float32 forms to 1e-6 of
-    the perturbation max |q - q0|."""
+    """Per variable: float64 to 1e-14 of max |q| (momentum: of rho0 c0 at
+    least, the scale of its flux's rounding), float32 forms to 1e-6 of the
+    perturbation from the free stream, max |q - (rho0, 0, E0)|."""
     d = np.abs(stitched - q_ref).max(axis=(0, 2))
     if prec == "fp64":
-        return d / np.abs(q_ref).max(axis=(0, 2)) < 1e-14
-    return d / np.abs(q_ref - q0).max(axis=(0, 2)) < 1e-6
+        scale = np.abs(q_ref).max(axis=(0, 2))
+        scale[1:4] = np.maximum(scale[1:4], W.RHO0_SI * np.sqrt(W.GAMMA * W.P0_SI / W.RHO0_SI))
+        return d / scale < 1e-14
+    base = W.uniform_state(q_ref.shape[0], q_ref.shape[2], W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
+    return d / np.abs(q_ref - base).max(axis=(0, 2)) < 1e-6
 
 
 def _single(p, prec, xyz, EToV, q0, dt, steps, dev):
@@ -117,8 +121,13 @@ def test_emulated_ranks_reproduce_the_single_domain_run(cuda_device, p, prec):
         S.close()
     assert not np.isnan(stitched).any()
     assert np.all(_close(stitched, q_ref, q0, prec)), np.abs(stitched - q_ref).max(axis=(0, 2))
+    # totals: float64 sums in another order (per rank, then over the ranks);
+    # in the float32 forms the summed states themselves differ by float32
+    # ulps of the perturbation (~1e-3 of an energy perturbation of ~1e4 at
+    # ~2.6e4 nodes): 1e-10 of the totals
     scale = np.abs(tot_ref).max()
-    np.testing.assert_allclose(tot, tot_ref, rtol=1e-13, atol=1e-13 * scale)
+    rt = 1e-13 if prec == "fp64" else 1e-10
+    np.testing.assert_allclose(tot, tot_ref, rtol=rt, atol=rt * scale)
     np.testing.assert_allclose(led, led_ref, rtol=1e-9, atol=1e-13 * scale)
 
 
@@ -220,6 +229,6 @@ def test_partitioned_solver_two_processes(cuda_device):
         stitched[ids] = q
         assert t == pytest.approx(4 * 2e-6, rel=1e-15)
         scale = np.abs(tot_ref).max()
-        np.testing.assert_allclose(tot, tot_ref, rtol=1e-13, atol=1e-13 * scale)
+        np.testing.assert_allclose(tot, tot_ref, rtol=1e-10, atol=1e-10 * scale)
         np.testing.assert_allclose(led, led_ref, rtol=1e-9, atol=1e-13 * scale)
     assert np.all(_close(stitched, q_ref, q0, "f32")), np.abs(stitched - q_ref).max(axis=(0, 2))
