@@ -551,7 +551,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     t_eval = time.perf_counter() - t0 - t_rec - t_train
     m = measure_form(args, "f32", xyz, EToV, dev, stream, dist, world, sample_clocks=False,
                      mlp=(w, WORKLOAD["radius"]))
-    return {
+    return ({
         "config": (f"radius-2 ball on the n={n} lattice ({len(nested.big[1])} tets), truncated at "
                    f"r=1 ({len(nested.small[1])} tets); p=3 float32; {runs} seeded pulse runs "
                    f"(centre |x|<0.5, width 0.2-0.4, amplitude 0.1-10% p0) sampled every "
@@ -570,7 +570,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
         "bench_workload_learned_bc": {"value": m["value"], "unit": UNIT,
                                       "ms_per_step": m["ms"] / args.steps,
                                       "avg_stage_launch_ms": m["kms"] / max(m["klaunch"], 1)},
-    }
+    }, w)
 
 
 def rest_cfl_dt(xyz, EToV, order, p_fast, rho_fast, cfl=0.5):
@@ -822,57 +822,92 @@ def paper_config_section(args, xyz, EToV, dev, stream):
     return out
 
 
-def production_section(args, dev, stream):
-    """The production-size configuration in the float32 form: p = 4 on the
-    7,986,000-element cube lattice (n = 110, 1.4e9 DOF), a pulse at rest,
-    the characteristic condition; timed like the bench workload."""
+def far_field_probes(n=32, radius=2.5):
+    """n points on the half-sphere of the given radius in front of the bell
+    (x > 0 about the bell's centre), spread by a Fibonacci spiral."""
+    k = np.arange(n) + 0.5
+    z = k / n                                     # cos of the angle from the axis, in (0, 1)
+    phi = np.pi * (1.0 + 5.0 ** 0.5) * k
+    r = np.sqrt(1.0 - z * z)
+    return radius * np.column_stack([z, r * np.cos(phi), r * np.sin(phi)])
+
+
+def production_section(args, dev, stream, weights=None):
+    """The production configuration: the horn in a sphere of radius 3 about
+    its bell's centre, with the region behind the bell kept (type A, ~8M
+    tets) and truncated (type B half-ball), p = 4, the float32 perturbation
+    form (the tensor-core form covers p <= 3), slip walls, the 10 % p0 inflow
+    pulse at the mouthpiece, the learned closure on the outer sphere
+    (``weights``: the network trained by the learned-closure section, else
+    the spherical-wave memory alone) and 32 far-field pressure probes at
+    radius 2.5; coordinates are shifted so the bell's centre is the origin,
+    the centre of the closure's spherical memory. Timed like the bench
+    workload."""
     import torch
     from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import learned_bc as LB
     from paper_1710_03887_gb300 import workloads as W
-    t0 = time.perf_counter()
-    xyz, EToV = W.kuhn_cube(110, jitter=0.1, seed=5)
-    S = B.Solver(4, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
-    S.set_stream(stream.cuda_stream)
-    S.upload_mesh(xyz, EToV)
-    Np, K = S.Np, S.K
-    ops = B.reference_operators(4)
-    wv = np.stack([-0.5 * (1 + ops["r"] + ops["s"] + ops["t"]), 0.5 * (1 + ops["r"]),
-                   0.5 * (1 + ops["s"]), 0.5 * (1 + ops["t"])])
-    q = torch.empty((K, 5, Np), dtype=torch.float64, device=dev)
-    dt = None
-    for k0 in range(0, K, 1 << 20):
-        k1 = min(K, k0 + (1 << 20))
-        nodes = np.einsum("kvd,vn->knd", xyz[EToV[k0:k1]], wv)
-        qc = W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, 0.1, 0.3)
-        q[k0:k1] = torch.from_numpy(qc).to(dev)
-    # the fastest state of the run: the pulse's peak, at rest
-    dt = rest_cfl_dt(xyz, EToV, 4, 1.1 * W.P0_SI, W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA))
-    setup = time.perf_counter() - t0
-    S.set_state(q)
-    S.step(1, dt)
-    S.set_state(q)
-    torch.cuda.synchronize(dev)
-    S.set_kernel_timing(True)
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    S.step(args.production_steps, dt)
-    stop.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = start.elapsed_time(stop)
-    kms, kl = S.read_kernel_timing()
-    S.set_kernel_timing(False)
-    S.sync()
-    dof = 5 * Np * K
-    avg = kms / max(kl, 1)
-    S.close()
-    return {"workload": "cube lattice n=110, 7,986,000 tets, jitter 0.1h seed 5; p=4 (Np=35); "
-                        "10% p0 pulse w=0.3; characteristic BC",
-            "elements": int(K), "dof": int(dof), "steps": args.production_steps,
+    w_net = LB.spherical_weights() if weights is None else np.asarray(weights, dtype=np.float32)
+    probes = far_field_probes()
+    out = {"order": 4, "steps": args.production_steps, "precision": "f32",
+           "closure": "trained network" if weights is not None else "spherical-wave memory",
+           "probes": "32 points at radius 2.5 about the bell's centre (Fibonacci half-sphere)"}
+    for name, kw in (("kept", dict(shape="sphere", room_length=3.0, behind=2.0, m1=3, growth=1.16,
+                                   aspect=2.5)),
+                     ("truncated", dict(shape="sphere", room_length=3.0))):
+        t0 = time.perf_counter()
+        xyz, EToV, tag, info = W.horn_in_room(**kw)
+        xyz = xyz - np.array([info["bell_x"], 0.0, 0.0])        # bell centre at the origin
+        S = B.Solver(4, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
+        S.set_stream(stream.cuda_stream)
+        S.upload_mesh(xyz, EToV, face_tag=tag)
+        S.set_bc(W.HORN_OUTER, B.DG_BC_LEARNED)
+        S.set_bc(W.HORN_WALL, B.DG_BC_SLIP_WALL)
+        S.set_bc(W.HORN_MOUTHPIECE, B.DG_BC_INFLOW_PULSE)
+        S.set_inflow(0.05, 565.0)
+        S.set_bc_mlp(w_net, 3.0)
+        S.set_probes(probes, capacity=max(args.production_steps, 1))
+        q0 = torch.empty((S.K, 5, S.Np), dtype=torch.float64, device=dev)
+        q0[:] = torch.from_numpy(W.uniform_state(1, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI,
+                                                 W.GAMMA)).to(dev)
+        # the fastest state of the run: the inflow pulse's peak, at rest
+        dt = rest_cfl_dt(xyz, EToV, 4, 1.1 * W.P0_SI, W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA))
+        setup = time.perf_counter() - t0
+        S.set_state(q0)
+        S.step(1, dt)
+        S.set_state(q0)
+        S.read_probes()
+        torch.cuda.synchronize(dev)
+        S.set_kernel_timing(True)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        S.step(args.production_steps, dt)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = start.elapsed_time(stop)
+        kms, kl = S.read_kernel_timing()
+        S.set_kernel_timing(False)
+        series = S.read_probes(args.production_steps)
+        led = S.boundary_flux()
+        S.sync()
+        dof = 5 * S.Np * S.K
+        avg = kms / max(kl, 1)
+        out[name] = {
+            "elements": int(S.K), "horn_elements": info["n_horn"], "dof": int(dof),
+            "lattice": {k: v for k, v in kw.items() if k != "shape"},
             "value": dof * args.production_steps / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms / args.production_steps, "avg_stage_launch_ms": avg,
-            "stage_tflops": stage_flops_per_element(4) * K / (avg * 1e-3) / 1e12,
+            "ms_per_step": ms / args.production_steps, "dt": dt,
+            "avg_stage_launch_ms_with_closure": avg,
+            "stage_tflops": stage_flops_per_element(4) * S.K / (avg * 1e-3) / 1e12,
+            "mass_in_through_mouthpiece": float(-led[0]),
+            "probe_max_abs_dp_rel_p0": float(np.abs(series[..., 4] - series[:1, :, 4]).max()
+                                             * (W.GAMMA - 1.0) / W.P0_SI),
             "setup_seconds": setup}
+        S.close()
+        del q0
+        torch.cuda.empty_cache()
+    return out
 
 
 # six probes near the axes at r = 0.5: images of one point inside an element
@@ -1084,7 +1119,7 @@ def run_gpu(args, rank, world):
         line["f32_vs_fp64_%d" % args.c2_steps] = c2_section(args, xyz, EToV, dev, stream)
     if args.learned_n > 0:
         # rank 0 only, after the replicas' timed regions: no barrier inside
-        lb = learned_bc_section(args, xyz, EToV, dev, stream, None, 1)
+        lb, trained = learned_bc_section(args, xyz, EToV, dev, stream, None, 1)
         lb["bench_workload_learned_bc"]["vs_characteristic"] = (
             lb["bench_workload_learned_bc"]["value"] / res["f32"]["value"] if "f32" in res else None)
         line["learned_bc"] = lb
@@ -1097,7 +1132,8 @@ def run_gpu(args, rank, world):
     if args.paper_steps > 0:
         line["paper_configuration"] = paper_config_section(args, xyz, EToV, dev, stream)
     if args.production_steps > 0:
-        line["production"] = production_section(args, dev, stream)
+        line["production"] = production_section(args, dev, stream,
+                                                 trained if args.learned_n > 0 else None)
     if not args.no_cpu_baseline:
         v, sample, _ = cpu_sample_run(args.cpu_steps, 1, xyz, EToV)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -1128,8 +1164,10 @@ def main():
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")
     ap.add_argument("--production-steps", type=int, default=0,
-                    help="steps timed on the p=4, 8M-element configuration (0: skip it; it "
-                         "builds the mesh on the host first, about a minute)")
+                    help="steps timed on the production configuration: p=4, the horn in a "
+                         "radius-3 sphere with the region behind the bell kept (~8M tets) and "
+                         "truncated, learned closure, 32 far-field probes (0: skip it; it builds "
+                         "the meshes on the host first, a few minutes)")
     ap.add_argument("--paper-steps", type=int, default=50,
                     help="steps timed per form in the paper-configuration section (0: skip it)")
     ap.add_argument("--locality-steps", type=int, default=20,

@@ -144,3 +144,14 @@ def test_precision_comparison_figures(bench):
     c0 = np.sqrt(gamma * p0 / rho0)
     assert out["balance_rel_f32"][2] == pytest.approx(2e-3 / (5.0 * c0))   # momentum: mass x c0
     assert out["ledger_f32_minus_fp64_rel_to_totals"][4] == pytest.approx(2e-3 / 1e6)
+
+
+def test_far_field_probes_cover_the_front_half_sphere(bench):
+    import numpy as np
+    p = bench.far_field_probes(32, 2.5)
+    assert p.shape == (32, 3)
+    np.testing.assert_allclose(np.linalg.norm(p, axis=1), 2.5, rtol=1e-14)
+    assert np.all(p[:, 0] > 0)
+    # spread: no two probes closer than a fifth of the mean spacing on the half-sphere
+    d = np.linalg.norm(p[:, None] - p[None], axis=2) + np.eye(32) * 1e9
+    assert d.min() > 0.2 * np.sqrt(2 * np.pi * 2.5 ** 2 / 32)
