@@ -8,12 +8,17 @@
 //
 // Both GEMMs run on tcgen05 (kind::tf32, float32 accumulators in tensor
 // memory) in three products of tf32 heads and tails (x = hi + lo;
-// A_hi B_hi + A_hi B_lo + A_lo B_hi), which keeps float32-level accuracy. One
-// thread per node: it forms the node's features (mlp::features), writes them
-// into the first operand, turns its accumulator row into H1 (written back as
-// the second GEMM's operand) and then into y0, and applies the closure: the
-// incoming invariant psi + rho0 c0^2 s y0, bounded, as the increment D over
-// the characteristic ghost's, and the memory psi's Runge-Kutta update. The
+// A_hi B_hi + A_hi B_lo + A_lo B_hi), which keeps float32-level accuracy.
+//
+// Two threads per node row: thread (row r, half h) reads accumulator columns
+// 32h .. 32h + 31 of lane r (warps w and w + 4 share lane quadrant w mod 4)
+// and handles hidden units 32h .. 32h + 31. The second GEMM runs as two
+// K-halves through one 32-column operand buffer (half 0's units, then half
+// 1's), so a CTA needs ~89 KB of shared memory and two CTAs (16 warps) share
+// an SM. The h = 0 thread of a row forms the node's features, and at the end
+// combines the two halves of y0 and applies the closure: the incoming
+// invariant psi + rho0 c0^2 s y0, bounded, as the increment D over the
+// characteristic ghost's, and the memory psi's Runge-Kutta update. The
 // weights are staged once per CTA as operand images; CTAs loop over tiles.
 #include <cmath>
 
@@ -25,13 +30,16 @@ namespace dgk {
 
 namespace {
 
-constexpr int kCT = 128;                                   // threads = rows of a tile
+constexpr int kRows = 128;                                 // node rows of a tile
+constexpr int kCT = 2 * kRows;                             // threads: two per row
 constexpr int kK1 = 16;                                    // layer-1 K: 12 features, padded
 constexpr int kH = mlp::kH;                                // 64 hidden units
+constexpr int kHH = kH / 2;                                // units of one half
 constexpr uint32_t kSBO1 = uint32_t(kK1 / 4) * 128u;       // operand row-group strides
-constexpr uint32_t kSBO2 = uint32_t(kH / 4) * 128u;
-constexpr uint32_t kA1 = uint32_t(kCT / 8) * kSBO1;        // bytes of one head or tail image
-constexpr uint32_t kA2 = uint32_t(kCT / 8) * kSBO2;
+constexpr uint32_t kSBOh = uint32_t(kHH / 4) * 128u;       // layer-2 A (one K-half)
+constexpr uint32_t kSBO2 = uint32_t(kH / 4) * 128u;        // layer-2 B (whole K)
+constexpr uint32_t kA1 = uint32_t(kRows / 8) * kSBO1;      // bytes of one head or tail image
+constexpr uint32_t kA2 = uint32_t(kRows / 8) * kSBOh;
 constexpr uint32_t kB1 = uint32_t(kH / 8) * kSBO1;
 constexpr uint32_t kB2 = uint32_t(kH / 8) * kSBO2;
 constexpr uint32_t oA1 = 0;                                // hi, then lo
@@ -39,9 +47,11 @@ constexpr uint32_t oA2 = oA1 + 2 * kA1;
 constexpr uint32_t oB1 = oA2 + 2 * kA2;
 constexpr uint32_t oB2 = oB1 + 2 * kB1;
 constexpr uint32_t oVec = oB2 + 2 * kB2;                   // b1[64], b2[64], w3[64], b3
-constexpr uint32_t oBar = (oVec + (3 * kH + 1) * 4 + 15) / 16 * 16;
+constexpr uint32_t oPart = (oVec + (3 * kH + 1) * 4 + 15) / 16 * 16;   // y0 of half 1 [128]
+constexpr uint32_t oBar = oPart + kRows * 4;
 constexpr uint32_t kSmem = oBar + 16;                      // mbarrier, tensor-memory slot
-constexpr uint32_t kWaitTries = 1u << 24;
+static_assert(kSmem <= 113u * 1024u, "two CTAs per SM");
+constexpr uint32_t kHintTries = 1u << 22;                  // bounded waits, 200 ns hint per try
 
 // head and tail of four consecutive entries (row, 4c .. 4c + 3) of an operand
 __device__ __forceinline__ void store4(unsigned char* base, uint32_t half, uint32_t off,
@@ -59,31 +69,43 @@ __device__ __forceinline__ void store4(unsigned char* base, uint32_t half, uint3
   *reinterpret_cast<float4*>(base + half + off) = l;
 }
 
-// the three products of one GEMM (K / 8 steps), committed to the mbarrier
-__device__ __forceinline__ void gemm3(uint32_t tmem, uint32_t a, uint32_t a_half, uint32_t b,
-                                      uint32_t b_half, uint32_t sbo, int ksteps, uint32_t idesc,
-                                      uint64_t* mbar) {
+// the three products of one GEMM (ksteps steps of K = 8), committed to the
+// mbarrier; a_sbo / b_sbo: row-group strides of the two operands
+__device__ __forceinline__ void gemm3(uint32_t tmem, uint32_t a, uint32_t a_half, uint32_t a_sbo,
+                                      uint32_t b, uint32_t b_half, uint32_t b_sbo, int ksteps,
+                                      uint32_t accumulate, uint32_t idesc, uint64_t* mbar) {
 #pragma unroll 1
   for (int s = 0; s < ksteps; ++s) {
     const uint32_t off = 256u * s;
-    const uint64_t ah = tc::smem_desc(a + off, 128u, sbo), al = tc::smem_desc(a + a_half + off, 128u, sbo);
-    const uint64_t bh = tc::smem_desc(b + off, 128u, sbo), bl = tc::smem_desc(b + b_half + off, 128u, sbo);
-    tc::mma_tf32(tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
+    const uint64_t ah = tc::smem_desc(a + off, 128u, a_sbo);
+    const uint64_t al = tc::smem_desc(a + a_half + off, 128u, a_sbo);
+    const uint64_t bh = tc::smem_desc(b + off, 128u, b_sbo);
+    const uint64_t bl = tc::smem_desc(b + b_half + off, 128u, b_sbo);
+    tc::mma_tf32(tmem, ah, bh, idesc, (s > 0 || accumulate) ? 1u : 0u);
     tc::mma_tf32(tmem, ah, bl, idesc, 1u);
     tc::mma_tf32(tmem, al, bh, idesc, 1u);
   }
   tc::mma_commit(mbar);
 }
 
-__global__ void __launch_bounds__(kCT, 1) closure_tc_kernel(ClosureArgs A, BaseGhost bg) {
+// every warp waits for the current phase: lane 0 polls, the warp follows
+__device__ __forceinline__ bool warp_wait(uint64_t* mbar, uint32_t phase) {
+  uint32_t ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = tc::mbar_wait_hint(mbar, phase, kHintTries, 200u) ? 1u : 0u;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseGhost bg) {
   extern __shared__ __align__(128) unsigned char smem[];
   float* vec = reinterpret_cast<float*>(smem + oVec);
+  float* part = reinterpret_cast<float*>(smem + oPart);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + oBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + oBar + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kRows - 1), half = tid >> 7;      // warp w: lane quadrant w mod 4
   const bool net = A.w != nullptr;
   const int64_t total = A.nb * A.Nfp;
-  const int ntiles = int((total + kCT - 1) / kCT);
+  const int ntiles = int((total + kRows - 1) / kRows);
 
   if (net) {
     // B1[j][i] = W1[i][j] (i < 12; zero to 16), B2[j][i] = W2[i][j]: the
@@ -109,8 +131,8 @@ __global__ void __launch_bounds__(kCT, 1) closure_tc_kernel(ClosureArgs A, BaseG
       vec[kH + j] = A.w[mlp::oB2 + j];
       vec[2 * kH + j] = A.w[mlp::oW3 + j * mlp::kOut];          // output 0 only
     }
-    if (tid == 0) vec[3 * kH] = A.w[mlp::oB3];
     if (tid == 0) {
+      vec[3 * kH] = A.w[mlp::oB3];
       tc::mbar_init(mbar, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -123,17 +145,18 @@ __global__ void __launch_bounds__(kCT, 1) closure_tc_kernel(ClosureArgs A, BaseG
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = net ? *tslot : 0u;
+  const uint32_t tq = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(kHH * half);
   const uint32_t sa = tc::smem_addr(smem);
-  constexpr uint32_t idesc = tc::idesc_tf32(kCT, kH);
+  constexpr uint32_t idesc = tc::idesc_tf32(kRows, kH);
   const float pref = bg.rho0 * bg.c0 * bg.c0;
   uint32_t phase = 0;
   bool gave_up = false;
 
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t i = int64_t(tile) * kCT + tid;
+    const int64_t i = int64_t(tile) * kRows + row;
     bool active = false;
     float qm[5] = {0, 0, 0, 0, 0}, nv[3] = {0, 0, 1}, xv[3] = {0, 0, 0}, psi = 0.0f;
-    if (i < total) {
+    if (half == 0 && i < total) {
       const int64_t slot = i / A.Nfp;
       const int m = int(i - slot * A.Nfp);
       const int32_t ef = A.bface[slot];
@@ -154,82 +177,82 @@ __global__ void __launch_bounds__(kCT, 1) closure_tc_kernel(ClosureArgs A, BaseG
         psi = A.psi[i];
       }
     }
-    float wo_m, wi_m;
-    acoustic_invariants(qm, nv, bg, wo_m, wi_m);
-    float y0 = 0.0f, s = 0.0f, wi_c = 0.0f;
+    float wo_m = 0.0f, y0 = 0.0f, s = 0.0f, wi_c = 0.0f;
+    if (half == 0) {
+      float wi_m;
+      acoustic_invariants(qm, nv, bg, wo_m, wi_m);
+    }
     if (net) {
-      float qc[5];
-      ghost_state_f(1, qm, nv, bg, qc);
-      float wo_c;
-      acoustic_invariants(qc, nv, bg, wo_c, wi_c);
-      float feat[kK1];
-      s = mlp::features(qm, nv, xv, psi, A.S, feat);
-      for (int k = mlp::kIn; k < kK1; ++k) feat[k] = 0.0f;
-      if (!active)
-        for (int k = 0; k < kK1; ++k) feat[k] = 0.0f;
-      // ---- layer 1: this thread's row of X
+      if (half == 0) {
+        float qc[5], wo_c;
+        ghost_state_f(1, qm, nv, bg, qc);
+        acoustic_invariants(qc, nv, bg, wo_c, wi_c);
+        float feat[kK1];
+        s = mlp::features(qm, nv, xv, psi, A.S, feat);
+        for (int k = 0; k < kK1; ++k)
+          if (k >= mlp::kIn || !active) feat[k] = 0.0f;
 #pragma unroll
-      for (int cq = 0; cq < kK1 / 4; ++cq)
-        store4(smem + oA1, kA1, tc::kmajor_offset(tid, 4 * cq, kSBO1), feat + 4 * cq);
+        for (int cq = 0; cq < kK1 / 4; ++cq)
+          store4(smem + oA1, kA1, tc::kmajor_offset(row, 4 * cq, kSBO1), feat + 4 * cq);
+      }
+      // ---- layer 1: X W1 -> tensor memory columns 0..63
       tc::fence_smem_to_async();
       tc::fence_before_sync();
       __syncthreads();
       if (tid == 0) {
         tc::fence_after_sync();
-        gemm3(tmem, sa + oA1, kA1, sa + oB1, kB1, kSBO1, kK1 / 8, idesc, mbar);
+        gemm3(tmem, sa + oA1, kA1, kSBO1, sa + oB1, kB1, kSBO1, kK1 / 8, 0u, idesc, mbar);
       }
-      bool ok = tc::mbar_wait(mbar, phase, kWaitTries);
+      bool ok = warp_wait(mbar, phase);
       phase ^= 1u;
       tc::fence_after_sync();
+      float h1[kHH];
       if (ok) {
-        // accumulator row tid (lane tid of tensor memory) -> H1 -> operand 2
+        float d[32];
+        tc::tmem_ld_32x32b_x32(tq, d);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float d[32];
-          tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(32 * half), d);
+        for (int j = 0; j < kHH; ++j) h1[j] = mlp::tanh_fast(d[j] + vec[kHH * half + j]);
+      }
+      // ---- layer 2 in two K-halves through one operand buffer: units of
+      // half 0, then of half 1 (the tensor-memory reads above are complete)
+#pragma unroll 1
+      for (int kh = 0; kh < 2; ++kh) {
+        if (ok && half == kh) {
 #pragma unroll
-          for (int cq = 0; cq < 8; ++cq) {
-            float h[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int j = 32 * half + 4 * cq + r;
-              h[r] = mlp::tanh_fast(d[4 * cq + r] + vec[j]);
-            }
-            store4(smem + oA2, kA2, tc::kmajor_offset(tid, 32 * half + 4 * cq, kSBO2), h);
-          }
+          for (int cq = 0; cq < kHH / 4; ++cq)
+            store4(smem + oA2, kA2, tc::kmajor_offset(row, 4 * cq, kSBOh), h1 + 4 * cq);
         }
-      }
-      // ---- layer 2 (the tensor-memory reads above are complete: wait::ld)
-      tc::fence_smem_to_async();
-      tc::fence_before_sync();
-      ok = __syncthreads_and(ok) != 0;
-      if (ok && tid == 0) {
-        tc::fence_after_sync();
-        gemm3(tmem, sa + oA2, kA2, sa + oB2, kB2, kSBO2, kH / 8, idesc, mbar);
-      }
-      if (ok) {
-        ok = tc::mbar_wait(mbar, phase, kWaitTries);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        if (tid == 0) {
+          tc::fence_after_sync();
+          gemm3(tmem, sa + oA2, kA2, kSBOh, sa + oB2 + 1024u * kh, kB2, kSBO2, kHH / 8,
+                uint32_t(kh), idesc, mbar);
+        }
+        ok = warp_wait(mbar, phase);
         phase ^= 1u;
         tc::fence_after_sync();
       }
+      float ypart = 0.0f;
       if (ok) {
-        y0 = vec[3 * kH];
+        float d[32];
+        tc::tmem_ld_32x32b_x32(tq, d);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float d[32];
-          tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(32 * half), d);
-#pragma unroll
-          for (int r = 0; r < 32; ++r)
-            y0 += vec[2 * kH + 32 * half + r] * mlp::tanh_fast(d[r] + vec[kH + 32 * half + r]);
-        }
-      } else {
+        for (int j = 0; j < kHH; ++j)
+          ypart += vec[2 * kH + kHH * half + j] * mlp::tanh_fast(d[j] + vec[kH + kHH * half + j]);
+      }
+      if (half == 1) part[row] = ypart;
+      if (__syncthreads_or(!ok)) {
         // a completion wait gave up: report it, keep the characteristic
         // ghost (D = 0) on this tile and stop
         if (tid == 0) atomicOr(A.status, kStatusTimeout);
         gave_up = true;
       }
+      y0 = vec[3 * kH] + ypart + (half == 0 ? part[row] : 0.0f);
     }
-    if (active) {
+    if (half == 0 && active) {
       float D = 0.0f;
       if (net && !gave_up) {
         // the spherical-wave value psi plus the network's correction,
@@ -248,16 +271,14 @@ __global__ void __launch_bounds__(kCT, 1) closure_tc_kernel(ClosureArgs A, BaseG
     }
     if (net) {
       tc::fence_before_sync();
-      if (__syncthreads_or(gave_up)) {
-        gave_up = true;
-        break;
-      }
+      __syncthreads();                 // operands, partial sums and tensor memory free again
+      if (gave_up) break;
     }
   }
   if (net) {
     // MMAs of a wait that gave up may still be in flight: a bounded chance to
-    // finish (on the parity that timed out) before tensor memory is freed
-    if (gave_up && tid == 0) tc::mbar_wait(mbar, phase ^ 1u, kWaitTries);
+    // finish (on the parity of that wait, phase ^ 1) before tensor memory is freed
+    if (gave_up && tid == 0) tc::mbar_wait_hint(mbar, phase ^ 1u, kHintTries, 200u);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -274,16 +295,20 @@ cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream
   if (total == 0) return cudaSuccess;
   static bool configured = false;
   if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(closure_tc_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
+    cudaError_t e = cudaFuncSetAttribute(closure_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(closure_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
     if (e != cudaSuccess) return e;
     configured = true;
   }
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t ntiles = (total + kCT - 1) / kCT;
-  const int grid = int(ntiles < sms ? ntiles : sms);
+  const int64_t ntiles = (total + kRows - 1) / kRows;
+  const int64_t want = 2 * int64_t(sms);                  // two CTAs per SM
+  const int grid = int(ntiles < want ? ntiles : want);
   closure_tc_kernel<<<grid, kCT, kSmem, s>>>(A, bg);
   return cudaGetLastError();
 }
