@@ -25,6 +25,8 @@ five-stage low-storage RK4 time step of the whole mesh.
   paper_configuration  p = 1 with RK2 on the bench mesh (the paper's own setting)
              in the paper's discretisation and the nodal forms, with device
              memory per element
+  order4     both float32 forms at p = 4 (the production configuration's order)
+             on the bench mesh, timed the same way
   locality   the float32 form on the bench mesh in lattice, Morton and random
              element order (how far tiles' gathers reach)
   horn       the horn-in-room workload (1,489,704 tets, p=3: a flared horn with
@@ -339,16 +341,18 @@ def repeat_stats(reps, steps, sm_mhz=None):
     return out
 
 
-def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_clocks, mlp=None):
+def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_clocks, mlp=None,
+                 order=None):
     """Time one arithmetic form on the bench workload; returns a dict. With
-    ``mlp`` = (weights, radius) the sphere takes the learned closure."""
+    ``mlp`` = (weights, radius) the sphere takes the learned closure;
+    ``order`` replaces the workload's polynomial order."""
     import torch
     from paper_1710_03887_gb300 import binding as B
     from paper_1710_03887_gb300 import workloads as W
     w = WORKLOAD
     prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC, "fp64": B.DG_PREC_FP64,
             "modal": B.DG_PREC_MODAL}[precision]
-    S = B.Solver(w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+    S = B.Solver(order or w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.set_stream(stream.cuda_stream)
     S.upload_mesh(xyz, EToV)
     if mlp is not None:
@@ -721,6 +725,34 @@ def domains_section(args, dev, stream):
                                               * (W.GAMMA - 1.0) / W.P0_SI)}
         S.close()
         del q0
+    return out
+
+
+def order4_section(args, xyz, EToV, dev, stream):
+    """Both float32 forms at p = 4 (Np = 35, the production configuration's
+    order) on the bench mesh, timed like the headline (median of repeated
+    regions), with the tensor-core form's difference from the SIMT form after
+    the same steps, relative to the perturbation."""
+    from paper_1710_03887_gb300 import workloads as W
+    sub = argparse.Namespace(**vars(args))
+    sub.steps = args.order4_steps
+    out = {"order": 4, "steps": sub.steps, "elements": int(len(EToV))}
+    res = {}
+    for f in ("f32", "f32_tc"):
+        m = measure_form(sub, f, xyz, EToV, dev, stream, None, 1, False, order=4)
+        res[f] = m
+        out[f] = {"value": m["value"], "unit": UNIT, "ms_per_step": m["ms"] / sub.steps,
+                  "avg_stage_launch_ms": m["kms"] / max(m["klaunch"], 1),
+                  "repeats": repeat_stats(m["reps"], sub.steps),
+                  "stage_tflops": stage_flops_per_element(4) * m["K"]
+                  / (m["kms"] / max(m["klaunch"], 1) * 1e-3) / 1e12}
+    a, b = res["f32_tc"], res["f32"]
+    base = W.uniform_state(a["q0"].shape[0], a["q0"].shape[2], W.RHO0_SI, (0, 0, 0), W.P0_SI,
+                           W.GAMMA)
+    num = np.abs(a["q_end"] - b["q_end"]).max(axis=(0, 2))
+    den = np.abs(b["q_end"] - base).max(axis=(0, 2))
+    out["f32_tc_vs_f32_max_diff_rel_to_perturbation"] = (num / den).tolist()
+    out["tc_speedup"] = a["value"] / b["value"]
     return out
 
 
@@ -1127,6 +1159,8 @@ def run_gpu(args, rank, world):
         line["horn"] = horn_section(args, dev, stream)
         if args.domains:
             line["domains"] = domains_section(args, dev, stream)
+    if args.order4_steps > 0:
+        line["order4"] = order4_section(args, xyz, EToV, dev, stream)
     if args.locality_steps > 0:
         line["locality"] = locality_section(args, xyz, EToV, dev, stream)
     if args.paper_steps > 0:
@@ -1170,6 +1204,8 @@ def main():
                          "the meshes on the host first, a few minutes)")
     ap.add_argument("--paper-steps", type=int, default=50,
                     help="steps timed per form in the paper-configuration section (0: skip it)")
+    ap.add_argument("--order4-steps", type=int, default=20,
+                    help="steps timed per float32 form at p = 4 on the bench mesh (0: skip it)")
     ap.add_argument("--locality-steps", type=int, default=20,
                     help="steps timed per element order in the locality section (0: skip it)")
     ap.add_argument("--horn-steps", type=int, default=20,

@@ -89,8 +89,8 @@ extern "C" {
                                 /* the ABI as total float64 q[K][5][Np].                 */
 #define DG_PREC_F32_TC 2        /* DG_PREC_F32 with both contractions (volume and LIFT,  */
                                 /* Eq. 10) as one tcgen05 tensor-core GEMM per tile of   */
-                                /* 25 elements, tf32 operands split in head + tail,      */
-                                /* float32 accumulation; orders 1..3                     */
+                                /* 12 elements, tf32 operands split in head + tail,      */
+                                /* float32 accumulation; orders 1..4                     */
 #define DG_PREC_MODAL 3         /* the paper's own discretisation (Appendix A): the weak */
                                 /* form of Eq. 10 in the orthonormal basis of Eq. 11,    */
                                 /* volume integral by a Gauss rule of degree 2p, surface */

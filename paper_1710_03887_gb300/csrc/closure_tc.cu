@@ -12,16 +12,21 @@
 //
 // Two threads per node row: thread (row r, half h) reads accumulator columns
 // 32h .. 32h + 31 of lane r (warps w and w + 4 share lane quadrant w mod 4)
-// and handles hidden units 32h .. 32h + 31. The second GEMM runs as two
+// and handles hidden units 32h .. 32h + 31. The first GEMM accumulates in
+// tensor-memory columns 0..63, the second in 64..127; the second runs as two
 // K-halves through one 32-column operand buffer (half 0's units, then half
-// 1's), so a CTA needs ~89 KB of shared memory and two CTAs (16 warps) share
-// an SM. The h = 0 thread of a row forms the node's features, and at the end
+// 1's, re-read from columns 0..63), which the first GEMM's operand overlays.
+// So a CTA needs ~73 KB of shared memory, no thread holds a row of hidden
+// units in registers, and three CTAs (24 warps) share an SM. The h = 0
+// thread of a row forms the node's features, and at the end
 // combines the two halves of y0 and applies the closure: the incoming
 // invariant psi + rho0 c0^2 s y0, bounded, as the increment D over the
 // characteristic ghost's, and the memory psi's Runge-Kutta update. The
-// weights are staged once per CTA as operand images; CTAs loop over tiles.
+// weights' operand images are built once per weight change and copied into
+// each CTA's shared memory; CTAs loop over tiles.
 #include <cmath>
 
+#include "cp_async.cuh"
 #include "dg_device.cuh"
 #include "ghost_f32.cuh"
 #include "tc_ptx.cuh"
@@ -42,15 +47,22 @@ constexpr uint32_t kA1 = uint32_t(kRows / 8) * kSBO1;      // bytes of one head 
 constexpr uint32_t kA2 = uint32_t(kRows / 8) * kSBOh;
 constexpr uint32_t kB1 = uint32_t(kH / 8) * kSBO1;
 constexpr uint32_t kB2 = uint32_t(kH / 8) * kSBO2;
-constexpr uint32_t oA1 = 0;                                // hi, then lo
-constexpr uint32_t oA2 = oA1 + 2 * kA1;
+static_assert(kA1 <= kA2, "the layer-1 operand overlays the layer-2 operand");
+constexpr uint32_t oA2 = 0;                                // hi, then lo
+constexpr uint32_t oA1 = oA2;                              // dead once layer 1 completes
 constexpr uint32_t oB1 = oA2 + 2 * kA2;
 constexpr uint32_t oB2 = oB1 + 2 * kB1;
 constexpr uint32_t oVec = oB2 + 2 * kB2;                   // b1[64], b2[64], w3[64], b3
-constexpr uint32_t oPart = (oVec + (3 * kH + 1) * 4 + 15) / 16 * 16;   // y0 of half 1 [128]
-constexpr uint32_t oBar = oPart + kRows * 4;
+// B1, B2 (head and tail) and the vectors form one contiguous image, built
+// once per weight change (closure_image_kernel) and copied whole per CTA
+constexpr uint32_t kImgBytes = (2 * kB1 + 2 * kB2 + (3 * kH + 1) * 4 + 15) / 16 * 16;
+static_assert(oB2 == oB1 + 2 * kB1 && oVec == oB2 + 2 * kB2 && oB1 % 16 == 0, "one image");
+constexpr uint32_t oPart = oB1 + kImgBytes;                // y0 of half 1 [128]
+constexpr uint32_t oFm = oPart + kRows * 4;               // face-node map [4 Nfp], Nfp <= 15
+constexpr uint32_t oBar = oFm + 64 * 4;
 constexpr uint32_t kSmem = oBar + 16;                      // mbarrier, tensor-memory slot
-static_assert(kSmem <= 113u * 1024u, "two CTAs per SM");
+static_assert(kSmem <= 75u * 1024u, "three CTAs per SM");
+constexpr uint32_t kCols = 2 * kH;                         // tensor-memory columns: two accumulators
 constexpr uint32_t kHintTries = 1u << 22;                  // bounded waits, 200 ns hint per try
 
 // head and tail of four consecutive entries (row, 4c .. 4c + 3) of an operand
@@ -95,7 +107,44 @@ __device__ __forceinline__ bool warp_wait(uint64_t* mbar, uint32_t phase) {
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-__global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseGhost bg) {
+// The weight image from the parameter vector w: B1[j][i] = W1[i][j] (i < 12,
+// zero to 16) and B2[j][i] = W2[i][j] in the operand layout (the hidden unit
+// is the operand row, the input the K index), each as tf32 head and tail,
+// then b1, b2, w3[:, 0] (output 0 only) and b3. One thread per entry;
+// consecutive threads read consecutive entries of a row of W.
+__global__ void closure_image_kernel(const float* __restrict__ w, unsigned char* __restrict__ img) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int n1 = kH * kK1, n2 = kH * kH;
+  float* vec = reinterpret_cast<float*>(img + 2 * kB1 + 2 * kB2);
+  if (t < n1 + n2) {
+    const bool first = t < n1;
+    const int u = first ? t : t - n1;
+    const int i = u / kH, j = u - (u / kH) * kH;
+    const float x = first ? (i < mlp::kIn ? w[mlp::oW1 + i * kH + j] : 0.0f) : w[mlp::oW2 + i * kH + j];
+    const float h = tc::to_tf32(x);
+    const uint32_t off = first ? tc::kmajor_offset(j, i, kSBO1) : 2 * kB1 + tc::kmajor_offset(j, i, kSBO2);
+    const uint32_t half = first ? kB1 : kB2;
+    *reinterpret_cast<float*>(img + off) = h;
+    *reinterpret_cast<float*>(img + off + half) = tc::to_tf32(x - h);
+  } else if (t < n1 + n2 + kH) {
+    const int j = t - n1 - n2;
+    vec[j] = w[mlp::oB1 + j];
+    vec[kH + j] = w[mlp::oB2 + j];
+    vec[2 * kH + j] = w[mlp::oW3 + j * mlp::kOut];
+  } else if (t == n1 + n2 + kH) {
+    vec[3 * kH] = w[mlp::oB3];
+  }
+}
+
+// tanh(accumulator + bias) of 16 consecutive columns of this thread's lane
+__device__ __forceinline__ void tanh16(uint32_t taddr, const float* bias, float (&h)[16]) {
+  float d[16];
+  tc::tmem_ld_32x32b_x16(taddr, d);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) h[j] = mlp::tanh_fast(d[j] + bias[j]);
+}
+
+__global__ void __launch_bounds__(kCT, 3) closure_tc_kernel(ClosureArgs A, BaseGhost bg) {
   extern __shared__ __align__(128) unsigned char smem[];
   float* vec = reinterpret_cast<float*>(smem + oVec);
   float* part = reinterpret_cast<float*>(smem + oPart);
@@ -106,40 +155,26 @@ __global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseG
   const bool net = A.w != nullptr;
   const int64_t total = A.nb * A.Nfp;
   const int ntiles = int((total + kRows - 1) / kRows);
+  // the stage kernel launched after this one may take SMs as CTAs of this
+  // grid finish: it waits for the whole grid before reading D
+  griddep_launch_dependents();
 
+  for (int j = tid; j < 4 * A.Nfp; j += kCT) reinterpret_cast<int32_t*>(smem + oFm)[j] = A.fmask[j];
   if (net) {
-    // B1[j][i] = W1[i][j] (i < 12; zero to 16), B2[j][i] = W2[i][j]: the
-    // hidden unit is the operand row, the input the K index
-    for (int t = tid; t < kH * kK1; t += kCT) {
-      const int j = t / kK1, i = t - (t / kK1) * kK1;
-      const float x = i < mlp::kIn ? A.w[mlp::oW1 + i * kH + j] : 0.0f;
-      const float h = tc::to_tf32(x);
-      const uint32_t off = tc::kmajor_offset(j, i, kSBO1);
-      *reinterpret_cast<float*>(smem + oB1 + off) = h;
-      *reinterpret_cast<float*>(smem + oB1 + kB1 + off) = tc::to_tf32(x - h);
-    }
-    for (int t = tid; t < kH * kH; t += kCT) {
-      const int j = t / kH, i = t - (t / kH) * kH;
-      const float x = A.w[mlp::oW2 + i * kH + j];
-      const float h = tc::to_tf32(x);
-      const uint32_t off = tc::kmajor_offset(j, i, kSBO2);
-      *reinterpret_cast<float*>(smem + oB2 + off) = h;
-      *reinterpret_cast<float*>(smem + oB2 + kB2 + off) = tc::to_tf32(x - h);
-    }
-    for (int j = tid; j < kH; j += kCT) {
-      vec[j] = A.w[mlp::oB1 + j];
-      vec[kH + j] = A.w[mlp::oB2 + j];
-      vec[2 * kH + j] = A.w[mlp::oW3 + j * mlp::kOut];          // output 0 only
-    }
+    // the weight image (B1, B2 head and tail, b1, b2, w3[:, 0], b3): 16-byte
+    // copies, all in flight at once
+    const uint4* src = reinterpret_cast<const uint4*>(A.wimg);
+    for (int t = tid; t < int(kImgBytes / 16); t += kCT) cp_async16(smem + oB1 + 16 * t, src + t);
+    cp_async_commit();
     if (tid == 0) {
-      vec[3 * kH] = A.w[mlp::oB3];
       tc::mbar_init(mbar, 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-      tc::tmem_alloc(tslot, kH);
+      tc::tmem_alloc(tslot, kCols);
       tc::tmem_relinquish();
     }
+    cp_async_wait_all();
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -157,25 +192,27 @@ __global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseG
     bool active = false;
     float qm[5] = {0, 0, 0, 0, 0}, nv[3] = {0, 0, 1}, xv[3] = {0, 0, 0}, psi = 0.0f;
     if (half == 0 && i < total) {
+      // one dependent global load (the face slot) before the rest: the
+      // trace, normal and connection all go out together; the mode test
+      // only decides what is written back
       const int64_t slot = i / A.Nfp;
       const int m = int(i - slot * A.Nfp);
+      xv[0] = A.bxyz[i * 3];
+      xv[1] = A.bxyz[i * 3 + 1];
+      xv[2] = A.bxyz[i * 3 + 2];
+      psi = A.psi[i];
       const int32_t ef = A.bface[slot];
       const int64_t e = ef >> 2;
       const int f = ef & 3;
+      const int nm = reinterpret_cast<const int32_t*>(smem + oFm)[f * A.Nfp + m];
       const int32_t c = A.conn[e * 4 + f];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
+      const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
+      nv[0] = g[0];
+      nv[1] = g[1];
+      nv[2] = g[2];
       active = c < 0 && A.bc_mode[(-1 - c) & 7] == 3;
-      if (active) {
-        const int nm = A.fmask[f * A.Nfp + m];
-        for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
-        const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
-        nv[0] = g[0];
-        nv[1] = g[1];
-        nv[2] = g[2];
-        xv[0] = A.bxyz[i * 3];
-        xv[1] = A.bxyz[i * 3 + 1];
-        xv[2] = A.bxyz[i * 3 + 2];
-        psi = A.psi[i];
-      }
     }
     float wo_m = 0.0f, y0 = 0.0f, s = 0.0f, wi_c = 0.0f;
     if (half == 0) {
@@ -206,21 +243,20 @@ __global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseG
       bool ok = warp_wait(mbar, phase);
       phase ^= 1u;
       tc::fence_after_sync();
-      float h1[kHH];
-      if (ok) {
-        float d[32];
-        tc::tmem_ld_32x32b_x32(tq, d);
-#pragma unroll
-        for (int j = 0; j < kHH; ++j) h1[j] = mlp::tanh_fast(d[j] + vec[kHH * half + j]);
-      }
-      // ---- layer 2 in two K-halves through one operand buffer: units of
-      // half 0, then of half 1 (the tensor-memory reads above are complete)
+      // ---- layer 2 in two K-halves through one operand buffer: the units
+      // of half 0, then of half 1, each read from columns 0..63 (which the
+      // second GEMM, accumulating in 64..127, leaves alone) when its turn comes
 #pragma unroll 1
       for (int kh = 0; kh < 2; ++kh) {
         if (ok && half == kh) {
 #pragma unroll
-          for (int cq = 0; cq < kHH / 4; ++cq)
-            store4(smem + oA2, kA2, tc::kmajor_offset(row, 4 * cq, kSBOh), h1 + 4 * cq);
+          for (int c16 = 0; c16 < kHH / 16; ++c16) {
+            float h[16];
+            tanh16(tq + uint32_t(16 * c16), vec + kHH * half + 16 * c16, h);
+#pragma unroll
+            for (int cq = 0; cq < 4; ++cq)
+              store4(smem + oA2, kA2, tc::kmajor_offset(row, 16 * c16 + 4 * cq, kSBOh), h + 4 * cq);
+          }
         }
         tc::fence_smem_to_async();
         tc::fence_before_sync();
@@ -228,8 +264,8 @@ __global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseG
         if (!ok) break;
         if (tid == 0) {
           tc::fence_after_sync();
-          gemm3(tmem, sa + oA2, kA2, kSBOh, sa + oB2 + 1024u * kh, kB2, kSBO2, kHH / 8,
-                uint32_t(kh), idesc, mbar);
+          gemm3(tmem + uint32_t(kH), sa + oA2, kA2, kSBOh, sa + oB2 + 1024u * kh, kB2, kSBO2,
+                kHH / 8, uint32_t(kh), idesc, mbar);
         }
         ok = warp_wait(mbar, phase);
         phase ^= 1u;
@@ -237,11 +273,13 @@ __global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseG
       }
       float ypart = 0.0f;
       if (ok) {
-        float d[32];
-        tc::tmem_ld_32x32b_x32(tq, d);
 #pragma unroll
-        for (int j = 0; j < kHH; ++j)
-          ypart += vec[2 * kH + kHH * half + j] * mlp::tanh_fast(d[j] + vec[kH + kHH * half + j]);
+        for (int c16 = 0; c16 < kHH / 16; ++c16) {
+          float h[16];
+          tanh16(tq + uint32_t(kH + 16 * c16), vec + kH + kHH * half + 16 * c16, h);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) ypart += vec[2 * kH + kHH * half + 16 * c16 + j] * h[j];
+        }
       }
       if (half == 1) part[row] = ypart;
       if (__syncthreads_or(!ok)) {
@@ -283,12 +321,20 @@ __global__ void __launch_bounds__(kCT, 2) closure_tc_kernel(ClosureArgs A, BaseG
     __syncthreads();
     if (warp == 0) {
       tc::fence_after_sync();
-      tc::tmem_dealloc(tmem, kH);
+      tc::tmem_dealloc(tmem, kCols);
     }
   }
 }
 
 }  // namespace
+
+size_t closure_image_bytes() { return kImgBytes; }
+
+cudaError_t launch_closure_image(const float* w, unsigned char* img, cudaStream_t s) {
+  constexpr int n = kH * kK1 + kH * kH + kH + 1;
+  closure_image_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, img);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s) {
   const int64_t total = A.nb * A.Nfp;
@@ -307,7 +353,7 @@ cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (total + kRows - 1) / kRows;
-  const int64_t want = 2 * int64_t(sms);                  // two CTAs per SM
+  const int64_t want = 3 * int64_t(sms);                  // three CTAs per SM
   const int grid = int(ntiles < want ? ntiles : want);
   closure_tc_kernel<<<grid, kCT, kSmem, s>>>(A, bg);
   return cudaGetLastError();

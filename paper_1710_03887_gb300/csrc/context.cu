@@ -117,6 +117,8 @@ struct dg_ctx {
   float* bD = nullptr;             // incoming-invariant increments [slot][Nfp]
   uint8_t* face_list = nullptr;    // float32 stage: faces each tile evaluates
   float* mlp_w = nullptr;          // network parameters (device), null until set
+  unsigned char* mlp_img = nullptr; // their operand image for the closure kernel
+  bool mlp_img_ok = false;          // image built from the current parameters
   float* mlp_m = nullptr;          // Adam moments
   float* mlp_v = nullptr;
   float* mlp_grad = nullptr;
@@ -226,10 +228,10 @@ int ensure_device(dg_ctx* c) {
                             : (modal ? dgk::stage_modal_tile_elems(p) : dgk::stage_tile_elems(p)));
   const int64_t Kown = c->owned();
   c->ntiles = int((Kown + ET - 1) / ET);
-  // the tensor-core stage is sized for two CTAs per SM (104 KB of shared
-  // memory each at p = 3); a grid of two per SM is correct whatever the
-  // occupancy query says (CTAs loop over tiles)
-  if (tcf) bps = std::max(bps, 2);
+  // the tensor-core stage is sized for two CTAs per SM at p <= 3 (104 KB of
+  // shared memory each at p = 3) and one at p = 4; a grid of that many per
+  // SM is correct whatever the occupancy query says (CTAs loop over tiles)
+  if (tcf) bps = std::max(bps, dgk::stage_tc_ctas_per_sm(p));
   c->grid = std::min(c->ntiles, c->sms * bps);
   const size_t nq = c->state_elems();
   if (f32) {
@@ -432,13 +434,20 @@ dgk::BaseGhost base_ghost(const dg_ctx* c) {
 // learned boundary faces get their increments D (and, in a time step, their
 // memory update); trace faces get their memory update while traces are
 // recorded. dg_eval_rhs (to_scratch) computes D without advancing anything.
-int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
+// *launched: whether a kernel went into the stream (the stage kernel is then
+// launched as its programmatic dependent).
+int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt, bool* launched) {
+  *launched = false;
   bool learned = false;
   for (int i = 0; i < 8; ++i) learned = learned || c->bc_mode[i] == DG_BC_LEARNED;
   if (learned && c->nbf > 0 && c->mesh.verts.empty())
     return c->fail(DG_ERR_ORDER, "the learned closure needs vertex coordinates (dg_upload_mesh)");
   const dgk::BaseGhost bg = base_ghost(c);
   if (learned && c->nbf > 0) {
+    if (c->mlp_w && !c->mlp_img_ok) {
+      DG_CUDA(dgk::launch_closure_image(c->mlp_w, c->mlp_img, c->stream));
+      c->mlp_img_ok = true;
+    }
     dgk::ClosureArgs C{};
     C.q = c->q32[c->cur];
     C.Np = c->ref.Np;
@@ -451,6 +460,7 @@ int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     C.bxyz = c->bxyz;
     for (int i = 0; i < 8; ++i) C.bc_mode[i] = c->bc_mode[i];
     C.w = c->mlp_w;
+    C.wimg = c->mlp_img;
     C.S = mlp_scales(c);
     C.psi = c->bpsi;
     C.psi_res = c->bpsi_res;
@@ -461,11 +471,14 @@ int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt) {
     C.advance = to_scratch ? 0 : 1;
     C.status = c->status;
     DG_CUDA(dgk::launch_closure(C, bg, c->stream));
+    *launched = C.nb * C.Nfp > 0;
   }
-  if (c->ntrace > 0 && !to_scratch)
+  if (c->ntrace > 0 && !to_scratch) {
     DG_CUDA(dgk::launch_trace_memory(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->tr_elem, c->tr_face,
                                      c->fmask, c->geo32, c->txyz, c->ntrace, bg, mlp_scales(c),
                                      c->tr_psi, c->tr_res, float(a), float(b), float(dt), c->stream));
+    *launched = true;
+  }
   return DG_OK;
 }
 
@@ -518,8 +531,13 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
     for (int i = 0; i < 3; ++i) A.inflow[i] = in_pert[i];
     A.bD = c->bD;
     A.face_list = c->face_list;
-    int rc = run_memory(c, to_scratch, a, b, dt);
+    bool after_kernel = false;
+    int rc = run_memory(c, to_scratch, a, b, dt, &after_kernel);
     if (rc) return rc;
+    // the stage kernel may start while the closure finishes: before its
+    // griddep_wait it touches nothing the closure writes (D, the memories),
+    // and it writes nothing the closure reads (q[cur] it only reads)
+    A.pdl = after_kernel ? 1 : 0;
     if (c->prec == DG_PREC_F32_TC)
       DG_CUDA(dgk::launch_stage_tc(c->ref.p, A, c->grid, c->stream));
     else
@@ -607,7 +625,6 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
   if (params->precision != DG_PREC_FP64 && params->precision != DG_PREC_F32 &&
       params->precision != DG_PREC_F32_TC && params->precision != DG_PREC_MODAL)
     return DG_ERR_UNSUPPORTED;
-  if (params->precision == DG_PREC_F32_TC && order > 3) return DG_ERR_UNSUPPORTED;
   if ((params->precision == DG_PREC_F32 || params->precision == DG_PREC_F32_TC) &&
       (params->u0[0] != 0.0 || params->u0[1] != 0.0 || params->u0[2] != 0.0))
     return DG_ERR_UNSUPPORTED;   // the perturbation form is built around a resting base state
@@ -647,7 +664,7 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
 int dg_destroy(dg_ctx* c) {
   if (!c) return DG_OK;
   c->free_device();
-  dfree(c->mlp_w); dfree(c->mlp_m); dfree(c->mlp_v); dfree(c->mlp_grad); dfree(c->mlp_loss);
+  dfree(c->mlp_img); dfree(c->mlp_w); dfree(c->mlp_m); dfree(c->mlp_v); dfree(c->mlp_grad); dfree(c->mlp_loss);
   dfree(c->mlp_part);
   delete c;
   return DG_OK;
@@ -1267,7 +1284,10 @@ static int ensure_mlp(dg_ctx* c) {
   DG_CUDA(cudaMalloc(&c->mlp_v, n * 4));
   DG_CUDA(cudaMalloc(&c->mlp_grad, n * 4));
   DG_CUDA(cudaMalloc(&c->mlp_loss, 8));
+  DG_CUDA(cudaMalloc(&c->mlp_img, dgk::closure_image_bytes()));
   DG_CUDA(cudaMemset(c->mlp_w, 0, n * 4));
+  DG_CUDA(cudaMemset(c->mlp_img, 0, dgk::closure_image_bytes()));
+  c->mlp_img_ok = false;
   return DG_OK;
 }
 
@@ -1277,6 +1297,7 @@ int dg_set_bc_mlp(dg_ctx* c, const float* w, double radius) {
   if (rc) return rc;
   if (c->dev_ready) DG_CUDA(cudaStreamSynchronize(c->stream));
   DG_CUDA(cudaMemcpy(c->mlp_w, w, size_t(dgk::mlp::kParams) * 4, cudaMemcpyHostToDevice));
+  c->mlp_img_ok = false;
   DG_CUDA(cudaMemset(c->mlp_m, 0, size_t(dgk::mlp::kParams) * 4));
   DG_CUDA(cudaMemset(c->mlp_v, 0, size_t(dgk::mlp::kParams) * 4));
   c->mlp_t = 0;
@@ -1386,6 +1407,7 @@ int dg_mlp_train(dg_ctx* c, const float* X, const float* Y, int64_t N, int iters
       DG_CUDA(cudaMemcpyAsync(loss_history + it, c->mlp_loss, 8, cudaMemcpyDeviceToHost, c->stream));
     ++c->mlp_t;
     DG_CUDA(dgk::launch_adam(c->mlp_w, c->mlp_grad, c->mlp_m, c->mlp_v, float(lr), c->mlp_t, c->stream));
+    c->mlp_img_ok = false;
   }
   DG_CUDA(cudaStreamSynchronize(c->stream));
   return DG_OK;

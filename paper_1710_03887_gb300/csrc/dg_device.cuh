@@ -124,7 +124,38 @@ struct StageArgsF32 {
   // << 2 | face), in that order: faces between two elements of the tile
   // (once, under the lower element), faces to other tiles, outer faces
   const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]
+  // launched as a programmatic dependent of the kernel before it in the
+  // stream (the closure, which writes bD): every CTA waits for that kernel
+  // (griddep_wait) before its first tile with outer faces, and before it exits
+  int pdl;
 };
+
+// Programmatic dependent launch (sm_90 and later). A kernel launched with
+// launch_stage_kernel(..., pdl = true) may start while the kernel before it
+// in the stream still runs, once every CTA of that kernel has executed
+// griddep_launch_dependents (or exited); griddep_wait returns when that
+// kernel has completed and its memory operations are visible. Without a
+// programmatic predecessor both are no-ops.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename T>
+inline cudaError_t launch_stage_kernel(void (*k)(T), int grid, int threads, size_t smem,
+                                       cudaStream_t s, const T& a, bool pdl) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(threads));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
 
 int stage_f32_tile_elems(int p);
 cudaError_t stage_f32_prepare(int p, int* blocks_per_sm);
@@ -138,10 +169,11 @@ cudaError_t launch_probe_sample_f32(const float* q, int Np, int n, const int32_t
                                     const double* rows, double rho0, double E0, double* out,
                                     cudaStream_t s);
 
-// Tensor-core form of the float32 stage (stage_tc.cu), orders 1..3; uses
+// Tensor-core form of the float32 stage (stage_tc.cu), orders 1..4; uses
 // StageArgsF32 with ops pointing at the image built by build_tc_ops.
 size_t stage_tc_ops_bytes(int p);
 int stage_tc_tile_elems(int p);
+int stage_tc_ctas_per_sm(int p);
 void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
                   const double* face_w, unsigned char* out);
 cudaError_t stage_tc_prepare(int p, int* blocks_per_sm);
@@ -170,6 +202,7 @@ struct ClosureArgs {
   const float* bxyz;         // [nb][Nfp][3]
   int bc_mode[8];
   const float* w;            // network parameters or null
+  const unsigned char* wimg; // their operand image (launch_closure_image), with w
   mlp::Scales S;
   float* psi;                // [nb][Nfp] memory
   float* psi_res;
@@ -179,6 +212,11 @@ struct ClosureArgs {
   int* status;               // kStatusTimeout when a tensor-core completion wait gives up
 };
 cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s);
+// The closure's weight image (operand layouts of W1 and W2 as tf32 head and
+// tail, and the vectors it reads) from the parameter vector; rebuild after
+// every change of the parameters.
+size_t closure_image_bytes();
+cudaError_t launch_closure_image(const float* w, unsigned char* img, cudaStream_t s);
 // The same memory at the nodes of the trace faces (inner traces), advanced
 // per stage while traces are recorded.
 cudaError_t launch_trace_memory(const float* q, int Np, int Nfp, const int32_t* tr_elem,

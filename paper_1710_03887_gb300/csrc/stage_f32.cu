@@ -193,6 +193,7 @@ stage_f32_kernel(const StageArgsF32 A) {
 
   int iter = 0;
   double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
+  bool waited = A.pdl == 0;          // for the closure's increments bD (uniform)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int e0i = int(e0);
@@ -213,6 +214,10 @@ stage_f32_kernel(const StageArgsF32 A) {
     // tiles, [bEnd, cEnd) outer faces (items = face x face node)
     const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
     const int aEnd = hdr[1] * Nfp, bEnd = (hdr[1] + hdr[2]) * Nfp, cEnd = hdr[0] * Nfp;
+    if (!waited && cEnd > bEnd) {
+      griddep_wait();                  // outer faces read the closure's increments
+      waited = true;
+    }
     for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
@@ -422,6 +427,8 @@ stage_f32_kernel(const StageArgsF32 A) {
       }
     }
   }
+  // the grid does not complete before the kernel it depends on
+  if (!waited) griddep_wait();
   ledger_finish(A.led, cled);
 }
 
@@ -457,13 +464,13 @@ cudaError_t stage_f32_prepare(int p, int* bps) {
 }
 
 cudaError_t launch_stage_f32(int p, const StageArgsF32& a, int grid, cudaStream_t s) {
+  const bool pdl = a.pdl != 0;
   switch (p) {
-    case 1: stage_f32_kernel<1><<<grid, OrderF<1>::NT, OrderF<1>::bytes, s>>>(a); break;
-    case 2: stage_f32_kernel<2><<<grid, OrderF<2>::NT, OrderF<2>::bytes, s>>>(a); break;
-    case 3: stage_f32_kernel<3><<<grid, OrderF<3>::NT, OrderF<3>::bytes, s>>>(a); break;
-    default: stage_f32_kernel<4><<<grid, OrderF<4>::NT, OrderF<4>::bytes, s>>>(a); break;
+    case 1: return launch_stage_kernel(stage_f32_kernel<1>, grid, OrderF<1>::NT, OrderF<1>::bytes, s, a, pdl);
+    case 2: return launch_stage_kernel(stage_f32_kernel<2>, grid, OrderF<2>::NT, OrderF<2>::bytes, s, a, pdl);
+    case 3: return launch_stage_kernel(stage_f32_kernel<3>, grid, OrderF<3>::NT, OrderF<3>::bytes, s, a, pdl);
+    default: return launch_stage_kernel(stage_f32_kernel<4>, grid, OrderF<4>::NT, OrderF<4>::bytes, s, a, pdl);
   }
-  return cudaGetLastError();
 }
 
 // ------------------------------------------------------- conversions, etc.

@@ -20,7 +20,8 @@
 // 16-byte chunk in place into head and tail (the tail into the second
 // image), whatever rows and columns the chunk holds. A tile needs ~104 KB
 // of shared memory at p = 3, so two CTAs share an SM and one computes while
-// the other waits at a barrier or on its MMAs. The accumulator rows come
+// the other waits at a barrier or on its MMAs; at p = 4 (~183 KB: the
+// operand images alone are ~140 KB) one CTA of 512 threads takes the SM. The accumulator rows come
 // back from tensor memory into a small staging array and the Runge-Kutta
 // update runs coalesced over the tile's state.
 #include <cmath>
@@ -43,7 +44,11 @@ struct OrderTC {
   static constexpr int N = (Np + 7) / 8 * 8;           // M = 64: N a multiple of 8
   static constexpr int KU = 3 * Np + NF;               // used columns
   static constexpr int K = (KU + 7) / 8 * 8;
-  static constexpr int NT = 256;
+  // p <= 3: two CTAs of 256 threads per SM (~104 KB of shared memory each at
+  // p = 3); p = 4: the operands alone take ~140 KB, one CTA of 512 threads
+  static constexpr int CPS = P <= 3 ? 2 : 1;
+  static constexpr int NT = P <= 3 ? 256 : 512;
+  static constexpr uint32_t TCOLS = N <= 32 ? 32u : 64u;   // tensor-memory columns (power of 2)
   static constexpr int NB = (Np + 3) / 4;              // node blocks of the node phase
   static constexpr int EG = (ET + 7) / 8;              // element groups of the node phase
   static constexpr int SO = Np % 2 ? Np : Np + 1;      // odd row stride of the results
@@ -75,7 +80,8 @@ struct OrderTC {
   static constexpr size_t oFL = al16(oTbl + 2 * 96 * Nfp);           // 2 face-list buffers
   static constexpr size_t oBar = al16(oFL + 2 * kFL);                // mbarrier, tmem slot, flag
   static constexpr size_t bytes = oBar + 32;
-  static_assert(bytes <= 113 * 1024, "two CTAs per SM");
+  static_assert(bytes <= (CPS == 2 ? 113 : 227) * 1024, "CTAs per SM");
+  static_assert(N <= 64, "accumulator rows read as 32 + 8 columns");
   static constexpr size_t kOpsBytes = 2 * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
 };
 
@@ -143,11 +149,11 @@ __device__ __forceinline__ void store_a(unsigned char* ahi, uint32_t off, float 
 //     lane 32 (r / 16) + r % 16) into R, and all threads update q and res
 //     with coalesced accesses.
 template <int P>
-__global__ void __launch_bounds__(OrderTC<P>::NT, 2)
+__global__ void __launch_bounds__(OrderTC<P>::NT, OrderTC<P>::CPS)
 stage_tc_kernel(const StageArgsF32 A) {
   using O = OrderTC<P>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
-  constexpr int KU = O::KU, K = O::K, SO = O::SO, kG = O::kG;
+  constexpr int K = O::K, SO = O::SO, kG = O::kG;
   constexpr uint32_t SBO = O::SBO;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* sAhi = smem + O::oAhi;
@@ -184,7 +190,7 @@ stage_tc_kernel(const StageArgsF32 A) {
     *sAbort = 0;
   }
   if (warp == 0) {
-    tc::tmem_alloc(tslot, 32);
+    tc::tmem_alloc(tslot, O::TCOLS);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -224,6 +230,7 @@ stage_tc_kernel(const StageArgsF32 A) {
 
   double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
   int iter = 0;
+  bool waited = A.pdl == 0;          // for the closure's increments bD (uniform)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
@@ -243,6 +250,10 @@ stage_tc_kernel(const StageArgsF32 A) {
     const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
     const int aEnd = hdr[1] * Nfp, bEnd = (hdr[1] + hdr[2]) * Nfp, cEnd = hdr[0] * Nfp;
     const int e0i = int(e0);
+    if (!waited && cEnd > bEnd) {
+      griddep_wait();                  // outer faces read the closure's increments
+      waited = true;
+    }
     for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
@@ -444,7 +455,16 @@ stage_tc_kernel(const StageArgsF32 A) {
         const int row = 16 * warp + lane;
         if (lane < 16 && row < 5 * nE) {
 #pragma unroll
-          for (int j = 0; j < Np; ++j) sR[row * SO + j] = d[j];
+          for (int j = 0; j < (Np < 32 ? Np : 32); ++j) sR[row * SO + j] = d[j];
+        }
+        if constexpr (Np > 32) {
+          // columns 32 .. 39 (p = 4: Np = 35)
+          float d8[8];
+          tc::tmem_ld_32x32b_x8(tmem + (uint32_t(32 * warp) << 16) + 32u, d8);
+          if (lane < 16 && row < 5 * nE) {
+#pragma unroll
+            for (int j = 32; j < Np; ++j) sR[row * SO + j] = d8[j - 32];
+          }
         }
       }
     }
@@ -465,6 +485,8 @@ stage_tc_kernel(const StageArgsF32 A) {
     }
   }
   cp_async_wait_all();
+  // the grid does not complete before the kernel it depends on
+  if (!waited) griddep_wait();
   // a wait that gave up may leave MMAs in flight: give them a bounded chance
   // to finish before the tensor memory is released. `phase` was flipped after
   // the wait that gave up, so that wait's parity is phase ^ 1 (waiting on
@@ -474,7 +496,7 @@ stage_tc_kernel(const StageArgsF32 A) {
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 32);
+    tc::tmem_dealloc(tmem, O::TCOLS);
   }
   ledger_finish(A.led, cled);
 }
@@ -483,11 +505,14 @@ size_t stage_tc_ops_bytes(int p) {
   switch (p) {
     case 1: return OrderTC<1>::kOpsBytes;
     case 2: return OrderTC<2>::kOpsBytes;
-    default: return OrderTC<3>::kOpsBytes;
+    case 3: return OrderTC<3>::kOpsBytes;
+    default: return OrderTC<4>::kOpsBytes;
   }
 }
 
 int stage_tc_tile_elems(int) { return 12; }
+
+int stage_tc_ctas_per_sm(int p) { return p <= 3 ? OrderTC<3>::CPS : OrderTC<4>::CPS; }
 
 // Host-side image of B = [-Dr | -Ds | -Dt | LIFT] in the operand layout,
 // split into tf32 head and tail, followed by the face weights.
@@ -530,7 +555,8 @@ void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, c
   switch (p) {
     case 1: build_ops_impl<1>(Dr, Ds, Dt, LIFT, face_w, out); break;
     case 2: build_ops_impl<2>(Dr, Ds, Dt, LIFT, face_w, out); break;
-    default: build_ops_impl<3>(Dr, Ds, Dt, LIFT, face_w, out); break;
+    case 3: build_ops_impl<3>(Dr, Ds, Dt, LIFT, face_w, out); break;
+    default: build_ops_impl<4>(Dr, Ds, Dt, LIFT, face_w, out); break;
   }
 }
 
@@ -539,7 +565,7 @@ static cudaError_t prepare_tc_impl(int* bps) {
   cudaError_t e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(OrderTC<P>::bytes));
   if (e != cudaSuccess) return e;
-  // the whole unified L1 as shared memory, so that two CTAs fit on an SM
+  // the whole unified L1 as shared memory (two CTAs per SM at p <= 3)
   e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            int(cudaSharedmemCarveoutMaxShared));
   if (e != cudaSuccess) return e;
@@ -551,17 +577,19 @@ cudaError_t stage_tc_prepare(int p, int* bps) {
   switch (p) {
     case 1: return prepare_tc_impl<1>(bps);
     case 2: return prepare_tc_impl<2>(bps);
-    default: return prepare_tc_impl<3>(bps);
+    case 3: return prepare_tc_impl<3>(bps);
+    default: return prepare_tc_impl<4>(bps);
   }
 }
 
 cudaError_t launch_stage_tc(int p, const StageArgsF32& a, int grid, cudaStream_t s) {
+  const bool pdl = a.pdl != 0;
   switch (p) {
-    case 1: stage_tc_kernel<1><<<grid, OrderTC<1>::NT, OrderTC<1>::bytes, s>>>(a); break;
-    case 2: stage_tc_kernel<2><<<grid, OrderTC<2>::NT, OrderTC<2>::bytes, s>>>(a); break;
-    default: stage_tc_kernel<3><<<grid, OrderTC<3>::NT, OrderTC<3>::bytes, s>>>(a); break;
+    case 1: return launch_stage_kernel(stage_tc_kernel<1>, grid, OrderTC<1>::NT, OrderTC<1>::bytes, s, a, pdl);
+    case 2: return launch_stage_kernel(stage_tc_kernel<2>, grid, OrderTC<2>::NT, OrderTC<2>::bytes, s, a, pdl);
+    case 3: return launch_stage_kernel(stage_tc_kernel<3>, grid, OrderTC<3>::NT, OrderTC<3>::bytes, s, a, pdl);
+    default: return launch_stage_kernel(stage_tc_kernel<4>, grid, OrderTC<4>::NT, OrderTC<4>::bytes, s, a, pdl);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace dgk

@@ -48,8 +48,6 @@ def perturbation_err(qg, qo, q0):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_f32_rhs_matches_oracle(cuda_device, p, prec):
-    if prec == "f32_tc" and p > 3:
-        pytest.skip("the tensor-core form covers orders 1..3")
     xyz, EToV = W.kuhn_cube(3, jitter=0.12, seed=p)
     probe = Case(p, xyz, EToV)
     tags = direction_tags(xyz, EToV, probe.geom)
