@@ -520,10 +520,10 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     characteristic and learned conditions on the truncated ball, and the
     trained closure is timed on the bench workload."""
     from paper_1710_03887_gb300 import learned_bc as L
-    n, runs, every, iters = args.learned_n, 8, args.learned_every, 600
+    n, runs, centred, every, iters = args.learned_n, 8, 24, args.learned_every, 600
     t0 = time.perf_counter()
     nested = L.nested_ball(n)
-    X, Y = L.record(WORKLOAD["order"], nested, L.run_seeds(0, runs), every=every, device=dev,
+    X, Y = L.record(WORKLOAD["order"], nested, L.run_seeds(0, runs, centred), every=every, device=dev,
                     width_scale=2.0, node_fraction=args.learned_fraction)
     t_rec = time.perf_counter() - t0
     w, hist = L.train(X, Y, iters=iters, lr=3e-3, seed=0, radius=nested.radius,
@@ -533,9 +533,11 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     for amp in LEARNED_AMPLITUDES:
         table[f"{100 * amp:g}% p0"] = L.reflection_table(WORKLOAD["order"], nested, amp, 0.3,
                                                          (0.0, 0.0, 0.0), w)
-    # a source off the centre, where the spherical memory is no longer exact
+    # sources off the centre, where the spherical memory is no longer exact
     table["2% p0 off-centre (0.3,0.1,-0.2)"] = L.reflection_table(
         WORKLOAD["order"], nested, 0.02, 0.25, (0.3, 0.1, -0.2), w)
+    table["2% p0 off-centre (-0.2,0.35,0.1)"] = L.reflection_table(
+        WORKLOAD["order"], nested, 0.02, 0.25, (-0.2, 0.35, 0.1), w)
     # plain float64 DG on the same pulse: the float32 form's reflected energy
     # and state against it (at 2 % p0)
     from paper_1710_03887_gb300 import binding as B
@@ -558,10 +560,11 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     return ({
         "config": (f"radius-2 ball on the n={n} lattice ({len(nested.big[1])} tets), truncated at "
                    f"r=1 ({len(nested.small[1])} tets); p=3 float32; {runs} seeded pulse runs "
-                   f"(centre |x|<0.5, width 0.2-0.4, amplitude 0.1-10% p0) sampled every "
+                   f"(centre |x|<0.5) and {centred} centred ones (width 0.2-0.4, amplitude "
+                   f"0.1-10% p0) sampled every "
                    f"{every} steps at r=1 (fraction {args.learned_fraction:g} of the trace nodes); "
-                   "measured with centred pulses of width 0.3 and one "
-                   "off-centre pulse of width 0.25; 'spherical' is the memory closure w_in = psi "
+                   "measured with centred pulses of width 0.3 and two "
+                   "off-centre pulses of width 0.25; 'spherical' is the memory closure w_in = psi "
                    "(the untrained network: its output layer starts at zero and its output "
                    "corrects psi)"),
         "samples": int(X.shape[0]), "iters": iters, "loss_first": float(hist[0]),
@@ -1214,7 +1217,7 @@ def main():
                     help="comma-separated outer domains of Table 1 timed at full size after the "
                          "horn section (names of bench.HORN_DOMAINS; empty: none)")
     ap.add_argument("--learned-every", type=int, default=10, help="steps between trace samples")
-    ap.add_argument("--learned-fraction", type=float, default=1.0,
+    ap.add_argument("--learned-fraction", type=float, default=0.25,
                     help="fraction of trace nodes kept per sample (seeded)")
     ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],
                     help="lattice size of the ball (32 = the benchmark; smaller for profiling)")

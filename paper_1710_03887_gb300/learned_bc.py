@@ -69,17 +69,26 @@ def pulse(nodes, amplitude, width, center):
     return W.gaussian_pulse_state(nodes, W.GAMMA, W.RHO0_SI, W.P0_SI, amplitude, width, center)
 
 
-def run_seeds(seed, count):
-    """Seeded pulse parameters: centre uniform in |x| < 0.5, width in [0.1, 0.2]
-    scaled by ``width_scale`` at the call site, amplitude log-uniform in
-    [0.1 %, 10 %] of p0."""
+def run_seeds(seed, count, centred=0):
+    """Seeded pulse parameters: ``count`` runs with the centre uniform in
+    |x| < 0.5, then ``centred`` runs centred at the origin; width in
+    [0.1, 0.2] (scaled by ``width_scale`` at the call site), amplitude
+    log-uniform in [0.1 %, 10 %] of p0.
+
+    Centred runs teach the network that a wave from the centre needs no
+    correction of the spherical memory: a face node's features cannot tell
+    it from an off-centre wave at the same incidence, so the network learns
+    the mean correction over the runs it sees."""
     rng = np.random.default_rng(seed)
     out = []
-    for _ in range(count):
-        while True:
-            c = rng.uniform(-0.5, 0.5, size=3)
-            if np.linalg.norm(c) < 0.5:
-                break
+    for k in range(count + centred):
+        if k < count:
+            while True:
+                c = rng.uniform(-0.5, 0.5, size=3)
+                if np.linalg.norm(c) < 0.5:
+                    break
+        else:
+            c = np.zeros(3)
         w = rng.uniform(0.1, 0.2)
         a = 10.0 ** rng.uniform(-3.0, -1.0)
         out.append((c, w, a))
