@@ -870,8 +870,8 @@ def far_field_probes(n=32, radius=2.5):
 def production_section(args, dev, stream, weights=None):
     """The production configuration: the horn in a sphere of radius 3 about
     its bell's centre, with the region behind the bell kept (type A, ~8M
-    tets) and truncated (type B half-ball), p = 4, the float32 perturbation
-    form (the tensor-core form covers p <= 3), slip walls, the 10 % p0 inflow
+    tets) and truncated (type B half-ball), p = 4, both float32 perturbation
+    forms (SIMT and tensor-core contractions), slip walls, the 10 % p0 inflow
     pulse at the mouthpiece, the learned closure on the outer sphere
     (``weights``: the network trained by the learned-closure section, else
     the spherical-wave memory alone) and 32 far-field pressure probes at
@@ -884,7 +884,7 @@ def production_section(args, dev, stream, weights=None):
     from paper_1710_03887_gb300 import workloads as W
     w_net = LB.spherical_weights() if weights is None else np.asarray(weights, dtype=np.float32)
     probes = far_field_probes()
-    out = {"order": 4, "steps": args.production_steps, "precision": "f32",
+    out = {"order": 4, "steps": args.production_steps, "precisions": ["f32", "f32_tc"],
            "closure": "trained network" if weights is not None else "spherical-wave memory",
            "probes": "32 points at radius 2.5 about the bell's centre (Fibonacci half-sphere)"}
     for name, kw in (("kept", dict(shape="sphere", room_length=3.0, behind=2.0, m1=3, growth=1.16,
@@ -893,56 +893,71 @@ def production_section(args, dev, stream, weights=None):
         t0 = time.perf_counter()
         xyz, EToV, tag, info = W.horn_in_room(**kw)
         xyz = xyz - np.array([info["bell_x"], 0.0, 0.0])        # bell centre at the origin
-        S = B.Solver(4, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
-        S.set_stream(stream.cuda_stream)
-        S.upload_mesh(xyz, EToV, face_tag=tag)
-        S.set_bc(W.HORN_OUTER, B.DG_BC_LEARNED)
-        S.set_bc(W.HORN_WALL, B.DG_BC_SLIP_WALL)
-        S.set_bc(W.HORN_MOUTHPIECE, B.DG_BC_INFLOW_PULSE)
-        S.set_inflow(0.05, 565.0)
-        S.set_bc_mlp(w_net, 3.0)
-        S.set_probes(probes, capacity=max(args.production_steps, 1))
-        q0 = torch.empty((S.K, 5, S.Np), dtype=torch.float64, device=dev)
-        q0[:] = torch.from_numpy(W.uniform_state(1, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI,
-                                                 W.GAMMA)).to(dev)
-        # the fastest state of the run: the inflow pulse's peak, at rest
-        dt = rest_cfl_dt(xyz, EToV, 4, 1.1 * W.P0_SI, W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA))
-        setup = time.perf_counter() - t0
-        S.set_state(q0)
-        S.step(1, dt)
-        S.set_state(q0)
-        S.read_probes()
-        torch.cuda.synchronize(dev)
-        S.set_kernel_timing(True)
-        start = torch.cuda.Event(enable_timing=True)
-        stop = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        S.step(args.production_steps, dt)
-        stop.record(stream)
-        torch.cuda.synchronize(dev)
-        ms = start.elapsed_time(stop)
-        kms, kl = S.read_kernel_timing()
-        S.set_kernel_timing(False)
-        series = S.read_probes(args.production_steps)
-        led = S.boundary_flux()
-        S.sync()
-        dof = 5 * S.Np * S.K
-        avg = kms / max(kl, 1)
-        out[name] = {
-            "elements": int(S.K), "horn_elements": info["n_horn"], "dof": int(dof),
-            "lattice": {k: v for k, v in kw.items() if k != "shape"},
-            "value": dof * args.production_steps / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms / args.production_steps, "dt": dt,
-            "avg_stage_launch_ms_with_closure": avg,
-            "stage_tflops": stage_flops_per_element(4) * S.K / (avg * 1e-3) / 1e12,
-            "mass_in_through_mouthpiece": float(-led[0]),
-            "probe_max_abs_dp_rel_p0": float(np.abs(series[..., 4] - series[:1, :, 4]).max()
-                                             * (W.GAMMA - 1.0) / W.P0_SI),
-            "setup_seconds": setup}
-        S.close()
-        del q0
-        torch.cuda.empty_cache()
+        mesh_s = time.perf_counter() - t0
+        out[name] = {"elements": int(len(EToV)), "horn_elements": info["n_horn"],
+                     "lattice": {k: v for k, v in kw.items() if k != "shape"},
+                     "mesh_seconds": mesh_s}
+        for prec_name, prec in (("f32", B.DG_PREC_F32), ("f32_tc", B.DG_PREC_F32_TC)):
+            out[name][prec_name] = _production_run(args, dev, stream, xyz, EToV, tag, prec, w_net,
+                                                   probes)
     return out
+
+
+def _production_run(args, dev, stream, xyz, EToV, tag, prec, w_net, probes):
+    """One float32 form on one production mesh, timed like the bench."""
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    from paper_1710_03887_gb300 import workloads as W
+    t0 = time.perf_counter()
+    S = B.Solver(4, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
+    S.set_stream(stream.cuda_stream)
+    S.upload_mesh(xyz, EToV, face_tag=tag)
+    S.set_bc(W.HORN_OUTER, B.DG_BC_LEARNED)
+    S.set_bc(W.HORN_WALL, B.DG_BC_SLIP_WALL)
+    S.set_bc(W.HORN_MOUTHPIECE, B.DG_BC_INFLOW_PULSE)
+    S.set_inflow(0.05, 565.0)
+    S.set_bc_mlp(w_net, 3.0)
+    S.set_probes(probes, capacity=max(args.production_steps, 1))
+    q0 = torch.empty((S.K, 5, S.Np), dtype=torch.float64, device=dev)
+    q0[:] = torch.from_numpy(W.uniform_state(1, S.Np, W.RHO0_SI, (0, 0, 0), W.P0_SI,
+                                             W.GAMMA)).to(dev)
+    # the fastest state of the run: the inflow pulse's peak, at rest
+    dt = rest_cfl_dt(xyz, EToV, 4, 1.1 * W.P0_SI, W.RHO0_SI * 1.1 ** (1.0 / W.GAMMA))
+    setup = time.perf_counter() - t0
+    S.set_state(q0)
+    S.step(1, dt)
+    S.set_state(q0)
+    S.read_probes()
+    torch.cuda.synchronize(dev)
+    S.set_kernel_timing(True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    S.step(args.production_steps, dt)
+    stop.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = start.elapsed_time(stop)
+    kms, kl = S.read_kernel_timing()
+    S.set_kernel_timing(False)
+    series = S.read_probes(args.production_steps)
+    led = S.boundary_flux()
+    S.sync()
+    dof = 5 * S.Np * S.K
+    avg = kms / max(kl, 1)
+    res = {
+        "dof": int(dof),
+        "value": dof * args.production_steps / (ms * 1e-3), "unit": UNIT,
+        "ms_per_step": ms / args.production_steps, "dt": dt,
+        "avg_stage_launch_ms_with_closure": avg,
+        "stage_tflops": stage_flops_per_element(4) * S.K / (avg * 1e-3) / 1e12,
+        "mass_in_through_mouthpiece": float(-led[0]),
+        "probe_max_abs_dp_rel_p0": float(np.abs(series[..., 4] - series[:1, :, 4]).max()
+                                         * (W.GAMMA - 1.0) / W.P0_SI),
+        "setup_seconds": setup}
+    S.close()
+    del q0
+    torch.cuda.empty_cache()
+    return res
 
 
 # six probes near the axes at r = 0.5: images of one point inside an element
@@ -1158,6 +1173,16 @@ def run_gpu(args, rank, world):
         lb["bench_workload_learned_bc"]["vs_characteristic"] = (
             lb["bench_workload_learned_bc"]["value"] / res["f32"]["value"] if "f32" in res else None)
         line["learned_bc"] = lb
+    if args.closure_timing:
+        # the closure's cost alone: the untrained network (the spherical
+        # memory) does the same work per stage as a trained one
+        from paper_1710_03887_gb300 import learned_bc as L
+        m = measure_form(args, "f32", xyz, EToV, dev, stream, None, 1, False,
+                         mlp=(L.spherical_weights(), WORKLOAD["radius"]))
+        line["closure_timing"] = {
+            "value": m["value"], "unit": UNIT, "ms_per_step": m["ms"] / args.steps,
+            "avg_stage_launch_ms": m["kms"] / max(m["klaunch"], 1),
+            "vs_characteristic": m["value"] / res["f32"]["value"] if "f32" in res else None}
     if args.horn_steps > 0:
         line["horn"] = horn_section(args, dev, stream)
         if args.domains:
@@ -1200,6 +1225,9 @@ def main():
     ap.add_argument("--learned-n", type=int, default=16,
                     help="lattice of the learned-closure experiment's radius-2 ball (0 = skip; "
                          "64 gives the ~200k-element truncated ball of the configuration)")
+    ap.add_argument("--closure-timing", action="store_true",
+                    help="time the bench workload with the learned closure on the untrained "
+                         "network, without the training experiment")
     ap.add_argument("--production-steps", type=int, default=0,
                     help="steps timed on the production configuration: p=4, the horn in a "
                          "radius-3 sphere with the region behind the bell kept (~8M tets) and "
