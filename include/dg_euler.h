@@ -46,7 +46,12 @@
  *     tensor-core completion wait that gave up) is latched in a status word
  *     on the device and reported as DG_ERR_NONFINITE (DG_ERR_TIMEOUT) by the
  *     next call that synchronises (dg_sync, dg_get_state, dg_read_*), which
- *     also clears it; the context stays usable.
+ *     also clears it; the context stays usable. In the debug build (the same
+ *     sources compiled with -DDG_BOUNDS_CHECK into libdgeuler_debug.so) every
+ *     index a kernel reads from the mesh tables (face lists, connection
+ *     words, node tables, boundary slots, halo rows) is checked before the
+ *     access it selects; a failed check skips that access and is reported as
+ *     DG_ERR_BOUNDS the same way.
  */
 #ifndef DG_EULER_H
 #define DG_EULER_H
@@ -65,6 +70,10 @@ extern "C" {
 #define DG_ERR_NONFINITE (-5)   /* device saw a non-finite or non-physical state */
 #define DG_ERR_UNSUPPORTED (-6) /* order / mode not built into this library      */
 #define DG_ERR_TIMEOUT (-7)     /* a bounded device wait gave up (kernel returned) */
+#define DG_ERR_BOUNDS (-8)      /* a device bounds check failed (debug build only)  */
+
+/* dg_build_flags bits */
+#define DG_BUILD_BOUNDS_CHECKS 1 /* kernels carry device bounds checks             */
 
 /* Boundary ghost rules (dg_set_bc) */
 #define DG_BC_FREESTREAM 0      /* ghost = free-stream state (section 2.2, Eq. 3)       */
@@ -266,6 +275,17 @@ int dg_conserved_totals(dg_ctx* ctx, double out[5]);
 
 /* Wait for the stream; report (and clear) a latched device error. */
 int dg_sync(dg_ctx* ctx);
+
+/* Build of the loaded library (no counterpart in the paper: a checking aid).
+ * *flags = DG_BUILD_BOUNDS_CHECKS for the debug build, 0 for the release
+ * build. DG_ERR_ARG for a null pointer. */
+int dg_build_flags(int* flags);
+/* Debug build only (no counterpart in the paper): one device thread fails a
+ * bounds check on purpose, with no out-of-range access, so a caller can see
+ * a failed check reach it: the next synchronising call returns
+ * DG_ERR_BOUNDS. Needs an uploaded mesh (DG_ERR_ORDER otherwise);
+ * DG_ERR_UNSUPPORTED in the release build. */
+int dg_bounds_selftest(dg_ctx* ctx);
 
 /* Per-launch timing of the Runge-Kutta stage kernel: when enabled, dg_step
  * records a CUDA event pair on the stream around every stage launch.

@@ -9,6 +9,7 @@ loaded the import of ``lib`` fails with the reason.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from pathlib import Path
 
 import numpy as np
@@ -23,6 +24,8 @@ DG_ERR_ORDER = -4
 DG_ERR_NONFINITE = -5
 DG_ERR_UNSUPPORTED = -6
 DG_ERR_TIMEOUT = -7
+DG_ERR_BOUNDS = -8
+DG_BUILD_BOUNDS_CHECKS = 1
 
 DG_BC_FREESTREAM = 0
 DG_BC_CHARACTERISTIC = 1
@@ -68,6 +71,8 @@ _SIGS = {
     "dg_read_boundary_flux": (C.c_int, [_P, _P]),
     "dg_conserved_totals": (C.c_int, [_P, _P]),
     "dg_sync": (C.c_int, [_P]),
+    "dg_build_flags": (C.c_int, [C.POINTER(C.c_int)]),
+    "dg_bounds_selftest": (C.c_int, [_P]),
     "dg_set_kernel_timing": (C.c_int, [_P, C.c_int]),
     "dg_read_kernel_timing": (C.c_int, [_P, _D, C.POINTER(C.c_int64)]),
     "dg_weighted_totals_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, _P, _P]),
@@ -105,11 +110,17 @@ def header_symbols():
 
 
 def load(build=True):
-    """Load (building first if needed) the shared library and declare signatures."""
+    """Load (building first if needed) the shared library and declare signatures.
+    With the environment variable DG_EULER_BUILD=debug the process loads the
+    debug variant (device bounds checks; ``build_lib.build(debug=True)``)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = build_lib.build() if build else build_lib.LIB
+    debug = os.environ.get("DG_EULER_BUILD", "") == "debug"
+    if build:
+        path = build_lib.build(debug=debug)
+    else:
+        path = build_lib.LIB_DEBUG if debug else build_lib.LIB
     if not Path(path).exists():
         raise OSError(f"{path} is missing: the CUDA library was not built")
     lib = C.CDLL(str(path))
@@ -119,6 +130,16 @@ def load(build=True):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def build_flags():
+    """dg_build_flags of the loaded library (DG_BUILD_BOUNDS_CHECKS for the
+    debug build)."""
+    f = C.c_int(0)
+    rc = load().dg_build_flags(C.byref(f))
+    if rc:
+        raise DGError(rc, "dg_build_flags")
+    return f.value
 
 
 class DGError(RuntimeError):
@@ -370,6 +391,11 @@ class Solver:
 
     def sync(self):
         self._check(self.lib.dg_sync(self.h))
+
+    def bounds_selftest(self):
+        """Debug build: latch a failed bounds check on the device (no
+        out-of-range access); the next synchronising call raises DG_ERR_BOUNDS."""
+        self._check(self.lib.dg_bounds_selftest(self.h))
 
     # -- learned closure
     def set_bc_mlp(self, w, radius):

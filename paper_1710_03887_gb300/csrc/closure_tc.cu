@@ -205,14 +205,16 @@ __global__ void __launch_bounds__(kCT, 3) closure_tc_kernel(ClosureArgs A, BaseG
       const int64_t e = ef >> 2;
       const int f = ef & 3;
       const int nm = reinterpret_cast<const int32_t*>(smem + oFm)[f * A.Nfp + m];
-      const int32_t c = A.conn[e * 4 + f];
+      if (DG_IN(e >= 0 && e < A.K_all && nm >= 0 && nm < A.Np, A.status)) {
+        const int32_t c = A.conn[e * 4 + f];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
-      const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
-      nv[0] = g[0];
-      nv[1] = g[1];
-      nv[2] = g[2];
-      active = c < 0 && A.bc_mode[(-1 - c) & 7] == 3;
+        for (int v = 0; v < 5; ++v) qm[v] = A.q[(e * 5 + v) * A.Np + nm];
+        const float* g = A.geo + e * kGeoStride + kGeoNrm + 3 * f;
+        nv[0] = g[0];
+        nv[1] = g[1];
+        nv[2] = g[2];
+        active = c < 0 && A.bc_mode[(-1 - c) & 7] == 3;
+      }
     }
     float wo_m = 0.0f, y0 = 0.0f, s = 0.0f, wi_c = 0.0f;
     if (half == 0) {

@@ -416,6 +416,7 @@ dgk::StageArgs stage_args(dg_ctx* c, const double* qin, double* qout, double* re
   A.led = ledger_args(c, update, a, b, dt);
   A.status = c->status;
   A.K = c->owned();
+  A.K_all = c->mesh.K;
   A.ntiles = c->ntiles;
   for (int i = 0; i < 8; ++i) A.bc_mode[i] = c->bc_mode[i];
   A.a = a;
@@ -470,6 +471,7 @@ int run_memory(dg_ctx* c, bool to_scratch, double a, double b, double dt, bool* 
     C.dt = float(dt);
     C.advance = to_scratch ? 0 : 1;
     C.status = c->status;
+    C.K_all = c->mesh.K;
     DG_CUDA(dgk::launch_closure(C, bg, c->stream));
     *launched = C.nb * C.Nfp > 0;
   }
@@ -522,6 +524,8 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
     A.led = ledger_args(c, !to_scratch, a, b, dt);
     A.status = c->status;
     A.K = c->owned();
+    A.K_all = c->mesh.K;
+    A.nb = c->nbf;
     A.ntiles = c->ntiles;
     for (int i = 0; i < 8; ++i) A.bc_mode[i] = c->bc_mode[i];
     A.a = float(a);
@@ -567,12 +571,26 @@ int current_state_f64(dg_ctx* c, double* dst) {
   return DG_OK;
 }
 
+// One thread fails a bounds check on purpose (a condition nothing meets):
+// the status word's path to the host, tested without an out-of-range access.
+__global__ void bounds_selftest_kernel(int* status, unsigned limit) {
+  if (!DG_IN(threadIdx.x > limit, status)) return;
+}
+
+cudaError_t bounds_selftest(int* status, cudaStream_t s) {
+  bounds_selftest_kernel<<<1, 1, 0, s>>>(status, 1024u);
+  return cudaGetLastError();
+}
+
 int check_status(dg_ctx* c) {
   int st = 0;
   DG_CUDA(cudaStreamSynchronize(c->stream));
   DG_CUDA(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st) {
     DG_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+    if (st & dgk::kStatusBounds)
+      return c->fail(DG_ERR_BOUNDS, "a device bounds check failed (an index read from the mesh "
+                                    "tables was out of range; debug build)");
     if (st & dgk::kStatusTimeout)
       return c->fail(DG_ERR_TIMEOUT, "a bounded wait for tensor-core completion gave up");
     return c->fail(DG_ERR_NONFINITE, "device saw a non-finite or non-physical state "
@@ -1089,10 +1107,12 @@ int dg_halo_pack(dg_ctx* c, void* buf) {
   if (!buf) return DG_ERR_ARG;
   if (c->f32())
     DG_CUDA(dgk::launch_halo_pack<float>(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->halo_send,
-                                         c->fmask, c->n_send, static_cast<float*>(buf), c->stream));
+                                         c->fmask, c->n_send, static_cast<float*>(buf), c->mesh.K,
+                                         c->status, c->stream));
   else
     DG_CUDA(dgk::launch_halo_pack<double>(c->q[c->cur], c->ref.Np, c->ref.Nfp, c->halo_send,
-                                          c->fmask, c->n_send, static_cast<double*>(buf), c->stream));
+                                          c->fmask, c->n_send, static_cast<double*>(buf), c->mesh.K,
+                                          c->status, c->stream));
   return DG_OK;
 }
 
@@ -1104,11 +1124,11 @@ int dg_halo_unpack(dg_ctx* c, const void* buf) {
   if (c->f32())
     DG_CUDA(dgk::launch_halo_unpack<float>(c->q32[c->cur], c->ref.Np, c->ref.Nfp, c->halo_recv,
                                            c->fmask, c->n_recv, static_cast<const float*>(buf),
-                                           c->stream));
+                                           c->mesh.K, c->status, c->stream));
   else
     DG_CUDA(dgk::launch_halo_unpack<double>(c->q[c->cur], c->ref.Np, c->ref.Nfp, c->halo_recv,
                                             c->fmask, c->n_recv, static_cast<const double*>(buf),
-                                            c->stream));
+                                            c->mesh.K, c->status, c->stream));
   return DG_OK;
 }
 
@@ -1223,6 +1243,21 @@ int dg_conserved_totals(dg_ctx* c, double out[5]) {
   int rc = check_status(c);
   if (rc) return rc;
   DG_CUDA(cudaMemcpy(out, c->totals_part + size_t(kTotalsBlocks) * 5, 5 * 8, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int dg_build_flags(int* flags) {
+  if (!flags) return DG_ERR_ARG;
+  *flags = dgk::kBoundsChecked ? DG_BUILD_BOUNDS_CHECKS : 0;
+  return DG_OK;
+}
+
+int dg_bounds_selftest(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  if (!dgk::kBoundsChecked) return c->fail(DG_ERR_UNSUPPORTED, "release build: no bounds checks");
+  int rc = ensure_device(c);
+  if (rc) return rc;
+  DG_CUDA(bounds_selftest(c->status, c->stream));
   return DG_OK;
 }
 

@@ -18,6 +18,20 @@ constexpr int kGeoJ = 29;       // 1: volume / (4/3)
 // status bits latched by the kernels
 constexpr int kStatusBadState = 1;
 constexpr int kStatusTimeout = 2;   // a bounded wait for tensor-core completion gave up
+constexpr int kStatusBounds = 4;    // a device bounds check failed (debug build)
+
+// Device bounds checks of the debug build (compiled with -DDG_BOUNDS_CHECK):
+// DG_IN(cond, status) is true where cond holds; where it does not, it
+// latches kStatusBounds in *status and is false, and the caller skips the
+// access it guards. In the release build it is the constant true and the
+// compiler removes the test: the kernels' code is unchanged.
+#ifdef DG_BOUNDS_CHECK
+#define DG_IN(cond, status) ((cond) ? true : (atomicOr((status), ::dgk::kStatusBounds), false))
+constexpr bool kBoundsChecked = true;
+#else
+#define DG_IN(cond, status) true
+constexpr bool kBoundsChecked = false;
+#endif
 
 // face connection word: >= 0: (neighbour element << 5) | (neighbour face << 3) | orientation;
 // < 0: boundary, id = -1 - word
@@ -92,6 +106,7 @@ struct StageArgs {
   double a, b, dt;
   Gas gas;
   double inflow[3];          // mode 4 ghost at the stage time: rho, rho u_in, E
+  int64_t K_all;             // elements of the local mesh (own and halo): bound of neighbour ids
   // the paper's discretisation (stage_modal.cu): Iq [Nq][Np] | Sv [3][Np][Nq] |
   // Ifn [4][7][Nfq][Nfp] | Sf [4][7][Np][Nfq] | wf [Nfq]; null for the nodal forms
   const double* modal_ops;
@@ -124,6 +139,8 @@ struct StageArgsF32 {
   // << 2 | face), in that order: faces between two elements of the tile
   // (once, under the lower element), faces to other tiles, outer faces
   const uint8_t* face_list;  // [ntiles][16 + 4 ET rounded up to 16 B]
+  int64_t K_all;             // elements of the local mesh (own and halo): bound of neighbour ids
+  int64_t nb;                // boundary face slots (rows of bD)
   // launched as a programmatic dependent of the kernel before it in the
   // stream (the closure, which writes bD): every CTA waits for that kernel
   // (griddep_wait) before its first tile with outer faces, and before it exits
@@ -210,6 +227,7 @@ struct ClosureArgs {
   float a, b, dt;
   int advance;
   int* status;               // kStatusTimeout when a tensor-core completion wait gives up
+  int64_t K_all;             // elements of the local mesh: bound of bface's element ids
 };
 cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s);
 // The closure's weight image (operand layouts of W1 and W2 as tf32 head and
@@ -250,10 +268,10 @@ cudaError_t launch_probe_sample(const double* q, int Np, int n, const int32_t* e
 // buffers [n][5][Nfp] of the state's type
 template <typename T>
 cudaError_t launch_halo_pack(const T* q, int Np, int Nfp, const int32_t* ef, const int32_t* fmask,
-                             int64_t n, T* buf, cudaStream_t s);
+                             int64_t n, T* buf, int64_t K_all, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_halo_unpack(T* q, int Np, int Nfp, const int32_t* ef, const int32_t* fmask,
-                               int64_t n, const T* buf, cudaStream_t s);
+                               int64_t n, const T* buf, int64_t K_all, int* status, cudaStream_t s);
 cudaError_t launch_totals(const double* q, const double* geo, const double* mass_w, int64_t K,
                           int Np, double* partial, int nblocks, double* out, cudaStream_t s);
 

@@ -18,7 +18,7 @@ namespace {
 template <typename T>
 __global__ void halo_pack_kernel(const T* __restrict__ q, int Np, int Nfp,
                                  const int32_t* __restrict__ ef, const int32_t* __restrict__ fmask,
-                                 int64_t n, T* __restrict__ buf) {
+                                 int64_t n, T* __restrict__ buf, int64_t K_all, int* status) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n * 5 * Nfp) return;
   const int64_t k = i / (5 * Nfp);
@@ -26,13 +26,15 @@ __global__ void halo_pack_kernel(const T* __restrict__ q, int Np, int Nfp,
   const int32_t w = ef[k];
   const int64_t e = w >> 2;
   const int f = w & 3;
-  buf[i] = q[(e * 5 + v) * Np + fmask[f * Nfp + m]];
+  const int node = fmask[f * Nfp + m];
+  if (!DG_IN(e >= 0 && e < K_all && node >= 0 && node < Np, status)) return;
+  buf[i] = q[(e * 5 + v) * Np + node];
 }
 
 template <typename T>
 __global__ void halo_unpack_kernel(T* __restrict__ q, int Np, int Nfp,
                                    const int32_t* __restrict__ ef, const int32_t* __restrict__ fmask,
-                                   int64_t n, const T* __restrict__ buf) {
+                                   int64_t n, const T* __restrict__ buf, int64_t K_all, int* status) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n * 5 * Nfp) return;
   const int64_t k = i / (5 * Nfp);
@@ -40,36 +42,41 @@ __global__ void halo_unpack_kernel(T* __restrict__ q, int Np, int Nfp,
   const int32_t w = ef[k];
   const int64_t e = w >> 2;
   const int f = w & 3;
-  q[(e * 5 + v) * Np + fmask[f * Nfp + m]] = buf[i];
+  const int node = fmask[f * Nfp + m];
+  if (!DG_IN(e >= 0 && e < K_all && node >= 0 && node < Np, status)) return;
+  q[(e * 5 + v) * Np + node] = buf[i];
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_halo_pack(const T* q, int Np, int Nfp, const int32_t* ef, const int32_t* fmask,
-                             int64_t n, T* buf, cudaStream_t s) {
+                             int64_t n, T* buf, int64_t K_all, int* status, cudaStream_t s) {
   const int64_t total = n * 5 * Nfp;
   if (total == 0) return cudaSuccess;
-  halo_pack_kernel<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(q, Np, Nfp, ef, fmask, n, buf);
+  halo_pack_kernel<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(q, Np, Nfp, ef, fmask, n, buf,
+                                                                     K_all, status);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_halo_unpack(T* q, int Np, int Nfp, const int32_t* ef, const int32_t* fmask,
-                               int64_t n, const T* buf, cudaStream_t s) {
+                               int64_t n, const T* buf, int64_t K_all, int* status, cudaStream_t s) {
   const int64_t total = n * 5 * Nfp;
   if (total == 0) return cudaSuccess;
-  halo_unpack_kernel<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(q, Np, Nfp, ef, fmask, n, buf);
+  halo_unpack_kernel<T><<<unsigned((total + 255) / 256), 256, 0, s>>>(q, Np, Nfp, ef, fmask, n, buf,
+                                                                       K_all, status);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_halo_pack<float>(const float*, int, int, const int32_t*, const int32_t*,
-                                             int64_t, float*, cudaStream_t);
+                                             int64_t, float*, int64_t, int*, cudaStream_t);
 template cudaError_t launch_halo_pack<double>(const double*, int, int, const int32_t*,
-                                              const int32_t*, int64_t, double*, cudaStream_t);
+                                              const int32_t*, int64_t, double*, int64_t, int*,
+                                              cudaStream_t);
 template cudaError_t launch_halo_unpack<float>(float*, int, int, const int32_t*, const int32_t*,
-                                               int64_t, const float*, cudaStream_t);
+                                               int64_t, const float*, int64_t, int*, cudaStream_t);
 template cudaError_t launch_halo_unpack<double>(double*, int, int, const int32_t*, const int32_t*,
-                                                int64_t, const double*, cudaStream_t);
+                                                int64_t, const double*, int64_t, int*, cudaStream_t);
 
 }  // namespace dgk

@@ -141,7 +141,9 @@ stage_fp64_kernel(const StageArgs A) {
     for (int it = tid; it < nF * Nfp; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
+      if (!DG_IN(le < nE, A.status)) continue;
       const int n = sFmask[f * Nfp + m];
+      if (!DG_IN(n >= 0 && n < Np, A.status)) continue;
       double qm[5], qp[5];
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
       const double* geo = sGeo + le * kGeoStride;
@@ -153,13 +155,17 @@ stage_fp64_kernel(const StageArgs A) {
       if (inside) {
         f2 = (c >> 3) & 3;
         const int o = c & 7;
+        if (!DG_IN(o < 6, A.status)) continue;
         const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
         m2 = sTbl[O::kTbl + ((f * 4 + f2) * 6 + o) * Nfp + m];
+        if (!DG_IN(n2 < Np && m2 < Nfp, A.status)) continue;
         for (int v = 0; v < 5; ++v) qp[v] = sQ[(le2 * 5 + v) * Np + n2];
       } else if (c >= 0) {
         const int64_t e2 = c >> 5;
         const int f2 = (c >> 3) & 3, o = c & 7;
+        if (!DG_IN(e2 < A.K_all && o < 6, A.status)) continue;
         const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+        if (!DG_IN(n2 < Np, A.status)) continue;
         const double* src = A.q_in + e2 * 5 * Np + n2;
         for (int v = 0; v < 5; ++v) qp[v] = __ldg(src + v * Np);
       } else {

@@ -111,7 +111,9 @@ stage_modal_kernel(const StageArgs A) {
       if (c < 0) continue;
       const int64_t e2 = c >> 5;
       const int f2 = (c >> 3) & 3, o = c & 7;
+      if (!DG_IN(e2 < A.K_all && o < 6, A.status)) continue;
       const int n2 = A.nbr_tbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+      if (!DG_IN(n2 < Np, A.status)) continue;
       const double* src = A.q_in + e2 * 5 * Np + n2;
 #pragma unroll
       for (int v = 0; v < 5; ++v) sUp[((le * 4 + f) * 5 + v) * Nfp + m] = src[v * Np];
@@ -125,11 +127,13 @@ stage_modal_kernel(const StageArgs A) {
       const int le = it / (4 * Nfq), r = it - le * 4 * Nfq, f = r / Nfq, q = r - f * Nfq;
       const int32_t c = sConn[le * 4 + f];
       const int var = (c < 0 || e0 + le <= int64_t(c >> 5)) ? 0 : 1 + (c & 7);
+      if (!DG_IN(var < 7, A.status)) continue;
       const double* I = Ifn + ((f * 7 + var) * Nfq + q) * Nfp;
       double qm[5] = {0, 0, 0, 0, 0}, qp[5] = {0, 0, 0, 0, 0};
       for (int m = 0; m < Nfp; ++m) {
         const double w = __ldg(I + m);
         const int n = __ldg(A.fmask + f * Nfp + m);
+        if (!DG_IN(n >= 0 && n < Np, A.status)) continue;
 #pragma unroll
         for (int v = 0; v < 5; ++v) qm[v] += w * sU[(le * 5 + v) * Np + n];
         if (c >= 0) {
@@ -214,6 +218,7 @@ stage_modal_kernel(const StageArgs A) {
       for (int f = 0; f < 4; ++f) {
         const int32_t c = sConn[le * 4 + f];
         const int var = (c < 0 || e0 + le <= int64_t(c >> 5)) ? 0 : 1 + (c & 7);
+        if (!DG_IN(var < 7, A.status)) continue;
         const double* S = Sf + ((f * 7 + var) * Np + n) * Nfq;
         const double* Fs = sFs + ((le * 4 + f) * 5 + v) * Nfq;
         for (int q = 0; q < Nfq; ++q) acc -= __ldg(S + q) * Fs[q];

@@ -257,10 +257,13 @@ stage_tc_kernel(const StageArgsF32 A) {
     for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
+      if (!DG_IN(le < nE, A.status)) continue;
       const int32_t c = sConn[le * 4 + f];
       const int64_t e2 = c >> 5;
       const int f2 = (c >> 3) & 3, o = c & 7;
+      if (!DG_IN(c >= 0 && e2 < A.K_all && o < 6, A.status)) continue;
       const int n2 = sTbl[((f * 4 + f2) * 6 + o) * Nfp + m];
+      if (!DG_IN(n2 < Np, A.status)) continue;
       const float* src = A.q_in + e2 * 5 * Np + n2;
 #pragma unroll
       for (int v = 0; v < 5; ++v) cp_async4(sG + v * kG + le * NF + fm, src + v * Np);
@@ -319,7 +322,9 @@ stage_tc_kernel(const StageArgsF32 A) {
     for (int it = tid; it < cEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
+      if (!DG_IN(le < nE, A.status)) continue;
       const int n = sFmask[f * Nfp + m];
+      if (!DG_IN(n >= 0 && n < Np, A.status)) continue;
       float qm[5], qp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) qm[v] = sQ[(le * 5 + v) * Np + n];
@@ -331,7 +336,9 @@ stage_tc_kernel(const StageArgsF32 A) {
       if (it < aEnd) {
         // both elements in the tile
         const int le2 = (c >> 5) - e0i, f2 = (c >> 3) & 3, o = c & 7;
+        if (!DG_IN(c >= 0 && le2 >= 0 && le2 < nE && o < 6, A.status)) continue;
         const int tb = ((f * 4 + f2) * 6 + o) * Nfp + m;
+        if (!DG_IN(sTbl[tb] < Np && sTbl[96 * Nfp + tb] < Nfp, A.status)) continue;
         const float* src = sQ + le2 * 5 * Np + sTbl[tb];
 #pragma unroll
         for (int v = 0; v < 5; ++v) qp[v] = src[v * Np];
@@ -358,6 +365,7 @@ stage_tc_kernel(const StageArgsF32 A) {
         // outer face: ghost state, and the flux integral for the ledger
         const int mode = A.bc_mode[(-1 - c) & 7];
         if (mode == 3) {
+          if (!DG_IN(c < 0 && ((-1 - c) >> 3) < A.nb, A.status)) continue;
           const float D = A.bD ? A.bD[size_t((-1 - c) >> 3) * Nfp + m] : 0.0f;
           ghost_learned_f(qm, nv, bg, D, qp);
         } else {
