@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(kCT, 3) closure_tc_kernel(ClosureArgs A, BaseG
   const int64_t total = A.nb * A.Nfp;
   const int ntiles = int((total + kRows - 1) / kRows);
   // the stage kernel launched after this one may take SMs as CTAs of this
-  // grid finish: it waits for the whole grid before reading D
+  // grid finish and run its prologue; it waits for the whole grid before
+  // its first tile
   griddep_launch_dependents();
 
   for (int j = tid; j < 4 * A.Nfp; j += kCT) reinterpret_cast<int32_t*>(smem + oFm)[j] = A.fmask[j];

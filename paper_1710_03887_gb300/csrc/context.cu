@@ -539,8 +539,8 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
     int rc = run_memory(c, to_scratch, a, b, dt, &after_kernel);
     if (rc) return rc;
     // the stage kernel may start while the closure finishes: before its
-    // griddep_wait it touches nothing the closure writes (D, the memories),
-    // and it writes nothing the closure reads (q[cur] it only reads)
+    // griddep_wait (after its prologue) it touches nothing the closure
+    // writes (D, the memories) and writes nothing the closure reads
     A.pdl = after_kernel ? 1 : 0;
     if (c->prec == DG_PREC_F32_TC)
       DG_CUDA(dgk::launch_stage_tc(c->ref.p, A, c->grid, c->stream));

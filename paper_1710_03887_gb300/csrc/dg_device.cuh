@@ -142,8 +142,8 @@ struct StageArgsF32 {
   int64_t K_all;             // elements of the local mesh (own and halo): bound of neighbour ids
   int64_t nb;                // boundary face slots (rows of bD)
   // launched as a programmatic dependent of the kernel before it in the
-  // stream (the closure, which writes bD): every CTA waits for that kernel
-  // (griddep_wait) before its first tile with outer faces, and before it exits
+  // stream (the closure, which writes bD): every CTA stages its operators and
+  // starts its first tile's copies, then waits for that kernel (griddep_wait)
   int pdl;
 };
 

@@ -190,10 +190,10 @@ stage_f32_kernel(const StageArgsF32 A) {
   };
   prefetch(blockIdx.x, 0);
   cp_async_commit();
+  if (A.pdl) griddep_wait();         // the closure's increments bD, read by outer faces
 
   int iter = 0;
   double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
-  bool waited = A.pdl == 0;          // for the closure's increments bD (uniform)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int e0i = int(e0);
@@ -214,10 +214,6 @@ stage_f32_kernel(const StageArgsF32 A) {
     // tiles, [bEnd, cEnd) outer faces (items = face x face node)
     const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
     const int aEnd = hdr[1] * Nfp, bEnd = (hdr[1] + hdr[2]) * Nfp, cEnd = hdr[0] * Nfp;
-    if (!waited && cEnd > bEnd) {
-      griddep_wait();                  // outer faces read the closure's increments
-      waited = true;
-    }
     for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
@@ -435,8 +431,6 @@ stage_f32_kernel(const StageArgsF32 A) {
       }
     }
   }
-  // the grid does not complete before the kernel it depends on
-  if (!waited) griddep_wait();
   ledger_finish(A.led, cled);
 }
 

@@ -227,10 +227,10 @@ stage_tc_kernel(const StageArgsF32 A) {
   };
   prefetch(blockIdx.x, 0);
   cp_async_commit();
+  if (A.pdl) griddep_wait();         // the closure's increments bD, read by outer faces
 
   double cled = 0.0;                 // this CTA's ledger sums (threads 0..4)
   int iter = 0;
-  bool waited = A.pdl == 0;          // for the closure's increments bD (uniform)
   for (int tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x, ++iter) {
     const int64_t e0 = int64_t(tile) * ET;
     const int nE = int((A.K - e0) < ET ? (A.K - e0) : int64_t(ET));
@@ -250,10 +250,6 @@ stage_tc_kernel(const StageArgsF32 A) {
     const int32_t* hdr = reinterpret_cast<const int32_t*>(sFL);
     const int aEnd = hdr[1] * Nfp, bEnd = (hdr[1] + hdr[2]) * Nfp, cEnd = hdr[0] * Nfp;
     const int e0i = int(e0);
-    if (!waited && cEnd > bEnd) {
-      griddep_wait();                  // outer faces read the closure's increments
-      waited = true;
-    }
     for (int it = aEnd + tid; it < bEnd; it += NT) {
       const int fi = it / Nfp, m = it - (it / Nfp) * Nfp;
       const int ent = sFL[16 + fi], le = ent >> 2, f = ent & 3, fm = f * Nfp + m;
@@ -493,8 +489,6 @@ stage_tc_kernel(const StageArgsF32 A) {
     }
   }
   cp_async_wait_all();
-  // the grid does not complete before the kernel it depends on
-  if (!waited) griddep_wait();
   // a wait that gave up may leave MMAs in flight: give them a bounded chance
   // to finish before the tensor memory is released. `phase` was flipped after
   // the wait that gave up, so that wait's parity is phase ^ 1 (waiting on
