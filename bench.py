@@ -17,7 +17,8 @@ five-stage low-storage RK4 time step of the whole mesh.
              bound) per launch / average launch time (CUDA event pairs around
              every stage launch on the solver's stream)
   forms      every arithmetic form (float32 perturbation, its tensor-core
-             variant, float64) timed the same way, with the float32 forms'
+             variant, float64, the paper's modal form, and the one-pass
+             tensor-core variant) timed the same way, with the float32 forms'
              error against float64 after the timed steps
   learned_bc the learned boundary closure: traces recorded, network trained
              and reflected energies measured on the GPU, and the closure timed on
@@ -351,7 +352,7 @@ def measure_form(args, precision, xyz, EToV, dev, stream, dist, world, sample_cl
     from paper_1710_03887_gb300 import workloads as W
     w = WORKLOAD
     prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC, "fp64": B.DG_PREC_FP64,
-            "modal": B.DG_PREC_MODAL}[precision]
+            "modal": B.DG_PREC_MODAL, "f32_tc1": B.DG_PREC_F32_TC1}[precision]
     S = B.Solver(order or w["order"], W.GAMMA, W.RHO0_SI, W.P0_SI, precision=prec)
     S.set_stream(stream.cuda_stream)
     S.upload_mesh(xyz, EToV)
@@ -496,8 +497,9 @@ def roofline_for(m, order):
     # 1,744 B per element) is below the ridge: bound by HBM
     return {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
             "frac": hbm_achieved / hbm,
-            "traffic": profiled_traffic("stage_tc_p3_ball.md", "stage_tc.cu"),
-            "kernel": "stage_tc_kernel<3>",
+            "traffic": (profiled_traffic("stage_tc_p3_ball.md", "stage_tc.cu")
+                        if m["precision"] == "f32_tc" else None),
+            "kernel": "stage_tc_kernel<3>" + (" (one pass)" if m["precision"] == "f32_tc1" else ""),
             "note": ("algorithmic bytes per stage: q, res read + q, res written (float32), "
                      "geometry record 128 B, connections 16 B; peak " + hbm_src),
             "flops_frac_fp32": flops / fp32_peak_tflops(2070.0),
@@ -1110,7 +1112,7 @@ def run_gpu(args, rank, world):
             }
             print(json.dumps(line), flush=True)
         return
-    forms = [args.precision] + [f for f in ("f32_tc", "f32", "fp64", "modal")
+    forms = [args.precision] + [f for f in ("f32_tc", "f32", "fp64", "modal", "f32_tc1")
                                 if f != args.precision and not args.one_form]
     res = {f: measure_form(args, f, xyz, EToV, dev, stream, dist, world, sample_clocks=(f == args.precision))
            for f in forms}
@@ -1141,7 +1143,7 @@ def run_gpu(args, rank, world):
                         "repeats": repeat_stats(m["reps"], args.steps),
                         "roofline": roofline_for(m, w["order"])}
     from paper_1710_03887_gb300 import workloads as W
-    for f in ("f32", "f32_tc"):
+    for f in ("f32", "f32_tc", "f32_tc1"):
         if f in res and "fp64" in res:
             a, b = res[f], res["fp64"]
             base = W.uniform_state(a["q0"].shape[0], a["q0"].shape[2], W.RHO0_SI, (0, 0, 0),
@@ -1216,7 +1218,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=50,
                     help="oracle steps on the CPU sample (about 10-20 s of one core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64", "modal"],
+    ap.add_argument("--precision", default="f32", choices=["f32", "f32_tc", "fp64", "modal", "f32_tc1"],
                     help="arithmetic form of the headline number (the other is measured beside it)")
     ap.add_argument("--one-form", action="store_true", help="measure only --precision")
     ap.add_argument("--partition", action="store_true",

@@ -110,6 +110,12 @@ extern "C" {
                                 /* The state crosses the ABI as nodal values of the same */
                                 /* polynomials (the nodes of the other forms), so probes,*/
                                 /* totals and dg_stable_dt work unchanged.               */
+#define DG_PREC_F32_TC1 4       /* DG_PREC_F32_TC with one MMA per k-step: the float32   */
+                                /* operands are read as tf32 by the tensor cores (no     */
+                                /* head/tail split), so the contractions carry ~2^-10    */
+                                /* relative operand error (about 1e-3 of the right-hand  */
+                                /* side) against float32's 2^-24: a measured variant of  */
+                                /* the contraction's precision, not the float32 form.    */
 
 /* Free-stream gas and defaults of a context. */
 typedef struct dg_params {

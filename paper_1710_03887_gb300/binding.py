@@ -38,6 +38,7 @@ DG_PREC_FP64 = 0
 DG_PREC_F32 = 1
 DG_PREC_F32_TC = 2
 DG_PREC_MODAL = 3
+DG_PREC_F32_TC1 = 4
 
 
 class dg_params(C.Structure):
@@ -485,7 +486,8 @@ class Solver:
 
     def halo_dtype(self):
         """Element type of halo buffers: the state's own representation."""
-        return np.float32 if self.precision in (DG_PREC_F32, DG_PREC_F32_TC) else np.float64
+        return (np.float32 if self.precision in (DG_PREC_F32, DG_PREC_F32_TC, DG_PREC_F32_TC1)
+                else np.float64)
 
     def halo_pack(self, buf):
         """buf: CUDA tensor [n_send, 5, Nfp] of halo_dtype()."""

@@ -177,7 +177,9 @@ struct dg_ctx {
   }
   size_t state_elems() const { return size_t(mesh.K) * 5 * ref.Np; }
   int64_t owned() const { return K_own < 0 ? mesh.K : K_own; }
-  bool f32() const { return prec == DG_PREC_F32 || prec == DG_PREC_F32_TC; }
+  bool f32() const { return prec == DG_PREC_F32 || tc(); }
+  bool tc() const { return prec == DG_PREC_F32_TC || prec == DG_PREC_F32_TC1; }
+  int tc_images() const { return prec == DG_PREC_F32_TC1 ? 1 : 2; }
 };
 
 namespace {
@@ -211,11 +213,11 @@ int ensure_device(dg_ctx* c) {
   DG_CUDA(cudaGetDevice(&dev));
   DG_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
   const bool f32 = c->f32();
-  const bool tcf = c->prec == DG_PREC_F32_TC;
+  const bool tcf = c->tc();
   const bool modal = c->prec == DG_PREC_MODAL;
   int bps = 0;
   if (tcf)
-    DG_CUDA(dgk::stage_tc_prepare(p, &bps));
+    DG_CUDA(dgk::stage_tc_prepare(p, c->tc_images(), &bps));
   else if (f32)
     DG_CUDA(dgk::stage_f32_prepare(p, &bps));
   else if (modal)
@@ -371,9 +373,9 @@ int ensure_device(dg_ctx* c) {
   }
   if (tcf) {
     // operator matrix [-Dr | -Ds | -Dt | LIFT] as the tensor-core operand image
-    std::vector<unsigned char> img(dgk::stage_tc_ops_bytes(p));
-    dgk::build_tc_ops(p, c->ref.Dr.data(), c->ref.Ds.data(), c->ref.Dt.data(), c->ref.LIFT.data(),
-                      c->ref.face_w.data(), img.data());
+    std::vector<unsigned char> img(dgk::stage_tc_ops_bytes(p, c->tc_images()));
+    dgk::build_tc_ops(p, c->tc_images(), c->ref.Dr.data(), c->ref.Ds.data(), c->ref.Dt.data(),
+                      c->ref.LIFT.data(), c->ref.face_w.data(), img.data());
     DG_CUDA(cudaMalloc(&c->ops32, img.size()));
     DG_CUDA(cudaMemcpy(c->ops32, img.data(), img.size(), cudaMemcpyHostToDevice));
   } else if (f32) {
@@ -542,8 +544,8 @@ int run_stage(dg_ctx* c, bool to_scratch, double a, double b, double dt, double 
     // griddep_wait (after its prologue) it touches nothing the closure
     // writes (D, the memories) and writes nothing the closure reads
     A.pdl = after_kernel ? 1 : 0;
-    if (c->prec == DG_PREC_F32_TC)
-      DG_CUDA(dgk::launch_stage_tc(c->ref.p, A, c->grid, c->stream));
+    if (c->tc())
+      DG_CUDA(dgk::launch_stage_tc(c->ref.p, c->tc_images(), A, c->grid, c->stream));
     else
       DG_CUDA(dgk::launch_stage_f32(c->ref.p, A, c->grid, c->stream));
   } else {
@@ -641,9 +643,11 @@ int dg_create(int order, const dg_params* params, dg_ctx** out) {
   if (!(params->gamma > 1.0) || !(params->rho0 > 0.0) || !(params->p0 > 0.0)) return DG_ERR_ARG;
   if (params->default_bc < 0 || params->default_bc > 2) return DG_ERR_ARG;
   if (params->precision != DG_PREC_FP64 && params->precision != DG_PREC_F32 &&
-      params->precision != DG_PREC_F32_TC && params->precision != DG_PREC_MODAL)
+      params->precision != DG_PREC_F32_TC && params->precision != DG_PREC_MODAL &&
+      params->precision != DG_PREC_F32_TC1)
     return DG_ERR_UNSUPPORTED;
-  if ((params->precision == DG_PREC_F32 || params->precision == DG_PREC_F32_TC) &&
+  if ((params->precision == DG_PREC_F32 || params->precision == DG_PREC_F32_TC ||
+       params->precision == DG_PREC_F32_TC1) &&
       (params->u0[0] != 0.0 || params->u0[1] != 0.0 || params->u0[2] != 0.0))
     return DG_ERR_UNSUPPORTED;   // the perturbation form is built around a resting base state
   if (order < 1 || order > dg::kMaxOrder) return DG_ERR_UNSUPPORTED;

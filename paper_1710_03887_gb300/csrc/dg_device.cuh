@@ -188,13 +188,16 @@ cudaError_t launch_probe_sample_f32(const float* q, int Np, int n, const int32_t
 
 // Tensor-core form of the float32 stage (stage_tc.cu), orders 1..4; uses
 // StageArgsF32 with ops pointing at the image built by build_tc_ops.
-size_t stage_tc_ops_bytes(int p);
+// images = 2: tf32 head and tail of both operands, three MMAs per k-step
+// (DG_PREC_F32_TC); images = 1: one MMA per k-step on the float32 values
+// read as tf32 (DG_PREC_F32_TC1).
+size_t stage_tc_ops_bytes(int p, int images);
 int stage_tc_tile_elems(int p);
 int stage_tc_ctas_per_sm(int p);
-void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
-                  const double* face_w, unsigned char* out);
-cudaError_t stage_tc_prepare(int p, int* blocks_per_sm);
-cudaError_t launch_stage_tc(int p, const StageArgsF32& a, int grid, cudaStream_t s);
+void build_tc_ops(int p, int images, const double* Dr, const double* Ds, const double* Dt,
+                  const double* LIFT, const double* face_w, unsigned char* out);
+cudaError_t stage_tc_prepare(int p, int images, int* blocks_per_sm);
+cudaError_t launch_stage_tc(int p, int images, const StageArgsF32& a, int grid, cudaStream_t s);
 
 // Learned closure (learned.cu)
 struct BaseGhost;

@@ -34,7 +34,10 @@
 
 namespace dgk {
 
-template <int P>
+// S = operand images per operand: 2 (tf32 head and tail, three MMAs per
+// k-step: the float32-level form) or 1 (the float32 values read as tf32 by
+// the MMA, one MMA per k-step: the one-pass variant, DG_PREC_F32_TC1)
+template <int P, int S = 2>
 struct OrderTC {
   static constexpr int Np = (P + 1) * (P + 2) * (P + 3) / 6;
   static constexpr int Nfp = (P + 1) * (P + 2) / 2;
@@ -63,10 +66,10 @@ struct OrderTC {
   // space, tables, face lists, barrier
   static constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
   static constexpr size_t oAhi = 0;
-  static constexpr size_t oAlo = oAhi + kABytes;
-  static constexpr size_t oBhi = oAlo + kABytes;
-  static constexpr size_t oBlo = oBhi + kBBytes;
-  static constexpr size_t oG = al16(oBlo + kBBytes);
+  static constexpr size_t oAlo = oAhi + kABytes;                   // (S = 2 only)
+  static constexpr size_t oBhi = oAhi + size_t(S) * kABytes;
+  static constexpr size_t oBlo = oBhi + kBBytes;                   // (S = 2 only)
+  static constexpr size_t oG = al16(oBhi + size_t(S) * kBBytes);
   static constexpr size_t oR = al16(oG + size_t(5 * kG) * 4);
   static constexpr size_t oQ = al16(oR + size_t(5 * ET) * SO * 4);
   static constexpr size_t oGeo = al16(oQ + 2 * size_t(kQT) * 4);
@@ -82,7 +85,7 @@ struct OrderTC {
   static constexpr size_t bytes = oBar + 32;
   static_assert(bytes <= (CPS == 2 ? 113 : 227) * 1024, "CTAs per SM");
   static_assert(N <= 64, "accumulator rows read as 32 + 8 columns");
-  static constexpr size_t kOpsBytes = 2 * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
+  static constexpr size_t kOpsBytes = S * size_t(kBBytes) + size_t(NF) * 4;   // B images + face weights
 };
 
 struct BaseF2 {
@@ -148,16 +151,16 @@ __device__ __forceinline__ void store_a(unsigned char* ahi, uint32_t off, float 
 //  6. warps 0..3 move their accumulator rows (M = 64: row r in tensor-memory
 //     lane 32 (r / 16) + r % 16) into R, and all threads update q and res
 //     with coalesced accesses.
-template <int P>
-__global__ void __launch_bounds__(OrderTC<P>::NT, OrderTC<P>::CPS)
+template <int P, int S>
+__global__ void __launch_bounds__(OrderTC<P, S>::NT, OrderTC<P, S>::CPS)
 stage_tc_kernel(const StageArgsF32 A) {
-  using O = OrderTC<P>;
+  using O = OrderTC<P, S>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NF = O::NF, ET = O::ET, NT = O::NT;
   constexpr int K = O::K, SO = O::SO, kG = O::kG;
   constexpr uint32_t SBO = O::SBO;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* sAhi = smem + O::oAhi;
-  unsigned char* sAlo = smem + O::oAlo;
+  [[maybe_unused]] unsigned char* sAlo = smem + O::oAlo;
   float* sG = reinterpret_cast<float*>(smem + O::oG);
   float* sR = reinterpret_cast<float*>(smem + O::oR);
   float* sW = reinterpret_cast<float*>(smem + O::oW);
@@ -175,11 +178,11 @@ stage_tc_kernel(const StageArgsF32 A) {
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.ops);
     uint4* dst = reinterpret_cast<uint4*>(smem + O::oBhi);
-    for (int i = tid; i < int(2 * O::kBBytes / 16); i += NT) dst[i] = src[i];
+    for (int i = tid; i < int(S * O::kBBytes / 16); i += NT) dst[i] = src[i];
     uint4* a = reinterpret_cast<uint4*>(smem + O::oAhi);
-    for (int i = tid; i < int(2 * O::kABytes / 16); i += NT) a[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < int(S * O::kABytes / 16); i += NT) a[i] = make_uint4(0, 0, 0, 0);
     const float* w = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(A.ops) +
-                                                    2 * O::kBBytes);
+                                                    S * O::kBBytes);
     for (int i = tid; i < NF; i += NT) sW[i] = w[i];
     for (int i = tid; i < 2 * 96 * Nfp; i += NT) sTbl[i] = A.nbr_tbl[i];   // volume- and face-node tables
     for (int i = tid; i < NF; i += NT) sFmask[i] = A.fmask[i];
@@ -393,7 +396,9 @@ stage_tc_kernel(const StageArgsF32 A) {
       }
     }
     // every A entry is written: split each 16-byte chunk of the head image
-    // into its tf32 head (in place) and tail (same offset in the tail image)
+    // into its tf32 head (in place) and tail (same offset in the tail image);
+    // the one-pass variant gives the float32 values to the MMA as they are
+    if constexpr (S == 2) {
     __syncthreads();
     for (int i = tid; i < int(O::kABytes / 16); i += NT) {
       const float4 x = *reinterpret_cast<const float4*>(sAhi + 16 * i);
@@ -409,6 +414,7 @@ stage_tc_kernel(const StageArgsF32 A) {
       *reinterpret_cast<float4*>(sAhi + 16 * i) = h;
       *reinterpret_cast<float4*>(sAlo + 16 * i) = l;
     }
+    }
     // operand writes become visible to the tensor cores
     tc::fence_smem_to_async();
     __syncthreads();
@@ -417,15 +423,23 @@ stage_tc_kernel(const StageArgsF32 A) {
       // descriptors of k-step s: the start address field (bits 0-13, in
       // 16-byte units) advances by 256 bytes = 16 units per step
       const uint64_t dAhi = tc::smem_desc(tc::smem_addr(sAhi), 128u, SBO);
-      const uint64_t dAlo = tc::smem_desc(tc::smem_addr(sAlo), 128u, SBO);
       const uint64_t dBhi = tc::smem_desc(tc::smem_addr(smem + O::oBhi), 128u, SBO);
-      const uint64_t dBlo = tc::smem_desc(tc::smem_addr(smem + O::oBlo), 128u, SBO);
+      if constexpr (S == 2) {
+        const uint64_t dAlo = tc::smem_desc(tc::smem_addr(sAlo), 128u, SBO);
+        const uint64_t dBlo = tc::smem_desc(tc::smem_addr(smem + O::oBlo), 128u, SBO);
 #pragma unroll
-      for (int s = 0; s < K / 8; ++s) {
-        const uint64_t step = 16u * uint64_t(s);
-        tc::mma_tf32(tmem, dAhi + step, dBhi + step, idesc, s > 0 ? 1u : 0u);
-        tc::mma_tf32(tmem, dAhi + step, dBlo + step, idesc, 1u);
-        tc::mma_tf32(tmem, dAlo + step, dBhi + step, idesc, 1u);
+        for (int s = 0; s < K / 8; ++s) {
+          const uint64_t step = 16u * uint64_t(s);
+          tc::mma_tf32(tmem, dAhi + step, dBhi + step, idesc, s > 0 ? 1u : 0u);
+          tc::mma_tf32(tmem, dAhi + step, dBlo + step, idesc, 1u);
+          tc::mma_tf32(tmem, dAlo + step, dBhi + step, idesc, 1u);
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < K / 8; ++s) {
+          const uint64_t step = 16u * uint64_t(s);
+          tc::mma_tf32(tmem, dAhi + step, dBhi + step, idesc, s > 0 ? 1u : 0u);
+        }
       }
       tc::mma_commit(mbar);
     }
@@ -503,25 +517,32 @@ stage_tc_kernel(const StageArgsF32 A) {
   ledger_finish(A.led, cled);
 }
 
-size_t stage_tc_ops_bytes(int p) {
-  switch (p) {
-    case 1: return OrderTC<1>::kOpsBytes;
-    case 2: return OrderTC<2>::kOpsBytes;
-    case 3: return OrderTC<3>::kOpsBytes;
-    default: return OrderTC<4>::kOpsBytes;
+// orders 1..4 x images 1, 2: f(P, S) for the runtime pair (p, images)
+#define DGK_TC_DISPATCH(p, images, F)                            \
+  switch ((p) * 4 + (images)) {                                  \
+    case 1 * 4 + 1: F(1, 1); case 1 * 4 + 2: F(1, 2);             \
+    case 2 * 4 + 1: F(2, 1); case 2 * 4 + 2: F(2, 2);             \
+    case 3 * 4 + 1: F(3, 1); case 3 * 4 + 2: F(3, 2);             \
+    case 4 * 4 + 1: F(4, 1); default: F(4, 2);                    \
   }
+
+size_t stage_tc_ops_bytes(int p, int images) {
+#define F(P, S) return OrderTC<P, S>::kOpsBytes
+  DGK_TC_DISPATCH(p, images, F)
+#undef F
 }
 
 int stage_tc_tile_elems(int) { return 12; }
 
 int stage_tc_ctas_per_sm(int p) { return p <= 3 ? OrderTC<3>::CPS : OrderTC<4>::CPS; }
 
-// Host-side image of B = [-Dr | -Ds | -Dt | LIFT] in the operand layout,
-// split into tf32 head and tail, followed by the face weights.
-template <int P>
+// Host-side image of B = [-Dr | -Ds | -Dt | LIFT] in the operand layout:
+// with S = 2 split into tf32 head and tail, with S = 1 the tf32 rounding
+// alone; followed by the face weights.
+template <int P, int S>
 static void build_ops_impl(const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
                            const double* face_w, unsigned char* out) {
-  using O = OrderTC<P>;
+  using O = OrderTC<P, S>;
   auto tf32 = [](float x) {
     uint32_t u;
     std::memcpy(&u, &x, 4);
@@ -546,52 +567,48 @@ static void build_ops_impl(const double* Dr, const double* Ds, const double* Dt,
       const float h = tf32(x);
       const uint32_t off = tc::kmajor_offset(i, k, O::SBO) / 4;
       hi[off] = h;
-      lo[off] = tf32(x - h);
+      if constexpr (S == 2) lo[off] = tf32(x - h);
     }
-  float* w = reinterpret_cast<float*>(out + 2 * O::kBBytes);
+  float* w = reinterpret_cast<float*>(out + S * O::kBBytes);
   for (int m = 0; m < O::NF; ++m) w[m] = float(face_w[m]);
 }
 
-void build_tc_ops(int p, const double* Dr, const double* Ds, const double* Dt, const double* LIFT,
-                  const double* face_w, unsigned char* out) {
-  switch (p) {
-    case 1: build_ops_impl<1>(Dr, Ds, Dt, LIFT, face_w, out); break;
-    case 2: build_ops_impl<2>(Dr, Ds, Dt, LIFT, face_w, out); break;
-    case 3: build_ops_impl<3>(Dr, Ds, Dt, LIFT, face_w, out); break;
-    default: build_ops_impl<4>(Dr, Ds, Dt, LIFT, face_w, out); break;
-  }
+void build_tc_ops(int p, int images, const double* Dr, const double* Ds, const double* Dt,
+                  const double* LIFT, const double* face_w, unsigned char* out) {
+#define F(P, S) return build_ops_impl<P, S>(Dr, Ds, Dt, LIFT, face_w, out)
+  DGK_TC_DISPATCH(p, images, F)
+#undef F
 }
 
-template <int P>
+template <int P, int S>
 static cudaError_t prepare_tc_impl(int* bps) {
-  cudaError_t e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(OrderTC<P>::bytes));
+  cudaError_t e = cudaFuncSetAttribute(stage_tc_kernel<P, S>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(OrderTC<P, S>::bytes));
   if (e != cudaSuccess) return e;
   // the whole unified L1 as shared memory (two CTAs per SM at p <= 3)
-  e = cudaFuncSetAttribute(stage_tc_kernel<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  e = cudaFuncSetAttribute(stage_tc_kernel<P, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            int(cudaSharedmemCarveoutMaxShared));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, stage_tc_kernel<P>, OrderTC<P>::NT,
-                                                       OrderTC<P>::bytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, stage_tc_kernel<P, S>,
+                                                       OrderTC<P, S>::NT, OrderTC<P, S>::bytes);
 }
 
-cudaError_t stage_tc_prepare(int p, int* bps) {
-  switch (p) {
-    case 1: return prepare_tc_impl<1>(bps);
-    case 2: return prepare_tc_impl<2>(bps);
-    case 3: return prepare_tc_impl<3>(bps);
-    default: return prepare_tc_impl<4>(bps);
-  }
+cudaError_t stage_tc_prepare(int p, int images, int* bps) {
+#define F(P, S) return prepare_tc_impl<P, S>(bps)
+  DGK_TC_DISPATCH(p, images, F)
+#undef F
 }
 
-cudaError_t launch_stage_tc(int p, const StageArgsF32& a, int grid, cudaStream_t s) {
+cudaError_t launch_stage_tc(int p, int images, const StageArgsF32& a, int grid, cudaStream_t s) {
   const bool pdl = a.pdl != 0;
-  switch (p) {
-    case 1: return launch_stage_kernel(stage_tc_kernel<1>, grid, OrderTC<1>::NT, OrderTC<1>::bytes, s, a, pdl);
-    case 2: return launch_stage_kernel(stage_tc_kernel<2>, grid, OrderTC<2>::NT, OrderTC<2>::bytes, s, a, pdl);
-    case 3: return launch_stage_kernel(stage_tc_kernel<3>, grid, OrderTC<3>::NT, OrderTC<3>::bytes, s, a, pdl);
-    default: return launch_stage_kernel(stage_tc_kernel<4>, grid, OrderTC<4>::NT, OrderTC<4>::bytes, s, a, pdl);
-  }
+#define F(P, S)                                                                               \
+  return launch_stage_kernel(stage_tc_kernel<P, S>, grid, OrderTC<P, S>::NT, OrderTC<P, S>::bytes, \
+                             s, a, pdl)
+  DGK_TC_DISPATCH(p, images, F)
+#undef F
 }
+
+#undef DGK_TC_DISPATCH
 
 }  // namespace dgk
