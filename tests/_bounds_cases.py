@@ -22,8 +22,8 @@ from paper_1710_03887_gb300 import workloads as W
 
 SI = dict(gamma=W.GAMMA, rho0=W.RHO0_SI, p0=W.P0_SI)
 PRECS = {"fp64": B.DG_PREC_FP64, "f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC,
-         "modal": B.DG_PREC_MODAL}
-FORMS = [("fp64", 2), ("fp64", 3), ("f32", 3), ("f32", 4), ("f32_tc", 3), ("f32_tc", 4),
+         "modal": B.DG_PREC_MODAL, "f32_tc1": B.DG_PREC_F32_TC1}
+FORMS = [("fp64", 2), ("fp64", 3), ("f32", 3), ("f32", 4), ("f32_tc", 3), ("f32_tc", 4), ("f32_tc1", 3),
          ("modal", 2)]
 PROBES = np.array([[0.1, 0.2, -0.3], [-0.5, 0.4, 0.6], [0.8, -0.7, 0.05]])
 
