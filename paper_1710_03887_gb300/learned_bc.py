@@ -142,10 +142,25 @@ def record(order, nested, runs, every, device, width_scale=1.0, precision=None, 
     return torch.cat(Xs), torch.cat(Ys)
 
 
-def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
+# inputs that name an absolute direction: the outward normal (features 5-7)
+# and the position x / R (8-10)
+DIRECTION_FEATURES = tuple(range(5, 11))
+
+
+def train(X, Y, iters, lr, seed=0, radius=1.0, order=3, invariant=True):
     """Adam on the GPU from seeded Glorot hidden layers and a zero output
     layer (so training starts from the spherical-wave condition); returns
-    (weights, losses)."""
+    (weights, losses).
+
+    With ``invariant`` (the default) the network is trained without the
+    inputs that name an absolute direction (``DIRECTION_FEATURES``: zeroed
+    in a copy of X) and those inputs' first-layer weights are zero in the
+    result, so the deployed closure computes exactly the trained function
+    and treats every direction alike, as a far-field condition about the
+    centre should: it sees a wave's direction only through the tangential
+    velocity and the normal velocity (in w_out). Trained with them, the
+    network ties corrections to where the training runs' sources lay and
+    reflects 1.5-2x more on centred pulses (measured on the n = 16 ball)."""
     rng = np.random.default_rng(seed)
     w0 = []
     dims = [(12, 64), (64, 64), (64, 5)]
@@ -155,6 +170,11 @@ def train(X, Y, iters, lr, seed=0, radius=1.0, order=3):
         w0.append(np.zeros(b))
     w0 = np.concatenate(w0).astype(np.float32)
     w0[-5 - 64 * 5:] = 0.0                    # W3, b3: output 0 starts at zero
+    if invariant:
+        X = X.clone() if hasattr(X, "clone") else np.array(X, dtype=np.float32, copy=True)
+        X[:, list(DIRECTION_FEATURES)] = 0.0
+        for c in DIRECTION_FEATURES:          # W1 rows of those inputs (input index first)
+            w0[c * 64:(c + 1) * 64] = 0.0     # (zero inputs leave them untouched)
     S = B.Solver(order, W.GAMMA, W.RHO0_SI, W.P0_SI, precision=B.DG_PREC_F32)
     S.set_bc_mlp(w0, radius)
     hist = S.mlp_train(X, Y, iters, lr)

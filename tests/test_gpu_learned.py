@@ -185,21 +185,23 @@ def test_spherical_closure_absorbs_a_centred_pulse(cuda_device):
 def test_learned_closure_against_characteristic_and_spherical(cuda_device):
     """Train on the method's own traces at r = 1 inside the radius-2 ball (the
     bench's seeded runs: 8 with random centres, 24 centred, a quarter of the
-    trace nodes sampled) and compare reflected energies on the truncated
-    ball (the large ball is the reference) with the two conditions the
-    network starts from or improves on:
+    trace nodes sampled; the network without the absolute-direction inputs)
+    and compare reflected energies on the truncated ball (the large ball is
+    the reference) with the two conditions the network starts from or
+    improves on:
 
     * the characteristic condition: the trained closure reflects far less,
       on centred and off-centre pulses;
     * the spherical-wave memory (the network's starting point, output zero):
       off the centre, where the memory's curvature is wrong, training
-      reduces the reflection below the memory's. On a centred pulse the
-      memory is exact up to discretisation (~1e-5 of the energy); the
-      network, which sees one face node's trace and cannot tell a centred
-      wavefront from an off-centre one at the same incidence, adds part of
-      its fitting error there (the centred runs keep that small): it stays
-      within 4 times the memory's reflection, over two orders below the
-      characteristic condition."""
+      reduces the reflection below the memory's (0.9x at most). On a
+      centred pulse the memory is exact up to discretisation (~1e-5 of the
+      energy); the network, which sees one face node's trace and cannot
+      tell a centred wavefront from an off-centre one at the same
+      incidence, adds a little of its fitting error there: it stays within
+      twice the memory's reflection, three orders below the characteristic
+      condition. The trained network has zero weights on the normal and
+      position inputs."""
     p, n = 3, 16
     nested = L.nested_ball(n)
     X, Y = L.record(p, nested, L.run_seeds(0, 8, 24), every=10, device=cuda_device,
@@ -207,6 +209,8 @@ def test_learned_closure_against_characteristic_and_spherical(cuda_device):
     assert X.shape[0] > 100000
     w, hist = L.train(X, Y, iters=600, lr=3e-3, seed=0, radius=1.0, order=p)
     assert hist[-1] < 0.9 * hist[0]
+    W1 = np.asarray(w)[:12 * 64].reshape(12, 64)
+    assert np.all(W1[list(L.DIRECTION_FEATURES)] == 0.0)
     table = {}
     for amp, width, centre in ((0.005, 0.3, (0.0, 0.0, 0.0)), (0.1, 0.3, (0.0, 0.0, 0.0)),
                                (0.02, 0.25, (0.3, 0.1, -0.2)), (0.02, 0.25, (-0.2, 0.35, 0.1))):
@@ -215,7 +219,7 @@ def test_learned_closure_against_characteristic_and_spherical(cuda_device):
     for (amp, centre), r in table.items():
         assert r["learned"] < 0.15 * r["characteristic"], (amp, centre, r)
         if centre == (0.0, 0.0, 0.0):
-            assert r["learned"] < 0.01 * r["characteristic"], (amp, centre, r)
-            assert r["learned"] < 4.0 * r["spherical"], (amp, centre, r)
+            assert r["learned"] < 1e-3 * r["characteristic"], (amp, centre, r)
+            assert r["learned"] < 2.0 * r["spherical"], (amp, centre, r)
         else:
-            assert r["learned"] < 0.95 * r["spherical"], (amp, centre, r)
+            assert r["learned"] < 0.9 * r["spherical"], (amp, centre, r)
