@@ -522,7 +522,7 @@ def learned_bc_section(args, xyz, EToV, dev, stream, dist, world):
     characteristic and learned conditions on the truncated ball, and the
     trained closure is timed on the bench workload."""
     from paper_1710_03887_gb300 import learned_bc as L
-    n, runs, centred, every, iters = args.learned_n, 8, 24, args.learned_every, 600
+    n, runs, centred, every, iters = args.learned_n, 8, 48, args.learned_every, 1200
     t0 = time.perf_counter()
     nested = L.nested_ball(n)
     X, Y = L.record(WORKLOAD["order"], nested, L.run_seeds(0, runs, centred), every=every, device=dev,
@@ -1247,7 +1247,7 @@ def main():
                     help="comma-separated outer domains of Table 1 timed at full size after the "
                          "horn section (names of bench.HORN_DOMAINS; empty: none)")
     ap.add_argument("--learned-every", type=int, default=10, help="steps between trace samples")
-    ap.add_argument("--learned-fraction", type=float, default=0.25,
+    ap.add_argument("--learned-fraction", type=float, default=0.125,
                     help="fraction of trace nodes kept per sample (seeded)")
     ap.add_argument("--mesh-n", type=int, default=WORKLOAD["n"],
                     help="lattice size of the ball (32 = the benchmark; smaller for profiling)")

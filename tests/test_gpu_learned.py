@@ -184,8 +184,9 @@ def test_spherical_closure_absorbs_a_centred_pulse(cuda_device):
 
 def test_learned_closure_against_characteristic_and_spherical(cuda_device):
     """Train on the method's own traces at r = 1 inside the radius-2 ball (the
-    bench's seeded runs: 8 with random centres, 24 centred, a quarter of the
-    trace nodes sampled; the network without the absolute-direction inputs)
+    bench's seeded runs: 8 with random centres, 48 centred, an eighth of the
+    trace nodes sampled, 1200 Adam iterations; the network without the
+    absolute-direction inputs)
     and compare reflected energies on the truncated ball (the large ball is
     the reference) with the two conditions the network starts from or
     improves on:
@@ -199,15 +200,15 @@ def test_learned_closure_against_characteristic_and_spherical(cuda_device):
       energy); the network, which sees one face node's trace and cannot
       tell a centred wavefront from an off-centre one at the same
       incidence, adds a little of its fitting error there: it stays within
-      twice the memory's reflection, three orders below the characteristic
-      condition. The trained network has zero weights on the normal and
-      position inputs."""
+      1.3 times the memory's reflection (measured 0.8-1.05), three orders
+      below the characteristic condition. The trained network has zero
+      weights on the normal and position inputs."""
     p, n = 3, 16
     nested = L.nested_ball(n)
-    X, Y = L.record(p, nested, L.run_seeds(0, 8, 24), every=10, device=cuda_device,
-                    width_scale=2.0, node_fraction=0.25)
+    X, Y = L.record(p, nested, L.run_seeds(0, 8, 48), every=10, device=cuda_device,
+                    width_scale=2.0, node_fraction=0.125)
     assert X.shape[0] > 100000
-    w, hist = L.train(X, Y, iters=600, lr=3e-3, seed=0, radius=1.0, order=p)
+    w, hist = L.train(X, Y, iters=1200, lr=3e-3, seed=0, radius=1.0, order=p)
     assert hist[-1] < 0.9 * hist[0]
     W1 = np.asarray(w)[:12 * 64].reshape(12, 64)
     assert np.all(W1[list(L.DIRECTION_FEATURES)] == 0.0)
@@ -220,6 +221,6 @@ def test_learned_closure_against_characteristic_and_spherical(cuda_device):
         assert r["learned"] < 0.15 * r["characteristic"], (amp, centre, r)
         if centre == (0.0, 0.0, 0.0):
             assert r["learned"] < 1e-3 * r["characteristic"], (amp, centre, r)
-            assert r["learned"] < 2.0 * r["spherical"], (amp, centre, r)
+            assert r["learned"] < 1.3 * r["spherical"], (amp, centre, r)
         else:
             assert r["learned"] < 0.9 * r["spherical"], (amp, centre, r)
