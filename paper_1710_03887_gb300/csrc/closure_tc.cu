@@ -339,22 +339,23 @@ cudaError_t launch_closure_image(const float* w, unsigned char* img, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t closure_prepare() {
+  // the attributes belong to the current device: set by every context on it
+  cudaError_t e = cudaFuncSetAttribute(closure_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(closure_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              int(cudaSharedmemCarveoutMaxShared));
+}
+
 cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s) {
   const int64_t total = A.nb * A.Nfp;
   if (total == 0) return cudaSuccess;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(closure_tc_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(closure_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             int(cudaSharedmemCarveoutMaxShared));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const int64_t ntiles = (total + kRows - 1) / kRows;
   const int64_t want = 3 * int64_t(sms);                  // three CTAs per SM
   const int grid = int(ntiles < want ? ntiles : want);

@@ -225,6 +225,7 @@ int ensure_device(dg_ctx* c) {
   else
     DG_CUDA(dgk::stage_prepare(p, &bps));
   if (bps < 1) return c->fail(DG_ERR_CUDA, "stage kernel does not fit on an SM");
+  if (f32) DG_CUDA(dgk::closure_prepare());
   const int ET = tcf ? dgk::stage_tc_tile_elems(p)
                      : (f32 ? dgk::stage_f32_tile_elems(p)
                             : (modal ? dgk::stage_modal_tile_elems(p) : dgk::stage_tile_elems(p)));
@@ -1324,6 +1325,7 @@ static int ensure_mlp(dg_ctx* c) {
   DG_CUDA(cudaMalloc(&c->mlp_grad, n * 4));
   DG_CUDA(cudaMalloc(&c->mlp_loss, 8));
   DG_CUDA(cudaMalloc(&c->mlp_img, dgk::closure_image_bytes()));
+  DG_CUDA(dgk::mlp_prepare());
   DG_CUDA(cudaMemset(c->mlp_w, 0, n * 4));
   DG_CUDA(cudaMemset(c->mlp_img, 0, dgk::closure_image_bytes()));
   c->mlp_img_ok = false;

@@ -233,6 +233,8 @@ struct ClosureArgs {
   int64_t K_all;             // elements of the local mesh: bound of bface's element ids
 };
 cudaError_t launch_closure(const ClosureArgs& A, const BaseGhost& bg, cudaStream_t s);
+// shared-memory attributes of the closure kernel on the current device
+cudaError_t closure_prepare();
 // The closure's weight image (operand layouts of W1 and W2 as tf32 head and
 // tail, and the vectors it reads) from the parameter vector; rebuild after
 // every change of the parameters.
@@ -246,6 +248,8 @@ cudaError_t launch_trace_memory(const float* q, int Np, int Nfp, const int32_t* 
                                 const mlp::Scales& S, float* psi, float* psi_res, float a,
                                 float b, float dt, cudaStream_t s);
 int mlp_grad_blocks(int64_t N, int sms);
+// shared-memory attribute of the training kernel on the current device
+cudaError_t mlp_prepare();
 cudaError_t launch_mlp_loss_grad(const float* w, const float* X, const float* Y, int64_t N,
                                  int nblocks, float* part_grad, float* part_loss, float* grad,
                                  double* loss, cudaStream_t s);

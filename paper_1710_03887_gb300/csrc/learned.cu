@@ -307,16 +307,15 @@ int mlp_grad_blocks(int64_t N, int sms) {
 
 size_t mlp_grad_smem() { return size_t(kGradSmemFloats) * 4; }
 
+cudaError_t mlp_prepare() {
+  // the attribute belongs to the current device: set by every context on it
+  return cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(mlp_grad_smem()));
+}
+
 cudaError_t launch_mlp_loss_grad(const float* w, const float* X, const float* Y, int64_t N,
                                  int nblocks, float* part_grad, float* part_loss, float* grad,
                                  double* loss, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(mlp_grad_smem()));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   const float inv_n = 1.0f / float(N);
   mlp_grad_kernel<<<nblocks, kThreads, mlp_grad_smem(), s>>>(w, X, Y, N, inv_n, part_grad, part_loss);
   mlp_reduce_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(part_grad, part_loss, nblocks, inv_n, grad,
