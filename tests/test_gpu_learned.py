@@ -76,8 +76,12 @@ def test_mlp_adam_training_matches_oracle(cuda_device):
     assert hist[-1] < 0.5 * hist[0]
 
 
-def test_learned_closure_rhs_matches_oracle(cuda_device):
-    p = 2
+@pytest.mark.parametrize("p,prec", [(2, B.DG_PREC_F32), (4, B.DG_PREC_F32),
+                                    (4, B.DG_PREC_F32_TC)])
+def test_learned_closure_rhs_matches_oracle(cuda_device, p, prec):
+    """The closure inside one right-hand side, against the oracle's: p = 2,
+    and p = 4 (15 nodes per face: the production configuration's order) in
+    both float32 forms."""
     xyz, EToV = W.kuhn_cube(3, jitter=0.1, seed=4)
     gas = Gas(SI["gamma"], SI["rho0"], SI["p0"])
     ref = ReferenceElement(p)
@@ -86,7 +90,7 @@ def test_learned_closure_rhs_matches_oracle(cuda_device):
     orc = OSolver(geom, gas, bc_mode={0: LEARNED}, mlp=(w, 1.3))
     q = W.random_smooth_state(geom.x, SI["gamma"], SI["rho0"], SI["p0"], 0.05, seed=6)
     ro = orc.rhs(q)
-    S = B.Solver(p, precision=B.DG_PREC_F32, **SI)
+    S = B.Solver(p, precision=prec, **SI)
     S.upload_mesh(xyz, EToV)
     S.set_bc(0, B.DG_BC_LEARNED)
     S.set_bc_mlp(w.astype(np.float32), 1.3)
