@@ -14,7 +14,8 @@ jumps, and the float64 oracle's own rounding (tests/_cases.f32_parity_bound)."""
 import numpy as np
 import pytest
 
-from oracle.euler_dg import Gas
+from oracle import mlp as OM
+from oracle.euler_dg import LEARNED, Gas
 from oracle.euler_dg import Solver as OSolver
 from oracle.geometry import Geometry
 from oracle.reference_element import ReferenceElement
@@ -45,7 +46,11 @@ def _device_pulse(S, xyz, EToV, order, dev, amplitude=0.05, width=0.3, chunk=1 <
     return q, w
 
 
-def _sampled_parity(S, xyz, EToV, order, q_dev, w, seed):
+def _sampled_parity(S, xyz, EToV, order, q_dev, w, seed, mlp=None, mlp_delta=0.0):
+    """Worst error / bound per node and variable at sampled elements. With
+    ``mlp`` = (parameters, radius) every outer face takes the learned
+    closure, and the bound adds what a network output off by ``mlp_delta``
+    does to the oracle's right-hand side (the float32 network's error)."""
     rhs = S.eval_rhs()
     g = S.geometry()
     rng = np.random.default_rng(seed)
@@ -57,18 +62,34 @@ def _sampled_parity(S, xyz, EToV, order, q_dev, w, seed):
     patch = patch[patch >= 0]
     sub_xyz, sub_EToV = W.submesh(xyz, EToV, np.isin(np.arange(K), patch))
     geom = Geometry(ReferenceElement(order), sub_xyz, sub_EToV)
-    osol = OSolver(geom, Gas(SI["gamma"], SI["rho0"], SI["p0"]))
+    gas = Gas(SI["gamma"], SI["rho0"], SI["p0"])
+    kw = {} if mlp is None else dict(bc_mode={0: LEARNED}, mlp=mlp)
+    osol = OSolver(geom, gas, **kw)
     import torch
     ro = osol.rhs(q_dev[torch.as_tensor(patch, device=q_dev.device)].cpu().numpy())
     local = np.searchsorted(patch, sample)
     assert np.array_equal(geom.boundary[local], g["EToE"][sample] < 0)
     qp = q_dev[torch.as_tensor(patch, device=q_dev.device)].cpu().numpy()
-    bound = f32_parity_bound(osol, qp, Gas(SI["gamma"], SI["rho0"], SI["p0"]))[local]
+    bound = f32_parity_bound(osol, qp, gas)[local]
+    if mlp is not None:
+        # the network's output error: output 0 shifted by +-delta (b3[0])
+        for sgn in (1.0, -1.0):
+            wd = np.array(mlp[0], dtype=np.float64)
+            wd[-5] += sgn * mlp_delta
+            od = OSolver(geom, gas, bc_mode={0: LEARNED}, mlp=(wd, mlp[1]))
+            bound = bound + 0.5 * np.abs(od.rhs(qp) - ro)[local]
     err = np.abs(rhs[sample] - ro[local])
     floor = 1e-7 * np.abs(ro[local]).max(axis=(0, 2))[None, :, None]
     ratio = err / (bound + floor)
     print("worst error / float32 bound per variable:", ratio.max(axis=(0, 2)))
-    return ratio
+    if mlp is None:
+        return ratio
+    # the same comparison against the characteristic condition's rhs: what
+    # the test could not tell apart from the closure
+    rc = OSolver(geom, gas).rhs(qp)
+    ratio_char = np.abs(rhs[sample] - rc[local]) / (bound + floor)
+    print("against the characteristic condition:", ratio_char.max(axis=(0, 2)))
+    return ratio, ratio_char
 
 
 @pytest.mark.parametrize("prec", [B.DG_PREC_F32, B.DG_PREC_F32_TC])
@@ -97,3 +118,28 @@ def test_c5_size_cube_p4(cuda_device):
     S.set_state(q)
     ratio = _sampled_parity(S, xyz, EToV, 4, q, w, seed=2)
     assert np.all(ratio <= 1.0), ratio.max(axis=(0, 2))
+
+
+def test_c5_size_cube_p4_learned_closure(cuda_device):
+    """The production configuration's order and size with the learned
+    closure on every outer face (seeded network, the memory at zero as after
+    dg_set_state). Bound: the float32 stage's, plus the effect of a network
+    output off by 2e-5 from the float64 one: the tensor-core GEMMs split
+    their operands into tf32 head and tail (2^-22 relative per product,
+    64-term sums of |h| <= 1 times weights of O(1): ~1.5e-5 at worst) and
+    the hidden units' tanh is accurate to ~1e-7."""
+    xyz, EToV = W.kuhn_cube(110, jitter=0.1, seed=5)
+    rng = np.random.default_rng(11)
+    w = OM.init_params(seed=11) + 0.05 * rng.normal(size=OM.N_PARAMS)
+    w[-5 - 64 * 5:] *= 0.2
+    S = B.Solver(4, precision=B.DG_PREC_F32, **SI)
+    S.upload_mesh(xyz, EToV)
+    S.set_bc(0, B.DG_BC_LEARNED)
+    S.set_bc_mlp(w.astype(np.float32), 1.0)
+    q, wn = _device_pulse(S, xyz, EToV, 4, cuda_device, width=0.8)     # reaches the faces
+    S.set_state(q)
+    ratio, ratio_char = _sampled_parity(S, xyz, EToV, 4, q, wn, seed=4,
+                                        mlp=(w.astype(np.float32).astype(np.float64), 1.0),
+                                        mlp_delta=2e-5)
+    assert np.all(ratio <= 1.0), ratio.max(axis=(0, 2))
+    assert ratio_char.max() > 10.0, ratio_char.max(axis=(0, 2))
