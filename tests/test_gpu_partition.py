@@ -54,11 +54,13 @@ def _close(stitched, q_ref, q0, prec):
     return d / np.abs(q_ref - base).max(axis=(0, 2)) < 1e-6
 
 
-def _single(p, prec, xyz, EToV, q0, dt, steps, dev):
+def _single(p, prec, xyz, EToV, q0, dt, steps, dev, setup=None):
     import torch
     S = B.Solver(p, precision=PRECS[prec], **SI)
     S.set_stream(torch.cuda.current_stream(dev).cuda_stream)
     S.upload_mesh(xyz, EToV)
+    if setup:
+        setup(S)
     S.set_state(q0)
     S.step(steps, dt)
     q, _ = S.get_state()
@@ -232,3 +234,80 @@ def test_partitioned_solver_two_processes(cuda_device):
         np.testing.assert_allclose(tot, tot_ref, rtol=1e-10, atol=1e-10 * scale)
         np.testing.assert_allclose(led, led_ref, rtol=1e-9, atol=1e-13 * scale)
     assert np.all(_close(stitched, q_ref, q0, "f32")), np.abs(stitched - q_ref).max(axis=(0, 2))
+
+
+def _emulated(p, prec, xyz, EToV, q0, dt, steps, dev, nranks=3, setup=None):
+    """Stitched own states of emulated ranks (see the module docstring)."""
+    import torch
+    part = PT.partition_elements(xyz, EToV, nranks)
+    locs = [PT.local_mesh(xyz, EToV, part, r) for r in range(nranks)]
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ctx, send, recv = [], [], []
+    for L in locs:
+        S = B.Solver(p, precision=PRECS[prec], **SI)
+        S.set_stream(stream)
+        S.upload_mesh(L.xyz, L.EToV, face_tag=L.face_tag)
+        S.set_bc(PT.HALO_TAG, B.DG_BC_FREESTREAM)
+        if setup:
+            setup(S)
+        S.set_owned(L.K_own)
+        S.set_halo(L.send_elem, L.send_face, L.recv_elem, L.recv_face)
+        S.set_state(q0[L.l2g])
+        tdt = getattr(torch, np.dtype(S.halo_dtype()).name)
+        send.append(torch.empty((L.send_elem.size, 5, S.Nfp), dtype=tdt, device=dev))
+        recv.append(torch.empty((L.recv_elem.size, 5, S.Nfp), dtype=tdt, device=dev))
+        ctx.append(S)
+    for _ in range(steps * 5):
+        for S, b in zip(ctx, send):
+            S.halo_pack(b)
+        for r, L in enumerate(locs):
+            for i, s in enumerate(L.peers):
+                j = locs[s].peers.index(r)
+                recv[r][L.recv_off[i]:L.recv_off[i + 1]].copy_(
+                    send[s][locs[s].send_off[j]:locs[s].send_off[j + 1]])
+        for S, b in zip(ctx, recv):
+            S.halo_unpack(b)
+        for S in ctx:
+            S.step_stages(1, dt)
+    stitched = np.full_like(q0, np.nan)
+    led = np.zeros(5)
+    for S, L in zip(ctx, locs):
+        q, _ = S.get_state()
+        stitched[L.l2g[:L.K_own]] = q[:L.K_own]
+        led += S.boundary_flux()
+        S.close()
+    return stitched, led
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_tc"])
+def test_emulated_ranks_with_the_learned_closure(cuda_device, prec):
+    """The learned closure on every outer face (a seeded network; the memory
+    of each outer-face node advanced by the rank that owns the face) under
+    the partition: the stitched own states equal the single-domain run to
+    rounding, and the ranks' ledgers add up to its ledger."""
+    from oracle import mlp as OM
+    xyz, EToV = _mesh()
+    rng = np.random.default_rng(21)
+    w = (OM.init_params(seed=21) + 0.05 * rng.normal(size=OM.N_PARAMS)).astype(np.float32)
+    w[-5 - 64 * 5:] *= 0.2
+
+    def setup(S):
+        S.set_bc(0, B.DG_BC_LEARNED)
+        S.set_bc_mlp(w, 1.0)
+    S0 = B.Solver(3, precision=PRECS[prec], **SI)
+    S0.upload_mesh(xyz, EToV)
+    q0 = W.gaussian_pulse_state(S0.node_coords(), W.GAMMA, W.RHO0_SI, W.P0_SI, 0.05, 0.6,
+                                center=(0.2, -0.1, 0.1))
+    dt = S0.stable_dt(q0, 0.5)
+    S0.close()
+    steps = 6
+    q_ref, _, led_ref = _single(3, prec, xyz, EToV, q0, dt, steps, cuda_device, setup)
+    stitched, led = _emulated(3, prec, xyz, EToV, q0, dt, steps, cuda_device, setup=setup)
+    assert not np.isnan(stitched).any()
+    assert np.all(_close(stitched, q_ref, q0, prec)), np.abs(stitched - q_ref).max(axis=(0, 2))
+    scale = np.abs(q_ref).max()
+    np.testing.assert_allclose(led, led_ref, rtol=1e-9, atol=1e-13 * scale * len(EToV))
+    # the closure is in play: the characteristic condition ends elsewhere
+    q_char, _, _ = _single(3, prec, xyz, EToV, q0, dt, steps, cuda_device)
+    base = W.uniform_state(q0.shape[0], q0.shape[2], W.RHO0_SI, (0, 0, 0), W.P0_SI, W.GAMMA)
+    assert np.abs(q_char - q_ref).max() > 1e-4 * np.abs(q_ref - base).max()
