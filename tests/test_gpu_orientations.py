@@ -50,7 +50,7 @@ def _modal_oracle(case):
 
 
 @pytest.mark.parametrize("prec,p", [("fp64", 2), ("fp64", 3), ("f32", 3), ("f32", 4),
-                                    ("f32_tc", 3), ("modal", 2), ("modal", 3)])
+                                    ("f32_tc", 3), ("f32_tc", 4), ("modal", 2), ("modal", 3)])
 def test_rhs_in_every_orientation(cuda_device, prec, p):
     case = _shuffled_case(p, seed=30 + p)
     q = case.smooth(0.05, seed=p)
