@@ -49,7 +49,20 @@ def bench():
     return mod
 
 
-def test_f32_against_fp64_over_2000_steps(cuda_device, bench):
+@pytest.fixture(scope="module")
+def fp64_run(cuda_device, bench):
+    import torch
+    from paper_1710_03887_gb300 import binding as B
+    xyz, EToV = W.ball(10, 1.0)
+    stream = torch.cuda.current_stream(cuda_device)
+    return bench.precision_run(3, xyz, EToV, B.DG_PREC_FP64, STEPS, AMPLITUDE, WIDTH, 0.5,
+                               cuda_device, stream)
+
+
+@pytest.mark.parametrize("form", ["f32", "f32_tc"])
+def test_f32_against_fp64_over_2000_steps(cuda_device, bench, fp64_run, form):
+    """Both float32 forms (SIMT and tensor-core contractions) against the
+    float64 run, with the same bars."""
     import torch
     from paper_1710_03887_gb300 import binding as B
     xyz, EToV = W.ball(10, 1.0)
@@ -57,10 +70,10 @@ def test_f32_against_fp64_over_2000_steps(cuda_device, bench):
     # bench.AXIS_PROBES: images of one point inside an element under the
     # mesh's reflections and axis swaps (the lattice symmetries), so the
     # discrete solution of a centred pulse is equal at all six
-    r64 = bench.precision_run(3, xyz, EToV, B.DG_PREC_FP64, STEPS, AMPLITUDE, WIDTH, 0.5,
-                              cuda_device, stream)
-    r32 = bench.precision_run(3, xyz, EToV, B.DG_PREC_F32, STEPS, AMPLITUDE, WIDTH, 0.5,
-                              cuda_device, stream)
+    r64 = fp64_run
+    prec = {"f32": B.DG_PREC_F32, "f32_tc": B.DG_PREC_F32_TC}[form]
+    r32 = bench.precision_run(3, xyz, EToV, prec, STEPS, AMPLITUDE, WIDTH, 0.5, cuda_device,
+                              stream)
     c0 = np.sqrt(W.GAMMA * W.P0_SI / W.RHO0_SI)
     assert c0 * r64["dt"] * STEPS > 0.8          # the front has reached the sphere
     out = bench.precision_comparison(r32, r64, AMPLITUDE, B.reference_mass(3), W.GAMMA,
